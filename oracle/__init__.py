@@ -1,0 +1,120 @@
+"""CPU oracle for the fork-join hot path -- TEST INFRASTRUCTURE ONLY.
+
+Only the tests, the smoke check and the benchmark's CPU-baseline leg import
+this package.  The product path (the CUDA library and its Python binding)
+never does, and this package imports nothing from it.
+
+The nests are evaluated by ``hx_oracle.c``: plain sequential loops that walk
+each fork grid in lexicographic order and fold every reduction in increasing
+thread-ID order (Hercules paper, Sec. 3.3), in double precision unless a
+function says otherwise.  This module only marshals numpy arrays in and out.
+
+Parity status: every function here is pinned by the ``-m "not gpu"`` tests
+(closed forms, library routines on special cases, brute force on tiny
+inputs); none is "parity unpinned".
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "hx_oracle.c")
+_LIB = os.path.join(_HERE, "libhx_oracle.so")
+
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (no fast-math, no FP contraction)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared",
+                               "-ffp-contract=off", "-fno-fast-math", "-Wall",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _get():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(build())
+        P = ctypes.c_void_p
+        lib.hxo_map_reduce_f64.argtypes = [P, P, ctypes.c_double, ctypes.c_int64, P, P]
+        lib.hxo_map_reduce_f64.restype = None
+        lib.hxo_monoid_reduce_f64.argtypes = [ctypes.c_int, P, P, ctypes.c_double,
+                                              ctypes.c_int64, P]
+        lib.hxo_monoid_reduce_f64.restype = ctypes.c_int
+        for name in ("hxo_jacobi_f64", "hxo_jacobi_f32"):
+            f = getattr(lib, name)
+            f.argtypes = [P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P, P]
+            f.restype = ctypes.c_int
+        lib.hxo_histogram_u8.argtypes = [P, ctypes.c_int64, P, P]
+        lib.hxo_histogram_u8.restype = None
+        _lib = lib
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    return ctypes.c_void_p(a.ctypes.data) if a.size else ctypes.c_void_p(0)
+
+
+def map_reduce(x: np.ndarray, y: np.ndarray, a: float, want_out: bool = True):
+    """out[i] = a*x[i] + y[i] (fp64), s = sum of out in index order (fp64).
+
+    Returns (out or None, s)."""
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    y = np.ascontiguousarray(y, dtype=np.float32)
+    assert x.shape == y.shape and x.ndim == 1
+    n = x.size
+    out = np.empty(n, dtype=np.float64) if want_out else None
+    s = np.zeros(1, dtype=np.float64)
+    _get().hxo_map_reduce_f64(_ptr(x), _ptr(y), float(a), n,
+                              _ptr(out) if want_out else ctypes.c_void_p(0), _ptr(s))
+    return out, float(s[0])
+
+
+MONOIDS = {"sum": 0, "max": 1, "min": 2, "prod": 3}
+
+
+def monoid_reduce(op: str, x: np.ndarray, a: float = 1.0, y: np.ndarray | None = None) -> float:
+    """Fold of a*x[i] + y[i] under the monoid ``op`` in index order (fp64)."""
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    if y is not None:
+        y = np.ascontiguousarray(y, dtype=np.float32)
+        assert y.shape == x.shape
+    r = np.zeros(1, dtype=np.float64)
+    rc = _get().hxo_monoid_reduce_f64(MONOIDS[op], _ptr(x),
+                                      _ptr(y) if y is not None else ctypes.c_void_p(0),
+                                      float(a), x.size, _ptr(r))
+    assert rc == 0
+    return float(r[0])
+
+
+def jacobi(u0: np.ndarray, iters: int, precision: str = "f64"):
+    """Clamp-to-edge 5-point Jacobi, ``iters`` sweeps; returns (u_final, resid[iters])."""
+    assert u0.ndim == 2
+    ny, nx = u0.shape
+    dt = np.float64 if precision == "f64" else np.float32
+    src = np.ascontiguousarray(u0, dtype=dt)
+    out = np.empty_like(src)
+    resid = np.zeros(max(iters, 0), dtype=dt)
+    fn = _get().hxo_jacobi_f64 if precision == "f64" else _get().hxo_jacobi_f32
+    rc = fn(_ptr(src), nx, ny, iters, _ptr(out), _ptr(resid) if iters > 0 else ctypes.c_void_p(0))
+    if rc:
+        raise MemoryError("oracle jacobi: allocation failed")
+    return out, resid
+
+
+def histogram(v: np.ndarray):
+    """256 uint32 bin counts of the bytes in ``v`` and their exclusive prefix sum."""
+    v = np.ascontiguousarray(v, dtype=np.uint8).ravel()
+    bins = np.zeros(256, dtype=np.uint32)
+    scan = np.zeros(256, dtype=np.uint32)
+    _get().hxo_histogram_u8(_ptr(v), v.size, _ptr(bins), _ptr(scan))
+    return bins, scan
