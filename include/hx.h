@@ -1,0 +1,140 @@
+/*
+ * hx.h -- C ABI of libhx, the sm_103a (B300) implementation of the
+ * data-parallel hot path that Hercules produces for fork-join loop nests
+ * with associative reductions (Hercules paper, Sec. 3.3 fork-joins, Sec. 3.4
+ * reduce attributes, Sec. 4.4 GPU lowering).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Pointers named d_* or documented as "device" are device pointers that
+ *    the CALLER allocates and owns.  Nothing here frees or retains them
+ *    beyond the call's stream work.
+ *  - Every compute call is asynchronous on `stream` (a cudaStream_t; NULL is
+ *    the legacy default stream).  Results are valid once that stream's work
+ *    has completed.  Host-side argument checks happen before any launch.
+ *  - A context (hx_ctx) owns the device workspace that the reductions need
+ *    (per-tile partials, arrival tickets), allocated once by hx_create, the
+ *    way a Hercules runner owns the backing memory of a call (Sec. 4.2 last
+ *    paragraph, Sec. 4.6).  The workspace is split into per-stream slots:
+ *    calls on the same stream share a slot (ordered by the stream), calls on
+ *    different streams use different slots, up to HX_MAX_STREAMS streams per
+ *    context.  A context is not thread-safe: serialise host calls on it.
+ *  - Reductions are deterministic: the combination order is a function of
+ *    the problem size alone (never of timing, grid size or batching), so a
+ *    result is bit-identical across runs and between a standalone call and
+ *    the same instance inside a batch.
+ *  - Errors: every call returns an hx_status.  HX_ERR_INVALID = bad argument
+ *    (nothing launched); HX_ERR_CUDA = a CUDA call failed; HX_ERR_NOMEM = a
+ *    workspace, budget or capacity limit was exceeded.  hx_last_error()
+ *    returns a message for the calling thread's last failure.  No C++
+ *    exception crosses this boundary.
+ */
+#ifndef HX_H
+#define HX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum hx_status {
+    HX_OK = 0,
+    HX_ERR_INVALID = 1,
+    HX_ERR_CUDA = 2,
+    HX_ERR_NOMEM = 3,
+    HX_ERR_TIMEOUT = 4,
+    HX_ERR_BUSY = 5
+} hx_status;
+
+typedef struct hx_ctx hx_ctx;
+typedef struct CUstream_st *hx_stream_t; /* identical to cudaStream_t */
+
+#define HX_MAX_STREAMS 16
+/* Largest element count of one map->reduce instance (tile partials must fit
+ * the per-stream workspace). */
+#define HX_MAP_REDUCE_MAX_N ((int64_t)1 << 34)
+/* Largest byte count of one histogram: counts are uint32. */
+#define HX_HISTOGRAM_MAX_N ((int64_t)0xFFFFFFFF)
+
+/* Library version, (major << 16) | minor. */
+int hx_version(void);
+
+/* Message for the calling thread's most recent failed call ("" if none). */
+const char *hx_last_error(void);
+
+/* Create a context on CUDA device `device`.  hbm_budget_bytes bounds the
+ * device memory that batched and served work may hold resident (0 = no
+ * limit).  Allocates the workspace (about 1 MiB) on that device.
+ * Returns HX_ERR_INVALID for a bad device or NULL out. */
+hx_status hx_create(hx_ctx **out, int device, size_t hbm_budget_bytes);
+
+/* Release the context's workspace.  The caller must first make sure no
+ * stream work issued through it is still running.  NULL is accepted. */
+void hx_destroy(hx_ctx *ctx);
+
+/* ------------------------------------------------------------------ map->reduce
+ * One fork of factor n (Sec. 3.3): thread i computes
+ *     out[i] = fmaf(a, x[i], y[i])            (one rounding, fp32)
+ * and a sum reduce folds the out[i] into s.  The sum is reassociated as the
+ * MonoidReduce attribute allows (Sec. 3.4) into the reduction tree of
+ * Sec. 5.2: each tile of consecutive elements is summed in a fixed order
+ * (per-thread fp32 partials over a fixed element set, then an fp64 warp and
+ * block tree), and the last tile to finish folds the tile partials in index
+ * order in fp64.  The map and the reduce are fused: out is written in the
+ * same pass (loop fusion, Sec. 5.1).
+ *
+ *   x, y     device, n fp32 each, read-only.  Any alignment (16-byte
+ *            aligned buffers take the vector path; results are identical).
+ *   out      device, n fp32, or NULL to skip storing the map result.
+ *   d_sum    device, 1 fp32: s rounded to fp32.  Required.
+ *   d_sum64  device, 1 fp64: s in fp64 (before the final rounding), or NULL.
+ *   n        0 <= n <= HX_MAP_REDUCE_MAX_N; n == 0 gives s = 0.
+ */
+hx_status hx_map_reduce(hx_ctx *ctx, const float *x, const float *y, float *out,
+                        float a, int64_t n, float *d_sum, double *d_sum64,
+                        hx_stream_t stream);
+
+/* ------------------------------------------------------------------ stencil
+ * `iters` sweeps of the clamp-to-edge 5-point Jacobi update over a row-major
+ * grid of ny rows by nx columns (element (i, j) at [i*nx + j]):
+ *     u'[i][j] = 0.25f * ((u[i-1][j] + u[i+1][j]) + (u[i][j-1] + u[i][j+1]))
+ * with out-of-range rows/columns clamped to the nearest edge, each rounded
+ * in fp32 in exactly that order; fused with a max reduce of |u' - u| per
+ * sweep (the max-gradient reduction of Sec. 5.2; max is exact, so the
+ * residual is order independent).  Sweep t reads one buffer and writes the
+ * other (u0 -> u1 -> u0 ...); sweeps are a sequential loop (Sec. 4.4 rule 1)
+ * issued as back-to-back launches with programmatic dependent launch.
+ *
+ *   u0       device, nx*ny fp32: input grid; overwritten when iters >= 2.
+ *   u1       device, nx*ny fp32: second buffer; must not overlap u0.
+ *   d_resid  device, iters fp32: resid[t] = max |u_{t+1} - u_t|; may be NULL
+ *            only when iters == 0.
+ *   result_in_u1  host int32 out (may be NULL): 1 if the final grid is in
+ *            u1 (iters odd), 0 if it is in u0.
+ *   1 <= nx, ny <= 65536, nx*ny <= 2^31, 0 <= iters <= 1<<20.
+ */
+hx_status hx_stencil2d(hx_ctx *ctx, float *u0, float *u1, int32_t nx, int32_t ny,
+                       int32_t iters, float *d_resid, int32_t *result_in_u1,
+                       hx_stream_t stream);
+
+/* ------------------------------------------------------------------ histogram
+ * 256-bin byte histogram, a reduce over a 256-entry collection (Sec. 3.2
+ * collections, Sec. 3.3 reduce; the per-thread private bins are what the
+ * ParallelReduce/MonoidReduce attributes of Sec. 3.4 license), followed by
+ * an exclusive prefix sum over the bins: scan[0] = 0,
+ * scan[k] = bins[0] + ... + bins[k-1].  Integer and exact.
+ *
+ *   v            device, n bytes, any alignment.
+ *   d_bins       device, 256 uint32 (overwritten, need not be zeroed).
+ *   d_excl_scan  device, 256 uint32, or NULL to skip the scan.
+ *   0 <= n <= HX_HISTOGRAM_MAX_N.
+ */
+hx_status hx_histogram(hx_ctx *ctx, const uint8_t *v, int64_t n, uint32_t *d_bins,
+                       uint32_t *d_excl_scan, hx_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HX_H */

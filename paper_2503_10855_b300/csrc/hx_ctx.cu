@@ -1,0 +1,93 @@
+// hx_ctx.cu -- context lifetime, error reporting and per-stream workspace
+// slots of libhx.  A context plays the part of the Hercules runner: it owns
+// the backing memory a call needs and allocates it once, up front
+// (Hercules paper, Sec. 4.2 last paragraph and Sec. 4.6).
+#include <cstdio>
+#include <cstring>
+
+#include "hx_internal.cuh"
+
+namespace {
+thread_local std::string g_last_error;
+}
+
+namespace hx {
+
+hx_status fail(hx_status st, const std::string &msg) {
+    g_last_error = msg;
+    return st;
+}
+
+hx_status cuda_fail(cudaError_t e, const char *what) {
+    std::string m = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    return fail(HX_ERR_CUDA, m);
+}
+
+hx_status slot_for(hx_ctx *ctx, hx_stream_t stream, WsSlot **slot) {
+    int free_i = -1;
+    for (int i = 0; i < HX_MAX_STREAMS; ++i) {
+        if (ctx->slot_used[i] && ctx->slot_stream[i] == stream) {
+            *slot = ctx->ws + i;
+            return HX_OK;
+        }
+        if (!ctx->slot_used[i] && free_i < 0) free_i = i;
+    }
+    if (free_i < 0) {
+        return fail(HX_ERR_NOMEM, "more than HX_MAX_STREAMS distinct streams used with one context");
+    }
+    ctx->slot_used[free_i] = true;
+    ctx->slot_stream[free_i] = stream;
+    *slot = ctx->ws + free_i;
+    return HX_OK;
+}
+
+}  // namespace hx
+
+extern "C" {
+
+int hx_version(void) { return (0 << 16) | 3; }
+
+const char *hx_last_error(void) { return g_last_error.c_str(); }
+
+hx_status hx_create(hx_ctx **out, int device, size_t hbm_budget_bytes) {
+    if (!out) return hx::fail(HX_ERR_INVALID, "hx_create: out is NULL");
+    *out = nullptr;
+    int count = 0;
+    cudaError_t e = cudaGetDeviceCount(&count);
+    if (e != cudaSuccess) return hx::cuda_fail(e, "hx_create: cudaGetDeviceCount");
+    if (device < 0 || device >= count) return hx::fail(HX_ERR_INVALID, "hx_create: no such device");
+    hx::DeviceGuard g(device);
+    hx_ctx *ctx = new (std::nothrow) hx_ctx();
+    if (!ctx) return hx::fail(HX_ERR_NOMEM, "hx_create: host allocation failed");
+    ctx->device = device;
+    ctx->hbm_budget = hbm_budget_bytes;
+    e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+    if (e != cudaSuccess) {
+        delete ctx;
+        return hx::cuda_fail(e, "hx_create: SM count");
+    }
+    const size_t bytes = sizeof(hx::WsSlot) * HX_MAX_STREAMS;
+    e = cudaMalloc(&ctx->ws, bytes);
+    if (e != cudaSuccess) {
+        delete ctx;
+        return hx::cuda_fail(e, "hx_create: workspace cudaMalloc");
+    }
+    e = cudaMemset(ctx->ws, 0, bytes);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        cudaFree(ctx->ws);
+        delete ctx;
+        return hx::cuda_fail(e, "hx_create: workspace clear");
+    }
+    *out = ctx;
+    return HX_OK;
+}
+
+void hx_destroy(hx_ctx *ctx) {
+    if (!ctx) return;
+    hx::DeviceGuard g(ctx->device);
+    if (ctx->ws) cudaFree(ctx->ws);
+    delete ctx;
+}
+
+}  // extern "C"

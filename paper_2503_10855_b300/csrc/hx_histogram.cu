@@ -1,0 +1,111 @@
+// hx_histogram.cu -- 256-bin byte histogram and exclusive scan of the bins.
+//
+// The histogram is a reduce over a 256-entry collection (Sec. 3.2, 3.3).
+// Each CTA keeps private bins in shared memory (a collection constant of a
+// block-level fork placed in shared memory, with an extra dimension for the
+// thread-level fork, as Sec. 4.4 describes), replicated per lane so that a
+// warp's 32 increments always hit 32 different banks.  CTAs then add their
+// bins into the workspace with integer atomics (exact and order independent)
+// and the last CTA to arrive publishes the bins and runs the exclusive scan
+// (a sequential fold over 256 entries, done as a warp-shuffle scan).
+#include "hx_internal.cuh"
+
+namespace hx {
+
+__global__ void __launch_bounds__(kHiThreads)
+histogram_kernel(const uint8_t *__restrict__ v, int64_t n, int head, int64_t nvec, int tail,
+                 WsSlot *ws, uint32_t *d_bins, uint32_t *d_scan) {
+    __shared__ unsigned int sh[kHiBins * kWarp];
+    __shared__ unsigned int wtot[kHiThreads / kWarp];
+    __shared__ bool is_last;
+    for (int i = threadIdx.x; i < kHiBins * kWarp; i += blockDim.x) sh[i] = 0u;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned int *sh_lane = sh + lane;
+    const uint4 *v4 = reinterpret_cast<const uint4 *>(v + head);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; i + stride < nvec; i += 2 * stride) {
+        const uint4 w0 = ld_stream_u4(v4 + i);
+        const uint4 w1 = ld_stream_u4(v4 + i + stride);
+        hist_count_word(sh_lane, w0.x);
+        hist_count_word(sh_lane, w0.y);
+        hist_count_word(sh_lane, w0.z);
+        hist_count_word(sh_lane, w0.w);
+        hist_count_word(sh_lane, w1.x);
+        hist_count_word(sh_lane, w1.y);
+        hist_count_word(sh_lane, w1.z);
+        hist_count_word(sh_lane, w1.w);
+    }
+    if (i < nvec) {
+        const uint4 w0 = ld_stream_u4(v4 + i);
+        hist_count_word(sh_lane, w0.x);
+        hist_count_word(sh_lane, w0.y);
+        hist_count_word(sh_lane, w0.z);
+        hist_count_word(sh_lane, w0.w);
+    }
+    if (blockIdx.x == 0) {   // unaligned head and ragged tail bytes
+        if (threadIdx.x < head) atomicAdd(sh_lane + (unsigned int)v[threadIdx.x] * kWarp, 1u);
+        if (threadIdx.x < tail) atomicAdd(sh_lane + (unsigned int)v[n - tail + threadIdx.x] * kWarp, 1u);
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < kHiBins; b += blockDim.x) {
+        unsigned int s = 0u;
+#pragma unroll 8
+        for (int k = 0; k < kWarp; ++k) s += sh[b * kWarp + ((k + b) & 31)];
+        if (s) atomicAdd(&ws->hi_bins[b], s);
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) is_last = atomicAdd(&ws->hi_ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    // Final: publish the bins, exclusive scan, reset the workspace.
+    unsigned int c = 0u;
+    if (threadIdx.x < kHiBins) {
+        c = atomicExch(&ws->hi_bins[threadIdx.x], 0u);
+        d_bins[threadIdx.x] = c;
+    }
+    unsigned int incl = c;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const unsigned int t = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += t;
+    }
+    if (lane == 31) wtot[warp] = incl;
+    __syncthreads();
+    unsigned int before = 0u;
+    for (int w = 0; w < warp; ++w) before += wtot[w];
+    if (d_scan && threadIdx.x < kHiBins) d_scan[threadIdx.x] = before + incl - c;
+    if (threadIdx.x == 0) ws->hi_ticket = 0u;
+}
+
+}  // namespace hx
+
+extern "C" hx_status hx_histogram(hx_ctx *ctx, const uint8_t *v, int64_t n, uint32_t *d_bins,
+                                  uint32_t *d_excl_scan, hx_stream_t stream) {
+    using namespace hx;
+    if (!ctx) return fail(HX_ERR_INVALID, "hx_histogram: ctx is NULL");
+    if (n < 0 || n > HX_HISTOGRAM_MAX_N) return fail(HX_ERR_INVALID, "hx_histogram: n out of range");
+    if (!d_bins) return fail(HX_ERR_INVALID, "hx_histogram: d_bins is NULL");
+    if (n > 0 && !v) return fail(HX_ERR_INVALID, "hx_histogram: v is NULL");
+    if ((((uintptr_t)d_bins | (uintptr_t)d_excl_scan) & 3u) != 0)
+        return fail(HX_ERR_INVALID, "hx_histogram: bins must be 4-byte aligned");
+    DeviceGuard g(ctx->device);
+    WsSlot *ws = nullptr;
+    hx_status st = slot_for(ctx, stream, &ws);
+    if (st != HX_OK) return st;
+    int head = (int)((16 - ((uintptr_t)v & 15u)) & 15u);
+    if (head > n) head = (int)n;
+    const int64_t nvec = (n - head) / 16;
+    const int tail = (int)((n - head) % 16);
+    int64_t want = (nvec + 2 * kHiThreads - 1) / (2 * kHiThreads);
+    int64_t cap = (int64_t)ctx->num_sms * (2048 / kHiThreads);
+    int grid = (int)(want < 1 ? 1 : (want > cap ? cap : want));
+    histogram_kernel<<<grid, kHiThreads, 0, (cudaStream_t)stream>>>(v, n, head, nvec, tail, ws, d_bins,
+                                                                      d_excl_scan);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "hx_histogram: launch");
+    return HX_OK;
+}

@@ -1,0 +1,316 @@
+// hx_internal.cuh -- device building blocks of libhx shared by the standalone
+// kernels and the batched persistent kernel.  Each nest is written once, as a
+// per-tile device function; a standalone launch runs one tile per CTA and the
+// batched kernel runs the same functions on work items, so an instance gives
+// bit-identical results alone and inside a batch.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <mutex>
+#include <string>
+
+#include "../../include/hx.h"
+
+namespace hx {
+
+// ---------------------------------------------------------------- constants
+constexpr int kWarp = 32;
+
+// map->reduce tile plan: a CTA of kMrThreads threads; thread t of the tile
+// owns the float4 vectors t, t + kMrThreads, t + 2 kMrThreads, ... (coalesced
+// per step).  The plan (vectors per thread) is a function of n only.
+constexpr int kMrThreads = 256;
+constexpr int kMrMinVecs = 4;        // vectors per thread in the smallest tile
+constexpr int kMrUnroll = 4;         // loads in flight per operand per thread
+constexpr int kMrMaxTiles = 2048;    // tile partials per instance (workspace)
+constexpr int kFinalThreads = 256;   // CTA width of every final combine
+
+// stencil: one warp walks a strip of columns down kStRows rows.
+constexpr int kStRows = 16;
+constexpr int kStWarps = 4;          // warps per CTA, stacked vertically
+
+// histogram: lane-replicated shared bins, 256 bins x 32 lanes of uint32.
+constexpr int kHiThreads = 512;
+constexpr int kHiBins = 256;
+
+// ---------------------------------------------------------------- workspace
+// One slot per stream.  Tickets count arriving tiles; the last arrival does
+// the final combine and resets its ticket and accumulators to zero, so a slot
+// is clean again when a call's stream work completes.
+struct WsSlot {
+    double mr_partial[kMrMaxTiles];
+    unsigned int mr_ticket;
+    unsigned int st_ticket;
+    unsigned int st_max_bits;   // running max |u'-u| as float bits (>= 0)
+    unsigned int hi_ticket;
+    unsigned int hi_bins[kHiBins];
+    unsigned int pad[60];
+};
+static_assert(sizeof(WsSlot) % 256 == 0, "slot alignment");
+
+// ---------------------------------------------------------------- plans
+struct MrPlan {
+    int64_t n;
+    int vecs_per_thread;   // multiple of kMrUnroll
+    int64_t tile_elems;    // kMrThreads * 4 * vecs_per_thread
+    int64_t tiles;
+};
+
+__host__ __device__ inline MrPlan mr_plan(int64_t n) {
+    MrPlan p;
+    p.n = n;
+    const int64_t per_vec_row = (int64_t)kMrThreads * 4;
+    int64_t need = (n + per_vec_row * kMrMaxTiles - 1) / (per_vec_row * kMrMaxTiles);
+    int64_t v = need < kMrMinVecs ? kMrMinVecs : need;
+    v = (v + kMrUnroll - 1) / kMrUnroll * kMrUnroll;
+    p.vecs_per_thread = (int)v;
+    p.tile_elems = per_vec_row * v;
+    p.tiles = (n + p.tile_elems - 1) / p.tile_elems;
+    return p;
+}
+
+// ---------------------------------------------------------------- loads
+__device__ __forceinline__ float4 ld_stream4(const float4 *p) {
+    float4 v;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::256B.v4.f32 {%0,%1,%2,%3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ uint4 ld_stream_u4(const uint4 *p) {
+    uint4 v;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::256B.v4.u32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ void st_stream4(float4 *p, float4 v) {
+    asm volatile("st.global.cs.v4.f32 [%0], {%1,%2,%3,%4};"
+                 :: "l"(p), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w) : "memory");
+}
+
+// ---------------------------------------------------------------- trees
+// Butterfly sum over a warp: every lane ends with the same value, and the
+// pairing order is fixed, so the result is deterministic.
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
+}
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, off));
+    return v;
+}
+
+// Fixed-shape block sum of one double per thread (blockDim.x a multiple of
+// 32, at most 1024).  Returns the total in every thread of warp 0.
+__device__ __forceinline__ double block_sum(double v, double *smem32) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    v = warp_sum(v);
+    if (lane == 0) smem32[warp] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (warp == 0) {
+        r = (lane < (int)(blockDim.x >> 5)) ? smem32[lane] : 0.0;
+        r = warp_sum(r);
+    }
+    __syncthreads();
+    return r;
+}
+
+// ---------------------------------------------------------------- map->reduce
+// Sum of out[e] over the elements of tile `tile` owned by this thread, in the
+// fixed order (vector u ascending, then lane j = 0..3 within the vector),
+// storing out[e] = fmaf(a, x[e], y[e]) when out != nullptr.  The vector path
+// (aligned, full tile) and the element path produce the same fp32 sequence.
+__device__ __forceinline__ float mr_thread_partial(const float *__restrict__ x,
+                                                   const float *__restrict__ y,
+                                                   float *__restrict__ out, float a,
+                                                   const MrPlan &p, int64_t tile,
+                                                   bool aligned, int t, int nthreads) {
+    const int64_t base = tile * p.tile_elems;
+    float acc = 0.0f;
+    const bool full = base + p.tile_elems <= p.n;
+    if (full && aligned) {
+        const float4 *x4 = reinterpret_cast<const float4 *>(x + base);
+        const float4 *y4 = reinterpret_cast<const float4 *>(y + base);
+        float4 *o4 = reinterpret_cast<float4 *>(out + base);
+        for (int u0 = 0; u0 < p.vecs_per_thread; u0 += kMrUnroll) {
+            float4 xv[kMrUnroll], yv[kMrUnroll];
+#pragma unroll
+            for (int k = 0; k < kMrUnroll; ++k) {
+                const int64_t vi = (int64_t)(u0 + k) * nthreads + t;
+                xv[k] = ld_stream4(x4 + vi);
+                yv[k] = ld_stream4(y4 + vi);
+            }
+#pragma unroll
+            for (int k = 0; k < kMrUnroll; ++k) {
+                float4 o;
+                o.x = fmaf(a, xv[k].x, yv[k].x);
+                o.y = fmaf(a, xv[k].y, yv[k].y);
+                o.z = fmaf(a, xv[k].z, yv[k].z);
+                o.w = fmaf(a, xv[k].w, yv[k].w);
+                if (out) st_stream4(o4 + (int64_t)(u0 + k) * nthreads + t, o);
+                acc += o.x;
+                acc += o.y;
+                acc += o.z;
+                acc += o.w;
+            }
+        }
+    } else {
+        for (int u = 0; u < p.vecs_per_thread; ++u) {
+            const int64_t e0 = base + ((int64_t)u * nthreads + t) * 4;
+            if (e0 >= p.n) break;   // later vectors of this thread are past n too
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int64_t e = e0 + j;
+                if (e < p.n) {
+                    const float o = fmaf(a, __ldg(x + e), __ldg(y + e));
+                    if (out) out[e] = o;
+                    acc += o;
+                }
+            }
+        }
+    }
+    return acc;
+}
+
+// Tile partial (fp64) of one map->reduce tile, computed by a whole CTA of
+// kMrThreads threads; valid in thread 0.
+__device__ __forceinline__ double mr_tile(const float *__restrict__ x, const float *__restrict__ y,
+                                          float *__restrict__ out, float a, const MrPlan &p,
+                                          int64_t tile, bool aligned, double *smem32) {
+    const float part = mr_thread_partial(x, y, out, a, p, tile, aligned, threadIdx.x, kMrThreads);
+    return block_sum((double)part, smem32);
+}
+
+// Final combine of `tiles` tile partials in a fixed order: thread t folds
+// partials t, t+256, t+512, ... in fp64, then the fixed block tree.  Called
+// by a whole CTA of kFinalThreads threads; result valid in thread 0.
+__device__ __forceinline__ double mr_final(const double *partials, int64_t tiles, double *smem32) {
+    double acc = 0.0;
+    for (int64_t i = threadIdx.x; i < tiles; i += kFinalThreads) {
+        acc += __ldcg(partials + i);
+    }
+    return block_sum(acc, smem32);
+}
+
+// ---------------------------------------------------------------- stencil
+__device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+__device__ __forceinline__ float jacobi_point(float n, float s, float w, float e) {
+    const float ns = n + s;
+    const float we = w + e;
+    return 0.25f * (ns + we);
+}
+
+// One warp updates columns [c_begin, c_begin + 128) (vector path, nx % 4 == 0
+// and 16-byte aligned rows) of rows [r_begin, r_end).  Returns the lane's
+// max |u' - u| over the points it wrote.
+__device__ __forceinline__ float stencil_strip_vec(const float *__restrict__ src, float *__restrict__ dst,
+                                                   int nx, int ny, int c_begin, int r_begin, int r_end) {
+    const int lane = threadIdx.x & 31;
+    const int c0 = c_begin + lane * 4;
+    const bool valid = c0 < nx;
+    const int cl = valid ? c0 : 0;   // keep inactive lanes' loads in bounds
+    float m = 0.0f;
+    auto row4 = [&](int r) -> float4 {
+        return *reinterpret_cast<const float4 *>(src + (size_t)r * nx + cl);
+    };
+    float4 prev = row4(clampi(r_begin - 1, 0, ny - 1));
+    float4 cur = row4(r_begin);
+    for (int r = r_begin; r < r_end; ++r) {
+        const float4 next = row4(clampi(r + 1, 0, ny - 1));
+        float left = __shfl_up_sync(0xffffffffu, cur.w, 1);
+        float right = __shfl_down_sync(0xffffffffu, cur.x, 1);
+        if (lane == 0) left = (c0 == 0 || !valid) ? cur.x : src[(size_t)r * nx + c0 - 1];
+        if (c0 + 4 >= nx) right = cur.w;
+        else if (lane == 31) right = src[(size_t)r * nx + c0 + 4];
+        float4 o;
+        o.x = jacobi_point(prev.x, next.x, left, cur.y);
+        o.y = jacobi_point(prev.y, next.y, cur.x, cur.z);
+        o.z = jacobi_point(prev.z, next.z, cur.y, cur.w);
+        o.w = jacobi_point(prev.w, next.w, cur.z, right);
+        if (valid) {
+            *reinterpret_cast<float4 *>(dst + (size_t)r * nx + c0) = o;
+            m = fmaxf(m, fmaxf(fmaxf(fabsf(o.x - cur.x), fabsf(o.y - cur.y)),
+                               fmaxf(fabsf(o.z - cur.z), fabsf(o.w - cur.w))));
+        }
+        prev = cur;
+        cur = next;
+    }
+    return m;
+}
+
+// Element path for any nx and alignment: one column per lane, 32 columns per
+// warp, same arithmetic per point.
+__device__ __forceinline__ float stencil_strip_scalar(const float *__restrict__ src, float *__restrict__ dst,
+                                                      int nx, int ny, int c_begin, int r_begin, int r_end) {
+    const int lane = threadIdx.x & 31;
+    const int c = c_begin + lane;
+    const bool valid = c < nx;
+    const int cl = valid ? c : nx - 1;
+    float m = 0.0f;
+    float prev = src[(size_t)clampi(r_begin - 1, 0, ny - 1) * nx + cl];
+    float cur = src[(size_t)r_begin * nx + cl];
+    for (int r = r_begin; r < r_end; ++r) {
+        const float next = src[(size_t)clampi(r + 1, 0, ny - 1) * nx + cl];
+        float left = __shfl_up_sync(0xffffffffu, cur, 1);
+        float right = __shfl_down_sync(0xffffffffu, cur, 1);
+        if (lane == 0) left = (c == 0) ? cur : src[(size_t)r * nx + clampi(c - 1, 0, nx - 1)];
+        if (c + 1 >= nx) right = cur;
+        else if (lane == 31) right = src[(size_t)r * nx + c + 1];
+        const float o = jacobi_point(prev, next, left, right);
+        if (valid) {
+            dst[(size_t)r * nx + c] = o;
+            m = fmaxf(m, fabsf(o - cur));
+        }
+        prev = cur;
+        cur = next;
+    }
+    return m;
+}
+
+// ---------------------------------------------------------------- histogram
+// Shared bins are laid out [bin][lane]: lane l only touches column l, so one
+// warp-wide atomic never has two lanes in the same bank.
+__device__ __forceinline__ void hist_count_word(unsigned int *sh_lane, unsigned int w) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const unsigned int b = (w >> (8 * k)) & 0xffu;
+        atomicAdd(sh_lane + b * kWarp, 1u);
+    }
+}
+
+// ---------------------------------------------------------------- host side
+struct Ctx;
+}  // namespace hx
+
+struct hx_ctx {
+    int device = 0;
+    int num_sms = 0;
+    size_t hbm_budget = 0;
+    hx::WsSlot *ws = nullptr;   // HX_MAX_STREAMS slots
+    hx_stream_t slot_stream[HX_MAX_STREAMS] = {};
+    bool slot_used[HX_MAX_STREAMS] = {};
+};
+
+namespace hx {
+hx_status fail(hx_status st, const std::string &msg);
+hx_status cuda_fail(cudaError_t e, const char *what);
+hx_status slot_for(hx_ctx *ctx, hx_stream_t stream, WsSlot **slot);
+
+struct DeviceGuard {
+    int prev = -1;
+    bool changed = false;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) {
+            changed = cudaSetDevice(dev) == cudaSuccess;
+        }
+    }
+    ~DeviceGuard() {
+        if (changed) cudaSetDevice(prev);
+    }
+};
+}  // namespace hx

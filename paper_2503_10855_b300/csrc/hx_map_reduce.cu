@@ -1,0 +1,79 @@
+// hx_map_reduce.cu -- fused map -> sum reduce (one fork of factor n).
+//
+// Lowering: the fork is chunked into tiles of consecutive elements (the
+// fork-chunk of Sec. 2.2), each tile's partial starts from the identity
+// (monoid-reassociate, Sec. 5.2), and the tile partials are combined by a
+// second level (fork-fission into a producer and a consumer, Sec. 5.2).  On
+// the GPU the two levels run in ONE launch: every CTA produces one tile
+// partial, and the CTA that arrives last (an atomic ticket, no waiting) runs
+// the consumer in a fixed order.  Inside a tile the leaf reduction is a
+// per-thread fp32 fold then fp64 warp shuffles, the warp reductions of
+// Sec. 4.4.
+#include "hx_internal.cuh"
+
+namespace hx {
+
+__global__ void __launch_bounds__(kMrThreads)
+map_reduce_kernel(const float *__restrict__ x, const float *__restrict__ y, float *__restrict__ out,
+                  float a, MrPlan p, bool aligned, WsSlot *ws, float *d_sum, double *d_sum64) {
+    __shared__ double red[32];
+    __shared__ bool is_last;
+    const int64_t tile = blockIdx.x;
+    const double part = mr_tile(x, y, out, a, p, tile, aligned, red);
+    if (threadIdx.x == 0) {
+        ws->mr_partial[tile] = part;
+        __threadfence();
+        const unsigned int prev = atomicAdd(&ws->mr_ticket, 1u);
+        is_last = (prev == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    const double s = mr_final(ws->mr_partial, p.tiles, red);
+    if (threadIdx.x == 0) {
+        *d_sum = (float)s;
+        if (d_sum64) *d_sum64 = s;
+        ws->mr_ticket = 0u;
+    }
+}
+
+__global__ void map_reduce_empty_kernel(float *d_sum, double *d_sum64) {
+    *d_sum = 0.0f;
+    if (d_sum64) *d_sum64 = 0.0;
+}
+
+static bool overlaps(const void *a, size_t abytes, const void *b, size_t bbytes) {
+    const uintptr_t pa = (uintptr_t)a, pb = (uintptr_t)b;
+    return pa < pb + bbytes && pb < pa + abytes;
+}
+
+}  // namespace hx
+
+extern "C" hx_status hx_map_reduce(hx_ctx *ctx, const float *x, const float *y, float *out, float a,
+                                   int64_t n, float *d_sum, double *d_sum64, hx_stream_t stream) {
+    using namespace hx;
+    if (!ctx) return fail(HX_ERR_INVALID, "hx_map_reduce: ctx is NULL");
+    if (n < 0 || n > HX_MAP_REDUCE_MAX_N) return fail(HX_ERR_INVALID, "hx_map_reduce: n out of range");
+    if (!d_sum) return fail(HX_ERR_INVALID, "hx_map_reduce: d_sum is NULL");
+    if (n > 0 && (!x || !y)) return fail(HX_ERR_INVALID, "hx_map_reduce: x or y is NULL");
+    if ((((uintptr_t)x | (uintptr_t)y | (uintptr_t)out) & 3u) != 0)
+        return fail(HX_ERR_INVALID, "hx_map_reduce: fp32 buffers must be 4-byte aligned");
+    const size_t bytes = (size_t)n * sizeof(float);
+    if (out && n > 0 && (overlaps(out, bytes, x, bytes) || overlaps(out, bytes, y, bytes)))
+        return fail(HX_ERR_INVALID, "hx_map_reduce: out overlaps an input");
+    DeviceGuard g(ctx->device);
+    WsSlot *ws = nullptr;
+    hx_status st = slot_for(ctx, stream, &ws);
+    if (st != HX_OK) return st;
+    if (n == 0) {
+        map_reduce_empty_kernel<<<1, 1, 0, (cudaStream_t)stream>>>(d_sum, d_sum64);
+    } else {
+        const MrPlan p = mr_plan(n);
+        const bool aligned = (((uintptr_t)x | (uintptr_t)y | (uintptr_t)out) & 15u) == 0;
+        map_reduce_kernel<<<(unsigned)p.tiles, kMrThreads, 0, (cudaStream_t)stream>>>(
+            x, y, out, a, p, aligned, ws, d_sum, d_sum64);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "hx_map_reduce: launch");
+    return HX_OK;
+}
