@@ -7,6 +7,9 @@ synthetic input:
   * Jacobi: 20 clamp-to-edge 5-point sweeps of a 2048 x 2048 fp32 grid with a
     max residual per sweep
   * histogram: 256 bins of 2^26 mixture bytes + exclusive scan
+  * batch: 512 independent map->reduce / stencil instances (log-uniform
+    sizes 1K-4M elements, square sides 32-2048, one sweep each) in one
+    persistent launch
 Inputs rotate over several buffer sets whose total exceeds the 126 MB L2, so
 each step starts from HBM.  value = algorithmic bytes of the step / device
 time (GB/s), summed over ranks (weak scaling: every rank runs its own
@@ -51,6 +54,34 @@ HI_BYTES = HI_N + 2 * 256 * 4                         # bytes read; bins and sca
 STEP_BYTES = MR_BYTES + ST_BYTES + HI_BYTES
 
 
+def batch_instances(dev):
+    """Device buffers and hx tasks of the 512-instance batched workload."""
+    import torch
+
+    import paper_2503_10855_b300 as hx
+
+    bufs, tasks, byts = [], [], 0
+    for spec in workloads.batch_mix():
+        if spec["kind"] == "map_reduce":
+            n = spec["n"]
+            x = workloads.uniform_pm1_f32_torch(spec["seed"], n, dev, 2, 0)
+            y = workloads.uniform_pm1_f32_torch(spec["seed"], n, dev, 2, 1)
+            out = torch.empty(n, device=dev)
+            s32 = torch.empty(1, device=dev)
+            tasks.append(hx.map_reduce_task(x, y, spec["a"], s32, out=out))
+            bufs.append((x, y, out, s32))
+            byts += 12 * n
+        else:
+            ny, nx = spec["ny"], spec["nx"]
+            u0 = workloads.uniform01_f32_torch(spec["seed"], ny * nx, dev).view(ny, nx)
+            u1 = torch.empty_like(u0)
+            res = torch.empty(1, device=dev)
+            tasks.append(hx.stencil_task(u0, u1, 1, res))
+            bufs.append((u0, u1, res))
+            byts += 8 * nx * ny
+    return bufs, tasks, byts
+
+
 def _dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -69,16 +100,23 @@ def _peaks():
 
 # ---------------------------------------------------------------- clocks
 class ClockSampler:
-    """Samples SM clock and throttle reasons through NVML while running."""
+    """Samples SM clock and throttle reasons while the timed region runs.
 
-    def __init__(self, index: int, period_s: float = 0.01):
+    Uses NVML when the pynvml module is importable, else an ``nvidia-smi
+    --query-gpu ... -lms`` process; both only read the GPU's state."""
+
+    REASONS = {"sw_power_cap": 0x4, "hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20,
+               "hw_thermal_slowdown": 0x40, "hw_power_brake_slowdown": 0x80}
+
+    def __init__(self, index: int, period_s: float = 0.02):
         self.index, self.period = index, period_s
         self.samples = []
         self.reasons = set()
         self.max_mhz = None
         self._stop = threading.Event()
         self._thr = None
-        self.ok = False
+        self._proc = None
+        self.mode = None
 
     def __enter__(self):
         try:
@@ -88,32 +126,37 @@ class ClockSampler:
             self._nv = pynvml
             self._h = pynvml.nvmlDeviceGetHandleByIndex(self.index)
             self.max_mhz = pynvml.nvmlDeviceGetMaxClockInfo(self._h, pynvml.NVML_CLOCK_SM)
-            self.ok = True
-            self._thr = threading.Thread(target=self._run, daemon=True)
+            self.mode = "nvml"
+            self._thr = threading.Thread(target=self._run_nvml, daemon=True)
             self._thr.start()
-        except Exception as e:  # NVML missing: record why, keep benchmarking
-            self.err = str(e)
+        except Exception:
+            import subprocess
+
+            try:
+                self._proc = subprocess.Popen(
+                    ["nvidia-smi", f"--id={self.index}",
+                     "--query-gpu=clocks.sm,clocks.max.sm,utilization.gpu,clocks_event_reasons.active",
+                     "--format=csv,noheader,nounits", f"-lms={int(self.period * 1000)}"],
+                    stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                self.mode = "nvidia-smi"
+                time.sleep(0.3)   # let the first sample land before the timed work
+            except Exception as e:
+                self.err = str(e)
         return self
 
-    def _run(self):
+    def _note(self, mhz, util, bits):
+        self.samples.append((mhz, util))
+        for k, bit in self.REASONS.items():
+            if bits & bit:
+                self.reasons.add(k)
+
+    def _run_nvml(self):
         nv = self._nv
-        names = {
-            "gpu_idle": getattr(nv, "nvmlClocksEventReasonGpuIdle", 0x1),
-            "sw_power_cap": getattr(nv, "nvmlClocksEventReasonSwPowerCap", 0x4),
-            "hw_slowdown": getattr(nv, "nvmlClocksEventReasonHwSlowdown", 0x8),
-            "sw_thermal_slowdown": getattr(nv, "nvmlClocksEventReasonSwThermalSlowdown", 0x20),
-            "hw_thermal_slowdown": getattr(nv, "nvmlClocksEventReasonHwThermalSlowdown", 0x40),
-            "hw_power_brake_slowdown": getattr(nv, "nvmlClocksEventReasonHwPowerBrakeSlowdown", 0x80),
-        }
         while not self._stop.is_set():
             try:
-                mhz = nv.nvmlDeviceGetClockInfo(self._h, nv.NVML_CLOCK_SM)
-                util = nv.nvmlDeviceGetUtilizationRates(self._h).gpu
-                r = nv.nvmlDeviceGetCurrentClocksEventReasons(self._h)
-                self.samples.append((mhz, util))
-                for k, bit in names.items():
-                    if r & bit and k != "gpu_idle":
-                        self.reasons.add(k)
+                self._note(nv.nvmlDeviceGetClockInfo(self._h, nv.NVML_CLOCK_SM),
+                           nv.nvmlDeviceGetUtilizationRates(self._h).gpu,
+                           nv.nvmlDeviceGetCurrentClocksEventReasons(self._h))
             except Exception:
                 pass
             time.sleep(self.period)
@@ -122,56 +165,79 @@ class ClockSampler:
         self._stop.set()
         if self._thr:
             self._thr.join()
+        if self._proc:
+            self._proc.terminate()
+            out, _ = self._proc.communicate(timeout=10)
+            for line in out.splitlines():
+                parts = [p.strip() for p in line.split(",")]
+                try:
+                    self.max_mhz = float(parts[1])
+                    self._note(float(parts[0]), float(parts[2]), int(parts[3], 16))
+                except (ValueError, IndexError):
+                    pass
 
     def summary(self):
-        if not self.ok:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "note": getattr(self, "err", "")}
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": self.max_mhz, "reasons": [],
+                    "note": getattr(self, "err", "no samples"), "source": self.mode}
         loaded = [m for m, u in self.samples if u > 0] or [m for m, _ in self.samples]
-        return {"sm_mhz": statistics.median(loaded) if loaded else None, "sm_max_mhz": self.max_mhz,
-                "reasons": sorted(self.reasons), "samples": len(self.samples)}
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": self.max_mhz,
+                "reasons": sorted(self.reasons), "samples": len(self.samples), "source": self.mode}
 
 
 # ---------------------------------------------------------------- CPU oracle
+_ORACLE_INPUTS = {}
+
+
+def _oracle_inputs():
+    if not _ORACLE_INPUTS:
+        x, y = workloads.map_reduce_inputs(MR_N)
+        _ORACLE_INPUTS.update(x=x, y=y, v=workloads.histogram_mixture_u8(HI_N),
+                              u0=workloads.stencil_grid(ST_SIDE, ST_SIDE).astype(np.float64))
+    return _ORACLE_INPUTS
+
+
 def run_oracle_sample(budget_s: float = 15.0):
     """Time the CPU oracle on a bounded sample of the step workload.
 
-    The sample: the full map->reduce instance, the full histogram, and the
-    2048 x 2048 Jacobi grid for as many sweeps as fit the time budget (at
-    least one).  Returns (GB/s of algorithmic bytes, seconds, description)."""
+    The sample: the full map->reduce instance, a prefix of the histogram
+    input and some sweeps of the 2048 x 2048 Jacobi grid, sized to about
+    ``budget_s`` of single-core work.  Returns (GB/s of algorithmic bytes,
+    seconds, description)."""
     import oracle
 
-    x, y = workloads.map_reduce_inputs(MR_N)
-    v = workloads.histogram_mixture_u8(HI_N)
-    u0 = workloads.stencil_grid(ST_SIDE, ST_SIDE).astype(np.float64)
-    oracle.map_reduce(x[:16], y[:16], 1.5)  # load the library outside the timing
+    d = _oracle_inputs()
+    oracle.map_reduce(d["x"][:16], d["y"][:16], 1.5)  # load the library outside the timing
     t0 = time.perf_counter()
-    oracle.map_reduce(x, y, 1.5)
+    oracle.map_reduce(d["x"], d["y"], 1.5)
     t_mr = time.perf_counter() - t0
+    hn = int(min(HI_N, max(1 << 20, (budget_s / 4) * 1e9)))  # ~1 ns per byte
     t0 = time.perf_counter()
-    oracle.histogram(v)
+    oracle.histogram(d["v"][:hn])
     t_hi = time.perf_counter() - t0
     t0 = time.perf_counter()
-    oracle.jacobi(u0, 1)
+    oracle.jacobi(d["u0"], 1)
     t_sweep = time.perf_counter() - t0
-    sweeps = int(max(1, min(ST_ITERS, (budget_s - t_mr - t_hi - t_sweep) // max(t_sweep, 1e-9))))
+    sweeps = int(max(1, min(ST_ITERS, (budget_s - t_mr - t_hi) // max(t_sweep, 1e-9))))
     t0 = time.perf_counter()
     if sweeps > 1:
-        oracle.jacobi(u0, sweeps)
+        oracle.jacobi(d["u0"], sweeps)
     t_st = (time.perf_counter() - t0) if sweeps > 1 else t_sweep
-    total_bytes = MR_BYTES + HI_BYTES + ST_BYTES_PER_SWEEP * sweeps
+    total_bytes = MR_BYTES + hn + 2048 + ST_BYTES_PER_SWEEP * sweeps
     total_s = t_mr + t_hi + t_st
-    desc = (f"map_reduce N=2^20 + histogram 2^26 + jacobi 2048^2 x {sweeps} sweeps (of 20), "
-            f"sequential fp64/int oracle, {total_s:.2f} s")
+    desc = (f"map_reduce N=2^20 + histogram first {hn} of 2^26 bytes + jacobi 2048^2 x {sweeps} "
+            f"of 20 sweeps; sequential C oracle (fp64 / integer), 1 thread, {total_s:.3f} s")
     return total_bytes / total_s / 1e9, total_s, desc
 
 
 def bench_reference(args, rank, world):
     if rank != 0:
         return 0
-    gbs, secs, desc = None, 0.0, ""
-    vals = []
+    _oracle_inputs()
+    per_step = min(15.0, 120.0 / (args.warmup + args.steps))
+    secs, desc, vals = 0.0, "", []
     for i in range(args.warmup + args.steps):
-        g, s, d = run_oracle_sample(budget_s=max(2.0, 60.0 / max(1, args.warmup + args.steps)))
+        g, s, d = run_oracle_sample(budget_s=per_step)
         if i >= args.warmup:
             vals.append(g)
             secs += s
@@ -181,9 +247,10 @@ def bench_reference(args, rank, world):
         "impl": "reference", "metric": "achieved HBM GB/s (algorithmic bytes / time) of the fork-join hot path",
         "value": round(gbs, 4), "unit": "GB/s", "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(1e3 * secs / max(1, args.steps), 3),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64/u8",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64/u32",
         "data": "synthetic (seeded SplitMix64)",
-        "config": {"workload": "cpu oracle on a bounded sample of the fork-join step", "sample": desc},
+        "config": {"workload": "fork-join step (map->reduce 2^20, jacobi 2048^2 x20, histogram 2^26), "
+                               "bounded sample per step", "sample": desc},
         "cpu_baseline": {"value": round(gbs, 4), "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": desc},
         "e2e": {"value": round(gbs, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -224,40 +291,67 @@ def bench_hx(args, rank, world, local):
             s = {
                 "x": x_d0.clone(), "y": y_d0.clone(), "out": torch.empty(MR_N, device=dev),
                 "s32": torch.empty(1, device=dev), "s64": torch.empty(1, dtype=torch.float64, device=dev),
-                "u0": u_d0.clone(), "u1": torch.empty_like(u_d0), "u_init": u_d0,
+                "u0": u_d0.clone(), "u1": torch.empty_like(u_d0),
                 "res": torch.empty(ST_ITERS, device=dev),
                 "v": v_d0.clone(), "bins": torch.empty(256, dtype=torch.int32, device=dev),
                 "scan": torch.empty(256, dtype=torch.int32, device=dev),
             }
             sets.append(s)
     stream.synchronize()
+    batch_bufs, batch_tasks, BATCH_BYTES = batch_instances(dev)
+    batch = hx.hx_batch_plan(ctx, batch_tasks)
+    step_bytes = STEP_BYTES + BATCH_BYTES
+    torch.cuda.synchronize()
 
-    def run_step(s, ev=None):
-        # the Jacobi sweeps overwrite u0: restore the input grid first (a copy,
-        # outside the per-kernel events, inside the step)
-        s["u0"].copy_(s["u_init"], non_blocking=True)
-        if ev is not None:
-            ev[0].record(stream)
-        hx.hx_map_reduce(ctx, s["x"], s["y"], 1.5, out=s["out"], sum_out=s["s32"], sum64_out=s["s64"],
-                         stream=stream)
-        if ev is not None:
-            ev[1].record(stream)
-        hx.hx_stencil2d(ctx, s["u0"], s["u1"], ST_ITERS, resid=s["res"], stream=stream)
-        if ev is not None:
-            ev[2].record(stream)
-        hx.hx_histogram(ctx, s["v"], bins=s["bins"], scan=s["scan"], stream=stream)
-        if ev is not None:
-            ev[3].record(stream)
+    # one CUDA graph per component and buffer set; events between graph
+    # launches time each component on the launching stream
+    comps = ("map_reduce", "jacobi", "histogram", "batch")
 
-    launches_per_step = 1 + ST_ITERS + 1
+    def issue(name, s):
+        if name == "map_reduce":
+            hx.hx_map_reduce(ctx, s["x"], s["y"], 1.5, out=s["out"], sum_out=s["s32"],
+                             sum64_out=s["s64"], stream=stream)
+        elif name == "jacobi":
+            # 20 sweeps end in u0 again; the grid keeps evolving from step to
+            # step (a sweep's cost does not depend on the values)
+            hx.hx_stencil2d(ctx, s["u0"], s["u1"], ST_ITERS, resid=s["res"], stream=stream)
+        elif name == "histogram":
+            hx.hx_histogram(ctx, s["v"], bins=s["bins"], scan=s["scan"], stream=stream)
+        else:
+            batch.launch(stream=stream)   # one buffer set: its 2.6 GB exceed L2 by themselves
+
+    with torch.cuda.stream(stream):
+        for s in sets:           # eager warm-up of every code path before capture
+            for c in comps:
+                issue(c, s)
+    stream.synchronize()
+    graphs = []
+    for s in sets:
+        gs = {}
+        for c in comps:
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=stream):
+                issue(c, s)
+            gs[c] = g
+        graphs.append(gs)
+    launches_per_step = 1 + ST_ITERS + 1 + batch.rounds
+
+    def run_step(i, ev=None):
+        gs = graphs[i % n_sets]
+        for j, c in enumerate(comps):
+            if ev is not None:
+                ev[j].record(stream)
+            gs[c].replay()
+        if ev is not None:
+            ev[len(comps)].record(stream)
 
     with torch.cuda.stream(stream):
         for i in range(args.warmup):
-            run_step(sets[i % n_sets])
+            run_step(i)
     stream.synchronize()
 
     K = args.steps
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K)]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(len(comps) + 1)] for _ in range(K)]
     t_start = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
     if dist:
@@ -267,18 +361,17 @@ def bench_hx(args, rank, world, local):
         wall0 = time.perf_counter()
         t_start.record(stream)
         for i in range(K):
-            run_step(sets[i % n_sets], evs[i])
+            run_step(i, evs[i])
         t_end.record(stream)
         torch.cuda.synchronize()
         wall = time.perf_counter() - wall0
     if dist:
         dist.barrier()
     total_ms = t_start.elapsed_time(t_end)
-    comp_ms = {"map_reduce": 0.0, "jacobi": 0.0, "histogram": 0.0}
+    comp_ms = {c: 0.0 for c in comps}
     for e in evs:
-        comp_ms["map_reduce"] += e[0].elapsed_time(e[1])
-        comp_ms["jacobi"] += e[1].elapsed_time(e[2])
-        comp_ms["histogram"] += e[2].elapsed_time(e[3])
+        for j, c in enumerate(comps):
+            comp_ms[c] += e[j].elapsed_time(e[j + 1])
     if dist:
         t = torch.tensor([total_ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -286,23 +379,26 @@ def bench_hx(args, rank, world, local):
 
     peak, peak_kind = _peaks()
     ms_per_step = total_ms / K
-    value = world * STEP_BYTES / (ms_per_step * 1e-3) / 1e9
+    value = world * step_bytes / (ms_per_step * 1e-3) / 1e9
 
     kern = {}
     for name, byts, launches in (("map_reduce", MR_BYTES, 1), ("jacobi", ST_BYTES, ST_ITERS),
-                                 ("histogram", HI_BYTES, 1)):
+                                 ("histogram", HI_BYTES, 1), ("batch", BATCH_BYTES, batch.rounds)):
         avg_ms = comp_ms[name] / K
         gbs = byts / (avg_ms * 1e-3) / 1e9
         kern[name] = {"ms": round(avg_ms, 5), "algorithmic_bytes": byts, "GB/s": round(gbs, 1),
                       "frac_of_measured_hbm": round(gbs / peak, 4), "launches": launches}
     kern["jacobi"]["note"] = "2 x 16 MiB grids are L2-resident after the first sweep"
-    dom = max(("map_reduce", "jacobi", "histogram"), key=lambda k: comp_ms[k])
+    dom = max(comps, key=lambda k: comp_ms[k])
     dom_per_launch_ms = comp_ms[dom] / K / kern[dom]["launches"]
     dom_bytes_per_launch = kern[dom]["algorithmic_bytes"] / kern[dom]["launches"]
     achieved = dom_bytes_per_launch / (dom_per_launch_ms * 1e-3) / 1e9
 
+    # ---- batched vs one launch per instance, same instances, same stream
+    batched = bench_batched_vs_per_launch(hx, ctx, batch, batch_tasks, stream, reps=10)
+
     # ---- end to end through the public API with pinned host buffers
-    e2e = bench_e2e(args, hx, ctx, dev, x_h, y_h, u_h, v_h)
+    e2e = bench_e2e(args, hx, ctx, dev, x_h, y_h, u_h, v_h, batch, batch_bufs, BATCH_BYTES)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -317,10 +413,11 @@ def bench_hx(args, rank, world, local):
         "data": "synthetic (seeded SplitMix64), inputs resident in HBM",
         "config": {
             "workload": "fork-join step: map->reduce N=2^20 a=1.5 + jacobi 2048x2048 x20 sweeps "
-                        "+ histogram 2^26 u8 mixture with exclusive scan",
+                        "+ histogram 2^26 u8 mixture with exclusive scan + batch of 512 map->reduce/stencil "
+                        "instances (sizes log-uniform 1K-4M, sides 32-2048) in one persistent launch",
             "parallelism": f"replicas x{world}",
             "l2": f"inputs rotate over {n_sets} buffer sets ({n_sets * per_set / 2**20:.0f} MiB > 126 MB L2)",
-            "step_bytes": STEP_BYTES,
+            "step_bytes": step_bytes,
         },
         "frac_of_hbm_roofline": round(value / world / peak, 4),
         "frac_of_nominal_8tbs": round(value / world / 8000.0, 4),
@@ -329,6 +426,7 @@ def bench_hx(args, rank, world, local):
                      "traffic": None},
         "kernels": kern,
         "cpu_baseline": cpu,
+        "batched": batched,
         "e2e": e2e,
         "gpu_launches": launches_per_step * K,
         "clocks": clk.summary(),
@@ -342,11 +440,56 @@ def bench_hx(args, rank, world, local):
     return 0
 
 
-def bench_e2e(args, hx, ctx, dev, x_h, y_h, u_h, v_h, steps=None):
-    """Same step through the public API, host buffers in and results out."""
+def bench_batched_vs_per_launch(hx, ctx, batch, tasks, stream, reps=10):
+    """requests/s of the 512 instances as one batch vs one launch per instance.
+
+    Per-launch is timed twice: issued from the host call by call, and with the
+    512 launches captured in one CUDA graph (no host overhead)."""
     import torch
 
-    steps = steps or max(3, min(args.steps, 20))
+    def per_launch():
+        for t in tasks:
+            if t.kind == hx.HX_TASK_MAP_REDUCE:
+                x, y, out, s32 = t.keep[0], t.keep[1], t.keep[2], t.keep[3]
+                hx.hx_map_reduce(ctx, x, y, t.u.mr.a, out=out, sum_out=s32, stream=stream)
+            else:
+                u0, u1, res = t.keep
+                hx.hx_stencil2d(ctx, u0, u1, 1, resid=res, stream=stream)
+
+    def timed(fn):
+        with torch.cuda.stream(stream):
+            fn()
+            stream.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(reps):
+                fn()
+            b.record(stream)
+            stream.synchronize()
+        return a.elapsed_time(b) / reps
+
+    g_batch = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g_batch, stream=stream):
+        batch.launch(stream=stream)
+    g_per = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g_per, stream=stream):
+        per_launch()
+    ms_b = timed(g_batch.replay)
+    ms_pg = timed(g_per.replay)
+    ms_pe = timed(per_launch)
+    n = len(tasks)
+    return {"instances": n, "batched_ms": round(ms_b, 4), "batched_req_per_s": round(n / ms_b * 1e3, 1),
+            "per_launch_graph_ms": round(ms_pg, 4), "per_launch_graph_req_per_s": round(n / ms_pg * 1e3, 1),
+            "per_launch_eager_ms": round(ms_pe, 4), "per_launch_eager_req_per_s": round(n / ms_pe * 1e3, 1),
+            "speedup_vs_graph": round(ms_pg / ms_b, 3), "speedup_vs_eager": round(ms_pe / ms_b, 3)}
+
+
+def bench_e2e(args, hx, ctx, dev, x_h, y_h, u_h, v_h, batch, batch_bufs, batch_bytes, steps=None):
+    """The whole step through the public API: inputs copied in from pinned host
+    memory and the reduction results copied back, inside the timed region."""
+    import torch
+
+    steps = steps or max(3, min(args.steps, 10))
     pin = lambda a: torch.from_numpy(a).pin_memory()  # noqa: E731
     xh, yh, uh, vh = pin(x_h), pin(y_h), pin(u_h), pin(v_h)
     xd, yd = torch.empty_like(xh, device=dev), torch.empty_like(yh, device=dev)
@@ -357,25 +500,41 @@ def bench_e2e(args, hx, ctx, dev, x_h, y_h, u_h, v_h, steps=None):
     res = torch.empty(ST_ITERS, device=dev)
     bins = torch.empty(256, dtype=torch.int32, device=dev)
     scan = torch.empty(256, dtype=torch.int32, device=dev)
+    # batch inputs (map x, y; stencil u0) staged in pinned host memory
+    b_in, b_res = [], []
+    for b in batch_bufs:
+        if len(b) == 4:
+            b_in += [(b[0].cpu().pin_memory(), b[0]), (b[1].cpu().pin_memory(), b[1])]
+            b_res.append(b[3])
+        else:
+            b_in.append((b[0].cpu().pin_memory(), b[0]))
+            b_res.append(b[2])
+    b_res_h = torch.empty(len(b_res), dtype=torch.float32).pin_memory()
+    b_res_d = torch.empty(len(b_res), dtype=torch.float32, device=dev)
     res_h = torch.empty(8 + 8 + 4 * ST_ITERS + 2048, dtype=torch.uint8).pin_memory()
     s = torch.cuda.Stream(device=dev)
-    h2d = 4 * MR_N * 2 + 4 * ST_SIDE * ST_SIDE + HI_N
-    d2h = 4 + 8 + 4 * ST_ITERS + 2 * 1024
+    h2d = 4 * MR_N * 2 + 4 * ST_SIDE * ST_SIDE + HI_N + sum(h.numel() * 4 for h, _ in b_in)
+    d2h = 4 + 8 + 4 * ST_ITERS + 2 * 1024 + 4 * len(b_res)
 
     def one():
         xd.copy_(xh, non_blocking=True)
         yd.copy_(yh, non_blocking=True)
         ud.copy_(uh, non_blocking=True)
         vd.copy_(vh, non_blocking=True)
+        for h, d in b_in:
+            d.copy_(h, non_blocking=True)
         _, s32, _ = hx.hx_map_reduce(ctx, xd, yd, 1.5, out=out, sum64_out=s64, stream=s)
         hx.hx_stencil2d(ctx, ud, u1, ST_ITERS, resid=res, stream=s)
         hx.hx_histogram(ctx, vd, bins=bins, scan=scan, stream=s)
+        batch.launch(stream=s)
         res_h[0:4].copy_(s32.view(torch.uint8), non_blocking=True)
         res_h[8:16].copy_(s64.view(torch.uint8), non_blocking=True)
         res_h[16:16 + 4 * ST_ITERS].copy_(res.view(torch.uint8), non_blocking=True)
         o = 16 + 4 * ST_ITERS
         res_h[o:o + 1024].copy_(bins.view(torch.uint8), non_blocking=True)
         res_h[o + 1024:o + 2048].copy_(scan.view(torch.uint8), non_blocking=True)
+        torch.cat(b_res, out=b_res_d)
+        b_res_h.copy_(b_res_d, non_blocking=True)
 
     with torch.cuda.stream(s):
         for _ in range(2):
@@ -388,14 +547,15 @@ def bench_e2e(args, hx, ctx, dev, x_h, y_h, u_h, v_h, steps=None):
         b.record(s)
         s.synchronize()
     ms = a.elapsed_time(b) / steps
-    return {"value": round(STEP_BYTES / (ms * 1e-3) / 1e9, 2), "unit": "GB/s", "ms_per_step": round(ms, 4),
+    total = STEP_BYTES + batch_bytes
+    return {"value": round(total / (ms * 1e-3) / 1e9, 2), "unit": "GB/s", "ms_per_step": round(ms, 4),
             "steps": steps, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["hx", "reference"], default="hx")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -134,6 +134,71 @@ hx_status hx_stencil2d(hx_ctx *ctx, float *u0, float *u1, int32_t nx, int32_t ny
 hx_status hx_histogram(hx_ctx *ctx, const uint8_t *v, int64_t n, uint32_t *d_bins,
                        uint32_t *d_excl_scan, hx_stream_t stream);
 
+/* ------------------------------------------------------------------ batches
+ * Many independent nest instances in one persistent launch.  The Hercules
+ * host backend runs independent calls and the iterations of parallel
+ * fork-joins as concurrent tasks (Sec. 4.5, the AsyncCall attribute of
+ * Sec. 3.4); here the instances become one device work-list of
+ * (instance, tile) items that resident CTAs pull from an atomic counter.
+ * Every item runs the same tile code as the standalone calls above and the
+ * tile plan of an instance depends only on its own sizes, so each result is
+ * bit-identical to the standalone call's.  The last tile of an instance to
+ * finish runs its final combine (no CTA ever waits for another).
+ *
+ * A stencil task with iters > 1 is executed as rounds: round r runs sweep r
+ * of every stencil instance that has one (plus, in round 0, all map->reduce
+ * and histogram instances); rounds are consecutive launches.
+ *
+ * Pointer, size and alignment rules of each task kind are those of the
+ * matching standalone call.  Instances of one batch must not write
+ * overlapping memory.  An instance's sweep count is capped at 4096. */
+typedef enum hx_task_kind {
+    HX_TASK_MAP_REDUCE = 0,
+    HX_TASK_STENCIL2D = 1,
+    HX_TASK_HISTOGRAM = 2
+} hx_task_kind;
+
+typedef struct hx_task {
+    int32_t kind; /* hx_task_kind */
+    int32_t reserved;
+    union {
+        struct { const float *x; const float *y; float *out; float *sum; double *sum64;
+                 float a; int32_t pad; int64_t n; } mr;          /* out, sum64 nullable */
+        struct { float *u0; float *u1; float *resid;
+                 int32_t nx; int32_t ny; int32_t iters; int32_t pad; } st;
+        struct { const uint8_t *v; uint32_t *bins; uint32_t *scan; int64_t n; } hi; /* scan nullable */
+    } u;
+} hx_task;
+
+typedef struct hx_batch hx_batch;
+
+/* Validate `tasks` and build their device work-list and workspace
+ * (allocates device memory; must not be called during stream capture).
+ * The tasks' buffers are bound to the plan: launching it again re-runs the
+ * same instances on the same buffers.  *out_rounds (nullable) receives the
+ * number of launches one hx_batch_launch issues. */
+hx_status hx_batch_plan(hx_ctx *ctx, const hx_task *tasks, int32_t n_tasks, hx_batch **out,
+                        int32_t *out_rounds);
+
+/* Run a planned batch on `stream`: one persistent launch per round, no host
+ * synchronisation, no allocation (may be captured in a CUDA graph).  A plan
+ * must not run on two streams at once. */
+hx_status hx_batch_launch(hx_batch *batch, hx_stream_t stream);
+
+/* Free a plan.  Its launches must have completed. */
+void hx_batch_free(hx_batch *batch);
+
+/* Plan, launch on `stream` and record completion in one call; *ticket_out
+ * identifies the submission for hx_batch_query.  The plan is released when
+ * a query sees it complete (or at hx_destroy). */
+hx_status hx_batch_submit(hx_ctx *ctx, const hx_task *tasks, int32_t n_tasks, hx_stream_t stream,
+                          uint64_t *ticket_out);
+
+/* HX_OK when the submission's device work has completed, HX_ERR_BUSY while
+ * it is pending, HX_ERR_INVALID for an unknown ticket (including one already
+ * reported complete). */
+hx_status hx_batch_query(hx_ctx *ctx, uint64_t ticket);
+
 #ifdef __cplusplus
 }
 #endif

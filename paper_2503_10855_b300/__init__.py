@@ -184,3 +184,159 @@ def hx_histogram(ctx: Context, v, bins=None, scan=None, want_scan: bool = True, 
                              _dev_ptr(scan, scan.dtype, "scan", 256) if scan is not None else _P(0),
                              _stream_handle(stream)), "hx_histogram")
     return bins, scan
+
+
+# ------------------------------------------------------------------ batches
+HX_TASK_MAP_REDUCE, HX_TASK_STENCIL2D, HX_TASK_HISTOGRAM = 0, 1, 2
+
+
+class _TaskMR(ctypes.Structure):
+    _fields_ = [("x", _P), ("y", _P), ("out", _P), ("sum", _P), ("sum64", _P),
+                ("a", ctypes.c_float), ("pad", _I32), ("n", _I64)]
+
+
+class _TaskST(ctypes.Structure):
+    _fields_ = [("u0", _P), ("u1", _P), ("resid", _P), ("nx", _I32), ("ny", _I32),
+                ("iters", _I32), ("pad", _I32)]
+
+
+class _TaskHI(ctypes.Structure):
+    _fields_ = [("v", _P), ("bins", _P), ("scan", _P), ("n", _I64)]
+
+
+class _TaskU(ctypes.Union):
+    _fields_ = [("mr", _TaskMR), ("st", _TaskST), ("hi", _TaskHI)]
+
+
+class HxTask(ctypes.Structure):
+    """Mirror of ``hx_task`` (64 bytes).  ``keep`` holds the tensors it points to."""
+
+    _fields_ = [("kind", _I32), ("reserved", _I32), ("u", _TaskU)]
+
+
+assert ctypes.sizeof(HxTask) == 64
+
+_lib.hx_batch_plan.argtypes = [_P, ctypes.POINTER(HxTask), _I32, ctypes.POINTER(_P), ctypes.POINTER(_I32)]
+_lib.hx_batch_plan.restype = ctypes.c_int
+_lib.hx_batch_launch.argtypes = [_P, _P]
+_lib.hx_batch_launch.restype = ctypes.c_int
+_lib.hx_batch_free.argtypes = [_P]
+_lib.hx_batch_free.restype = None
+_lib.hx_batch_submit.argtypes = [_P, ctypes.POINTER(HxTask), _I32, _P, ctypes.POINTER(ctypes.c_uint64)]
+_lib.hx_batch_submit.restype = ctypes.c_int
+_lib.hx_batch_query.argtypes = [_P, ctypes.c_uint64]
+_lib.hx_batch_query.restype = ctypes.c_int
+
+
+def map_reduce_task(x, y, a: float, sum_out, out=None, sum64_out=None) -> HxTask:
+    import torch
+
+    n = x.numel()
+    if y.numel() != n:
+        raise ValueError("x and y differ in length")
+    t = HxTask()
+    t.kind = HX_TASK_MAP_REDUCE
+    m = t.u.mr
+    m.x, m.y = _dev_ptr(x, torch.float32, "x"), _dev_ptr(y, torch.float32, "y")
+    m.out = _dev_ptr(out, torch.float32, "out", n)
+    m.sum = _dev_ptr(sum_out, torch.float32, "sum_out", 1)
+    m.sum64 = _dev_ptr(sum64_out, torch.float64, "sum64_out", 1)
+    m.a, m.n = float(a), n
+    t.keep = (x, y, out, sum_out, sum64_out)
+    return t
+
+
+def stencil_task(u0, u1, iters: int, resid) -> HxTask:
+    import torch
+
+    if u0.dim() != 2 or u0.shape != u1.shape:
+        raise ValueError("u0 and u1 must be 2-D of the same shape")
+    t = HxTask()
+    t.kind = HX_TASK_STENCIL2D
+    s = t.u.st
+    s.u0, s.u1 = _dev_ptr(u0, torch.float32, "u0"), _dev_ptr(u1, torch.float32, "u1")
+    s.resid = _dev_ptr(resid, torch.float32, "resid", iters)
+    s.ny, s.nx = u0.shape
+    s.iters = iters
+    t.keep = (u0, u1, resid)
+    return t
+
+
+def histogram_task(v, bins, scan=None) -> HxTask:
+    import torch
+
+    t = HxTask()
+    t.kind = HX_TASK_HISTOGRAM
+    h = t.u.hi
+    h.v = _dev_ptr(v, torch.uint8, "v")
+    h.bins = _dev_ptr(bins, bins.dtype, "bins", 256)
+    h.scan = _dev_ptr(scan, scan.dtype, "scan", 256) if scan is not None else _P(0)
+    h.n = v.numel()
+    t.keep = (v, bins, scan)
+    return t
+
+
+def _task_array(tasks):
+    arr = (HxTask * len(tasks))()
+    for i, t in enumerate(tasks):
+        ctypes.memmove(ctypes.byref(arr[i]), ctypes.byref(t), ctypes.sizeof(HxTask))
+    return arr
+
+
+class Batch:
+    """A planned batch (``hx_batch``): device work-list bound to the tasks' buffers."""
+
+    def __init__(self, ctx: Context, tasks):
+        self.ctx = ctx
+        self.keep = [getattr(t, "keep", None) for t in tasks]
+        arr = _task_array(tasks)
+        h = _P()
+        rounds = _I32(0)
+        _check(_lib.hx_batch_plan(ctx.handle, arr, len(tasks), ctypes.byref(h), ctypes.byref(rounds)),
+               "hx_batch_plan")
+        self.handle = h
+        self.rounds = rounds.value
+
+    def launch(self, stream=None) -> None:
+        _check(_lib.hx_batch_launch(self.handle, _stream_handle(stream)), "hx_batch_launch")
+
+    def close(self) -> None:
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            _lib.hx_batch_free(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def hx_batch_plan(ctx: Context, tasks) -> Batch:
+    return Batch(ctx, tasks)
+
+
+def hx_batch_launch(batch: Batch, stream=None) -> None:
+    batch.launch(stream)
+
+
+def hx_batch_free(batch: Batch) -> None:
+    batch.close()
+
+
+def hx_batch_submit(ctx: Context, tasks, stream=None) -> int:
+    """Plan + launch + completion record; returns a ticket for hx_batch_query."""
+    arr = _task_array(tasks)
+    ticket = ctypes.c_uint64(0)
+    _check(_lib.hx_batch_submit(ctx.handle, arr, len(tasks), _stream_handle(stream), ctypes.byref(ticket)),
+           "hx_batch_submit")
+    return ticket.value
+
+
+def hx_batch_query(ctx: Context, ticket: int) -> bool:
+    """True once the submission completed (the ticket is then retired), False while pending."""
+    st = _lib.hx_batch_query(ctx.handle, ticket)
+    if st == HX_ERR_BUSY:
+        return False
+    _check(st, "hx_batch_query")
+    return True

@@ -1,0 +1,463 @@
+// hx_batch.cu -- many independent nest instances in one persistent launch.
+//
+// The Hercules host backend runs independent calls and the iterations of
+// parallel fork-joins as concurrent tasks (Sec. 4.5; the AsyncCall attribute
+// of Sec. 3.4).  On one GPU that becomes a device work-list: every instance
+// is cut into the same tiles its standalone call would use, the tiles of all
+// instances are listed as (instance, tile) items, and resident CTAs pull
+// items from an atomic counter until the list is empty.  Per-instance arrival
+// tickets let the last tile of an instance run its final combine, so no CTA
+// ever waits for another.  A stencil instance with several sweeps contributes
+// one sweep per round; rounds are consecutive launches chained with
+// programmatic dependent launch.
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "hx_internal.cuh"
+
+namespace hx {
+
+enum : int { kKindMap = 0, kKindStencil = 1, kKindHist = 2 };
+
+constexpr int kBatchThreads = 256;                         // == kMrThreads == kFinalThreads
+constexpr int kBStWarps = kBatchThreads / kWarp;           // stencil warps per item
+constexpr int kBStTileRows = kBStWarps * kStRows;          // rows per stencil item
+constexpr int64_t kBHiTile = (int64_t)kBatchThreads * 16 * 32;   // 128 KiB per histogram item
+constexpr int kMaxSweeps = 4096;
+static_assert(kBatchThreads == kMrThreads && kBatchThreads == kFinalThreads,
+              "batched map tiles must reproduce the standalone tile shape");
+
+struct BInst {
+    int kind;
+    int vec;            // map: 16-byte aligned operands; stencil: vector path; hist: unused
+    int nx, ny;
+    float a;
+    int iters;          // stencil sweeps
+    int64_t n;
+    int64_t tiles;      // items per round
+    int tiles_x;        // stencil tiles across
+    int pad;
+    MrPlan plan;
+    const void *in0;    // map x | stencil u0 | hist v
+    const void *in1;    // map y | stencil u1
+    void *o0;           // map out | stencil resid | hist bins
+    void *o1;           // map sum | hist scan
+    void *o2;           // map sum64
+    double *partials;   // map tile partials
+    unsigned int *ticket;
+    unsigned int *acc;  // stencil: max bits (1); hist: 256 bins
+};
+
+__device__ __forceinline__ void batch_map_item(const BInst &I, int64_t tile, double *red, int *flag) {
+    const MrPlan p = I.plan;
+    const float *x = static_cast<const float *>(I.in0);
+    const float *y = static_cast<const float *>(I.in1);
+    float *out = static_cast<float *>(I.o0);
+    const double part = mr_tile(x, y, out, I.a, p, tile, I.vec != 0, red);
+    if (threadIdx.x == 0) {
+        I.partials[tile] = part;
+        __threadfence();
+        *flag = atomicAdd(I.ticket, 1u) == (unsigned int)(p.tiles - 1);
+    }
+    __syncthreads();
+    if (*flag) {
+        __threadfence();
+        const double s = mr_final(I.partials, p.tiles, red);
+        if (threadIdx.x == 0) {
+            *static_cast<float *>(I.o1) = (float)s;
+            if (I.o2) *static_cast<double *>(I.o2) = s;
+            *I.ticket = 0u;
+        }
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ void batch_stencil_item(const BInst &I, int64_t tile, int round, float *wmax,
+                                                   int *flag) {
+    const float *src = static_cast<const float *>((round & 1) ? I.in1 : I.in0);
+    float *dst = const_cast<float *>(static_cast<const float *>((round & 1) ? I.in0 : I.in1));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int bx = (int)(tile % I.tiles_x), by = (int)(tile / I.tiles_x);
+    const int c_begin = bx * (I.vec ? 128 : 32);
+    const int r_begin = by * kBStTileRows + warp * kStRows;
+    float m = 0.0f;
+    if (r_begin < I.ny) {
+        m = I.vec ? stencil_block_vec<kStRows>(src, dst, I.nx, I.ny, c_begin, r_begin)
+                  : stencil_block_scalar<kStRows>(src, dst, I.nx, I.ny, c_begin, r_begin);
+    }
+    m = warp_max(m);
+    if (lane == 0) wmax[warp] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float bm = wmax[0];
+        for (int w = 1; w < kBStWarps; ++w) bm = fmaxf(bm, wmax[w]);
+        atomicMax(I.acc, __float_as_uint(bm));
+        __threadfence();
+        if (atomicAdd(I.ticket, 1u) == (unsigned int)(I.tiles - 1)) {
+            __threadfence();
+            const unsigned int bits = atomicExch(I.acc, 0u);
+            static_cast<float *>(I.o0)[round] = __uint_as_float(bits);
+            *I.ticket = 0u;
+        }
+    }
+    __syncthreads();
+    (void)flag;
+}
+
+__device__ __forceinline__ void batch_hist_item(const BInst &I, int64_t tile, unsigned int *sh,
+                                                unsigned int *wtot, int *flag) {
+    for (int i = threadIdx.x; i < kHiBins * kWarp; i += kBatchThreads) sh[i] = 0u;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t base_lane = smem_addr(sh) + 4u * lane;
+    const uint8_t *v = static_cast<const uint8_t *>(I.in0);
+    const int64_t s = tile * kBHiTile;
+    const int64_t e = min(I.n, s + kBHiTile);
+    int head = (int)((16 - ((uintptr_t)(v + s) & 15u)) & 15u);
+    if (head > e - s) head = (int)(e - s);
+    const int64_t nvec = (e - s - head) / 16;
+    const int tail = (int)((e - s - head) % 16);
+    hist_count_strided(base_lane, reinterpret_cast<const uint4 *>(v + s + head), threadIdx.x, kBatchThreads,
+                       nvec);
+    if (threadIdx.x < head) hist_count_byte(base_lane, v[s + threadIdx.x]);
+    if (threadIdx.x < tail) hist_count_byte(base_lane, v[e - tail + threadIdx.x]);
+    __syncthreads();
+    for (int b = threadIdx.x; b < kHiBins; b += kBatchThreads) {
+        unsigned int c = 0u;
+#pragma unroll 8
+        for (int k = 0; k < kWarp; ++k) c += sh[b * kWarp + ((k + b) & 31)];
+        if (c) atomicAdd(I.acc + b, c);
+    }
+    __threadfence();   // every thread of the 256 wrote one bin
+    __syncthreads();
+    if (threadIdx.x == 0) *flag = atomicAdd(I.ticket, 1u) == (unsigned int)(I.tiles - 1);
+    __syncthreads();
+    if (*flag) {
+        __threadfence();
+        const unsigned int c = atomicExch(I.acc + threadIdx.x, 0u);   // 256 threads == 256 bins
+        static_cast<uint32_t *>(I.o0)[threadIdx.x] = c;
+        unsigned int incl = c;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const unsigned int t = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += t;
+        }
+        if (lane == 31) wtot[warp] = incl;
+        __syncthreads();
+        unsigned int before = 0u;
+        for (int w = 0; w < warp; ++w) before += wtot[w];
+        if (I.o1) static_cast<uint32_t *>(I.o1)[threadIdx.x] = before + incl - c;
+        if (threadIdx.x == 0) *I.ticket = 0u;
+    }
+    __syncthreads();
+}
+
+// ctrl[0]: next item of this round; ctrl[1]: CTAs that have left the loop.
+__global__ void __launch_bounds__(kBatchThreads)
+batch_kernel(const BInst *__restrict__ insts, const unsigned long long *__restrict__ items,
+             unsigned int n_items, int round, unsigned int *ctrl) {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;");
+    __shared__ unsigned int sh[kHiBins * kWarp];
+    __shared__ double red[32];
+    __shared__ float wmax[kBStWarps];
+    __shared__ unsigned int wtot[kBStWarps];
+    __shared__ unsigned int s_item;
+    __shared__ int s_flag;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(&ctrl[0], 1u);
+        __syncthreads();
+        const unsigned int it = s_item;
+        __syncthreads();
+        if (it >= n_items) break;
+        const unsigned long long item = items[it];
+        const BInst &I = insts[item >> 32];
+        const int64_t tile = (int64_t)(item & 0xffffffffull);
+        const int kind = I.kind;
+        if (kind == kKindMap) batch_map_item(I, tile, red, &s_flag);
+        else if (kind == kKindStencil) batch_stencil_item(I, tile, round, wmax, &s_flag);
+        else batch_hist_item(I, tile, sh, wtot, &s_flag);
+    }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(&ctrl[1], 1u) == gridDim.x - 1) {
+            ctrl[0] = 0u;
+            ctrl[1] = 0u;
+        }
+    }
+}
+
+}  // namespace hx
+
+struct hx_batch {
+    hx_ctx *ctx = nullptr;
+    int rounds = 0;
+    std::vector<uint32_t> round_begin;   // rounds + 1 offsets into the item list
+    void *d_mem = nullptr;
+    hx::BInst *d_insts = nullptr;
+    unsigned long long *d_items = nullptr;
+    unsigned int *d_ctrl = nullptr;
+    int ctas_per_sm = 1;
+};
+
+namespace hx {
+
+static hx_status validate_task(const hx_task &t, int idx) {
+    char where[64];
+    snprintf(where, sizeof where, "hx_batch_plan: task %d: ", idx);
+    switch (t.kind) {
+    case HX_TASK_MAP_REDUCE: {
+        const auto &m = t.u.mr;
+        if (m.n < 0 || m.n > HX_MAP_REDUCE_MAX_N) return fail(HX_ERR_INVALID, std::string(where) + "n out of range");
+        if (!m.sum) return fail(HX_ERR_INVALID, std::string(where) + "sum is NULL");
+        if (m.n > 0 && (!m.x || !m.y)) return fail(HX_ERR_INVALID, std::string(where) + "x or y is NULL");
+        if ((((uintptr_t)m.x | (uintptr_t)m.y | (uintptr_t)m.out) & 3u) != 0)
+            return fail(HX_ERR_INVALID, std::string(where) + "fp32 buffers must be 4-byte aligned");
+        return HX_OK;
+    }
+    case HX_TASK_STENCIL2D: {
+        const auto &s = t.u.st;
+        if (s.nx < 1 || s.ny < 1 || s.nx > 65536 || s.ny > 65536 || (int64_t)s.nx * s.ny > ((int64_t)1 << 31))
+            return fail(HX_ERR_INVALID, std::string(where) + "grid size out of range");
+        if (s.iters < 0 || s.iters > kMaxSweeps) return fail(HX_ERR_INVALID, std::string(where) + "iters out of range");
+        if (!s.u0 || !s.u1) return fail(HX_ERR_INVALID, std::string(where) + "grid pointer is NULL");
+        if (s.iters > 0 && !s.resid) return fail(HX_ERR_INVALID, std::string(where) + "resid is NULL");
+        if ((((uintptr_t)s.u0 | (uintptr_t)s.u1) & 3u) != 0)
+            return fail(HX_ERR_INVALID, std::string(where) + "grids must be 4-byte aligned");
+        const size_t bytes = (size_t)s.nx * s.ny * sizeof(float);
+        if ((uintptr_t)s.u0 < (uintptr_t)s.u1 + bytes && (uintptr_t)s.u1 < (uintptr_t)s.u0 + bytes)
+            return fail(HX_ERR_INVALID, std::string(where) + "u0 and u1 overlap");
+        return HX_OK;
+    }
+    case HX_TASK_HISTOGRAM: {
+        const auto &h = t.u.hi;
+        if (h.n < 0 || h.n > HX_HISTOGRAM_MAX_N) return fail(HX_ERR_INVALID, std::string(where) + "n out of range");
+        if (!h.bins) return fail(HX_ERR_INVALID, std::string(where) + "bins is NULL");
+        if (h.n > 0 && !h.v) return fail(HX_ERR_INVALID, std::string(where) + "v is NULL");
+        if ((((uintptr_t)h.bins | (uintptr_t)h.scan) & 3u) != 0)
+            return fail(HX_ERR_INVALID, std::string(where) + "bins must be 4-byte aligned");
+        return HX_OK;
+    }
+    default:
+        return fail(HX_ERR_INVALID, std::string(where) + "unknown task kind");
+    }
+}
+
+}  // namespace hx
+
+extern "C" hx_status hx_batch_plan(hx_ctx *ctx, const hx_task *tasks, int32_t n_tasks, hx_batch **out,
+                                   int32_t *out_rounds) {
+    using namespace hx;
+    if (!ctx || !out) return fail(HX_ERR_INVALID, "hx_batch_plan: ctx or out is NULL");
+    *out = nullptr;
+    if (n_tasks < 0 || (n_tasks > 0 && !tasks)) return fail(HX_ERR_INVALID, "hx_batch_plan: bad task list");
+    for (int i = 0; i < n_tasks; ++i) {
+        hx_status st = validate_task(tasks[i], i);
+        if (st != HX_OK) return st;
+    }
+    std::vector<BInst> insts(n_tasks);
+    int rounds = n_tasks > 0 ? 1 : 0;
+    int64_t n_partials = 0, n_acc = 0;
+    for (int i = 0; i < n_tasks; ++i) {
+        const hx_task &t = tasks[i];
+        BInst &I = insts[i];
+        memset(&I, 0, sizeof I);
+        I.kind = t.kind;
+        if (t.kind == HX_TASK_MAP_REDUCE) {
+            const auto &m = t.u.mr;
+            I.n = m.n;
+            I.a = m.a;
+            I.plan = mr_plan(m.n > 0 ? m.n : 1);
+            I.plan.n = m.n;
+            I.tiles = m.n > 0 ? I.plan.tiles : 0;
+            I.vec = (((uintptr_t)m.x | (uintptr_t)m.y | (uintptr_t)m.out) & 15u) == 0;
+            I.in0 = m.x; I.in1 = m.y; I.o0 = m.out; I.o1 = m.sum; I.o2 = m.sum64;
+            n_partials += I.tiles;
+        } else if (t.kind == HX_TASK_STENCIL2D) {
+            const auto &s = t.u.st;
+            I.nx = s.nx; I.ny = s.ny; I.iters = s.iters;
+            I.n = (int64_t)s.nx * s.ny;
+            I.vec = (s.nx % 4 == 0) && ((((uintptr_t)s.u0 | (uintptr_t)s.u1) & 15u) == 0);
+            const int width = I.vec ? 128 : 32;
+            I.tiles_x = (s.nx + width - 1) / width;
+            I.tiles = s.iters > 0 ? (int64_t)I.tiles_x * ((s.ny + kBStTileRows - 1) / kBStTileRows) : 0;
+            I.in0 = s.u0; I.in1 = s.u1; I.o0 = s.resid;
+            n_acc += 1;
+            rounds = std::max(rounds, s.iters);
+        } else {
+            const auto &h = t.u.hi;
+            I.n = h.n;
+            I.tiles = h.n > 0 ? (h.n + kBHiTile - 1) / kBHiTile : 0;
+            I.in0 = h.v; I.o0 = h.bins; I.o1 = h.scan;
+            n_acc += kHiBins;
+        }
+        if (I.tiles > 0xffffffffll) return fail(HX_ERR_INVALID, "hx_batch_plan: instance too large");
+    }
+    // Items, round by round.  Round 0 holds the one-pass instances; stencil
+    // sweep r of each instance goes to round r.
+    std::vector<unsigned long long> items;
+    std::vector<uint32_t> round_begin;
+    std::vector<int> empty_map, empty_hist;
+    for (int r = 0; r < rounds; ++r) {
+        round_begin.push_back((uint32_t)items.size());
+        for (int i = 0; i < n_tasks; ++i) {
+            const BInst &I = insts[i];
+            const bool active = (I.kind == kKindStencil) ? (r < I.iters) : (r == 0);
+            if (!active) continue;
+            for (int64_t k = 0; k < I.tiles; ++k) items.push_back(((unsigned long long)i << 32) | (unsigned long long)k);
+        }
+    }
+    round_begin.push_back((uint32_t)items.size());
+    if (items.size() > 0xffffffffull) return fail(HX_ERR_INVALID, "hx_batch_plan: too many items");
+
+    // One device allocation: insts | items | partials | tickets | accumulators | ctrl.
+    auto align = [](size_t v) { return (v + 255) & ~(size_t)255; };
+    const size_t off_items = align(sizeof(BInst) * insts.size());
+    const size_t off_part = off_items + align(sizeof(unsigned long long) * items.size());
+    const size_t off_tick = off_part + align(sizeof(double) * n_partials);
+    const size_t off_acc = off_tick + align(sizeof(unsigned int) * insts.size());
+    const size_t off_ctrl = off_acc + align(sizeof(unsigned int) * n_acc);
+    const size_t total = off_ctrl + 256;
+    DeviceGuard g(ctx->device);
+    hx_batch *b = new (std::nothrow) hx_batch();
+    if (!b) return fail(HX_ERR_NOMEM, "hx_batch_plan: host allocation failed");
+    b->ctx = ctx;
+    b->rounds = rounds;
+    b->round_begin = round_begin;
+    cudaError_t e = cudaMalloc(&b->d_mem, total);
+    if (e != cudaSuccess) {
+        delete b;
+        return cuda_fail(e, "hx_batch_plan: cudaMalloc");
+    }
+    char *base = static_cast<char *>(b->d_mem);
+    b->d_insts = reinterpret_cast<BInst *>(base);
+    b->d_items = reinterpret_cast<unsigned long long *>(base + off_items);
+    b->d_ctrl = reinterpret_cast<unsigned int *>(base + off_ctrl);
+    int64_t pcur = 0, acur = 0;
+    for (int i = 0; i < n_tasks; ++i) {
+        BInst &I = insts[i];
+        I.ticket = reinterpret_cast<unsigned int *>(base + off_tick) + i;
+        if (I.kind == kKindMap) {
+            I.partials = reinterpret_cast<double *>(base + off_part) + pcur;
+            pcur += I.tiles;
+        } else if (I.kind == kKindStencil) {
+            I.acc = reinterpret_cast<unsigned int *>(base + off_acc) + acur;
+            acur += 1;
+        } else {
+            I.acc = reinterpret_cast<unsigned int *>(base + off_acc) + acur;
+            acur += kHiBins;
+        }
+    }
+    e = cudaMemset(b->d_mem, 0, total);
+    if (e == cudaSuccess && !insts.empty())
+        e = cudaMemcpy(b->d_insts, insts.data(), sizeof(BInst) * insts.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !items.empty())
+        e = cudaMemcpy(b->d_items, items.data(), sizeof(unsigned long long) * items.size(), cudaMemcpyHostToDevice);
+    int occ = 0;
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_kernel, kBatchThreads, 0);
+    if (e != cudaSuccess) {
+        cudaFree(b->d_mem);
+        delete b;
+        return cuda_fail(e, "hx_batch_plan: upload");
+    }
+    b->ctas_per_sm = occ > 0 ? occ : 1;
+    // Instances with no tiles still owe their outputs (n == 0 sums, empty
+    // histograms): write those directly now, they do not depend on inputs.
+    for (int i = 0; i < n_tasks; ++i) {
+        const hx_task &t = tasks[i];
+        if (t.kind == HX_TASK_MAP_REDUCE && t.u.mr.n == 0) {
+            const float z = 0.0f;
+            const double z64 = 0.0;
+            e = cudaMemcpy(t.u.mr.sum, &z, sizeof z, cudaMemcpyHostToDevice);
+            if (e == cudaSuccess && t.u.mr.sum64) e = cudaMemcpy(t.u.mr.sum64, &z64, sizeof z64, cudaMemcpyHostToDevice);
+        } else if (t.kind == HX_TASK_HISTOGRAM && t.u.hi.n == 0) {
+            e = cudaMemset(t.u.hi.bins, 0, 256 * sizeof(uint32_t));
+            if (e == cudaSuccess && t.u.hi.scan) e = cudaMemset(t.u.hi.scan, 0, 256 * sizeof(uint32_t));
+        }
+        if (e != cudaSuccess) {
+            cudaFree(b->d_mem);
+            delete b;
+            return cuda_fail(e, "hx_batch_plan: empty instance outputs");
+        }
+    }
+    *out = b;
+    if (out_rounds) *out_rounds = rounds;
+    return HX_OK;
+}
+
+extern "C" hx_status hx_batch_launch(hx_batch *b, hx_stream_t stream) {
+    using namespace hx;
+    if (!b) return fail(HX_ERR_INVALID, "hx_batch_launch: batch is NULL");
+    DeviceGuard g(b->ctx->device);
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    for (int r = 0; r < b->rounds; ++r) {
+        const uint32_t n_items = b->round_begin[r + 1] - b->round_begin[r];
+        if (n_items == 0) continue;
+        const int64_t cap = (int64_t)b->ctx->num_sms * b->ctas_per_sm;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)std::min<int64_t>(cap, n_items));
+        cfg.blockDim = dim3(kBatchThreads);
+        cfg.stream = (cudaStream_t)stream;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        cudaError_t e = cudaLaunchKernelEx(&cfg, batch_kernel, (const BInst *)b->d_insts,
+                                           (const unsigned long long *)(b->d_items + b->round_begin[r]), n_items, r,
+                                           b->d_ctrl);
+        if (e != cudaSuccess) return cuda_fail(e, "hx_batch_launch: launch");
+    }
+    return HX_OK;
+}
+
+extern "C" void hx_batch_free(hx_batch *b) {
+    if (!b) return;
+    hx::DeviceGuard g(b->ctx->device);
+    if (b->d_mem) cudaFree(b->d_mem);
+    delete b;
+}
+
+extern "C" hx_status hx_batch_submit(hx_ctx *ctx, const hx_task *tasks, int32_t n_tasks, hx_stream_t stream,
+                                     uint64_t *ticket_out) {
+    using namespace hx;
+    if (!ctx || !ticket_out) return fail(HX_ERR_INVALID, "hx_batch_submit: ctx or ticket_out is NULL");
+    hx_batch *b = nullptr;
+    hx_status st = hx_batch_plan(ctx, tasks, n_tasks, &b, nullptr);
+    if (st != HX_OK) return st;
+    st = hx_batch_launch(b, stream);
+    if (st != HX_OK) {
+        cudaStreamSynchronize((cudaStream_t)stream);
+        hx_batch_free(b);
+        return st;
+    }
+    DeviceGuard g(ctx->device);
+    cudaEvent_t ev;
+    cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(ev, (cudaStream_t)stream);
+    if (e != cudaSuccess) {
+        cudaStreamSynchronize((cudaStream_t)stream);
+        hx_batch_free(b);
+        return cuda_fail(e, "hx_batch_submit: completion event");
+    }
+    const uint64_t ticket = ctx->next_ticket++;
+    ctx->pending[ticket] = {b, ev};
+    *ticket_out = ticket;
+    return HX_OK;
+}
+
+extern "C" hx_status hx_batch_query(hx_ctx *ctx, uint64_t ticket) {
+    using namespace hx;
+    if (!ctx) return fail(HX_ERR_INVALID, "hx_batch_query: ctx is NULL");
+    auto it = ctx->pending.find(ticket);
+    if (it == ctx->pending.end()) return fail(HX_ERR_INVALID, "hx_batch_query: unknown ticket");
+    DeviceGuard g(ctx->device);
+    cudaError_t e = cudaEventQuery(it->second.second);
+    if (e == cudaErrorNotReady) return HX_ERR_BUSY;
+    cudaEventDestroy(it->second.second);
+    hx_batch_free(it->second.first);
+    ctx->pending.erase(it);
+    if (e != cudaSuccess) return cuda_fail(e, "hx_batch_query: device work failed");
+    return HX_OK;
+}

@@ -86,6 +86,14 @@ hx_status hx_create(hx_ctx **out, int device, size_t hbm_budget_bytes) {
 void hx_destroy(hx_ctx *ctx) {
     if (!ctx) return;
     hx::DeviceGuard g(ctx->device);
+    if (!ctx->pending.empty()) {
+        cudaDeviceSynchronize();
+        for (auto &kv : ctx->pending) {
+            cudaEventDestroy(kv.second.second);
+            hx_batch_free(kv.second.first);
+        }
+        ctx->pending.clear();
+    }
     if (ctx->ws) cudaFree(ctx->ws);
     delete ctx;
 }

@@ -21,32 +21,13 @@ histogram_kernel(const uint8_t *__restrict__ v, int64_t n, int head, int64_t nve
     for (int i = threadIdx.x; i < kHiBins * kWarp; i += blockDim.x) sh[i] = 0u;
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    unsigned int *sh_lane = sh + lane;
+    const uint32_t base_lane = smem_addr(sh) + 4u * lane;
     const uint4 *v4 = reinterpret_cast<const uint4 *>(v + head);
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    for (; i + stride < nvec; i += 2 * stride) {
-        const uint4 w0 = ld_stream_u4(v4 + i);
-        const uint4 w1 = ld_stream_u4(v4 + i + stride);
-        hist_count_word(sh_lane, w0.x);
-        hist_count_word(sh_lane, w0.y);
-        hist_count_word(sh_lane, w0.z);
-        hist_count_word(sh_lane, w0.w);
-        hist_count_word(sh_lane, w1.x);
-        hist_count_word(sh_lane, w1.y);
-        hist_count_word(sh_lane, w1.z);
-        hist_count_word(sh_lane, w1.w);
-    }
-    if (i < nvec) {
-        const uint4 w0 = ld_stream_u4(v4 + i);
-        hist_count_word(sh_lane, w0.x);
-        hist_count_word(sh_lane, w0.y);
-        hist_count_word(sh_lane, w0.z);
-        hist_count_word(sh_lane, w0.w);
-    }
+    hist_count_strided(base_lane, v4, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
+                       (int64_t)gridDim.x * blockDim.x, nvec);
     if (blockIdx.x == 0) {   // unaligned head and ragged tail bytes
-        if (threadIdx.x < head) atomicAdd(sh_lane + (unsigned int)v[threadIdx.x] * kWarp, 1u);
-        if (threadIdx.x < tail) atomicAdd(sh_lane + (unsigned int)v[n - tail + threadIdx.x] * kWarp, 1u);
+        if (threadIdx.x < head) hist_count_byte(base_lane, v[threadIdx.x]);
+        if (threadIdx.x < tail) hist_count_byte(base_lane, v[n - tail + threadIdx.x]);
     }
     __syncthreads();
     for (int b = threadIdx.x; b < kHiBins; b += blockDim.x) {
@@ -55,7 +36,7 @@ histogram_kernel(const uint8_t *__restrict__ v, int64_t n, int head, int64_t nve
         for (int k = 0; k < kWarp; ++k) s += sh[b * kWarp + ((k + b) & 31)];
         if (s) atomicAdd(&ws->hi_bins[b], s);
     }
-    __threadfence();
+    if (threadIdx.x < kHiBins) __threadfence();   // only these threads wrote bins
     __syncthreads();
     if (threadIdx.x == 0) is_last = atomicAdd(&ws->hi_ticket, 1u) == gridDim.x - 1;
     __syncthreads();

@@ -8,8 +8,10 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include <mutex>
+#include <cstdio>
+#include <map>
 #include <string>
+#include <utility>
 
 #include "../../include/hx.h"
 
@@ -27,8 +29,8 @@ constexpr int kMrUnroll = 4;         // loads in flight per operand per thread
 constexpr int kMrMaxTiles = 2048;    // tile partials per instance (workspace)
 constexpr int kFinalThreads = 256;   // CTA width of every final combine
 
-// stencil: one warp walks a strip of columns down kStRows rows.
-constexpr int kStRows = 16;
+// stencil: one warp owns a block of kStRows rows x (128 | 32) columns.
+constexpr int kStRows = 8;
 constexpr int kStWarps = 4;          // warps per CTA, stacked vertically
 
 // histogram: lane-replicated shared bins, 256 bins x 32 lanes of uint32.
@@ -205,87 +207,161 @@ __device__ __forceinline__ float jacobi_point(float n, float s, float w, float e
     return 0.25f * (ns + we);
 }
 
-// One warp updates columns [c_begin, c_begin + 128) (vector path, nx % 4 == 0
-// and 16-byte aligned rows) of rows [r_begin, r_end).  Returns the lane's
-// max |u' - u| over the points it wrote.
-__device__ __forceinline__ float stencil_strip_vec(const float *__restrict__ src, float *__restrict__ dst,
-                                                   int nx, int ny, int c_begin, int r_begin, int r_end) {
+// One warp updates a block of R rows [r_begin, r_begin + R) x 128 columns
+// [c_begin, c_begin + 128) (vector path: nx % 4 == 0 and 16-byte aligned
+// rows; each lane owns 4 consecutive columns).  All R + 2 input rows and the
+// two halo columns are loaded before any arithmetic, so a warp has its whole
+// block in flight at once; vertical neighbours come from registers and
+// horizontal ones from the neighbouring lanes.  Rows past ny are clamped on
+// load and not stored.  Returns the lane's max |u' - u|.
+template <int R>
+__device__ __forceinline__ float stencil_block_vec(const float *__restrict__ src, float *__restrict__ dst,
+                                                   int nx, int ny, int c_begin, int r_begin) {
     const int lane = threadIdx.x & 31;
     const int c0 = c_begin + lane * 4;
     const bool valid = c0 < nx;
     const int cl = valid ? c0 : 0;   // keep inactive lanes' loads in bounds
+    float4 rows[R + 2];
+#pragma unroll
+    for (int k = 0; k < R + 2; ++k) {
+        const int r = clampi(r_begin - 1 + k, 0, ny - 1);
+        rows[k] = __ldg(reinterpret_cast<const float4 *>(src + (size_t)r * nx + cl));
+    }
+    // halo columns: lane 0 needs column c0 - 1, lane 31 column c0 + 4
+    const bool need_left = (lane == 0) && valid && c0 > 0;
+    const bool need_right = (lane == 31) && (c0 + 4 < nx);
+    const int hc = need_left ? c0 - 1 : (need_right ? c0 + 4 : 0);
+    float halo[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+        const int r = min(r_begin + k, ny - 1);
+        halo[k] = (need_left || need_right) ? __ldg(src + (size_t)r * nx + hc) : 0.0f;
+    }
     float m = 0.0f;
-    auto row4 = [&](int r) -> float4 {
-        return *reinterpret_cast<const float4 *>(src + (size_t)r * nx + cl);
-    };
-    float4 prev = row4(clampi(r_begin - 1, 0, ny - 1));
-    float4 cur = row4(r_begin);
-    for (int r = r_begin; r < r_end; ++r) {
-        const float4 next = row4(clampi(r + 1, 0, ny - 1));
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+        const float4 up = rows[k], cur = rows[k + 1], dn = rows[k + 2];
         float left = __shfl_up_sync(0xffffffffu, cur.w, 1);
         float right = __shfl_down_sync(0xffffffffu, cur.x, 1);
-        if (lane == 0) left = (c0 == 0 || !valid) ? cur.x : src[(size_t)r * nx + c0 - 1];
+        if (lane == 0) left = need_left ? halo[k] : cur.x;
         if (c0 + 4 >= nx) right = cur.w;
-        else if (lane == 31) right = src[(size_t)r * nx + c0 + 4];
+        else if (lane == 31) right = halo[k];
         float4 o;
-        o.x = jacobi_point(prev.x, next.x, left, cur.y);
-        o.y = jacobi_point(prev.y, next.y, cur.x, cur.z);
-        o.z = jacobi_point(prev.z, next.z, cur.y, cur.w);
-        o.w = jacobi_point(prev.w, next.w, cur.z, right);
-        if (valid) {
+        o.x = jacobi_point(up.x, dn.x, left, cur.y);
+        o.y = jacobi_point(up.y, dn.y, cur.x, cur.z);
+        o.z = jacobi_point(up.z, dn.z, cur.y, cur.w);
+        o.w = jacobi_point(up.w, dn.w, cur.z, right);
+        const int r = r_begin + k;
+        if (valid && r < ny) {
             *reinterpret_cast<float4 *>(dst + (size_t)r * nx + c0) = o;
             m = fmaxf(m, fmaxf(fmaxf(fabsf(o.x - cur.x), fabsf(o.y - cur.y)),
                                fmaxf(fabsf(o.z - cur.z), fabsf(o.w - cur.w))));
         }
-        prev = cur;
-        cur = next;
     }
     return m;
 }
 
 // Element path for any nx and alignment: one column per lane, 32 columns per
-// warp, same arithmetic per point.
-__device__ __forceinline__ float stencil_strip_scalar(const float *__restrict__ src, float *__restrict__ dst,
-                                                      int nx, int ny, int c_begin, int r_begin, int r_end) {
+// warp, the same loads-first structure and the same arithmetic per point.
+template <int R>
+__device__ __forceinline__ float stencil_block_scalar(const float *__restrict__ src, float *__restrict__ dst,
+                                                      int nx, int ny, int c_begin, int r_begin) {
     const int lane = threadIdx.x & 31;
     const int c = c_begin + lane;
     const bool valid = c < nx;
     const int cl = valid ? c : nx - 1;
+    float rows[R + 2];
+#pragma unroll
+    for (int k = 0; k < R + 2; ++k) {
+        const int r = clampi(r_begin - 1 + k, 0, ny - 1);
+        rows[k] = __ldg(src + (size_t)r * nx + cl);
+    }
+    const bool need_left = (lane == 0) && valid && c > 0;
+    const bool need_right = (lane == 31) && (c + 1 < nx);
+    const int hc = need_left ? c - 1 : (need_right ? c + 1 : 0);
+    float halo[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+        const int r = min(r_begin + k, ny - 1);
+        halo[k] = (need_left || need_right) ? __ldg(src + (size_t)r * nx + hc) : 0.0f;
+    }
     float m = 0.0f;
-    float prev = src[(size_t)clampi(r_begin - 1, 0, ny - 1) * nx + cl];
-    float cur = src[(size_t)r_begin * nx + cl];
-    for (int r = r_begin; r < r_end; ++r) {
-        const float next = src[(size_t)clampi(r + 1, 0, ny - 1) * nx + cl];
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+        const float cur = rows[k + 1];
         float left = __shfl_up_sync(0xffffffffu, cur, 1);
         float right = __shfl_down_sync(0xffffffffu, cur, 1);
-        if (lane == 0) left = (c == 0) ? cur : src[(size_t)r * nx + clampi(c - 1, 0, nx - 1)];
+        if (lane == 0) left = need_left ? halo[k] : cur;
         if (c + 1 >= nx) right = cur;
-        else if (lane == 31) right = src[(size_t)r * nx + c + 1];
-        const float o = jacobi_point(prev, next, left, right);
-        if (valid) {
+        else if (lane == 31) right = halo[k];
+        const float o = jacobi_point(rows[k], rows[k + 2], left, right);
+        const int r = r_begin + k;
+        if (valid && r < ny) {
             dst[(size_t)r * nx + c] = o;
             m = fmaxf(m, fabsf(o - cur));
         }
-        prev = cur;
-        cur = next;
     }
     return m;
 }
 
 // ---------------------------------------------------------------- histogram
 // Shared bins are laid out [bin][lane]: lane l only touches column l, so one
-// warp-wide atomic never has two lanes in the same bank.
-__device__ __forceinline__ void hist_count_word(unsigned int *sh_lane, unsigned int w) {
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const unsigned int b = (w >> (8 * k)) & 0xffu;
-        atomicAdd(sh_lane + b * kWarp, 1u);
+// warp-wide increment never has two lanes in the same bank, whatever the
+// data.  base_lane is the 32-bit shared address of column `lane` of bin 0;
+// bin b of that column is at base_lane + 128 b.  One byte costs a byte
+// extract (prmt), an address (lea) and a reduction (red.shared).
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void red_shared_inc(uint32_t addr) {
+    asm volatile("red.shared.add.u32 [%0], 1;" ::"r"(addr) : "memory");
+}
+__device__ __forceinline__ void hist_count_word(uint32_t base_lane, unsigned int w) {
+    red_shared_inc(base_lane + (__byte_perm(w, 0u, 0x4440u) << 7));
+    red_shared_inc(base_lane + (__byte_perm(w, 0u, 0x4441u) << 7));
+    red_shared_inc(base_lane + (__byte_perm(w, 0u, 0x4442u) << 7));
+    red_shared_inc(base_lane + ((w >> 24) << 7));
+}
+__device__ __forceinline__ void hist_count_vec(uint32_t base_lane, const uint4 &w) {
+    hist_count_word(base_lane, w.x);
+    hist_count_word(base_lane, w.y);
+    hist_count_word(base_lane, w.z);
+    hist_count_word(base_lane, w.w);
+}
+__device__ __forceinline__ void hist_count_byte(uint32_t base_lane, unsigned int b) {
+    red_shared_inc(base_lane + (b << 7));
+}
+
+// Count the 16-byte vectors v4[first], v4[first + stride], ... below nvec into
+// the shared bins, keeping the next two vectors' loads in flight while the
+// current two are counted.
+__device__ __forceinline__ void hist_count_strided(uint32_t base_lane, const uint4 *__restrict__ v4,
+                                                   int64_t first, int64_t stride, int64_t nvec) {
+    int64_t i = first;
+    bool h0 = i < nvec, h1 = i + stride < nvec;
+    uint4 a0 = make_uint4(0, 0, 0, 0), a1 = a0;
+    if (h0) a0 = ld_stream_u4(v4 + i);
+    if (h1) a1 = ld_stream_u4(v4 + i + stride);
+    while (h0) {
+        const int64_t j = i + 2 * stride;
+        const bool g0 = j < nvec, g1 = j + stride < nvec;
+        uint4 b0 = make_uint4(0, 0, 0, 0), b1 = b0;
+        if (g0) b0 = ld_stream_u4(v4 + j);
+        if (g1) b1 = ld_stream_u4(v4 + j + stride);
+        hist_count_vec(base_lane, a0);
+        if (h1) hist_count_vec(base_lane, a1);
+        a0 = b0;
+        a1 = b1;
+        h0 = g0;
+        h1 = g1;
+        i = j;
     }
 }
 
 // ---------------------------------------------------------------- host side
-struct Ctx;
 }  // namespace hx
+
+extern "C" void hx_batch_free(hx_batch *batch);
 
 struct hx_ctx {
     int device = 0;
@@ -294,6 +370,9 @@ struct hx_ctx {
     hx::WsSlot *ws = nullptr;   // HX_MAX_STREAMS slots
     hx_stream_t slot_stream[HX_MAX_STREAMS] = {};
     bool slot_used[HX_MAX_STREAMS] = {};
+    // hx_batch_submit bookkeeping: ticket -> (plan, completion event)
+    uint64_t next_ticket = 1;
+    std::map<uint64_t, std::pair<hx_batch *, cudaEvent_t>> pending;
 };
 
 namespace hx {

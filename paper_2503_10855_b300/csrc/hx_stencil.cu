@@ -25,11 +25,10 @@ stencil_kernel(const float *__restrict__ src, float *__restrict__ dst, int nx, i
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int c_begin = blockIdx.x * (vec ? 128 : 32);
     const int r_begin = (blockIdx.y * kStWarps + warp) * kStRows;
-    const int r_end = min(r_begin + kStRows, ny);
     float m = 0.0f;
     if (r_begin < ny) {
-        m = vec ? stencil_strip_vec(src, dst, nx, ny, c_begin, r_begin, r_end)
-                : stencil_strip_scalar(src, dst, nx, ny, c_begin, r_begin, r_end);
+        m = vec ? stencil_block_vec<kStRows>(src, dst, nx, ny, c_begin, r_begin)
+                : stencil_block_scalar<kStRows>(src, dst, nx, ny, c_begin, r_begin);
     }
     m = warp_max(m);
     if (lane == 0) wmax[warp] = m;

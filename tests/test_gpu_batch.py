@@ -1,0 +1,218 @@
+"""Batched persistent launch: every instance bit-identical to its standalone
+call, and matching the oracle (tolerances as in test_gpu_parity)."""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def ctx(gpu):
+    c = gpu.hx_create(0)
+    yield c
+    c.close()
+
+
+class Inst:
+    """Device buffers of one instance, built from its seed."""
+
+    def __init__(self, spec, offset=0):
+        self.spec = spec
+        k = spec["kind"]
+        if k == "map_reduce":
+            n = spec["n"]
+            self.x = torch.empty(n + offset, device=DEV)[offset:]
+            self.y = torch.empty(n + offset, device=DEV)[offset:]
+            self.x.copy_(workloads.uniform_pm1_f32_torch(spec["seed"], n, DEV, 2, 0))
+            self.y.copy_(workloads.uniform_pm1_f32_torch(spec["seed"], n, DEV, 2, 1))
+            self.out = torch.full((n,), float("nan"), device=DEV)
+            self.s32 = torch.full((1,), float("nan"), device=DEV)
+            self.s64 = torch.full((1,), float("nan"), dtype=torch.float64, device=DEV)
+        elif k == "stencil":
+            ny, nx = spec["ny"], spec["nx"]
+            base = torch.empty(ny * nx + offset, device=DEV)
+            base[offset:] = workloads.uniform01_f32_torch(spec["seed"], ny * nx, DEV)
+            self.u0 = base[offset:].view(ny, nx)
+            self.u_init = self.u0.clone()
+            self.u1 = torch.full((ny, nx), float("nan"), device=DEV)
+            self.res = torch.full((max(1, spec["iters"]),), -1.0, device=DEV)
+        else:
+            n = spec["n"]
+            vb = torch.empty(n + offset, dtype=torch.uint8, device=DEV)
+            vb[offset:] = torch.from_numpy(workloads.histogram_mixture_u8(n, seed=spec["seed"] & 0xFFFF)).to(DEV)
+            self.v = vb[offset:]
+            self.bins = torch.full((256,), -1, dtype=torch.int32, device=DEV)
+            self.scan = torch.full((256,), -1, dtype=torch.int32, device=DEV)
+
+    def task(self, hx):
+        k = self.spec["kind"]
+        if k == "map_reduce":
+            return hx.map_reduce_task(self.x, self.y, self.spec["a"], self.s32, out=self.out, sum64_out=self.s64)
+        if k == "stencil":
+            return hx.stencil_task(self.u0, self.u1, self.spec["iters"], self.res)
+        return hx.histogram_task(self.v, self.bins, self.scan)
+
+    def result(self):
+        k = self.spec["kind"]
+        if k == "map_reduce":
+            return (self.out.cpu().numpy(), float(self.s32.item()), float(self.s64.item()))
+        if k == "stencil":
+            it = self.spec["iters"]
+            fin = self.u1 if it % 2 == 1 else self.u0
+            return (fin.cpu().numpy(), self.res.cpu().numpy()[:it])
+        return (self.bins.cpu().numpy().view(np.uint32), self.scan.cpu().numpy().view(np.uint32))
+
+    def standalone(self, hx, ctx):
+        """The same instance through the standalone call, on fresh buffers."""
+        k = self.spec["kind"]
+        if k == "map_reduce":
+            out = torch.empty_like(self.out)
+            _, s32, s64 = hx.hx_map_reduce(ctx, self.x, self.y, self.spec["a"], out=out,
+                                           sum64_out=torch.empty(1, dtype=torch.float64, device=DEV))
+            torch.cuda.synchronize()
+            return (out.cpu().numpy(), float(s32.item()), float(s64.item()))
+        if k == "stencil":
+            a, b = self.u_init.clone(), torch.empty_like(self.u_init)
+            fin, res = hx.hx_stencil2d(ctx, a, b, self.spec["iters"])
+            torch.cuda.synchronize()
+            return (fin.cpu().numpy(), res.cpu().numpy()[:self.spec["iters"]])
+        bins, scan = hx.hx_histogram(ctx, self.v)
+        torch.cuda.synchronize()
+        return (bins.cpu().numpy().view(np.uint32), scan.cpu().numpy().view(np.uint32))
+
+    def check_oracle(self, res):
+        k = self.spec["kind"]
+        if k == "map_reduce":
+            out, s32, s64 = res
+            x, y = self.x.cpu().numpy(), self.y.cpu().numpy()
+            out_o, s_o = oracle.map_reduce(x, y, self.spec["a"])
+            assert np.array_equal(out, out_o.astype(np.float32))
+            assert abs(s64 - s_o) <= 1e-5 * np.abs(out_o).sum()
+            assert np.float32(s64) == np.float32(s32)
+        elif k == "stencil":
+            fin, r = res
+            u32, r32 = oracle.jacobi(self.u_init.cpu().numpy(), self.spec["iters"], "f32")
+            assert np.array_equal(fin.view(np.uint32), u32.view(np.uint32))
+            assert np.array_equal(r.view(np.uint32), r32.view(np.uint32))
+        else:
+            bins, scan = res
+            b_o, s_o = oracle.histogram(self.v.cpu().numpy())
+            assert np.array_equal(bins, b_o) and np.array_equal(scan, s_o)
+
+
+def _same(a, b):
+    for u, v in zip(a, b):
+        if isinstance(u, np.ndarray):
+            assert np.array_equal(u.view(np.uint8), v.view(np.uint8))
+        else:
+            assert u == v or (u != u and v != v)
+
+
+def _run(gpu, insts, ctx):
+    b = gpu.hx_batch_plan(ctx, [i.task(gpu) for i in insts])
+    b.launch()
+    torch.cuda.synchronize()
+    return b
+
+
+@pytest.mark.slow
+def test_standard_batch_alone_equals_mix_and_oracle(gpu, ctx):
+    insts = [Inst(s) for s in workloads.batch_mix()]
+    b = _run(gpu, insts, ctx)
+    assert b.rounds == 1
+    for inst in insts:
+        r = inst.result()
+        _same(r, inst.standalone(gpu, ctx))
+        inst.check_oracle(r)
+    b.close()
+
+
+def _mixed_specs():
+    specs = [
+        {"kind": "map_reduce", "n": 1, "a": 1.5, "seed": 1},
+        {"kind": "map_reduce", "n": 4097, "a": -0.75, "seed": 2},
+        {"kind": "map_reduce", "n": 3_000_001, "a": 1.5, "seed": 3},
+        {"kind": "map_reduce", "n": (1 << 23) + 9, "a": 1.5, "seed": 4},
+        {"kind": "stencil", "nx": 1, "ny": 1, "iters": 3, "seed": 5},
+        {"kind": "stencil", "nx": 33, "ny": 70, "iters": 5, "seed": 6},
+        {"kind": "stencil", "nx": 256, "ny": 129, "iters": 2, "seed": 7},
+        {"kind": "stencil", "nx": 1000, "ny": 3, "iters": 1, "seed": 8},
+        {"kind": "histogram", "n": 17, "seed": 9},
+        {"kind": "histogram", "n": (1 << 20) + 5, "seed": 10},
+        {"kind": "histogram", "n": 300_000, "seed": 11},
+    ]
+    return specs
+
+
+@pytest.mark.parametrize("offset", [0, 1])
+def test_mixed_batch_with_rounds(gpu, ctx, offset):
+    insts = [Inst(s, offset) for s in _mixed_specs()]
+    b = _run(gpu, insts, ctx)
+    assert b.rounds == 5
+    for inst in insts:
+        r = inst.result()
+        _same(r, inst.standalone(gpu, ctx))
+        inst.check_oracle(r)
+    b.close()
+
+
+def test_batch_empty_instances(gpu, ctx):
+    specs = [{"kind": "map_reduce", "n": 0, "a": 1.5, "seed": 1},
+             {"kind": "histogram", "n": 0, "seed": 2},
+             {"kind": "stencil", "nx": 4, "ny": 4, "iters": 0, "seed": 3}]
+    insts = [Inst(s) for s in specs]
+    b = _run(gpu, insts, ctx)
+    assert insts[0].s32.item() == 0.0 and insts[0].s64.item() == 0.0
+    assert not insts[1].bins.any() and not insts[1].scan.any()
+    assert torch.equal(insts[2].u0, insts[2].u_init)
+    b.close()
+    assert gpu.hx_batch_plan(ctx, []).rounds == 0
+
+
+def test_batch_relaunch_and_graph_replay(gpu, ctx):
+    specs = [{"kind": "map_reduce", "n": 200_003, "a": 1.5, "seed": 21},
+             {"kind": "stencil", "nx": 300, "ny": 200, "iters": 1, "seed": 22},
+             {"kind": "histogram", "n": 500_001, "seed": 23}]
+    insts = [Inst(s) for s in specs]
+    b = _run(gpu, insts, ctx)
+    first = [i.result() for i in insts]
+    b.launch()
+    torch.cuda.synchronize()
+    for i, f in zip(insts, first):
+        _same(i.result(), f)
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        b.launch(stream=s)
+    for _ in range(3):
+        g.replay()
+    torch.cuda.synchronize()
+    for i, f in zip(insts, first):
+        _same(i.result(), f)
+        i.check_oracle(i.result())
+    b.close()
+
+
+def test_batch_submit_and_query(gpu, ctx):
+    insts = [Inst(s) for s in _mixed_specs()[:3]]
+    t = gpu.hx_batch_submit(ctx, [i.task(gpu) for i in insts])
+    torch.cuda.synchronize()
+    assert gpu.hx_batch_query(ctx, t) is True
+    with pytest.raises(gpu.HxError):
+        gpu.hx_batch_query(ctx, t)           # retired
+    for inst in insts:
+        inst.check_oracle(inst.result())
+
+
+def test_batch_rejects_bad_task(gpu, ctx):
+    x = torch.zeros(8, device=DEV)
+    bad = gpu.stencil_task(x.view(2, 4), x.view(2, 4), 1, torch.zeros(1, device=DEV))
+    with pytest.raises(gpu.HxError):
+        gpu.hx_batch_plan(ctx, [bad])
