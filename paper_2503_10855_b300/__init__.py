@@ -18,7 +18,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "lib", "libhx.so")
 
 if not os.path.exists(LIB_PATH):
-    raise ImportError(f"libhx.so is not built ({LIB_PATH}); run `python -m paper_2503_10855_b300._build`")
+    raise ImportError(f"libhx.so is not built ({LIB_PATH}); run `python paper_2503_10855_b300/_build.py`")
 
 _lib = ctypes.CDLL(LIB_PATH)
 

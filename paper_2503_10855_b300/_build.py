@@ -1,6 +1,7 @@
 """Build libhx.so (the C-ABI CUDA library) in-tree for sm_103a.
 
-Usage: ``python -m paper_2503_10855_b300._build [--force]``.  Each ``.cu`` /
+Usage: ``python paper_2503_10855_b300/_build.py [--force] [-v]`` (run it as a
+file: importing the package requires the library this script builds).  Each ``.cu`` /
 ``.cpp`` file under ``csrc/`` is compiled separately (in parallel) with nvcc
 and linked into ``paper_2503_10855_b300/lib/libhx.so`` with the CUDA runtime
 linked statically, so the library needs only the NVIDIA driver at run time.

@@ -4,10 +4,13 @@
 // parallel fork-joins as concurrent tasks (Sec. 4.5; the AsyncCall attribute
 // of Sec. 3.4).  On one GPU that becomes a device work-list: every instance
 // is cut into the same tiles its standalone call would use, the tiles of all
-// instances are listed as (instance, tile) items, and resident CTAs pull
-// items from an atomic counter until the list is empty.  Per-instance arrival
-// tickets let the last tile of an instance run its final combine, so no CTA
-// ever waits for another.  A stencil instance with several sweeps contributes
+// instances are listed as work items, and resident workers take them in a
+// fixed round-robin order.  Map->reduce tiles and stencil blocks form WARP
+// runs (a warp computes and reduces a run of consecutive tiles of one
+// instance on its own, with no block barrier); histogram chunks are CTA items
+// (the CTA's warps share one set of shared-memory bins) and run first.
+// Per-instance arrival tickets let the last run of an instance do its final
+// combine, so no worker ever waits for another.  A stencil instance with several sweeps contributes
 // one sweep per round; rounds are consecutive launches chained with
 // programmatic dependent launch.
 #include <algorithm>
@@ -21,13 +24,12 @@ namespace hx {
 
 enum : int { kKindMap = 0, kKindStencil = 1, kKindHist = 2 };
 
-constexpr int kBatchThreads = 256;                         // == kMrThreads == kFinalThreads
-constexpr int kBStWarps = kBatchThreads / kWarp;           // stencil warps per item
-constexpr int kBStTileRows = kBStWarps * kStRows;          // rows per stencil item
+constexpr int kBatchThreads = 256;                               // 8 warps
 constexpr int64_t kBHiTile = (int64_t)kBatchThreads * 16 * 32;   // 128 KiB per histogram item
 constexpr int kMaxSweeps = 4096;
-static_assert(kBatchThreads == kMrThreads && kBatchThreads == kFinalThreads,
-              "batched map tiles must reproduce the standalone tile shape");
+static_assert(kBatchThreads == kHiBins, "the histogram finish maps one thread to one bin");
+constexpr int64_t kMapRun = 8;       // map tiles per warp run (48 KiB of traffic at the smallest tile)
+constexpr int64_t kStencilRun = 16;  // stencil blocks per warp run (64 rows of one column strip)
 
 struct BInst {
     int kind;
@@ -37,74 +39,18 @@ struct BInst {
     int iters;          // stencil sweeps
     int64_t n;
     int64_t tiles;      // items per round
-    int tiles_x;        // stencil tiles across
-    int pad;
+    int tiles_x;        // stencil warp blocks across
+    int tiles_y;        // stencil warp blocks down
     MrPlan plan;
     const void *in0;    // map x | stencil u0 | hist v
     const void *in1;    // map y | stencil u1
     void *o0;           // map out | stencil resid | hist bins
     void *o1;           // map sum | hist scan
     void *o2;           // map sum64
-    double *partials;   // map tile partials
+    float2 *partials;   // map tile partials (hi, lo)
     unsigned int *ticket;
     unsigned int *acc;  // stencil: max bits (1); hist: 256 bins
 };
-
-__device__ __forceinline__ void batch_map_item(const BInst &I, int64_t tile, double *red, int *flag) {
-    const MrPlan p = I.plan;
-    const float *x = static_cast<const float *>(I.in0);
-    const float *y = static_cast<const float *>(I.in1);
-    float *out = static_cast<float *>(I.o0);
-    const double part = mr_tile(x, y, out, I.a, p, tile, I.vec != 0, red);
-    if (threadIdx.x == 0) {
-        I.partials[tile] = part;
-        __threadfence();
-        *flag = atomicAdd(I.ticket, 1u) == (unsigned int)(p.tiles - 1);
-    }
-    __syncthreads();
-    if (*flag) {
-        __threadfence();
-        const double s = mr_final(I.partials, p.tiles, red);
-        if (threadIdx.x == 0) {
-            *static_cast<float *>(I.o1) = (float)s;
-            if (I.o2) *static_cast<double *>(I.o2) = s;
-            *I.ticket = 0u;
-        }
-    }
-    __syncthreads();
-}
-
-__device__ __forceinline__ void batch_stencil_item(const BInst &I, int64_t tile, int round, float *wmax,
-                                                   int *flag) {
-    const float *src = static_cast<const float *>((round & 1) ? I.in1 : I.in0);
-    float *dst = const_cast<float *>(static_cast<const float *>((round & 1) ? I.in0 : I.in1));
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int bx = (int)(tile % I.tiles_x), by = (int)(tile / I.tiles_x);
-    const int c_begin = bx * (I.vec ? 128 : 32);
-    const int r_begin = by * kBStTileRows + warp * kStRows;
-    float m = 0.0f;
-    if (r_begin < I.ny) {
-        m = I.vec ? stencil_block_vec<kStRows>(src, dst, I.nx, I.ny, c_begin, r_begin)
-                  : stencil_block_scalar<kStRows>(src, dst, I.nx, I.ny, c_begin, r_begin);
-    }
-    m = warp_max(m);
-    if (lane == 0) wmax[warp] = m;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        float bm = wmax[0];
-        for (int w = 1; w < kBStWarps; ++w) bm = fmaxf(bm, wmax[w]);
-        atomicMax(I.acc, __float_as_uint(bm));
-        __threadfence();
-        if (atomicAdd(I.ticket, 1u) == (unsigned int)(I.tiles - 1)) {
-            __threadfence();
-            const unsigned int bits = atomicExch(I.acc, 0u);
-            static_cast<float *>(I.o0)[round] = __uint_as_float(bits);
-            *I.ticket = 0u;
-        }
-    }
-    __syncthreads();
-    (void)flag;
-}
 
 __device__ __forceinline__ void batch_hist_item(const BInst &I, int64_t tile, unsigned int *sh,
                                                 unsigned int *wtot, int *flag) {
@@ -154,39 +100,89 @@ __device__ __forceinline__ void batch_hist_item(const BInst &I, int64_t tile, un
     __syncthreads();
 }
 
-// ctrl[0]: next item of this round; ctrl[1]: CTAs that have left the loop.
-__global__ void __launch_bounds__(kBatchThreads)
-batch_kernel(const BInst *__restrict__ insts, const unsigned long long *__restrict__ items,
-             unsigned int n_items, int round, unsigned int *ctrl) {
+// The arrival ticket of a warp run is resolved one run later (or after the
+// warp's last run), so the atomic's round trip overlaps useful work.  The
+// warp whose run completes an instance runs the instance's final combine.
+__device__ __forceinline__ void batch_resolve(const BInst *__restrict__ insts, unsigned int inst,
+                                              unsigned int prev, unsigned int cnt, int round, int lane) {
+    prev = __shfl_sync(0xffffffffu, prev, 0);
+    const BInst &I = insts[inst];
+    if ((int64_t)prev + cnt != I.tiles) return;
+    __threadfence();
+    if (I.kind == kKindMap) {
+        const ff sf = mr_final(I.partials, I.plan.tiles, lane);
+        if (lane == 0) {
+            const double s = ff_to_double(sf);
+            *static_cast<float *>(I.o1) = (float)s;
+            if (I.o2) *static_cast<double *>(I.o2) = s;
+            *I.ticket = 0u;
+        }
+    } else if (lane == 0) {
+        static_cast<float *>(I.o0)[round] = __uint_as_float(atomicExch(I.acc, 0u));
+        *I.ticket = 0u;
+    }
+}
+
+// Phase 1 runs the CTA items (histogram chunks, CTA c takes items c, c + G,
+// ...); phase 2 the warp runs (warp w takes runs w, w + W, ...).  The static
+// assignment needs no shared counter; runs are small and uniform enough for
+// round-robin to balance.  A warp run is {instance, first tile, tile count};
+// it publishes once: one fence and one ticket increment by the run length.
+__global__ void __launch_bounds__(kBatchThreads, 4)
+batch_kernel(const BInst *__restrict__ insts, const unsigned long long *__restrict__ cta_items,
+             unsigned int n_cta, const uint4 *__restrict__ warp_runs, unsigned int n_runs, int round) {
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;");
     __shared__ unsigned int sh[kHiBins * kWarp];
-    __shared__ double red[32];
-    __shared__ float wmax[kBStWarps];
-    __shared__ unsigned int wtot[kBStWarps];
-    __shared__ unsigned int s_item;
+    __shared__ unsigned int wtot[kBatchThreads / kWarp];
     __shared__ int s_flag;
-    for (;;) {
-        if (threadIdx.x == 0) s_item = atomicAdd(&ctrl[0], 1u);
-        __syncthreads();
-        const unsigned int it = s_item;
-        __syncthreads();
-        if (it >= n_items) break;
-        const unsigned long long item = items[it];
-        const BInst &I = insts[item >> 32];
-        const int64_t tile = (int64_t)(item & 0xffffffffull);
-        const int kind = I.kind;
-        if (kind == kKindMap) batch_map_item(I, tile, red, &s_flag);
-        else if (kind == kKindStencil) batch_stencil_item(I, tile, round, wmax, &s_flag);
-        else batch_hist_item(I, tile, sh, wtot, &s_flag);
+    const int lane = threadIdx.x & 31;
+
+    for (unsigned int it = blockIdx.x; it < n_cta; it += gridDim.x) {
+        const unsigned long long item = cta_items[it];
+        batch_hist_item(insts[item >> 32], (int64_t)(item & 0xffffffffull), sh, wtot, &s_flag);
     }
-    if (threadIdx.x == 0) {
-        __threadfence();
-        if (atomicAdd(&ctrl[1], 1u) == gridDim.x - 1) {
-            ctrl[0] = 0u;
-            ctrl[1] = 0u;
+
+    constexpr unsigned int kWarpsPerCta = kBatchThreads / kWarp;
+    const unsigned int nw = gridDim.x * kWarpsPerCta;
+    unsigned int pend_inst = 0xffffffffu, pend_prev = 0u, pend_cnt = 0u;
+    for (unsigned int it = blockIdx.x * kWarpsPerCta + (threadIdx.x >> 5); it < n_runs; it += nw) {
+        const uint4 run = warp_runs[it];
+        const BInst &I = insts[run.x];
+        if (I.kind == kKindMap) {
+            const float *x = static_cast<const float *>(I.in0);
+            const float *y = static_cast<const float *>(I.in1);
+            float *out = static_cast<float *>(I.o0);
+            for (unsigned int k = 0; k < run.z; ++k) {
+                const int64_t tile = (int64_t)run.y + k;
+                const ff part = mr_tile(x, y, out, I.a, I.plan, tile, I.vec != 0, lane);
+                if (lane == 0) I.partials[tile] = make_float2(part.hi, part.lo);
+            }
+        } else {
+            const float *src = static_cast<const float *>((round & 1) ? I.in1 : I.in0);
+            float *dst = const_cast<float *>(static_cast<const float *>((round & 1) ? I.in0 : I.in1));
+            float m = 0.0f;
+            for (unsigned int k = 0; k < run.z; ++k) {
+                const unsigned int tile = run.y + k;
+                const int wy = (int)(tile % (unsigned int)I.tiles_y), wx = (int)(tile / (unsigned int)I.tiles_y);
+                const int c_begin = wx * (I.vec ? 128 : 32), r_begin = wy * kBatchStRows;
+                m = fmaxf(m, I.vec ? stencil_block_vec<kBatchStRows>(src, dst, I.nx, I.ny, c_begin, r_begin)
+                                   : stencil_block_scalar<kBatchStRows>(src, dst, I.nx, I.ny, c_begin, r_begin));
+            }
+            m = warp_max(m);
+            if (lane == 0) atomicMax(I.acc, __float_as_uint(m));
         }
+        unsigned int prev = 0u;
+        if (lane == 0) {
+            __threadfence();
+            prev = atomicAdd(I.ticket, run.z);
+        }
+        if (pend_inst != 0xffffffffu) batch_resolve(insts, pend_inst, pend_prev, pend_cnt, round, lane);
+        pend_inst = run.x;
+        pend_prev = prev;
+        pend_cnt = run.z;
     }
+    if (pend_inst != 0xffffffffu) batch_resolve(insts, pend_inst, pend_prev, pend_cnt, round, lane);
 }
 
 }  // namespace hx
@@ -194,11 +190,12 @@ batch_kernel(const BInst *__restrict__ insts, const unsigned long long *__restri
 struct hx_batch {
     hx_ctx *ctx = nullptr;
     int rounds = 0;
-    std::vector<uint32_t> round_begin;   // rounds + 1 offsets into the item list
+    std::vector<uint32_t> cta_begin;    // rounds + 1 offsets into the CTA item list
+    std::vector<uint32_t> warp_begin;   // rounds + 1 offsets into the warp run list
     void *d_mem = nullptr;
     hx::BInst *d_insts = nullptr;
-    unsigned long long *d_items = nullptr;
-    unsigned int *d_ctrl = nullptr;
+    unsigned long long *d_cta_items = nullptr;
+    uint4 *d_warp_runs = nullptr;
     int ctas_per_sm = 1;
 };
 
@@ -282,7 +279,8 @@ extern "C" hx_status hx_batch_plan(hx_ctx *ctx, const hx_task *tasks, int32_t n_
             I.vec = (s.nx % 4 == 0) && ((((uintptr_t)s.u0 | (uintptr_t)s.u1) & 15u) == 0);
             const int width = I.vec ? 128 : 32;
             I.tiles_x = (s.nx + width - 1) / width;
-            I.tiles = s.iters > 0 ? (int64_t)I.tiles_x * ((s.ny + kBStTileRows - 1) / kBStTileRows) : 0;
+            I.tiles_y = (s.ny + kBatchStRows - 1) / kBatchStRows;
+            I.tiles = s.iters > 0 ? (int64_t)I.tiles_x * I.tiles_y : 0;
             I.in0 = s.u0; I.in1 = s.u1; I.o0 = s.resid;
             n_acc += 1;
             rounds = std::max(rounds, s.iters);
@@ -296,36 +294,47 @@ extern "C" hx_status hx_batch_plan(hx_ctx *ctx, const hx_task *tasks, int32_t n_
         if (I.tiles > 0xffffffffll) return fail(HX_ERR_INVALID, "hx_batch_plan: instance too large");
     }
     // Items, round by round.  Round 0 holds the one-pass instances; stencil
-    // sweep r of each instance goes to round r.
-    std::vector<unsigned long long> items;
-    std::vector<uint32_t> round_begin;
-    std::vector<int> empty_map, empty_hist;
+    // sweep r of each instance goes to round r.  Histogram chunks are CTA
+    // items, everything else warp items.
+    std::vector<unsigned long long> cta_items;
+    std::vector<uint4> warp_items;   // runs {instance, first tile, count, 0}
+    std::vector<uint32_t> cta_begin, warp_begin;
     for (int r = 0; r < rounds; ++r) {
-        round_begin.push_back((uint32_t)items.size());
+        cta_begin.push_back((uint32_t)cta_items.size());
+        warp_begin.push_back((uint32_t)warp_items.size());
         for (int i = 0; i < n_tasks; ++i) {
             const BInst &I = insts[i];
             const bool active = (I.kind == kKindStencil) ? (r < I.iters) : (r == 0);
             if (!active) continue;
-            for (int64_t k = 0; k < I.tiles; ++k) items.push_back(((unsigned long long)i << 32) | (unsigned long long)k);
+            if (I.kind == kKindHist) {
+                for (int64_t k = 0; k < I.tiles; ++k) cta_items.push_back(((unsigned long long)i << 32) | (unsigned long long)k);
+            } else {
+                const int64_t run = I.kind == kKindMap ? kMapRun : kStencilRun;
+                for (int64_t k = 0; k < I.tiles; k += run)
+                    warp_items.push_back(make_uint4((unsigned)i, (unsigned)k, (unsigned)std::min<int64_t>(run, I.tiles - k), 0u));
+            }
         }
     }
-    round_begin.push_back((uint32_t)items.size());
-    if (items.size() > 0xffffffffull) return fail(HX_ERR_INVALID, "hx_batch_plan: too many items");
+    cta_begin.push_back((uint32_t)cta_items.size());
+    warp_begin.push_back((uint32_t)warp_items.size());
+    if (cta_items.size() > 0xffffffffull || warp_items.size() > 0xffffffffull)
+        return fail(HX_ERR_INVALID, "hx_batch_plan: too many items");
 
-    // One device allocation: insts | items | partials | tickets | accumulators | ctrl.
+    // One device allocation: insts | CTA items | warp runs | partials | tickets | accumulators.
     auto align = [](size_t v) { return (v + 255) & ~(size_t)255; };
     const size_t off_items = align(sizeof(BInst) * insts.size());
-    const size_t off_part = off_items + align(sizeof(unsigned long long) * items.size());
-    const size_t off_tick = off_part + align(sizeof(double) * n_partials);
+    const size_t off_witems = off_items + align(sizeof(unsigned long long) * cta_items.size());
+    const size_t off_part = off_witems + align(sizeof(uint4) * warp_items.size());
+    const size_t off_tick = off_part + align(sizeof(float2) * n_partials);
     const size_t off_acc = off_tick + align(sizeof(unsigned int) * insts.size());
-    const size_t off_ctrl = off_acc + align(sizeof(unsigned int) * n_acc);
-    const size_t total = off_ctrl + 256;
+    const size_t total = off_acc + align(sizeof(unsigned int) * n_acc);
     DeviceGuard g(ctx->device);
     hx_batch *b = new (std::nothrow) hx_batch();
     if (!b) return fail(HX_ERR_NOMEM, "hx_batch_plan: host allocation failed");
     b->ctx = ctx;
     b->rounds = rounds;
-    b->round_begin = round_begin;
+    b->cta_begin = cta_begin;
+    b->warp_begin = warp_begin;
     cudaError_t e = cudaMalloc(&b->d_mem, total);
     if (e != cudaSuccess) {
         delete b;
@@ -333,14 +342,14 @@ extern "C" hx_status hx_batch_plan(hx_ctx *ctx, const hx_task *tasks, int32_t n_
     }
     char *base = static_cast<char *>(b->d_mem);
     b->d_insts = reinterpret_cast<BInst *>(base);
-    b->d_items = reinterpret_cast<unsigned long long *>(base + off_items);
-    b->d_ctrl = reinterpret_cast<unsigned int *>(base + off_ctrl);
+    b->d_cta_items = reinterpret_cast<unsigned long long *>(base + off_items);
+    b->d_warp_runs = reinterpret_cast<uint4 *>(base + off_witems);
     int64_t pcur = 0, acur = 0;
     for (int i = 0; i < n_tasks; ++i) {
         BInst &I = insts[i];
         I.ticket = reinterpret_cast<unsigned int *>(base + off_tick) + i;
         if (I.kind == kKindMap) {
-            I.partials = reinterpret_cast<double *>(base + off_part) + pcur;
+            I.partials = reinterpret_cast<float2 *>(base + off_part) + pcur;
             pcur += I.tiles;
         } else if (I.kind == kKindStencil) {
             I.acc = reinterpret_cast<unsigned int *>(base + off_acc) + acur;
@@ -353,8 +362,12 @@ extern "C" hx_status hx_batch_plan(hx_ctx *ctx, const hx_task *tasks, int32_t n_
     e = cudaMemset(b->d_mem, 0, total);
     if (e == cudaSuccess && !insts.empty())
         e = cudaMemcpy(b->d_insts, insts.data(), sizeof(BInst) * insts.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess && !items.empty())
-        e = cudaMemcpy(b->d_items, items.data(), sizeof(unsigned long long) * items.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !cta_items.empty())
+        e = cudaMemcpy(b->d_cta_items, cta_items.data(), sizeof(unsigned long long) * cta_items.size(),
+                       cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !warp_items.empty())
+        e = cudaMemcpy(b->d_warp_runs, warp_items.data(), sizeof(uint4) * warp_items.size(),
+                       cudaMemcpyHostToDevice);
     int occ = 0;
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_kernel, kBatchThreads, 0);
     if (e != cudaSuccess) {
@@ -395,18 +408,21 @@ extern "C" hx_status hx_batch_launch(hx_batch *b, hx_stream_t stream) {
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     for (int r = 0; r < b->rounds; ++r) {
-        const uint32_t n_items = b->round_begin[r + 1] - b->round_begin[r];
-        if (n_items == 0) continue;
+        const uint32_t n_cta = b->cta_begin[r + 1] - b->cta_begin[r];
+        const uint32_t n_warp = b->warp_begin[r + 1] - b->warp_begin[r];
+        if (n_cta == 0 && n_warp == 0) continue;
         const int64_t cap = (int64_t)b->ctx->num_sms * b->ctas_per_sm;
+        const int64_t want = std::max<int64_t>(n_cta, ((int64_t)n_warp + kBatchThreads / kWarp - 1) /
+                                                          (kBatchThreads / kWarp));
         cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3((unsigned)std::min<int64_t>(cap, n_items));
+        cfg.gridDim = dim3((unsigned)std::min<int64_t>(cap, want));
         cfg.blockDim = dim3(kBatchThreads);
         cfg.stream = (cudaStream_t)stream;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         cudaError_t e = cudaLaunchKernelEx(&cfg, batch_kernel, (const BInst *)b->d_insts,
-                                           (const unsigned long long *)(b->d_items + b->round_begin[r]), n_items, r,
-                                           b->d_ctrl);
+                                           (const unsigned long long *)(b->d_cta_items + b->cta_begin[r]), n_cta,
+                                           (const uint4 *)(b->d_warp_runs + b->warp_begin[r]), n_warp, r);
         if (e != cudaSuccess) return cuda_fail(e, "hx_batch_launch: launch");
     }
     return HX_OK;

@@ -20,18 +20,19 @@ namespace hx {
 // ---------------------------------------------------------------- constants
 constexpr int kWarp = 32;
 
-// map->reduce tile plan: a CTA of kMrThreads threads; thread t of the tile
-// owns the float4 vectors t, t + kMrThreads, t + 2 kMrThreads, ... (coalesced
-// per step).  The plan (vectors per thread) is a function of n only.
-constexpr int kMrThreads = 256;
-constexpr int kMrMinVecs = 4;        // vectors per thread in the smallest tile
-constexpr int kMrUnroll = 4;         // loads in flight per operand per thread
-constexpr int kMrMaxTiles = 2048;    // tile partials per instance (workspace)
-constexpr int kFinalThreads = 256;   // CTA width of every final combine
+// map->reduce tile plan: a tile is owned by ONE warp; lane l of the tile owns
+// the float4 vectors l, l + 32, l + 64, ... (coalesced per step).  Warps work
+// independently (no block barriers); the plan (vectors per lane) is a
+// function of n only.
+constexpr int kMrMinVecs = 4;        // vectors per lane in the smallest tile (one load round)
+constexpr int kMrUnroll = 4;         // loads in flight per operand per lane
+constexpr int kMrMaxTiles = 4096;    // tile partials per instance (workspace)
+constexpr int kMrWarpsPerCta = 4;    // standalone launch: tiles per CTA
 
 // stencil: one warp owns a block of kStRows rows x (128 | 32) columns.
 constexpr int kStRows = 8;
 constexpr int kStWarps = 4;          // warps per CTA, stacked vertically
+constexpr int kBatchStRows = 4;      // rows per warp block inside the batched kernel
 
 // histogram: lane-replicated shared bins, 256 bins x 32 lanes of uint32.
 constexpr int kHiThreads = 512;
@@ -42,7 +43,7 @@ constexpr int kHiBins = 256;
 // the final combine and resets its ticket and accumulators to zero, so a slot
 // is clean again when a call's stream work completes.
 struct WsSlot {
-    double mr_partial[kMrMaxTiles];
+    float2 mr_partial[kMrMaxTiles];   // (hi, lo) tile partials
     unsigned int mr_ticket;
     unsigned int st_ticket;
     unsigned int st_max_bits;   // running max |u'-u| as float bits (>= 0)
@@ -55,15 +56,15 @@ static_assert(sizeof(WsSlot) % 256 == 0, "slot alignment");
 // ---------------------------------------------------------------- plans
 struct MrPlan {
     int64_t n;
-    int vecs_per_thread;   // multiple of kMrUnroll
-    int64_t tile_elems;    // kMrThreads * 4 * vecs_per_thread
+    int vecs_per_thread;   // float4 vectors per lane, multiple of kMrUnroll
+    int64_t tile_elems;    // 32 * 4 * vecs_per_thread
     int64_t tiles;
 };
 
 __host__ __device__ inline MrPlan mr_plan(int64_t n) {
     MrPlan p;
     p.n = n;
-    const int64_t per_vec_row = (int64_t)kMrThreads * 4;
+    const int64_t per_vec_row = (int64_t)kWarp * 4;
     int64_t need = (n + per_vec_row * kMrMaxTiles - 1) / (per_vec_row * kMrMaxTiles);
     int64_t v = need < kMrMinVecs ? kMrMinVecs : need;
     v = (v + kMrUnroll - 1) / kMrUnroll * kMrUnroll;
@@ -76,13 +77,13 @@ __host__ __device__ inline MrPlan mr_plan(int64_t n) {
 // ---------------------------------------------------------------- loads
 __device__ __forceinline__ float4 ld_stream4(const float4 *p) {
     float4 v;
-    asm volatile("ld.global.nc.L1::no_allocate.L2::256B.v4.f32 {%0,%1,%2,%3}, [%4];"
+    asm("ld.global.nc.L1::no_allocate.L2::256B.v4.f32 {%0,%1,%2,%3}, [%4];"
                  : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p));
     return v;
 }
 __device__ __forceinline__ uint4 ld_stream_u4(const uint4 *p) {
     uint4 v;
-    asm volatile("ld.global.nc.L1::no_allocate.L2::256B.v4.u32 {%0,%1,%2,%3}, [%4];"
+    asm("ld.global.nc.L1::no_allocate.L2::256B.v4.u32 {%0,%1,%2,%3}, [%4];"
                  : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p));
     return v;
 }
@@ -92,11 +93,42 @@ __device__ __forceinline__ void st_stream4(float4 *p, float4 v) {
 }
 
 // ---------------------------------------------------------------- trees
-// Butterfly sum over a warp: every lane ends with the same value, and the
-// pairing order is fixed, so the result is deterministic.
-__device__ __forceinline__ double warp_sum(double v) {
+// Sums are carried as unevaluated pairs hi + lo of fp32 numbers (the
+// "double-float" representation): TwoSum (Knuth) yields the exact rounding
+// error of an fp32 addition, so a pair holds about 48 significant bits while
+// using only the fp32 pipes (B300's fp64 rate is a small fraction of its
+// fp32 rate).  TwoSum's error term is exact whichever operand comes first,
+// so ff_add is commutative bit for bit and a butterfly leaves the same value
+// in every lane: the combination order, and hence the result, is fixed.
+struct ff {
+    float hi, lo;
+};
+
+__device__ __forceinline__ ff two_sum(float a, float b) {
+    const float s = a + b;
+    const float bb = s - a;
+    const float e = (a - (s - bb)) + (b - bb);
+    return {s, e};
+}
+// Renormalise (s, e) with |e| small against s: hi = fl(s + e), lo = the rest.
+__device__ __forceinline__ ff fast_two_sum(float s, float e) {
+    const float h = s + e;
+    return {h, e - (h - s)};
+}
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+    const ff s = two_sum(a.hi, b.hi);
+    return fast_two_sum(s.hi, s.lo + (a.lo + b.lo));
+}
+__device__ __forceinline__ ff ff_add_f(ff a, float b) {
+    const ff s = two_sum(a.hi, b);
+    return fast_two_sum(s.hi, s.lo + a.lo);
+}
+__device__ __forceinline__ ff ff_shfl_xor(ff v, int off) {
+    return {__shfl_xor_sync(0xffffffffu, v.hi, off), __shfl_xor_sync(0xffffffffu, v.lo, off)};
+}
+__device__ __forceinline__ ff warp_sum(ff v) {
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    for (int off = 16; off > 0; off >>= 1) v = ff_add(v, ff_shfl_xor(v, off));
     return v;
 }
 __device__ __forceinline__ float warp_max(float v) {
@@ -105,34 +137,23 @@ __device__ __forceinline__ float warp_max(float v) {
     return v;
 }
 
-// Fixed-shape block sum of one double per thread (blockDim.x a multiple of
-// 32, at most 1024).  Returns the total in every thread of warp 0.
-__device__ __forceinline__ double block_sum(double v, double *smem32) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    v = warp_sum(v);
-    if (lane == 0) smem32[warp] = v;
-    __syncthreads();
-    double r = 0.0;
-    if (warp == 0) {
-        r = (lane < (int)(blockDim.x >> 5)) ? smem32[lane] : 0.0;
-        r = warp_sum(r);
-    }
-    __syncthreads();
-    return r;
-}
+// The exact value hi + lo of a pair (fits a double: the two parts span at
+// most 48 bits).
+__device__ __forceinline__ double ff_to_double(ff v) { return (double)v.hi + (double)v.lo; }
 
 // ---------------------------------------------------------------- map->reduce
 // Sum of out[e] over the elements of tile `tile` owned by this thread, in the
 // fixed order (vector u ascending, then lane j = 0..3 within the vector),
-// storing out[e] = fmaf(a, x[e], y[e]) when out != nullptr.  The vector path
-// (aligned, full tile) and the element path produce the same fp32 sequence.
-__device__ __forceinline__ float mr_thread_partial(const float *__restrict__ x,
+// accumulated as a compensated pair, storing out[e] = fmaf(a, x[e], y[e])
+// when out != nullptr.  The vector path (aligned, full tile) and the element
+// path produce the same sequence of operations.
+__device__ __forceinline__ ff mr_thread_partial(const float *__restrict__ x,
                                                    const float *__restrict__ y,
                                                    float *__restrict__ out, float a,
                                                    const MrPlan &p, int64_t tile,
                                                    bool aligned, int t, int nthreads) {
     const int64_t base = tile * p.tile_elems;
-    float acc = 0.0f;
+    ff acc = {0.0f, 0.0f};
     const bool full = base + p.tile_elems <= p.n;
     if (full && aligned) {
         const float4 *x4 = reinterpret_cast<const float4 *>(x + base);
@@ -154,10 +175,10 @@ __device__ __forceinline__ float mr_thread_partial(const float *__restrict__ x,
                 o.z = fmaf(a, xv[k].z, yv[k].z);
                 o.w = fmaf(a, xv[k].w, yv[k].w);
                 if (out) st_stream4(o4 + (int64_t)(u0 + k) * nthreads + t, o);
-                acc += o.x;
-                acc += o.y;
-                acc += o.z;
-                acc += o.w;
+                acc = ff_add_f(acc, o.x);
+                acc = ff_add_f(acc, o.y);
+                acc = ff_add_f(acc, o.z);
+                acc = ff_add_f(acc, o.w);
             }
         }
     } else {
@@ -170,7 +191,7 @@ __device__ __forceinline__ float mr_thread_partial(const float *__restrict__ x,
                 if (e < p.n) {
                     const float o = fmaf(a, __ldg(x + e), __ldg(y + e));
                     if (out) out[e] = o;
-                    acc += o;
+                    acc = ff_add_f(acc, o);
                 }
             }
         }
@@ -178,24 +199,50 @@ __device__ __forceinline__ float mr_thread_partial(const float *__restrict__ x,
     return acc;
 }
 
-// Tile partial (fp64) of one map->reduce tile, computed by a whole CTA of
-// kMrThreads threads; valid in thread 0.
-__device__ __forceinline__ double mr_tile(const float *__restrict__ x, const float *__restrict__ y,
-                                          float *__restrict__ out, float a, const MrPlan &p,
-                                          int64_t tile, bool aligned, double *smem32) {
-    const float part = mr_thread_partial(x, y, out, a, p, tile, aligned, threadIdx.x, kMrThreads);
-    return block_sum((double)part, smem32);
+// Partial of one map->reduce tile, computed by one whole warp (lane = its
+// lane index); the same value in every lane.
+__device__ __forceinline__ ff mr_tile(const float *__restrict__ x, const float *__restrict__ y,
+                                      float *__restrict__ out, float a, const MrPlan &p, int64_t tile,
+                                      bool aligned, int lane) {
+    return warp_sum(mr_thread_partial(x, y, out, a, p, tile, aligned, lane, kWarp));
 }
 
-// Final combine of `tiles` tile partials in a fixed order: thread t folds
-// partials t, t+256, t+512, ... in fp64, then the fixed block tree.  Called
-// by a whole CTA of kFinalThreads threads; result valid in thread 0.
-__device__ __forceinline__ double mr_final(const double *partials, int64_t tiles, double *smem32) {
-    double acc = 0.0;
-    for (int64_t i = threadIdx.x; i < tiles; i += kFinalThreads) {
-        acc += __ldcg(partials + i);
+// Final combine of `tiles` tile partials in a fixed order, by one warp: lane
+// l folds partials l, l+32, l+64, ... then the butterfly.  Same value in
+// every lane.
+__device__ __forceinline__ ff mr_final(const float2 *partials, int64_t tiles, int lane) {
+    ff acc = {0.0f, 0.0f};
+    for (int64_t i = lane; i < tiles; i += kWarp) {
+        const float2 q = __ldcg(partials + i);
+        acc = ff_add(acc, ff{q.x, q.y});
     }
-    return block_sum(acc, smem32);
+    return warp_sum(acc);
+}
+
+// One warp-tile of a map->reduce instance, end to end: tile partial, arrival
+// ticket, and the final combine when this warp is the last to arrive.
+__device__ __forceinline__ void mr_warp_item(const float *__restrict__ x, const float *__restrict__ y,
+                                             float *__restrict__ out, float a, const MrPlan &p, int64_t tile,
+                                             bool aligned, float2 *partials, unsigned int *ticket,
+                                             float *d_sum, double *d_sum64) {
+    const int lane = threadIdx.x & 31;
+    const ff part = mr_tile(x, y, out, a, p, tile, aligned, lane);
+    unsigned int prev = 0u;
+    if (lane == 0) {
+        partials[tile] = make_float2(part.hi, part.lo);
+        __threadfence();
+        prev = atomicAdd(ticket, 1u);
+    }
+    prev = __shfl_sync(0xffffffffu, prev, 0);
+    if (prev != (unsigned int)(p.tiles - 1)) return;
+    __threadfence();
+    const ff sf = mr_final(partials, p.tiles, lane);
+    if (lane == 0) {
+        const double s = ff_to_double(sf);
+        *d_sum = (float)s;
+        if (d_sum64) *d_sum64 = s;
+        *ticket = 0u;
+    }
 }
 
 // ---------------------------------------------------------------- stencil

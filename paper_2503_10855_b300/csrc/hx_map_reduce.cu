@@ -4,37 +4,22 @@
 // fork-chunk of Sec. 2.2), each tile's partial starts from the identity
 // (monoid-reassociate, Sec. 5.2), and the tile partials are combined by a
 // second level (fork-fission into a producer and a consumer, Sec. 5.2).  On
-// the GPU the two levels run in ONE launch: every CTA produces one tile
-// partial, and the CTA that arrives last (an atomic ticket, no waiting) runs
+// the GPU the two levels run in ONE launch: every warp produces one tile
+// partial, and the warp that arrives last (an atomic ticket, no waiting) runs
 // the consumer in a fixed order.  Inside a tile the leaf reduction is a
-// per-thread fp32 fold then fp64 warp shuffles, the warp reductions of
-// Sec. 4.4.
+// per-lane compensated fold, then a warp-shuffle butterfly, the warp
+// reductions of Sec. 4.4.
 #include "hx_internal.cuh"
 
 namespace hx {
 
-__global__ void __launch_bounds__(kMrThreads)
+// One warp per tile, kMrWarpsPerCta tiles per CTA; no block-level barrier.
+__global__ void __launch_bounds__(kMrWarpsPerCta * kWarp)
 map_reduce_kernel(const float *__restrict__ x, const float *__restrict__ y, float *__restrict__ out,
                   float a, MrPlan p, bool aligned, WsSlot *ws, float *d_sum, double *d_sum64) {
-    __shared__ double red[32];
-    __shared__ bool is_last;
-    const int64_t tile = blockIdx.x;
-    const double part = mr_tile(x, y, out, a, p, tile, aligned, red);
-    if (threadIdx.x == 0) {
-        ws->mr_partial[tile] = part;
-        __threadfence();
-        const unsigned int prev = atomicAdd(&ws->mr_ticket, 1u);
-        is_last = (prev == gridDim.x - 1);
-    }
-    __syncthreads();
-    if (!is_last) return;
-    __threadfence();
-    const double s = mr_final(ws->mr_partial, p.tiles, red);
-    if (threadIdx.x == 0) {
-        *d_sum = (float)s;
-        if (d_sum64) *d_sum64 = s;
-        ws->mr_ticket = 0u;
-    }
+    const int64_t tile = (int64_t)blockIdx.x * kMrWarpsPerCta + (threadIdx.x >> 5);
+    if (tile >= p.tiles) return;
+    mr_warp_item(x, y, out, a, p, tile, aligned, ws->mr_partial, &ws->mr_ticket, d_sum, d_sum64);
 }
 
 __global__ void map_reduce_empty_kernel(float *d_sum, double *d_sum64) {
@@ -70,7 +55,8 @@ extern "C" hx_status hx_map_reduce(hx_ctx *ctx, const float *x, const float *y, 
     } else {
         const MrPlan p = mr_plan(n);
         const bool aligned = (((uintptr_t)x | (uintptr_t)y | (uintptr_t)out) & 15u) == 0;
-        map_reduce_kernel<<<(unsigned)p.tiles, kMrThreads, 0, (cudaStream_t)stream>>>(
+        const unsigned grid = (unsigned)((p.tiles + kMrWarpsPerCta - 1) / kMrWarpsPerCta);
+        map_reduce_kernel<<<grid, kMrWarpsPerCta * kWarp, 0, (cudaStream_t)stream>>>(
             x, y, out, a, p, aligned, ws, d_sum, d_sum64);
     }
     cudaError_t e = cudaGetLastError();

@@ -1,12 +1,13 @@
 // hx_stencil.cu -- clamp-to-edge 5-point Jacobi sweeps fused with a max
 // residual reduce.
 //
-// One sweep is a 2-D fork over the grid (Sec. 3.3); the block-level fork
-// keeps each column strip's three live rows in registers and exchanges the
-// horizontal neighbours with warp shuffles, so every input point is read from
-// memory about once per sweep.  The max of |u' - u| is the fused reduction
-// (loop fusion, Sec. 5.1; max reduction tree, Sec. 5.2): warp shuffle max,
-// then one atomic max per CTA into the workspace (max is exact and order
+// One sweep is a 2-D fork over the grid (Sec. 3.3) tiled into warp blocks of
+// kStRows rows x 128 columns, stacked kStWarps to a CTA; a warp loads its rows and halo columns up front
+// into registers and takes horizontal neighbours from the adjacent lanes, so
+// each input point is read from memory about once per sweep.  The max of
+// |u' - u| is the fused reduction (loop fusion, Sec. 5.1; max reduction tree,
+// Sec. 5.2): warp shuffle max, a shared-memory max over the CTA's warps, one
+// atomic max per CTA into the workspace (max is exact and order
 // independent), and the last CTA to arrive publishes it.  Sweeps form a
 // sequential loop (Sec. 4.4 rule 1): one launch each, chained with
 // programmatic dependent launch so that a sweep's CTAs are already resident
@@ -15,13 +16,16 @@
 
 namespace hx {
 
+// A CTA covers one 128-column (or 32-column) strip and kStWarps warp blocks
+// stacked vertically; CTAs run row band by row band.  The CTA folds its
+// warps' maxima in shared memory and publishes once: one atomic max and one
+// arrival ticket per CTA, the last CTA writes the residual.
 __global__ void __launch_bounds__(kStWarps * kWarp)
 stencil_kernel(const float *__restrict__ src, float *__restrict__ dst, int nx, int ny, bool vec,
                WsSlot *ws, float *d_resid_t) {
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;");
     __shared__ float wmax[kStWarps];
-    __shared__ bool is_last;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int c_begin = blockIdx.x * (vec ? 128 : 32);
     const int r_begin = (blockIdx.y * kStWarps + warp) * kStRows;
@@ -35,15 +39,12 @@ stencil_kernel(const float *__restrict__ src, float *__restrict__ dst, int nx, i
     __syncthreads();
     if (threadIdx.x == 0) {
         float bm = wmax[0];
-        for (int w = 1; w < kStWarps; ++w) bm = fmaxf(bm, wmax[w]);
+        for (int i = 1; i < kStWarps; ++i) bm = fmaxf(bm, wmax[i]);
         atomicMax(&ws->st_max_bits, __float_as_uint(bm));
         __threadfence();
-        const unsigned int total = gridDim.x * gridDim.y;
-        is_last = atomicAdd(&ws->st_ticket, 1u) == total - 1;
-        if (is_last) {
+        if (atomicAdd(&ws->st_ticket, 1u) == gridDim.x * gridDim.y - 1) {
             __threadfence();
-            const unsigned int bits = atomicExch(&ws->st_max_bits, 0u);
-            *d_resid_t = __uint_as_float(bits);
+            *d_resid_t = __uint_as_float(atomicExch(&ws->st_max_bits, 0u));
             ws->st_ticket = 0u;
         }
     }
