@@ -96,6 +96,37 @@ hx_status hx_map_reduce(hx_ctx *ctx, const float *x, const float *y, float *out,
                         float a, int64_t n, float *d_sum, double *d_sum64,
                         hx_stream_t stream);
 
+/* ------------------------------------------------------------------ map->reduce, no allocation
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that may not allocate device memory -- for example a plugin whose host
+ * application owns all device memory through its own pool, or
+ * latency-critical code that cannot afford cudaMalloc/cudaFree (which can
+ * synchronise the device).  Such callers cannot use hx_create either,
+ * because a context allocates its workspace.
+ *
+ * Computes exactly what hx_map_reduce computes (same tile plan and device
+ * code, so the same results) without a context and without allocating:
+ * the reduction's scratch (HX_NOALLOC_MAX_TILES tile partials plus an
+ * arrival ticket, about 33 KiB) is a static device array of this library,
+ * held on every GPU that loads the library until the process exits.
+ *   - Arguments, layout and alignment rules are those of hx_map_reduce;
+ *     the caller still allocates and owns x, y, out, d_sum and d_sum64.
+ *   - n must be in [0, HX_MAP_REDUCE_NOALLOC_MAX_N]; larger n returns
+ *     HX_ERR_INVALID with a message.
+ *   - Runs on the calling thread's current device.  The first call on a
+ *     device looks up the scratch's device address (cudaGetSymbolAddress);
+ *     make that first call before any stream capture begins.
+ *   - Every call shares the one scratch array, which keeps the last call's
+ *     contents; each call clears the arrival ticket on `stream` before its
+ *     kernel.  Calls whose work overlaps on the GPU (different streams, or
+ *     several host threads) race on the scratch and give wrong sums:
+ *     serialise them.
+ *   - Calls no cudaMalloc, cudaFree or other allocating routine. */
+#define HX_NOALLOC_MAX_TILES 4096
+#define HX_MAP_REDUCE_NOALLOC_MAX_N ((int64_t)1 << 31)
+hx_status hx_map_reduce_noalloc(const float *x, const float *y, float *out, float a, int64_t n,
+                                float *d_sum, double *d_sum64, hx_stream_t stream);
+
 /* ------------------------------------------------------------------ stencil
  * `iters` sweeps of the clamp-to-edge 5-point Jacobi update over a row-major
  * grid of ny rows by nx columns (element (i, j) at [i*nx + j]):
