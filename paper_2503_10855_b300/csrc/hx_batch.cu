@@ -165,7 +165,7 @@ batch_kernel(const BInst *__restrict__ insts, const unsigned long long *__restri
             for (unsigned int k = 0; k < run.z; ++k) {
                 const unsigned int tile = run.y + k;
                 const int wy = (int)(tile % (unsigned int)I.tiles_y), wx = (int)(tile / (unsigned int)I.tiles_y);
-                const int c_begin = wx * (I.vec ? 128 : 32), r_begin = wy * kBatchStRows;
+                const int c_begin = wx * 128, r_begin = wy * kBatchStRows;
                 m = fmaxf(m, I.vec ? stencil_block_vec<kBatchStRows>(src, dst, I.nx, I.ny, c_begin, r_begin)
                                    : stencil_block_scalar<kBatchStRows>(src, dst, I.nx, I.ny, c_begin, r_begin));
             }
@@ -277,7 +277,7 @@ extern "C" hx_status hx_batch_plan(hx_ctx *ctx, const hx_task *tasks, int32_t n_
             I.nx = s.nx; I.ny = s.ny; I.iters = s.iters;
             I.n = (int64_t)s.nx * s.ny;
             I.vec = (s.nx % 4 == 0) && ((((uintptr_t)s.u0 | (uintptr_t)s.u1) & 15u) == 0);
-            const int width = I.vec ? 128 : 32;
+            const int width = 128;   // both stencil paths cover 128 columns per warp block
             I.tiles_x = (s.nx + width - 1) / width;
             I.tiles_y = (s.ny + kBatchStRows - 1) / kBatchStRows;
             I.tiles = s.iters > 0 ? (int64_t)I.tiles_x * I.tiles_y : 0;

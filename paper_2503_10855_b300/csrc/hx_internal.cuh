@@ -308,44 +308,58 @@ __device__ __forceinline__ float stencil_block_vec(const float *__restrict__ src
     return m;
 }
 
-// Element path for any nx and alignment: one column per lane, 32 columns per
-// warp, the same loads-first structure and the same arithmetic per point.
+// Element path for any nx and alignment: each lane owns 4 consecutive
+// columns read with 4 scalar loads per row (the warp still covers 128
+// columns and keeps as many bytes in flight as the vector path; L1 serves
+// the neighbouring words of each sector).  Every column index is clamped to
+// [0, nx-1] when loading, which makes the clamp-to-edge rule automatic:
+// past the last column a lane just re-reads column nx-1.  Same arithmetic per
+// point as the vector path.
 template <int R>
 __device__ __forceinline__ float stencil_block_scalar(const float *__restrict__ src, float *__restrict__ dst,
                                                       int nx, int ny, int c_begin, int r_begin) {
     const int lane = threadIdx.x & 31;
-    const int c = c_begin + lane;
-    const bool valid = c < nx;
-    const int cl = valid ? c : nx - 1;
-    float rows[R + 2];
+    const int c0 = c_begin + lane * 4;
+    int cc[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) cc[j] = min(c0 + j, nx - 1);
+    float rows[R + 2][4];
 #pragma unroll
     for (int k = 0; k < R + 2; ++k) {
-        const int r = clampi(r_begin - 1 + k, 0, ny - 1);
-        rows[k] = __ldg(src + (size_t)r * nx + cl);
+        const float *row = src + (size_t)clampi(r_begin - 1 + k, 0, ny - 1) * nx;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) rows[k][j] = __ldg(row + cc[j]);
     }
-    const bool need_left = (lane == 0) && valid && c > 0;
-    const bool need_right = (lane == 31) && (c + 1 < nx);
-    const int hc = need_left ? c - 1 : (need_right ? c + 1 : 0);
+    const int hc = (lane == 0) ? max(c0 - 1, 0) : min(c0 + 4, nx - 1);
     float halo[R];
 #pragma unroll
     for (int k = 0; k < R; ++k) {
         const int r = min(r_begin + k, ny - 1);
-        halo[k] = (need_left || need_right) ? __ldg(src + (size_t)r * nx + hc) : 0.0f;
+        halo[k] = (lane == 0 || lane == 31) ? __ldg(src + (size_t)r * nx + hc) : 0.0f;
     }
     float m = 0.0f;
 #pragma unroll
     for (int k = 0; k < R; ++k) {
-        const float cur = rows[k + 1];
-        float left = __shfl_up_sync(0xffffffffu, cur, 1);
-        float right = __shfl_down_sync(0xffffffffu, cur, 1);
-        if (lane == 0) left = need_left ? halo[k] : cur;
-        if (c + 1 >= nx) right = cur;
-        else if (lane == 31) right = halo[k];
-        const float o = jacobi_point(rows[k], rows[k + 2], left, right);
+        const float *up = rows[k], *cur = rows[k + 1], *dn = rows[k + 2];
+        float left = __shfl_up_sync(0xffffffffu, cur[3], 1);
+        float right = __shfl_down_sync(0xffffffffu, cur[0], 1);
+        if (lane == 0) left = halo[k];
+        if (lane == 31) right = halo[k];
+        float o[4];
+        o[0] = jacobi_point(up[0], dn[0], left, cur[1]);
+        o[1] = jacobi_point(up[1], dn[1], cur[0], cur[2]);
+        o[2] = jacobi_point(up[2], dn[2], cur[1], cur[3]);
+        o[3] = jacobi_point(up[3], dn[3], cur[2], right);
         const int r = r_begin + k;
-        if (valid && r < ny) {
-            dst[(size_t)r * nx + c] = o;
-            m = fmaxf(m, fabsf(o - cur));
+        if (r < ny) {
+            float *drow = dst + (size_t)r * nx;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (c0 + j < nx) {
+                    drow[c0 + j] = o[j];
+                    m = fmaxf(m, fabsf(o[j] - cur[j]));
+                }
+            }
         }
     }
     return m;

@@ -20,18 +20,19 @@ namespace hx {
 // stacked vertically; CTAs run row band by row band.  The CTA folds its
 // warps' maxima in shared memory and publishes once: one atomic max and one
 // arrival ticket per CTA, the last CTA writes the residual.
+template <bool VEC>
 __global__ void __launch_bounds__(kStWarps * kWarp)
-stencil_kernel(const float *__restrict__ src, float *__restrict__ dst, int nx, int ny, bool vec,
+stencil_kernel(const float *__restrict__ src, float *__restrict__ dst, int nx, int ny,
                WsSlot *ws, float *d_resid_t) {
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;");
     __shared__ float wmax[kStWarps];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int c_begin = blockIdx.x * (vec ? 128 : 32);
+    const int c_begin = blockIdx.x * 128;
     const int r_begin = (blockIdx.y * kStWarps + warp) * kStRows;
     float m = 0.0f;
     if (r_begin < ny) {
-        m = vec ? stencil_block_vec<kStRows>(src, dst, nx, ny, c_begin, r_begin)
+        m = VEC ? stencil_block_vec<kStRows>(src, dst, nx, ny, c_begin, r_begin)
                 : stencil_block_scalar<kStRows>(src, dst, nx, ny, c_begin, r_begin);
     }
     m = warp_max(m);
@@ -75,7 +76,7 @@ extern "C" hx_status hx_stencil2d(hx_ctx *ctx, float *u0, float *u1, int32_t nx,
     if (st != HX_OK) return st;
 
     const bool vec = (nx % 4 == 0) && ((((uintptr_t)u0 | (uintptr_t)u1) & 15u) == 0);
-    const int width = vec ? 128 : 32;
+    const int width = 128;   // both paths: 32 lanes x 4 columns
     dim3 grid((nx + width - 1) / width, (ny + kStWarps * kStRows - 1) / (kStWarps * kStRows));
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -90,8 +91,9 @@ extern "C" hx_status hx_stencil2d(hx_ctx *ctx, float *u0, float *u1, int32_t nx,
     for (int t = 0; t < iters; ++t) {
         const float *src = (t & 1) ? u1 : u0;
         float *dst = (t & 1) ? u0 : u1;
-        cudaError_t e = cudaLaunchKernelEx(&cfg, stencil_kernel, src, dst, (int)nx, (int)ny, vec, ws,
-                                           d_resid + t);
+        cudaError_t e = vec ? cudaLaunchKernelEx(&cfg, stencil_kernel<true>, src, dst, (int)nx, (int)ny, ws, d_resid + t)
+                            : cudaLaunchKernelEx(&cfg, stencil_kernel<false>, src, dst, (int)nx, (int)ny, ws,
+                                                 d_resid + t);
         if (e != cudaSuccess) return cuda_fail(e, "hx_stencil2d: launch");
     }
     return HX_OK;
