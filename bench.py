@@ -82,6 +82,21 @@ def batch_instances(dev):
     return bufs, tasks, byts
 
 
+TUNE_FILE = os.path.join(ROOT, "paper_2503_10855_b300", "tune", "b300.json")
+
+
+def apply_tuning(hx, ctx, args) -> str:
+    """Tuning table for the run: measured now (--autotune), else the table the
+    autotuner wrote on a B300 (shipped with the package), else the defaults."""
+    if args.autotune:
+        hx.hx_autotune(ctx, 28)
+        return "autotuned at start (hx_autotune, classes up to 2^28)"
+    if os.path.exists(TUNE_FILE):
+        hx.hx_tune_set(ctx, hx.hx_tune_table_load(TUNE_FILE))
+        return "paper_2503_10855_b300/tune/b300.json (written by hx_autotune on a B300)"
+    return "built-in defaults"
+
+
 def _dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -274,6 +289,7 @@ def bench_hx(args, rank, world, local):
 
     ctx = hx.hx_create(local)
     stream = torch.cuda.Stream(device=dev)
+    tune_src = apply_tuning(hx, ctx, args)
 
     # ---- inputs, rotated over buffer sets larger than L2 in total
     x_h, y_h = workloads.map_reduce_inputs(MR_N)
@@ -418,6 +434,7 @@ def bench_hx(args, rank, world, local):
             "parallelism": f"replicas x{world}",
             "l2": f"inputs rotate over {n_sets} buffer sets ({n_sets * per_set / 2**20:.0f} MiB > 126 MB L2)",
             "step_bytes": step_bytes,
+            "tuning": tune_src,
         },
         "frac_of_hbm_roofline": round(value / world / peak, 4),
         "frac_of_nominal_8tbs": round(value / world / 8000.0, 4),
@@ -559,6 +576,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["hx", "reference"], default="hx")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--autotune", action="store_true", help="re-measure the tuning table before timing")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

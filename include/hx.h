@@ -20,9 +20,10 @@
  *    different streams use different slots, up to HX_MAX_STREAMS streams per
  *    context.  A context is not thread-safe: serialise host calls on it.
  *  - Reductions are deterministic: the combination order is a function of
- *    the problem size alone (never of timing, grid size or batching), so a
- *    result is bit-identical across runs and between a standalone call and
- *    the same instance inside a batch.
+ *    the problem size and the context's tuning table alone (never of timing,
+ *    grid size or batching), so a result is bit-identical across runs and
+ *    between a standalone call and the same instance inside a batch planned
+ *    on the same context.
  *  - Errors: every call returns an hx_status.  HX_ERR_INVALID = bad argument
  *    (nothing launched); HX_ERR_CUDA = a CUDA call failed; HX_ERR_NOMEM = a
  *    workspace, budget or capacity limit was exceeded.  hx_last_error()
@@ -79,17 +80,19 @@ void hx_destroy(hx_ctx *ctx);
  *     out[i] = fmaf(a, x[i], y[i])            (one rounding, fp32)
  * and a sum reduce folds the out[i] into s.  The sum is reassociated as the
  * MonoidReduce attribute allows (Sec. 3.4) into the reduction tree of
- * Sec. 5.2: each tile of consecutive elements is summed in a fixed order
- * (per-thread fp32 partials over a fixed element set, then an fp64 warp and
- * block tree), and the last tile to finish folds the tile partials in index
- * order in fp64.  The map and the reduce are fused: out is written in the
- * same pass (loop fusion, Sec. 5.1).
+ * Sec. 5.2: each tile of consecutive elements belongs to one warp and is
+ * summed in a fixed order (each lane folds its own elements, then a fixed
+ * shuffle butterfly), and the warp that finishes last folds the tile
+ * partials in a fixed order.  Partial sums are carried as compensated
+ * (hi, lo) pairs of fp32 numbers, about 48 significant bits.  The map and
+ * the reduce are fused: out is written in the same pass (loop fusion,
+ * Sec. 5.1).
  *
  *   x, y     device, n fp32 each, read-only.  Any alignment (16-byte
  *            aligned buffers take the vector path; results are identical).
  *   out      device, n fp32, or NULL to skip storing the map result.
  *   d_sum    device, 1 fp32: s rounded to fp32.  Required.
- *   d_sum64  device, 1 fp64: s in fp64 (before the final rounding), or NULL.
+ *   d_sum64  device, 1 fp64: hi + lo of the final pair, or NULL.
  *   n        0 <= n <= HX_MAP_REDUCE_MAX_N; n == 0 gives s = 0.
  */
 hx_status hx_map_reduce(hx_ctx *ctx, const float *x, const float *y, float *out,
@@ -104,8 +107,9 @@ hx_status hx_map_reduce(hx_ctx *ctx, const float *x, const float *y, float *out,
  * synchronise the device).  Such callers cannot use hx_create either,
  * because a context allocates its workspace.
  *
- * Computes exactly what hx_map_reduce computes (same tile plan and device
- * code, so the same results) without a context and without allocating:
+ * Computes exactly what hx_map_reduce computes with the built-in default
+ * tuning table (same tile plan and device code, so the same results),
+ * without a context and without allocating:
  * the reduction's scratch (HX_NOALLOC_MAX_TILES tile partials plus an
  * arrival ticket, about 33 KiB) is a static device array of this library,
  * held on every GPU that loads the library until the process exits.
@@ -164,6 +168,53 @@ hx_status hx_stencil2d(hx_ctx *ctx, float *u0, float *u1, int32_t nx, int32_t ny
  */
 hx_status hx_histogram(hx_ctx *ctx, const uint8_t *v, int64_t n, uint32_t *d_bins,
                        uint32_t *d_excl_scan, hx_stream_t stream);
+
+/* ------------------------------------------------------------------ tuning
+ * The paper leaves tile, chunk and vector choices to a hand-written schedule
+ * per target (Sec. 2.2: fork-chunk, fork-tile, fork-reshape; Sec. 5.2: the
+ * reduction-tree and multicore schedules).  Here an autotuner measures the
+ * candidates on the device and keeps, per size class, the fastest:
+ *   map_vecs[c]      float4 vectors per lane in one map->reduce tile, for
+ *                    n in class c (a multiple of 4; raised automatically so
+ *                    that an instance never has more than 4096 tiles).  This
+ *                    choice fixes the summation tree, so it changes the sum's
+ *                    rounding (still within tolerance, still deterministic);
+ *                    a standalone call and a batch planned with the same
+ *                    table give identical results.
+ *   hist_threads[c]  histogram CTA width (256, 512 or 1024), n in class c.
+ *   stencil_rows[c]  rows per warp block of a standalone sweep (4, 8 or
+ *                    16), class of nx*ny; results do not depend on it.
+ *   batch_map_run, batch_stencil_run: tiles per warp run in batches.
+ * Size class c holds sizes in [2^c, 2^(c+1)); sizes 0 and 1 are class 0.
+ * A context starts from the built-in defaults, or from the JSON file named
+ * by the environment variable HX_TUNE_FILE when it is set. */
+#define HX_TUNE_CLASSES 40
+typedef struct hx_tune_table {
+    int32_t map_vecs[HX_TUNE_CLASSES];
+    int32_t hist_threads[HX_TUNE_CLASSES];
+    int32_t stencil_rows[HX_TUNE_CLASSES];
+    int32_t batch_map_run;
+    int32_t batch_stencil_run;
+} hx_tune_table;
+
+/* Built-in defaults (host only, no device needed). */
+void hx_tune_table_default(hx_tune_table *t);
+/* HX_OK if every entry is one of the allowed values, else HX_ERR_INVALID. */
+hx_status hx_tune_table_check(const hx_tune_table *t);
+/* Write / read a table as JSON (host only).  Read validates the result. */
+hx_status hx_tune_table_save(const hx_tune_table *t, const char *path);
+hx_status hx_tune_table_load(hx_tune_table *t, const char *path);
+
+/* Copy the context's table out / replace it (validated).  Batches planned
+ * earlier keep the plans they were made with. */
+hx_status hx_tune_get(const hx_ctx *ctx, hx_tune_table *out);
+hx_status hx_tune_set(hx_ctx *ctx, const hx_tune_table *t);
+
+/* Measure the candidates for every size class up to 2^max_log2 elements
+ * (10 <= max_log2 <= 30) on this context's device and store the fastest in
+ * the context's table.  Allocates and frees about 1.5 GiB of temporary
+ * device memory, synchronises `stream`, takes a few seconds. */
+hx_status hx_autotune(hx_ctx *ctx, int32_t max_log2, hx_stream_t stream);
 
 /* ------------------------------------------------------------------ batches
  * Many independent nest instances in one persistent launch.  The Hercules

@@ -340,3 +340,73 @@ def hx_batch_query(ctx: Context, ticket: int) -> bool:
         return False
     _check(st, "hx_batch_query")
     return True
+
+
+# ------------------------------------------------------------------ tuning
+HX_TUNE_CLASSES = 40
+
+
+class TuneTable(ctypes.Structure):
+    """Mirror of ``hx_tune_table``: per-size-class choices (see include/hx.h)."""
+
+    _fields_ = [("map_vecs", _I32 * HX_TUNE_CLASSES), ("hist_threads", _I32 * HX_TUNE_CLASSES),
+                ("stencil_rows", _I32 * HX_TUNE_CLASSES), ("batch_map_run", _I32),
+                ("batch_stencil_run", _I32)]
+
+    def as_dict(self) -> dict:
+        return {"map_vecs": list(self.map_vecs), "hist_threads": list(self.hist_threads),
+                "stencil_rows": list(self.stencil_rows), "batch_map_run": self.batch_map_run,
+                "batch_stencil_run": self.batch_stencil_run}
+
+
+_TP = ctypes.POINTER(TuneTable)
+_lib.hx_tune_table_default.argtypes = [_TP]
+_lib.hx_tune_table_default.restype = None
+_lib.hx_tune_table_check.argtypes = [_TP]
+_lib.hx_tune_table_check.restype = ctypes.c_int
+_lib.hx_tune_table_save.argtypes = [_TP, ctypes.c_char_p]
+_lib.hx_tune_table_save.restype = ctypes.c_int
+_lib.hx_tune_table_load.argtypes = [_TP, ctypes.c_char_p]
+_lib.hx_tune_table_load.restype = ctypes.c_int
+_lib.hx_tune_get.argtypes = [_P, _TP]
+_lib.hx_tune_get.restype = ctypes.c_int
+_lib.hx_tune_set.argtypes = [_P, _TP]
+_lib.hx_tune_set.restype = ctypes.c_int
+_lib.hx_autotune.argtypes = [_P, _I32, _P]
+_lib.hx_autotune.restype = ctypes.c_int
+
+
+def hx_tune_table_default() -> TuneTable:
+    t = TuneTable()
+    _lib.hx_tune_table_default(ctypes.byref(t))
+    return t
+
+
+def hx_tune_table_check(t: TuneTable) -> None:
+    _check(_lib.hx_tune_table_check(ctypes.byref(t)), "hx_tune_table_check")
+
+
+def hx_tune_table_save(t: TuneTable, path: str) -> None:
+    _check(_lib.hx_tune_table_save(ctypes.byref(t), os.fsencode(path)), "hx_tune_table_save")
+
+
+def hx_tune_table_load(path: str) -> TuneTable:
+    t = TuneTable()
+    _check(_lib.hx_tune_table_load(ctypes.byref(t), os.fsencode(path)), "hx_tune_table_load")
+    return t
+
+
+def hx_tune_get(ctx: Context) -> TuneTable:
+    t = TuneTable()
+    _check(_lib.hx_tune_get(ctx.handle, ctypes.byref(t)), "hx_tune_get")
+    return t
+
+
+def hx_tune_set(ctx: Context, t: TuneTable) -> None:
+    _check(_lib.hx_tune_set(ctx.handle, ctypes.byref(t)), "hx_tune_set")
+
+
+def hx_autotune(ctx: Context, max_log2: int = 26, stream=None) -> TuneTable:
+    """Measure every size class up to 2^max_log2 on the device; returns the new table."""
+    _check(_lib.hx_autotune(ctx.handle, max_log2, _stream_handle(stream)), "hx_autotune")
+    return hx_tune_get(ctx)

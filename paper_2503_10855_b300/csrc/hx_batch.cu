@@ -25,11 +25,10 @@ namespace hx {
 enum : int { kKindMap = 0, kKindStencil = 1, kKindHist = 2 };
 
 constexpr int kBatchThreads = 256;                               // 8 warps
-constexpr int64_t kBHiTile = (int64_t)kBatchThreads * 16 * 32;   // 128 KiB per histogram item
+constexpr int64_t kBHiTile = (int64_t)256 * 1024;                // bytes per histogram item
 constexpr int kMaxSweeps = 4096;
 static_assert(kBatchThreads == kHiBins, "the histogram finish maps one thread to one bin");
-constexpr int64_t kMapRun = 8;       // map tiles per warp run (48 KiB of traffic at the smallest tile)
-constexpr int64_t kStencilRun = 16;  // stencil blocks per warp run (64 rows of one column strip)
+
 
 struct BInst {
     int kind;
@@ -52,12 +51,15 @@ struct BInst {
     unsigned int *acc;  // stencil: max bits (1); hist: 256 bins
 };
 
+// One histogram chunk counted by the whole CTA into its shared counters
+// (dynamic shared memory, kHiSmemBytes), merged into the instance's bins;
+// the CTA that merges the instance's last chunk publishes bins and scan.
 __device__ __forceinline__ void batch_hist_item(const BInst &I, int64_t tile, unsigned int *sh,
                                                 unsigned int *wtot, int *flag) {
-    for (int i = threadIdx.x; i < kHiBins * kWarp; i += kBatchThreads) sh[i] = 0u;
+    hist_zero(sh);
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t base_lane = smem_addr(sh) + 4u * lane;
+    const unsigned int slot = hist_slot_offset();
     const uint8_t *v = static_cast<const uint8_t *>(I.in0);
     const int64_t s = tile * kBHiTile;
     const int64_t e = min(I.n, s + kBHiTile);
@@ -65,18 +67,11 @@ __device__ __forceinline__ void batch_hist_item(const BInst &I, int64_t tile, un
     if (head > e - s) head = (int)(e - s);
     const int64_t nvec = (e - s - head) / 16;
     const int tail = (int)((e - s - head) % 16);
-    hist_count_strided(base_lane, reinterpret_cast<const uint4 *>(v + s + head), threadIdx.x, kBatchThreads,
-                       nvec);
-    if (threadIdx.x < head) hist_count_byte(base_lane, v[s + threadIdx.x]);
-    if (threadIdx.x < tail) hist_count_byte(base_lane, v[e - tail + threadIdx.x]);
+    hist_count_strided(sh, slot, reinterpret_cast<const uint4 *>(v + s + head), threadIdx.x, kBatchThreads, nvec);
+    if (threadIdx.x < head) hist_count_byte(sh, slot, v[s + threadIdx.x]);
+    if (threadIdx.x < tail) hist_count_byte(sh, slot, v[e - tail + threadIdx.x]);
     __syncthreads();
-    for (int b = threadIdx.x; b < kHiBins; b += kBatchThreads) {
-        unsigned int c = 0u;
-#pragma unroll 8
-        for (int k = 0; k < kWarp; ++k) c += sh[b * kWarp + ((k + b) & 31)];
-        if (c) atomicAdd(I.acc + b, c);
-    }
-    __threadfence();   // every thread of the 256 wrote one bin
+    if (hist_merge(sh, I.acc)) __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) *flag = atomicAdd(I.ticket, 1u) == (unsigned int)(I.tiles - 1);
     __syncthreads();
@@ -133,7 +128,7 @@ batch_kernel(const BInst *__restrict__ insts, const unsigned long long *__restri
              unsigned int n_cta, const uint4 *__restrict__ warp_runs, unsigned int n_runs, int round) {
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;");
-    __shared__ unsigned int sh[kHiBins * kWarp];
+    extern __shared__ __align__(16) unsigned int sh[];   // kHiSmemBytes when the round has CTA items
     __shared__ unsigned int wtot[kBatchThreads / kWarp];
     __shared__ int s_flag;
     const int lane = threadIdx.x & 31;
@@ -185,6 +180,18 @@ batch_kernel(const BInst *__restrict__ insts, const unsigned long long *__restri
     if (pend_inst != 0xffffffffu) batch_resolve(insts, pend_inst, pend_prev, pend_cnt, round, lane);
 }
 
+hx_status batch_setup(hx_ctx *ctx) {
+    cudaError_t e = cudaFuncSetAttribute((void *)batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kHiSmemBytes);
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+        int occ = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_kernel, kBatchThreads, i ? kHiSmemBytes : 0);
+        ctx->batch_ctas_per_sm[i] = occ > 0 ? occ : 1;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "hx_create: batch kernel set-up");
+    return HX_OK;
+}
+
 }  // namespace hx
 
 struct hx_batch {
@@ -196,7 +203,6 @@ struct hx_batch {
     hx::BInst *d_insts = nullptr;
     unsigned long long *d_cta_items = nullptr;
     uint4 *d_warp_runs = nullptr;
-    int ctas_per_sm = 1;
 };
 
 namespace hx {
@@ -266,7 +272,7 @@ extern "C" hx_status hx_batch_plan(hx_ctx *ctx, const hx_task *tasks, int32_t n_
             const auto &m = t.u.mr;
             I.n = m.n;
             I.a = m.a;
-            I.plan = mr_plan(m.n > 0 ? m.n : 1);
+            I.plan = mr_plan(m.n > 0 ? m.n : 1, ctx->tune.map_vecs[size_class(m.n)]);
             I.plan.n = m.n;
             I.tiles = m.n > 0 ? I.plan.tiles : 0;
             I.vec = (((uintptr_t)m.x | (uintptr_t)m.y | (uintptr_t)m.out) & 15u) == 0;
@@ -309,7 +315,7 @@ extern "C" hx_status hx_batch_plan(hx_ctx *ctx, const hx_task *tasks, int32_t n_
             if (I.kind == kKindHist) {
                 for (int64_t k = 0; k < I.tiles; ++k) cta_items.push_back(((unsigned long long)i << 32) | (unsigned long long)k);
             } else {
-                const int64_t run = I.kind == kKindMap ? kMapRun : kStencilRun;
+                const int64_t run = I.kind == kKindMap ? ctx->tune.batch_map_run : ctx->tune.batch_stencil_run;
                 for (int64_t k = 0; k < I.tiles; k += run)
                     warp_items.push_back(make_uint4((unsigned)i, (unsigned)k, (unsigned)std::min<int64_t>(run, I.tiles - k), 0u));
             }
@@ -368,14 +374,11 @@ extern "C" hx_status hx_batch_plan(hx_ctx *ctx, const hx_task *tasks, int32_t n_
     if (e == cudaSuccess && !warp_items.empty())
         e = cudaMemcpy(b->d_warp_runs, warp_items.data(), sizeof(uint4) * warp_items.size(),
                        cudaMemcpyHostToDevice);
-    int occ = 0;
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_kernel, kBatchThreads, 0);
     if (e != cudaSuccess) {
         cudaFree(b->d_mem);
         delete b;
         return cuda_fail(e, "hx_batch_plan: upload");
     }
-    b->ctas_per_sm = occ > 0 ? occ : 1;
     // Instances with no tiles still owe their outputs (n == 0 sums, empty
     // histograms): write those directly now, they do not depend on inputs.
     for (int i = 0; i < n_tasks; ++i) {
@@ -411,12 +414,13 @@ extern "C" hx_status hx_batch_launch(hx_batch *b, hx_stream_t stream) {
         const uint32_t n_cta = b->cta_begin[r + 1] - b->cta_begin[r];
         const uint32_t n_warp = b->warp_begin[r + 1] - b->warp_begin[r];
         if (n_cta == 0 && n_warp == 0) continue;
-        const int64_t cap = (int64_t)b->ctx->num_sms * b->ctas_per_sm;
+        const int64_t cap = (int64_t)b->ctx->num_sms * b->ctx->batch_ctas_per_sm[n_cta > 0 ? 1 : 0];
         const int64_t want = std::max<int64_t>(n_cta, ((int64_t)n_warp + kBatchThreads / kWarp - 1) /
                                                           (kBatchThreads / kWarp));
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3((unsigned)std::min<int64_t>(cap, want));
         cfg.blockDim = dim3(kBatchThreads);
+        cfg.dynamicSmemBytes = n_cta > 0 ? kHiSmemBytes : 0;
         cfg.stream = (cudaStream_t)stream;
         cfg.attrs = attr;
         cfg.numAttrs = 1;

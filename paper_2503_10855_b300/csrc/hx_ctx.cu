@@ -3,6 +3,7 @@
 // the backing memory a call needs and allocates it once, up front
 // (Hercules paper, Sec. 4.2 last paragraph and Sec. 4.6).
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 
 #include "hx_internal.cuh"
@@ -61,6 +62,14 @@ hx_status hx_create(hx_ctx **out, int device, size_t hbm_budget_bytes) {
     if (!ctx) return hx::fail(HX_ERR_NOMEM, "hx_create: host allocation failed");
     ctx->device = device;
     ctx->hbm_budget = hbm_budget_bytes;
+    hx_tune_table_default(&ctx->tune);
+    if (const char *tf = getenv("HX_TUNE_FILE")) {
+        if (tf[0] && hx_tune_table_load(&ctx->tune, tf) != HX_OK) {
+            const std::string msg = std::string("hx_create: HX_TUNE_FILE: ") + hx_last_error();
+            delete ctx;
+            return hx::fail(HX_ERR_INVALID, msg);
+        }
+    }
     e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
     if (e != cudaSuccess) {
         delete ctx;
@@ -78,6 +87,13 @@ hx_status hx_create(hx_ctx **out, int device, size_t hbm_budget_bytes) {
         cudaFree(ctx->ws);
         delete ctx;
         return hx::cuda_fail(e, "hx_create: workspace clear");
+    }
+    hx_status st = hx::histogram_setup(ctx);
+    if (st == HX_OK) st = hx::batch_setup(ctx);
+    if (st != HX_OK) {
+        cudaFree(ctx->ws);
+        delete ctx;
+        return st;
     }
     *out = ctx;
     return HX_OK;

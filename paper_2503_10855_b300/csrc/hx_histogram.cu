@@ -3,7 +3,7 @@
 // The histogram is a reduce over a 256-entry collection (Sec. 3.2, 3.3).
 // Each CTA keeps private bins in shared memory (a collection constant of a
 // block-level fork placed in shared memory, with an extra dimension for the
-// thread-level fork, as Sec. 4.4 describes), replicated per lane so that a
+// thread-level fork, as Sec. 4.4 describes), replicated per slot so that a
 // warp's 32 increments always hit 32 different banks.  CTAs then add their
 // bins into the workspace with integer atomics (exact and order independent)
 // and the last CTA to arrive publishes the bins and runs the exclusive scan
@@ -12,31 +12,26 @@
 
 namespace hx {
 
-__global__ void __launch_bounds__(kHiThreads)
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS)
 histogram_kernel(const uint8_t *__restrict__ v, int64_t n, int head, int64_t nvec, int tail,
                  WsSlot *ws, uint32_t *d_bins, uint32_t *d_scan) {
-    __shared__ unsigned int sh[kHiBins * kWarp];
-    __shared__ unsigned int wtot[kHiThreads / kWarp];
+    extern __shared__ __align__(16) unsigned int sh[];   // kHiSmemBytes of counters
+    __shared__ unsigned int wtot[THREADS / kWarp];
     __shared__ bool is_last;
-    for (int i = threadIdx.x; i < kHiBins * kWarp; i += blockDim.x) sh[i] = 0u;
+    static_assert(THREADS >= kHiBins, "the finish maps one thread to one bin");
+    hist_zero(sh);
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t base_lane = smem_addr(sh) + 4u * lane;
-    const uint4 *v4 = reinterpret_cast<const uint4 *>(v + head);
-    hist_count_strided(base_lane, v4, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
-                       (int64_t)gridDim.x * blockDim.x, nvec);
+    const unsigned int slot = hist_slot_offset();
+    hist_count_strided(sh, slot, reinterpret_cast<const uint4 *>(v + head),
+                       (int64_t)blockIdx.x * THREADS + threadIdx.x, (int64_t)gridDim.x * THREADS, nvec);
     if (blockIdx.x == 0) {   // unaligned head and ragged tail bytes
-        if (threadIdx.x < head) hist_count_byte(base_lane, v[threadIdx.x]);
-        if (threadIdx.x < tail) hist_count_byte(base_lane, v[n - tail + threadIdx.x]);
+        if (threadIdx.x < head) hist_count_byte(sh, slot, v[threadIdx.x]);
+        if (threadIdx.x < tail) hist_count_byte(sh, slot, v[n - tail + threadIdx.x]);
     }
     __syncthreads();
-    for (int b = threadIdx.x; b < kHiBins; b += blockDim.x) {
-        unsigned int s = 0u;
-#pragma unroll 8
-        for (int k = 0; k < kWarp; ++k) s += sh[b * kWarp + ((k + b) & 31)];
-        if (s) atomicAdd(&ws->hi_bins[b], s);
-    }
-    if (threadIdx.x < kHiBins) __threadfence();   // only these threads wrote bins
+    if (hist_merge(sh, ws->hi_bins)) __threadfence();   // only threads that wrote bins
     __syncthreads();
     if (threadIdx.x == 0) is_last = atomicAdd(&ws->hi_ticket, 1u) == gridDim.x - 1;
     __syncthreads();
@@ -62,6 +57,21 @@ histogram_kernel(const uint8_t *__restrict__ v, int64_t n, int head, int64_t nve
     if (threadIdx.x == 0) ws->hi_ticket = 0u;
 }
 
+// Opt the kernels into 64 KiB of dynamic shared memory and record how many
+// CTAs of each width fit on an SM (called once per context).
+hx_status histogram_setup(hx_ctx *ctx) {
+    const int widths[3] = {256, 512, 1024};
+    void *fns[3] = {(void *)histogram_kernel<256>, (void *)histogram_kernel<512>, (void *)histogram_kernel<1024>};
+    for (int i = 0; i < 3; ++i) {
+        cudaError_t e = cudaFuncSetAttribute(fns[i], cudaFuncAttributeMaxDynamicSharedMemorySize, kHiSmemBytes);
+        int occ = 0;
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fns[i], widths[i], kHiSmemBytes);
+        if (e != cudaSuccess) return cuda_fail(e, "hx_create: histogram kernel set-up");
+        ctx->hist_ctas_per_sm[i] = occ > 0 ? occ : 1;
+    }
+    return HX_OK;
+}
+
 }  // namespace hx
 
 extern "C" hx_status hx_histogram(hx_ctx *ctx, const uint8_t *v, int64_t n, uint32_t *d_bins,
@@ -81,11 +91,15 @@ extern "C" hx_status hx_histogram(hx_ctx *ctx, const uint8_t *v, int64_t n, uint
     if (head > n) head = (int)n;
     const int64_t nvec = (n - head) / 16;
     const int tail = (int)((n - head) % 16);
-    int64_t want = (nvec + 2 * kHiThreads - 1) / (2 * kHiThreads);
-    int64_t cap = (int64_t)ctx->num_sms * (2048 / kHiThreads);
-    int grid = (int)(want < 1 ? 1 : (want > cap ? cap : want));
-    histogram_kernel<<<grid, kHiThreads, 0, (cudaStream_t)stream>>>(v, n, head, nvec, tail, ws, d_bins,
-                                                                      d_excl_scan);
+    const int threads = ctx->tune.hist_threads[size_class(n)];
+    const int wi = threads == 256 ? 0 : (threads == 512 ? 1 : 2);
+    const int64_t want = (nvec + 2 * threads - 1) / (2 * threads);
+    const int64_t cap = (int64_t)ctx->num_sms * ctx->hist_ctas_per_sm[wi];
+    const int grid = (int)(want < 1 ? 1 : (want > cap ? cap : want));
+    cudaStream_t s = (cudaStream_t)stream;
+    if (wi == 0) histogram_kernel<256><<<grid, 256, kHiSmemBytes, s>>>(v, n, head, nvec, tail, ws, d_bins, d_excl_scan);
+    else if (wi == 1) histogram_kernel<512><<<grid, 512, kHiSmemBytes, s>>>(v, n, head, nvec, tail, ws, d_bins, d_excl_scan);
+    else histogram_kernel<1024><<<grid, 1024, kHiSmemBytes, s>>>(v, n, head, nvec, tail, ws, d_bins, d_excl_scan);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "hx_histogram: launch");
     return HX_OK;

@@ -29,13 +29,13 @@ constexpr int kMrUnroll = 4;         // loads in flight per operand per lane
 constexpr int kMrMaxTiles = 4096;    // tile partials per instance (workspace)
 constexpr int kMrWarpsPerCta = 4;    // standalone launch: tiles per CTA
 
-// stencil: one warp owns a block of kStRows rows x (128 | 32) columns.
+// stencil: one warp owns a block of R rows x 128 columns (R tuned per size
+// class; kStRows is the default).
 constexpr int kStRows = 8;
 constexpr int kStWarps = 4;          // warps per CTA, stacked vertically
 constexpr int kBatchStRows = 4;      // rows per warp block inside the batched kernel
 
-// histogram: lane-replicated shared bins, 256 bins x 32 lanes of uint32.
-constexpr int kHiThreads = 512;
+// histogram: 256 bins; per-CTA shared counters replicated per slot (below).
 constexpr int kHiBins = 256;
 
 // ---------------------------------------------------------------- workspace
@@ -61,11 +61,14 @@ struct MrPlan {
     int64_t tiles;
 };
 
-__host__ __device__ inline MrPlan mr_plan(int64_t n) {
+// vecs_pref: preferred float4 vectors per lane (the tuned value for n's size
+// class); raised when n would otherwise need more than kMrMaxTiles tiles.
+__host__ __device__ inline MrPlan mr_plan(int64_t n, int vecs_pref = kMrMinVecs) {
     MrPlan p;
     p.n = n;
     const int64_t per_vec_row = (int64_t)kWarp * 4;
     int64_t need = (n + per_vec_row * kMrMaxTiles - 1) / (per_vec_row * kMrMaxTiles);
+    if (need < vecs_pref) need = vecs_pref;
     int64_t v = need < kMrMinVecs ? kMrMinVecs : need;
     v = (v + kMrUnroll - 1) / kMrUnroll * kMrUnroll;
     p.vecs_per_thread = (int)v;
@@ -366,38 +369,66 @@ __device__ __forceinline__ float stencil_block_scalar(const float *__restrict__ 
 }
 
 // ---------------------------------------------------------------- histogram
-// Shared bins are laid out [bin][lane]: lane l only touches column l, so one
-// warp-wide increment never has two lanes in the same bank, whatever the
-// data.  base_lane is the 32-bit shared address of column `lane` of bin 0;
-// bin b of that column is at base_lane + 128 b.  One byte costs a byte
-// extract (prmt), an address (lea) and a reduction (red.shared).
-__device__ __forceinline__ uint32_t smem_addr(const void *p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
+// Shared counters are laid out [bin][slot], 256 bins x 64 slots of uint32
+// (64 KiB, dynamic shared memory).  A thread owns slot (lane + 32 * (warp &
+// 1)): one warp-wide increment touches 32 different banks whatever the data,
+// and neighbouring warps share no counter.  A bin row is 256 bytes, so the
+// byte offset of bin b in a thread's slot is (b << 8) | slot_offset, with
+// slot_offset < 256: one prmt builds it straight from the loaded word (byte k
+// of the word into bits 8-15, the slot offset into bits 0-7), and the shared
+// atomic adds the array base as an immediate.  Two instructions per byte.
+constexpr int kHiSlots = 64;
+constexpr int kHiSmemBytes = kHiBins * kHiSlots * 4;
+
+__device__ __forceinline__ unsigned int hist_slot_offset() {
+    return ((threadIdx.x & 31u) << 2) | (((threadIdx.x >> 5) & 1u) << 7);
 }
-__device__ __forceinline__ void red_shared_inc(uint32_t addr) {
-    asm volatile("red.shared.add.u32 [%0], 1;" ::"r"(addr) : "memory");
+__device__ __forceinline__ void hist_inc(unsigned int *sh, unsigned int byte_off) {
+    atomicAdd(reinterpret_cast<unsigned int *>(reinterpret_cast<char *>(sh) + byte_off), 1u);
 }
-__device__ __forceinline__ void hist_count_word(uint32_t base_lane, unsigned int w) {
-    red_shared_inc(base_lane + (__byte_perm(w, 0u, 0x4440u) << 7));
-    red_shared_inc(base_lane + (__byte_perm(w, 0u, 0x4441u) << 7));
-    red_shared_inc(base_lane + (__byte_perm(w, 0u, 0x4442u) << 7));
-    red_shared_inc(base_lane + ((w >> 24) << 7));
+__device__ __forceinline__ void hist_count_word(unsigned int *sh, unsigned int slot, unsigned int w) {
+    hist_inc(sh, __byte_perm(w, slot, 0x5504u));
+    hist_inc(sh, __byte_perm(w, slot, 0x5514u));
+    hist_inc(sh, __byte_perm(w, slot, 0x5524u));
+    hist_inc(sh, __byte_perm(w, slot, 0x5534u));
 }
-__device__ __forceinline__ void hist_count_vec(uint32_t base_lane, const uint4 &w) {
-    hist_count_word(base_lane, w.x);
-    hist_count_word(base_lane, w.y);
-    hist_count_word(base_lane, w.z);
-    hist_count_word(base_lane, w.w);
+__device__ __forceinline__ void hist_count_vec(unsigned int *sh, unsigned int slot, const uint4 &w) {
+    hist_count_word(sh, slot, w.x);
+    hist_count_word(sh, slot, w.y);
+    hist_count_word(sh, slot, w.z);
+    hist_count_word(sh, slot, w.w);
 }
-__device__ __forceinline__ void hist_count_byte(uint32_t base_lane, unsigned int b) {
-    red_shared_inc(base_lane + (b << 7));
+__device__ __forceinline__ void hist_count_byte(unsigned int *sh, unsigned int slot, unsigned int b) {
+    hist_inc(sh, (b << 8) | slot);
+}
+// Zero the counters (all threads of the CTA; a barrier must follow).
+__device__ __forceinline__ void hist_zero(unsigned int *sh) {
+    uint4 *s4 = reinterpret_cast<uint4 *>(sh);
+    for (int i = threadIdx.x; i < kHiSmemBytes / 16; i += blockDim.x) s4[i] = make_uint4(0, 0, 0, 0);
+}
+// Fold the 64 slots of each bin (rotated start: conflict-free) and add the
+// non-zero totals into bins_out with integer atomics (exact, any order).
+// Called after a barrier; returns whether this thread issued an atomic.
+__device__ __forceinline__ bool hist_merge(const unsigned int *sh, unsigned int *bins_out) {
+    bool wrote = false;
+    for (int b = threadIdx.x; b < kHiBins; b += blockDim.x) {
+        unsigned int c = 0u;
+#pragma unroll 8
+        for (int k = 0; k < kHiSlots; ++k) c += sh[b * kHiSlots + ((k + b) & (kHiSlots - 1))];
+        if (c) {
+            atomicAdd(bins_out + b, c);
+            wrote = true;
+        }
+    }
+    return wrote;
 }
 
 // Count the 16-byte vectors v4[first], v4[first + stride], ... below nvec into
-// the shared bins, keeping the next two vectors' loads in flight while the
-// current two are counted.
-__device__ __forceinline__ void hist_count_strided(uint32_t base_lane, const uint4 *__restrict__ v4,
-                                                   int64_t first, int64_t stride, int64_t nvec) {
+// the shared counters, keeping the next two vectors' loads in flight while
+// the current two are counted.
+__device__ __forceinline__ void hist_count_strided(unsigned int *sh, unsigned int slot,
+                                                   const uint4 *__restrict__ v4, int64_t first, int64_t stride,
+                                                   int64_t nvec) {
     int64_t i = first;
     bool h0 = i < nvec, h1 = i + stride < nvec;
     uint4 a0 = make_uint4(0, 0, 0, 0), a1 = a0;
@@ -409,8 +440,8 @@ __device__ __forceinline__ void hist_count_strided(uint32_t base_lane, const uin
         uint4 b0 = make_uint4(0, 0, 0, 0), b1 = b0;
         if (g0) b0 = ld_stream_u4(v4 + j);
         if (g1) b1 = ld_stream_u4(v4 + j + stride);
-        hist_count_vec(base_lane, a0);
-        if (h1) hist_count_vec(base_lane, a1);
+        hist_count_vec(sh, slot, a0);
+        if (h1) hist_count_vec(sh, slot, a1);
         a0 = b0;
         a1 = b1;
         h0 = g0;
@@ -431,6 +462,9 @@ struct hx_ctx {
     hx::WsSlot *ws = nullptr;   // HX_MAX_STREAMS slots
     hx_stream_t slot_stream[HX_MAX_STREAMS] = {};
     bool slot_used[HX_MAX_STREAMS] = {};
+    hx_tune_table tune = {};             // per-size-class choices (see hx.h)
+    int hist_ctas_per_sm[3] = {1, 1, 1}; // resident CTAs per SM for widths 256, 512, 1024
+    int batch_ctas_per_sm[2] = {1, 1};   // batched kernel without / with histogram counters
     // hx_batch_submit bookkeeping: ticket -> (plan, completion event)
     uint64_t next_ticket = 1;
     std::map<uint64_t, std::pair<hx_batch *, cudaEvent_t>> pending;
@@ -440,6 +474,14 @@ namespace hx {
 hx_status fail(hx_status st, const std::string &msg);
 hx_status cuda_fail(cudaError_t e, const char *what);
 hx_status slot_for(hx_ctx *ctx, hx_stream_t stream, WsSlot **slot);
+hx_status histogram_setup(hx_ctx *ctx);
+// Size class of a problem size: floor(log2(n)) clamped to the table, 0 for n <= 1.
+inline int size_class(int64_t n) {
+    int c = 0;
+    while (c + 1 < HX_TUNE_CLASSES && ((int64_t)1 << (c + 1)) <= n) ++c;
+    return c;
+}
+hx_status batch_setup(hx_ctx *ctx);
 
 struct DeviceGuard {
     int prev = -1;

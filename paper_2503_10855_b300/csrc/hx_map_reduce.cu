@@ -53,7 +53,7 @@ extern "C" hx_status hx_map_reduce(hx_ctx *ctx, const float *x, const float *y, 
     if (n == 0) {
         map_reduce_empty_kernel<<<1, 1, 0, (cudaStream_t)stream>>>(d_sum, d_sum64);
     } else {
-        const MrPlan p = mr_plan(n);
+        const MrPlan p = mr_plan(n, ctx->tune.map_vecs[size_class(n)]);
         const bool aligned = (((uintptr_t)x | (uintptr_t)y | (uintptr_t)out) & 15u) == 0;
         const unsigned grid = (unsigned)((p.tiles + kMrWarpsPerCta - 1) / kMrWarpsPerCta);
         map_reduce_kernel<<<grid, kMrWarpsPerCta * kWarp, 0, (cudaStream_t)stream>>>(

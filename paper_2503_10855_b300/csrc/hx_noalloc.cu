@@ -8,8 +8,9 @@
 // entry point that allocates nothing: the scratch the reduction needs (the
 // per-tile partials and the arrival ticket) lives in a file-scope __device__
 // array that the CUDA module holds on every device that loads this library,
-// until the process exits.  The computation is exactly hx_map_reduce's (same
-// tile plan, same device code), so the results are the same.
+// until the process exits.  The computation is exactly hx_map_reduce's with
+// the built-in default tuning (same tile plan, same device code), so the
+// results are the same.
 #include <mutex>
 
 #include "hx_internal.cuh"
@@ -76,7 +77,7 @@ extern "C" hx_status hx_map_reduce_noalloc(const float *x, const float *y, float
     };
     if (out && n > 0 && (overlaps(out, x, bytes) || overlaps(out, y, bytes)))
         return fail(HX_ERR_INVALID, "hx_map_reduce_noalloc: out overlaps an input");
-    const MrPlan p = mr_plan(n > 0 ? n : 1);
+    const MrPlan p = mr_plan(n > 0 ? n : 1);   // the built-in default tile plan
     if (n > 0 && p.tiles > HX_NOALLOC_MAX_TILES)
         return fail(HX_ERR_INVALID, "hx_map_reduce_noalloc: n needs more tile partials than the scratch holds");
     int dev = -1;

@@ -2,7 +2,7 @@
 // residual reduce.
 //
 // One sweep is a 2-D fork over the grid (Sec. 3.3) tiled into warp blocks of
-// kStRows rows x 128 columns, stacked kStWarps to a CTA; a warp loads its rows and halo columns up front
+// R rows x 128 columns (R tuned per size class), stacked kStWarps to a CTA; a warp loads its rows and halo columns up front
 // into registers and takes horizontal neighbours from the adjacent lanes, so
 // each input point is read from memory about once per sweep.  The max of
 // |u' - u| is the fused reduction (loop fusion, Sec. 5.1; max reduction tree,
@@ -20,7 +20,7 @@ namespace hx {
 // stacked vertically; CTAs run row band by row band.  The CTA folds its
 // warps' maxima in shared memory and publishes once: one atomic max and one
 // arrival ticket per CTA, the last CTA writes the residual.
-template <bool VEC>
+template <bool VEC, int R>
 __global__ void __launch_bounds__(kStWarps * kWarp)
 stencil_kernel(const float *__restrict__ src, float *__restrict__ dst, int nx, int ny,
                WsSlot *ws, float *d_resid_t) {
@@ -29,11 +29,11 @@ stencil_kernel(const float *__restrict__ src, float *__restrict__ dst, int nx, i
     __shared__ float wmax[kStWarps];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int c_begin = blockIdx.x * 128;
-    const int r_begin = (blockIdx.y * kStWarps + warp) * kStRows;
+    const int r_begin = (blockIdx.y * kStWarps + warp) * R;
     float m = 0.0f;
     if (r_begin < ny) {
-        m = VEC ? stencil_block_vec<kStRows>(src, dst, nx, ny, c_begin, r_begin)
-                : stencil_block_scalar<kStRows>(src, dst, nx, ny, c_begin, r_begin);
+        m = VEC ? stencil_block_vec<R>(src, dst, nx, ny, c_begin, r_begin)
+                : stencil_block_scalar<R>(src, dst, nx, ny, c_begin, r_begin);
     }
     m = warp_max(m);
     if (lane == 0) wmax[warp] = m;
@@ -77,7 +77,13 @@ extern "C" hx_status hx_stencil2d(hx_ctx *ctx, float *u0, float *u1, int32_t nx,
 
     const bool vec = (nx % 4 == 0) && ((((uintptr_t)u0 | (uintptr_t)u1) & 15u) == 0);
     const int width = 128;   // both paths: 32 lanes x 4 columns
-    dim3 grid((nx + width - 1) / width, (ny + kStWarps * kStRows - 1) / (kStWarps * kStRows));
+    const int rows = ctx->tune.stencil_rows[size_class((int64_t)nx * ny)];
+    dim3 grid((nx + width - 1) / width, (ny + kStWarps * rows - 1) / (kStWarps * rows));
+    using KernelFn = void (*)(const float *, float *, int, int, WsSlot *, float *);
+    KernelFn fn;
+    if (rows == 4) fn = vec ? stencil_kernel<true, 4> : stencil_kernel<false, 4>;
+    else if (rows == 16) fn = vec ? stencil_kernel<true, 16> : stencil_kernel<false, 16>;
+    else fn = vec ? stencil_kernel<true, 8> : stencil_kernel<false, 8>;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
@@ -91,9 +97,7 @@ extern "C" hx_status hx_stencil2d(hx_ctx *ctx, float *u0, float *u1, int32_t nx,
     for (int t = 0; t < iters; ++t) {
         const float *src = (t & 1) ? u1 : u0;
         float *dst = (t & 1) ? u0 : u1;
-        cudaError_t e = vec ? cudaLaunchKernelEx(&cfg, stencil_kernel<true>, src, dst, (int)nx, (int)ny, ws, d_resid + t)
-                            : cudaLaunchKernelEx(&cfg, stencil_kernel<false>, src, dst, (int)nx, (int)ny, ws,
-                                                 d_resid + t);
+        cudaError_t e = cudaLaunchKernelEx(&cfg, fn, src, dst, (int)nx, (int)ny, ws, d_resid + t);
         if (e != cudaSuccess) return cuda_fail(e, "hx_stencil2d: launch");
     }
     return HX_OK;

@@ -1,0 +1,342 @@
+// hx_tune.cu -- the autotuner: per-size-class tile, width and run choices.
+//
+// In Hercules the performance engineer writes a schedule per target that
+// chunks, tiles and reshapes the fork-joins (Sec. 2.2) and builds reduction
+// trees (Sec. 5.2), and schedule writing is driven by profiling (Sec. 5).
+// Here the same role is played by measurement: for every size class the
+// tuner times each candidate decomposition of a nest on the device and keeps
+// the fastest.  The table lives in the context; every standalone call and
+// every batch plan reads it, so a standalone call and a batch made from the
+// same context always agree bit for bit.
+#include <algorithm>
+#include <cerrno>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "hx_internal.cuh"
+
+namespace hx {
+
+// Seeded fill of a device buffer (timing inputs only; values do not matter
+// beyond being ordinary finite numbers / a spread of byte values).
+__global__ void tune_fill_f32(float *p, int64_t n, uint32_t seed) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t h = (uint32_t)i * 2654435761u ^ seed;
+        h ^= h >> 15;
+        h *= 2246822519u;
+        h ^= h >> 13;
+        p[i] = (float)(h >> 8) * (1.0f / 8388608.0f) - 1.0f;
+    }
+}
+
+namespace {
+
+bool allowed_vecs(int v) { return v >= 4 && v <= 1024 && v % kMrUnroll == 0; }
+bool allowed_threads(int t) { return t == 256 || t == 512 || t == 1024; }
+bool allowed_rows(int r) { return r == 4 || r == 8 || r == 16; }
+
+// Median of `reps` timings (ms) of fn(rep) on `stream`, after one warm-up.
+template <class Fn>
+float time_median(cudaStream_t stream, int reps, Fn fn, hx_status *st) {
+    std::vector<float> ms;
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    *st = fn(0);
+    for (int r = 1; r <= reps && *st == HX_OK; ++r) {
+        cudaEventRecord(a, stream);
+        *st = fn(r);
+        cudaEventRecord(b, stream);
+        cudaEventSynchronize(b);
+        float t = 0.0f;
+        cudaEventElapsedTime(&t, a, b);
+        ms.push_back(t);
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (ms.empty()) return 1e30f;
+    std::sort(ms.begin(), ms.end());
+    return ms[ms.size() / 2];
+}
+
+// Extract "key": <int> or "key": [<int>, ...] from a JSON text.
+bool json_ints(const std::string &text, const char *key, std::vector<long> *out) {
+    const std::string k = std::string("\"") + key + "\"";
+    size_t p = text.find(k);
+    if (p == std::string::npos) return false;
+    p = text.find(':', p + k.size());
+    if (p == std::string::npos) return false;
+    ++p;
+    while (p < text.size() && isspace((unsigned char)text[p])) ++p;
+    const bool array = p < text.size() && text[p] == '[';
+    if (array) ++p;
+    out->clear();
+    const char *c = text.c_str() + p;
+    for (;;) {
+        while (*c && (isspace((unsigned char)*c) || *c == ',')) ++c;
+        if (!*c || *c == ']' || *c == '}') break;
+        char *end = nullptr;
+        errno = 0;
+        long v = strtol(c, &end, 10);
+        if (end == c || errno) return false;
+        out->push_back(v);
+        c = end;
+        if (!array) break;
+    }
+    return !out->empty();
+}
+
+}  // namespace
+}  // namespace hx
+
+extern "C" {
+
+void hx_tune_table_default(hx_tune_table *t) {
+    if (!t) return;
+    for (int c = 0; c < HX_TUNE_CLASSES; ++c) {
+        t->map_vecs[c] = hx::kMrMinVecs;
+        t->hist_threads[c] = 512;
+        t->stencil_rows[c] = hx::kStRows;
+    }
+    t->batch_map_run = 8;
+    t->batch_stencil_run = 16;
+}
+
+hx_status hx_tune_table_check(const hx_tune_table *t) {
+    using namespace hx;
+    if (!t) return fail(HX_ERR_INVALID, "hx_tune_table_check: table is NULL");
+    for (int c = 0; c < HX_TUNE_CLASSES; ++c) {
+        if (!allowed_vecs(t->map_vecs[c])) return fail(HX_ERR_INVALID, "tune table: map_vecs must be a multiple of 4 in [4, 1024]");
+        if (!allowed_threads(t->hist_threads[c])) return fail(HX_ERR_INVALID, "tune table: hist_threads must be 256, 512 or 1024");
+        if (!allowed_rows(t->stencil_rows[c])) return fail(HX_ERR_INVALID, "tune table: stencil_rows must be 4, 8 or 16");
+    }
+    if (t->batch_map_run < 1 || t->batch_map_run > 64) return fail(HX_ERR_INVALID, "tune table: batch_map_run must be in [1, 64]");
+    if (t->batch_stencil_run < 1 || t->batch_stencil_run > 256)
+        return fail(HX_ERR_INVALID, "tune table: batch_stencil_run must be in [1, 256]");
+    return HX_OK;
+}
+
+hx_status hx_tune_table_save(const hx_tune_table *t, const char *path) {
+    using namespace hx;
+    if (!path) return fail(HX_ERR_INVALID, "hx_tune_table_save: path is NULL");
+    hx_status st = hx_tune_table_check(t);
+    if (st != HX_OK) return st;
+    FILE *f = fopen(path, "w");
+    if (!f) return fail(HX_ERR_INVALID, std::string("hx_tune_table_save: cannot open ") + path);
+    auto arr = [&](const char *key, const int32_t *v) {
+        fprintf(f, "  \"%s\": [", key);
+        for (int c = 0; c < HX_TUNE_CLASSES; ++c) fprintf(f, "%s%d", c ? ", " : "", v[c]);
+        fprintf(f, "],\n");
+    };
+    fprintf(f, "{\n  \"format\": \"hx_tune_table/1\",\n  \"classes\": %d,\n", HX_TUNE_CLASSES);
+    arr("map_vecs", t->map_vecs);
+    arr("hist_threads", t->hist_threads);
+    arr("stencil_rows", t->stencil_rows);
+    fprintf(f, "  \"batch_map_run\": %d,\n  \"batch_stencil_run\": %d\n}\n", t->batch_map_run, t->batch_stencil_run);
+    const bool ok = fclose(f) == 0;
+    return ok ? HX_OK : fail(HX_ERR_INVALID, "hx_tune_table_save: write failed");
+}
+
+hx_status hx_tune_table_load(hx_tune_table *t, const char *path) {
+    using namespace hx;
+    if (!t || !path) return fail(HX_ERR_INVALID, "hx_tune_table_load: NULL argument");
+    FILE *f = fopen(path, "r");
+    if (!f) return fail(HX_ERR_INVALID, std::string("hx_tune_table_load: cannot open ") + path);
+    std::string text;
+    char buf[4096];
+    size_t got;
+    while ((got = fread(buf, 1, sizeof buf, f)) > 0) text.append(buf, got);
+    fclose(f);
+    hx_tune_table tmp;
+    hx_tune_table_default(&tmp);
+    std::vector<long> v;
+    struct { const char *key; int32_t *dst; } arrays[] = {
+        {"map_vecs", tmp.map_vecs}, {"hist_threads", tmp.hist_threads}, {"stencil_rows", tmp.stencil_rows}};
+    for (auto &a : arrays) {
+        if (!json_ints(text, a.key, &v) || v.size() != HX_TUNE_CLASSES)
+            return fail(HX_ERR_INVALID, std::string("hx_tune_table_load: bad or missing ") + a.key);
+        for (int c = 0; c < HX_TUNE_CLASSES; ++c) a.dst[c] = (int32_t)v[c];
+    }
+    if (!json_ints(text, "batch_map_run", &v)) return fail(HX_ERR_INVALID, "hx_tune_table_load: missing batch_map_run");
+    tmp.batch_map_run = (int32_t)v[0];
+    if (!json_ints(text, "batch_stencil_run", &v))
+        return fail(HX_ERR_INVALID, "hx_tune_table_load: missing batch_stencil_run");
+    tmp.batch_stencil_run = (int32_t)v[0];
+    hx_status st = hx_tune_table_check(&tmp);
+    if (st != HX_OK) return st;
+    *t = tmp;
+    return HX_OK;
+}
+
+hx_status hx_tune_get(const hx_ctx *ctx, hx_tune_table *out) {
+    if (!ctx || !out) return hx::fail(HX_ERR_INVALID, "hx_tune_get: NULL argument");
+    *out = ctx->tune;
+    return HX_OK;
+}
+
+hx_status hx_tune_set(hx_ctx *ctx, const hx_tune_table *t) {
+    if (!ctx) return hx::fail(HX_ERR_INVALID, "hx_tune_set: ctx is NULL");
+    hx_status st = hx_tune_table_check(t);
+    if (st != HX_OK) return st;
+    ctx->tune = *t;
+    return HX_OK;
+}
+
+hx_status hx_autotune(hx_ctx *ctx, int32_t max_log2, hx_stream_t stream) {
+    using namespace hx;
+    if (!ctx) return fail(HX_ERR_INVALID, "hx_autotune: ctx is NULL");
+    if (max_log2 < 10 || max_log2 > 30) return fail(HX_ERR_INVALID, "hx_autotune: max_log2 must be in [10, 30]");
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int map_top = std::min<int>(max_log2, 26);   // above this the 4096-tile rule decides the plan
+    // Pool: 3 fp32 arrays of 2^map_top (rotated through, so small classes
+    // start cold), and it also serves as the histogram and stencil input.
+    const size_t pool_elems = std::max<size_t>((size_t)3 << map_top, (size_t)3 << 26);
+    float *pool = nullptr;
+    cudaError_t e = cudaMalloc(&pool, pool_elems * sizeof(float));
+    if (e != cudaSuccess) return cuda_fail(e, "hx_autotune: pool cudaMalloc");
+    float *res = nullptr;   // sums, residuals, bins
+    e = cudaMalloc(&res, 4096 * sizeof(float));
+    if (e != cudaSuccess) {
+        cudaFree(pool);
+        return cuda_fail(e, "hx_autotune: result cudaMalloc");
+    }
+    tune_fill_f32<<<ctx->num_sms * 8, 256, 0, s>>>(pool, (int64_t)pool_elems, 12345u);
+    e = cudaStreamSynchronize(s);
+    hx_status st = e == cudaSuccess ? HX_OK : cuda_fail(e, "hx_autotune: fill");
+    hx_tune_table t = ctx->tune;
+    const int reps = 5;
+
+    // map->reduce tile length per class
+    for (int c = 10; c <= map_top && st == HX_OK; ++c) {
+        const int64_t n = (int64_t)1 << c;
+        const size_t stride = ((size_t)3 * n + 63) & ~(size_t)63;
+        const size_t regions = std::max<size_t>(1, pool_elems / stride);
+        float best = 1e30f;
+        int best_v = t.map_vecs[c];
+        for (int v : {4, 8, 16, 32}) {
+            if (mr_plan(n, v).vecs_per_thread != v) continue;   // forced up by the tile cap
+            ctx->tune.map_vecs[c] = v;
+            const float ms = time_median(s, reps, [&](int r) {
+                float *base = pool + (r % regions) * stride;
+                return hx_map_reduce(ctx, base, base + n, base + 2 * n, 1.5f, n, res, nullptr, stream);
+            }, &st);
+            if (st == HX_OK && ms < best) { best = ms; best_v = v; }
+        }
+        t.map_vecs[c] = best_v;
+        ctx->tune.map_vecs[c] = best_v;
+    }
+    for (int c = map_top + 1; c < HX_TUNE_CLASSES; ++c) t.map_vecs[c] = t.map_vecs[map_top];
+
+    // histogram CTA width per class
+    const int hist_top = std::min<int>(max_log2, 28);
+    const size_t pool_bytes = pool_elems * sizeof(float);
+    for (int c = 10; c <= hist_top && st == HX_OK; ++c) {
+        const int64_t n = (int64_t)1 << c;
+        const size_t stride = ((size_t)n + 255) & ~(size_t)255;
+        const size_t regions = std::max<size_t>(1, pool_bytes / stride);
+        float best = 1e30f;
+        int best_t = t.hist_threads[c];
+        for (int w : {256, 512, 1024}) {
+            ctx->tune.hist_threads[c] = w;
+            const float ms = time_median(s, reps, [&](int r) {
+                const uint8_t *base = reinterpret_cast<const uint8_t *>(pool) + (r % regions) * stride;
+                return hx_histogram(ctx, base, n, reinterpret_cast<uint32_t *>(res),
+                                    reinterpret_cast<uint32_t *>(res) + 256, stream);
+            }, &st);
+            if (st == HX_OK && ms < best) { best = ms; best_t = w; }
+        }
+        t.hist_threads[c] = best_t;
+        ctx->tune.hist_threads[c] = best_t;
+    }
+    for (int c = hist_top + 1; c < HX_TUNE_CLASSES; ++c) t.hist_threads[c] = t.hist_threads[hist_top];
+
+    // stencil rows per warp block per class (square grids of 2^c points)
+    const int st_top = std::min<int>(max_log2, 26);
+    for (int c = 10; c <= st_top && st == HX_OK; c += 2) {
+        const int side = 1 << (c / 2);
+        const int64_t pts = (int64_t)side * side;
+        float best = 1e30f;
+        int best_r = t.stencil_rows[c];
+        for (int rows : {4, 8, 16}) {
+            ctx->tune.stencil_rows[c] = rows;
+            ctx->tune.stencil_rows[c + 1 < HX_TUNE_CLASSES ? c + 1 : c] = rows;
+            const float ms = time_median(s, reps, [&](int) {
+                return hx_stencil2d(ctx, pool, pool + pts, side, side, 2, res, nullptr, stream);
+            }, &st);
+            if (st == HX_OK && ms < best) { best = ms; best_r = rows; }
+        }
+        t.stencil_rows[c] = best_r;
+        if (c + 1 < HX_TUNE_CLASSES) t.stencil_rows[c + 1] = best_r;
+        ctx->tune.stencil_rows[c] = best_r;
+        if (c + 1 < HX_TUNE_CLASSES) ctx->tune.stencil_rows[c + 1] = best_r;
+    }
+    for (int c = st_top + 2; c < HX_TUNE_CLASSES; ++c) t.stencil_rows[c] = t.stencil_rows[st_top];
+
+    // batch run lengths: a mixed batch of 48 map->reduce (2^20) and 48
+    // stencil (512^2, ragged and aligned) instances
+    if (st == HX_OK) {
+        const int64_t mn = (int64_t)1 << 20;
+        const int side = 512;
+        std::vector<hx_task> tasks;
+        size_t off = 0;
+        for (int i = 0; i < 48; ++i) {
+            hx_task tk;
+            memset(&tk, 0, sizeof tk);
+            tk.kind = HX_TASK_MAP_REDUCE;
+            tk.u.mr.x = pool + off;
+            tk.u.mr.y = pool + off + mn;
+            tk.u.mr.out = pool + off + 2 * mn;
+            tk.u.mr.sum = res + i;
+            tk.u.mr.a = 1.5f;
+            tk.u.mr.n = mn;
+            off += 3 * mn;
+            tasks.push_back(tk);
+        }
+        for (int i = 0; i < 48; ++i) {
+            const int nx = side - (i & 1) * 3;   // half ragged (element path), half aligned
+            hx_task tk;
+            memset(&tk, 0, sizeof tk);
+            tk.kind = HX_TASK_STENCIL2D;
+            tk.u.st.u0 = pool + off;
+            tk.u.st.u1 = pool + off + (size_t)side * side;
+            tk.u.st.resid = res + 1024 + i;
+            tk.u.st.nx = nx;
+            tk.u.st.ny = side;
+            tk.u.st.iters = 1;
+            off += 2 * (size_t)side * side;
+            tasks.push_back(tk);
+        }
+        float best = 1e30f;
+        int best_m = t.batch_map_run, best_s = t.batch_stencil_run;
+        for (int mr : {4, 8, 16}) {
+            for (int sr : {8, 16, 32}) {
+                ctx->tune.batch_map_run = mr;
+                ctx->tune.batch_stencil_run = sr;
+                hx_batch *b = nullptr;
+                st = hx_batch_plan(ctx, tasks.data(), (int32_t)tasks.size(), &b, nullptr);
+                if (st != HX_OK) break;
+                const float ms = time_median(s, reps, [&](int) { return hx_batch_launch(b, stream); }, &st);
+                cudaStreamSynchronize(s);
+                hx_batch_free(b);
+                if (st == HX_OK && ms < best) { best = ms; best_m = mr; best_s = sr; }
+            }
+        }
+        t.batch_map_run = best_m;
+        t.batch_stencil_run = best_s;
+    }
+    cudaStreamSynchronize(s);
+    cudaFree(pool);
+    cudaFree(res);
+    if (st != HX_OK) {
+        ctx->tune = t;   // keep what was measured so far; the rest stays as before
+        return st;
+    }
+    ctx->tune = t;
+    return hx_tune_table_check(&t);
+}
+
+}  // extern "C"
