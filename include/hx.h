@@ -281,6 +281,84 @@ hx_status hx_batch_submit(hx_ctx *ctx, const hx_task *tasks, int32_t n_tasks, hx
  * reported complete). */
 hx_status hx_batch_query(hx_ctx *ctx, uint64_t ticket);
 
+/* ------------------------------------------------------------------ serving
+ * A request loop over the same nests.  Requests (hx_task, buffers already
+ * on the device) arrive at any time; the server admits them in arrival order
+ * while the summed device footprint of admitted, unfinished requests stays
+ * within a budget (the footprint is a closed form of the request's sizes,
+ * as Hercules sizes a call's backing memory from its dynamic constants,
+ * Sec. 4.2 and 4.6), and runs them in one of two modes:
+ *
+ *   HX_SERVE_CONTINUOUS  continuous batching: a scheduler thread repeatedly
+ *       forms a step out of every admitted request's next piece of work
+ *       (a whole map->reduce or histogram, or the next sweep of a stencil)
+ *       and runs the step as one launch of the batched kernel; up to
+ *       max_steps_in_flight steps are queued on the device, so requests that
+ *       arrive while a step runs join the next one and their work overlaps
+ *       with the requests already running.  Each request computes exactly
+ *       what its standalone call computes (same tile plans, same device
+ *       code), so its results do not depend on what it was batched with.
+ *   HX_SERVE_PER_LAUNCH  the baseline: every admitted request is issued as
+ *       its own standalone call(s), in arrival order, on one stream.
+ *
+ * A completion thread watches the device and retires each request when the
+ * launch carrying its last piece of work has finished; latency = completion
+ * time - arrival time (host steady clock).  While a server runs, its context
+ * must not be used from other threads.  The caller keeps every request's
+ * buffers alive and untouched until the request completes. */
+typedef enum hx_serve_mode { HX_SERVE_CONTINUOUS = 0, HX_SERVE_PER_LAUNCH = 1 } hx_serve_mode;
+
+typedef struct hx_server_config {
+    int32_t mode;                 /* hx_serve_mode */
+    int32_t max_inflight;         /* admitted, unfinished requests at most (0: 65536) */
+    size_t hbm_budget_bytes;      /* admission budget (0: the context's budget; 0 there too: unlimited).
+                                   * A request larger than the budget is admitted only when nothing else
+                                   * is in flight. */
+    int32_t max_steps_in_flight;  /* continuous mode: steps queued on the device (0: 2) */
+    int32_t max_step_requests;    /* continuous mode: requests per step at most (0: 4096) */
+} hx_server_config;
+
+typedef struct hx_server_stats {
+    int64_t submitted, admitted, completed;
+    int64_t launches;             /* batched steps (continuous) or request launches (per-launch) */
+    int64_t failed;               /* requests whose launch failed */
+    size_t footprint_in_flight;   /* bytes currently admitted */
+    size_t peak_footprint;        /* most bytes admitted at once */
+} hx_server_stats;
+
+typedef struct hx_server hx_server;
+
+/* Start a server (its threads, its stream and, in continuous mode, about
+ * 3 x 60 MiB of device staging per queued step) on ctx's device. */
+hx_status hx_server_create(hx_ctx *ctx, const hx_server_config *cfg, hx_server **out);
+
+/* Wait for in-flight work, stop the threads, free the server. */
+void hx_server_destroy(hx_server *s);
+
+/* Submit one request now (thread-safe).  The task is validated as its
+ * standalone call would be; *req_id identifies it for hx_server_poll. */
+hx_status hx_server_submit(hx_server *s, const hx_task *task, uint64_t *req_id);
+
+/* HX_OK when the request has completed (its latency in *latency_s, may be
+ * NULL), HX_ERR_BUSY while pending, HX_ERR_CUDA if its launch failed,
+ * HX_ERR_INVALID for an unknown id. */
+hx_status hx_server_poll(hx_server *s, uint64_t req_id, double *latency_s);
+
+/* Block until every submitted request has completed, at most timeout_s
+ * seconds (HX_ERR_TIMEOUT otherwise). */
+hx_status hx_server_drain(hx_server *s, double timeout_s);
+
+hx_status hx_server_get_stats(hx_server *s, hx_server_stats *out);
+
+/* Open-loop replay: submit tasks[i] at start + arrival_s[i] (arrival_s
+ * non-decreasing, seconds), pacing from the calling thread, then drain.
+ * latency_s[i] (required) = completion - scheduled arrival of request i;
+ * *makespan_s (nullable) = last completion - start.  Fails with
+ * HX_ERR_TIMEOUT if the requests have not completed timeout_s seconds after
+ * the last arrival. */
+hx_status hx_server_run_trace(hx_server *s, const hx_task *tasks, const double *arrival_s, int32_t n,
+                              double timeout_s, double *latency_s, double *makespan_s);
+
 #ifdef __cplusplus
 }
 #endif

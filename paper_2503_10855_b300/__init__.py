@@ -410,3 +410,108 @@ def hx_autotune(ctx: Context, max_log2: int = 26, stream=None) -> TuneTable:
     """Measure every size class up to 2^max_log2 on the device; returns the new table."""
     _check(_lib.hx_autotune(ctx.handle, max_log2, _stream_handle(stream)), "hx_autotune")
     return hx_tune_get(ctx)
+
+
+# ------------------------------------------------------------------ serving
+HX_SERVE_CONTINUOUS, HX_SERVE_PER_LAUNCH = 0, 1
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("mode", _I32), ("max_inflight", _I32), ("hbm_budget_bytes", ctypes.c_size_t),
+                ("max_steps_in_flight", _I32), ("max_step_requests", _I32)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", _I64), ("admitted", _I64), ("completed", _I64), ("launches", _I64),
+                ("failed", _I64), ("footprint_in_flight", ctypes.c_size_t), ("peak_footprint", ctypes.c_size_t)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib.hx_server_create.argtypes = [_P, ctypes.POINTER(ServerConfig), ctypes.POINTER(_P)]
+_lib.hx_server_create.restype = ctypes.c_int
+_lib.hx_server_destroy.argtypes = [_P]
+_lib.hx_server_destroy.restype = None
+_lib.hx_server_submit.argtypes = [_P, ctypes.POINTER(HxTask), ctypes.POINTER(ctypes.c_uint64)]
+_lib.hx_server_submit.restype = ctypes.c_int
+_lib.hx_server_poll.argtypes = [_P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double)]
+_lib.hx_server_poll.restype = ctypes.c_int
+_lib.hx_server_drain.argtypes = [_P, ctypes.c_double]
+_lib.hx_server_drain.restype = ctypes.c_int
+_lib.hx_server_get_stats.argtypes = [_P, ctypes.POINTER(ServerStats)]
+_lib.hx_server_get_stats.restype = ctypes.c_int
+_lib.hx_server_run_trace.argtypes = [_P, ctypes.POINTER(HxTask), ctypes.POINTER(ctypes.c_double), _I32,
+                                     ctypes.c_double, ctypes.POINTER(ctypes.c_double),
+                                     ctypes.POINTER(ctypes.c_double)]
+_lib.hx_server_run_trace.restype = ctypes.c_int
+
+
+class Server:
+    """An ``hx_server``: admission + continuous batching (or per-launch) request loop."""
+
+    def __init__(self, ctx: Context, mode: int = HX_SERVE_CONTINUOUS, hbm_budget_bytes: int = 0,
+                 max_inflight: int = 0, max_steps_in_flight: int = 0, max_step_requests: int = 0):
+        cfg = ServerConfig(mode, max_inflight, hbm_budget_bytes, max_steps_in_flight, max_step_requests)
+        h = _P()
+        _check(_lib.hx_server_create(ctx.handle, ctypes.byref(cfg), ctypes.byref(h)), "hx_server_create")
+        self.ctx = ctx
+        self.handle = h
+        self.keep = []
+
+    def submit(self, task: HxTask) -> int:
+        rid = ctypes.c_uint64(0)
+        self.keep.append(getattr(task, "keep", None))
+        _check(_lib.hx_server_submit(self.handle, ctypes.byref(task), ctypes.byref(rid)), "hx_server_submit")
+        return rid.value
+
+    def poll(self, req_id: int):
+        """(done, latency_s or None)."""
+        lat = ctypes.c_double(0.0)
+        st = _lib.hx_server_poll(self.handle, req_id, ctypes.byref(lat))
+        if st == HX_ERR_BUSY:
+            return False, None
+        _check(st, "hx_server_poll")
+        return True, lat.value
+
+    def drain(self, timeout_s: float = 60.0) -> None:
+        _check(_lib.hx_server_drain(self.handle, timeout_s), "hx_server_drain")
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(_lib.hx_server_get_stats(self.handle, ctypes.byref(st)), "hx_server_get_stats")
+        return st.as_dict()
+
+    def run_trace(self, tasks, arrival_s, timeout_s: float = 60.0):
+        """Open-loop replay; returns (latencies_s list, makespan_s)."""
+        n = len(tasks)
+        arr = _task_array(tasks)
+        self.keep.append([getattr(t, "keep", None) for t in tasks])
+        arrivals = (ctypes.c_double * n)(*arrival_s)
+        lat = (ctypes.c_double * n)()
+        mk = ctypes.c_double(0.0)
+        _check(_lib.hx_server_run_trace(self.handle, arr, arrivals, n, timeout_s, lat, ctypes.byref(mk)),
+               "hx_server_run_trace")
+        return list(lat), mk.value
+
+    def close(self) -> None:
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            _lib.hx_server_destroy(self.handle)
+        self.handle = None
+        self.keep = []
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def hx_server_create(ctx: Context, **kw) -> Server:
+    return Server(ctx, **kw)

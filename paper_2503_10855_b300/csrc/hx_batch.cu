@@ -18,38 +18,9 @@
 #include <new>
 #include <vector>
 
-#include "hx_internal.cuh"
+#include "hx_batch.cuh"
 
 namespace hx {
-
-enum : int { kKindMap = 0, kKindStencil = 1, kKindHist = 2 };
-
-constexpr int kBatchThreads = 256;                               // 8 warps
-constexpr int64_t kBHiTile = (int64_t)256 * 1024;                // bytes per histogram item
-constexpr int kMaxSweeps = 4096;
-static_assert(kBatchThreads == kHiBins, "the histogram finish maps one thread to one bin");
-
-
-struct BInst {
-    int kind;
-    int vec;            // map: 16-byte aligned operands; stencil: vector path; hist: unused
-    int nx, ny;
-    float a;
-    int iters;          // stencil sweeps
-    int64_t n;
-    int64_t tiles;      // items per round
-    int tiles_x;        // stencil warp blocks across
-    int tiles_y;        // stencil warp blocks down
-    MrPlan plan;
-    const void *in0;    // map x | stencil u0 | hist v
-    const void *in1;    // map y | stencil u1
-    void *o0;           // map out | stencil resid | hist bins
-    void *o1;           // map sum | hist scan
-    void *o2;           // map sum64
-    float2 *partials;   // map tile partials (hi, lo)
-    unsigned int *ticket;
-    unsigned int *acc;  // stencil: max bits (1); hist: 256 bins
-};
 
 // One histogram chunk counted by the whole CTA into its shared counters
 // (dynamic shared memory, kHiSmemBytes), merged into the instance's bins;
@@ -113,7 +84,7 @@ __device__ __forceinline__ void batch_resolve(const BInst *__restrict__ insts, u
             *I.ticket = 0u;
         }
     } else if (lane == 0) {
-        static_cast<float *>(I.o0)[round] = __uint_as_float(atomicExch(I.acc, 0u));
+        static_cast<float *>(I.o0)[I.sweep0 + round] = __uint_as_float(atomicExch(I.acc, 0u));
         *I.ticket = 0u;
     }
 }
@@ -154,8 +125,9 @@ batch_kernel(const BInst *__restrict__ insts, const unsigned long long *__restri
                 if (lane == 0) I.partials[tile] = make_float2(part.hi, part.lo);
             }
         } else {
-            const float *src = static_cast<const float *>((round & 1) ? I.in1 : I.in0);
-            float *dst = const_cast<float *>(static_cast<const float *>((round & 1) ? I.in0 : I.in1));
+            const int sweep = I.sweep0 + round;
+            const float *src = static_cast<const float *>((sweep & 1) ? I.in1 : I.in0);
+            float *dst = const_cast<float *>(static_cast<const float *>((sweep & 1) ? I.in0 : I.in1));
             float m = 0.0f;
             for (unsigned int k = 0; k < run.z; ++k) {
                 const unsigned int tile = run.y + k;
@@ -178,6 +150,83 @@ batch_kernel(const BInst *__restrict__ insts, const unsigned long long *__restri
         pend_cnt = run.z;
     }
     if (pend_inst != 0xffffffffu) batch_resolve(insts, pend_inst, pend_prev, pend_cnt, round, lane);
+}
+
+void describe_instance(const hx_ctx *ctx, const hx_task &t, BInst *out, int64_t *partials, int64_t *acc_words) {
+    BInst &I = *out;
+    memset(&I, 0, sizeof I);
+    I.kind = t.kind;
+    *partials = 0;
+    *acc_words = 0;
+    if (t.kind == HX_TASK_MAP_REDUCE) {
+        const auto &m = t.u.mr;
+        I.n = m.n;
+        I.a = m.a;
+        I.plan = mr_plan(m.n > 0 ? m.n : 1, ctx->tune.map_vecs[size_class(m.n)]);
+        I.plan.n = m.n;
+        I.tiles = m.n > 0 ? I.plan.tiles : 0;
+        I.vec = (((uintptr_t)m.x | (uintptr_t)m.y | (uintptr_t)m.out) & 15u) == 0;
+        I.in0 = m.x; I.in1 = m.y; I.o0 = m.out; I.o1 = m.sum; I.o2 = m.sum64;
+        *partials = I.tiles;
+    } else if (t.kind == HX_TASK_STENCIL2D) {
+        const auto &s = t.u.st;
+        I.nx = s.nx; I.ny = s.ny; I.iters = s.iters;
+        I.n = (int64_t)s.nx * s.ny;
+        I.vec = (s.nx % 4 == 0) && ((((uintptr_t)s.u0 | (uintptr_t)s.u1) & 15u) == 0);
+        const int width = 128;   // both stencil paths cover 128 columns per warp block
+        I.tiles_x = (s.nx + width - 1) / width;
+        I.tiles_y = (s.ny + kBatchStRows - 1) / kBatchStRows;
+        I.tiles = s.iters > 0 ? (int64_t)I.tiles_x * I.tiles_y : 0;
+        I.in0 = s.u0; I.in1 = s.u1; I.o0 = s.resid;
+        *acc_words = 1;
+    } else {
+        const auto &h = t.u.hi;
+        I.n = h.n;
+        I.tiles = h.n > 0 ? (h.n + kBHiTile - 1) / kBHiTile : 0;
+        I.in0 = h.v; I.o0 = h.bins; I.o1 = h.scan;
+        *acc_words = kHiBins;
+    }
+}
+
+void append_round(const hx_ctx *ctx, const BInst &I, unsigned int idx, std::vector<unsigned long long> *cta_items,
+                  std::vector<uint4> *warp_runs) {
+    if (I.kind == kKindHist) {
+        for (int64_t k = 0; k < I.tiles; ++k) cta_items->push_back(((unsigned long long)idx << 32) | (unsigned long long)k);
+        return;
+    }
+    const int64_t run = I.kind == kKindMap ? ctx->tune.batch_map_run : ctx->tune.batch_stencil_run;
+    for (int64_t k = 0; k < I.tiles; k += run)
+        warp_runs->push_back(make_uint4(idx, (unsigned)k, (unsigned)std::min<int64_t>(run, I.tiles - k), 0u));
+}
+
+hx_status launch_batch_round(const hx_ctx *ctx, const BInst *d_insts, const unsigned long long *d_cta, uint32_t n_cta,
+                             const uint4 *d_runs, uint32_t n_runs, int round, cudaStream_t stream) {
+    if (n_cta == 0 && n_runs == 0) return HX_OK;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    const int64_t cap = (int64_t)ctx->num_sms * ctx->batch_ctas_per_sm[n_cta > 0 ? 1 : 0];
+    const int64_t want = std::max<int64_t>(n_cta, ((int64_t)n_runs + kBatchThreads / kWarp - 1) / (kBatchThreads / kWarp));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)std::min<int64_t>(cap, want));
+    cfg.blockDim = dim3(kBatchThreads);
+    cfg.dynamicSmemBytes = n_cta > 0 ? kHiSmemBytes : 0;
+    cfg.stream = stream;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, batch_kernel, d_insts, d_cta, n_cta, d_runs, n_runs, round);
+    if (e != cudaSuccess) return cuda_fail(e, "batched kernel launch");
+    return HX_OK;
+}
+
+size_t task_footprint(const hx_task &t) {
+    if (t.kind == HX_TASK_MAP_REDUCE) {
+        const size_t n = (size_t)(t.u.mr.n > 0 ? t.u.mr.n : 0);
+        return n * 4 * (t.u.mr.out ? 3 : 2) + 16;
+    }
+    if (t.kind == HX_TASK_STENCIL2D)
+        return (size_t)t.u.st.nx * t.u.st.ny * 8 + (size_t)(t.u.st.iters > 0 ? t.u.st.iters : 0) * 4;
+    return (size_t)(t.u.hi.n > 0 ? t.u.hi.n : 0) + 2048;
 }
 
 hx_status batch_setup(hx_ctx *ctx) {
@@ -207,9 +256,9 @@ struct hx_batch {
 
 namespace hx {
 
-static hx_status validate_task(const hx_task &t, int idx) {
-    char where[64];
-    snprintf(where, sizeof where, "hx_batch_plan: task %d: ", idx);
+hx_status validate_task(const hx_task &t, int idx, const char *who) {
+    char where[96];
+    snprintf(where, sizeof where, "%s: task %d: ", who, idx);
     switch (t.kind) {
     case HX_TASK_MAP_REDUCE: {
         const auto &m = t.u.mr;
@@ -257,51 +306,22 @@ extern "C" hx_status hx_batch_plan(hx_ctx *ctx, const hx_task *tasks, int32_t n_
     *out = nullptr;
     if (n_tasks < 0 || (n_tasks > 0 && !tasks)) return fail(HX_ERR_INVALID, "hx_batch_plan: bad task list");
     for (int i = 0; i < n_tasks; ++i) {
-        hx_status st = validate_task(tasks[i], i);
+        hx_status st = validate_task(tasks[i], i, "hx_batch_plan");
         if (st != HX_OK) return st;
     }
     std::vector<BInst> insts(n_tasks);
     int rounds = n_tasks > 0 ? 1 : 0;
     int64_t n_partials = 0, n_acc = 0;
     for (int i = 0; i < n_tasks; ++i) {
-        const hx_task &t = tasks[i];
-        BInst &I = insts[i];
-        memset(&I, 0, sizeof I);
-        I.kind = t.kind;
-        if (t.kind == HX_TASK_MAP_REDUCE) {
-            const auto &m = t.u.mr;
-            I.n = m.n;
-            I.a = m.a;
-            I.plan = mr_plan(m.n > 0 ? m.n : 1, ctx->tune.map_vecs[size_class(m.n)]);
-            I.plan.n = m.n;
-            I.tiles = m.n > 0 ? I.plan.tiles : 0;
-            I.vec = (((uintptr_t)m.x | (uintptr_t)m.y | (uintptr_t)m.out) & 15u) == 0;
-            I.in0 = m.x; I.in1 = m.y; I.o0 = m.out; I.o1 = m.sum; I.o2 = m.sum64;
-            n_partials += I.tiles;
-        } else if (t.kind == HX_TASK_STENCIL2D) {
-            const auto &s = t.u.st;
-            I.nx = s.nx; I.ny = s.ny; I.iters = s.iters;
-            I.n = (int64_t)s.nx * s.ny;
-            I.vec = (s.nx % 4 == 0) && ((((uintptr_t)s.u0 | (uintptr_t)s.u1) & 15u) == 0);
-            const int width = 128;   // both stencil paths cover 128 columns per warp block
-            I.tiles_x = (s.nx + width - 1) / width;
-            I.tiles_y = (s.ny + kBatchStRows - 1) / kBatchStRows;
-            I.tiles = s.iters > 0 ? (int64_t)I.tiles_x * I.tiles_y : 0;
-            I.in0 = s.u0; I.in1 = s.u1; I.o0 = s.resid;
-            n_acc += 1;
-            rounds = std::max(rounds, s.iters);
-        } else {
-            const auto &h = t.u.hi;
-            I.n = h.n;
-            I.tiles = h.n > 0 ? (h.n + kBHiTile - 1) / kBHiTile : 0;
-            I.in0 = h.v; I.o0 = h.bins; I.o1 = h.scan;
-            n_acc += kHiBins;
-        }
-        if (I.tiles > 0xffffffffll) return fail(HX_ERR_INVALID, "hx_batch_plan: instance too large");
+        int64_t np = 0, na = 0;
+        describe_instance(ctx, tasks[i], &insts[i], &np, &na);
+        if (insts[i].tiles > 0xffffffffll) return fail(HX_ERR_INVALID, "hx_batch_plan: instance too large");
+        n_partials += np;
+        n_acc += na;
+        if (insts[i].kind == kKindStencil) rounds = std::max(rounds, insts[i].iters);
     }
     // Items, round by round.  Round 0 holds the one-pass instances; stencil
-    // sweep r of each instance goes to round r.  Histogram chunks are CTA
-    // items, everything else warp items.
+    // sweep r of each instance goes to round r.
     std::vector<unsigned long long> cta_items;
     std::vector<uint4> warp_items;   // runs {instance, first tile, count, 0}
     std::vector<uint32_t> cta_begin, warp_begin;
@@ -311,14 +331,7 @@ extern "C" hx_status hx_batch_plan(hx_ctx *ctx, const hx_task *tasks, int32_t n_
         for (int i = 0; i < n_tasks; ++i) {
             const BInst &I = insts[i];
             const bool active = (I.kind == kKindStencil) ? (r < I.iters) : (r == 0);
-            if (!active) continue;
-            if (I.kind == kKindHist) {
-                for (int64_t k = 0; k < I.tiles; ++k) cta_items.push_back(((unsigned long long)i << 32) | (unsigned long long)k);
-            } else {
-                const int64_t run = I.kind == kKindMap ? ctx->tune.batch_map_run : ctx->tune.batch_stencil_run;
-                for (int64_t k = 0; k < I.tiles; k += run)
-                    warp_items.push_back(make_uint4((unsigned)i, (unsigned)k, (unsigned)std::min<int64_t>(run, I.tiles - k), 0u));
-            }
+            if (active) append_round(ctx, I, (unsigned)i, &cta_items, &warp_items);
         }
     }
     cta_begin.push_back((uint32_t)cta_items.size());
@@ -407,27 +420,12 @@ extern "C" hx_status hx_batch_launch(hx_batch *b, hx_stream_t stream) {
     using namespace hx;
     if (!b) return fail(HX_ERR_INVALID, "hx_batch_launch: batch is NULL");
     DeviceGuard g(b->ctx->device);
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
     for (int r = 0; r < b->rounds; ++r) {
         const uint32_t n_cta = b->cta_begin[r + 1] - b->cta_begin[r];
         const uint32_t n_warp = b->warp_begin[r + 1] - b->warp_begin[r];
-        if (n_cta == 0 && n_warp == 0) continue;
-        const int64_t cap = (int64_t)b->ctx->num_sms * b->ctx->batch_ctas_per_sm[n_cta > 0 ? 1 : 0];
-        const int64_t want = std::max<int64_t>(n_cta, ((int64_t)n_warp + kBatchThreads / kWarp - 1) /
-                                                          (kBatchThreads / kWarp));
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3((unsigned)std::min<int64_t>(cap, want));
-        cfg.blockDim = dim3(kBatchThreads);
-        cfg.dynamicSmemBytes = n_cta > 0 ? kHiSmemBytes : 0;
-        cfg.stream = (cudaStream_t)stream;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        cudaError_t e = cudaLaunchKernelEx(&cfg, batch_kernel, (const BInst *)b->d_insts,
-                                           (const unsigned long long *)(b->d_cta_items + b->cta_begin[r]), n_cta,
-                                           (const uint4 *)(b->d_warp_runs + b->warp_begin[r]), n_warp, r);
-        if (e != cudaSuccess) return cuda_fail(e, "hx_batch_launch: launch");
+        hx_status st = launch_batch_round(b->ctx, b->d_insts, b->d_cta_items + b->cta_begin[r], n_cta,
+                                          b->d_warp_runs + b->warp_begin[r], n_warp, r, (cudaStream_t)stream);
+        if (st != HX_OK) return st;
     }
     return HX_OK;
 }

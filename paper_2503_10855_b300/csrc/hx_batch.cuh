@@ -1,0 +1,60 @@
+// hx_batch.cuh -- the batched kernel's work description, shared by the batch
+// planner (hx_batch.cu) and the serving engine (hx_serve.cu).
+#pragma once
+
+#include <vector>
+
+#include "hx_internal.cuh"
+
+namespace hx {
+
+enum : int { kKindMap = 0, kKindStencil = 1, kKindHist = 2 };
+
+constexpr int kBatchThreads = 256;                               // 8 warps
+constexpr int64_t kBHiTile = (int64_t)256 * 1024;                // bytes per histogram item
+constexpr int kMaxSweeps = 4096;
+static_assert(kBatchThreads == kHiBins, "the histogram finish maps one thread to one bin");
+
+
+struct BInst {
+    int kind;
+    int vec;            // map: 16-byte aligned operands; stencil: vector path; hist: unused
+    int nx, ny;
+    float a;
+    int iters;          // stencil sweeps
+    int sweep0;         // stencil: sweep index of this launch's round 0
+    int64_t n;
+    int64_t tiles;      // items per round
+    int tiles_x;        // stencil warp blocks across
+    int tiles_y;        // stencil warp blocks down
+    MrPlan plan;
+    const void *in0;    // map x | stencil u0 | hist v
+    const void *in1;    // map y | stencil u1
+    void *o0;           // map out | stencil resid | hist bins
+    void *o1;           // map sum | hist scan
+    void *o2;           // map sum64
+    float2 *partials;   // map tile partials (hi, lo)
+    unsigned int *ticket;
+    unsigned int *acc;  // stencil: max bits (1); hist: 256 bins
+};
+
+// Checks one task against the rules of its standalone call.
+hx_status validate_task(const hx_task &t, int idx, const char *who);
+
+// Describes one task as an instance (no workspace pointers yet) and reports
+// the workspace it needs: tile partials and accumulator words.
+void describe_instance(const hx_ctx *ctx, const hx_task &t, BInst *out, int64_t *partials, int64_t *acc_words);
+
+// Appends the work items of one round of instance `idx` (the whole instance
+// for map->reduce and histogram, one sweep for a stencil) to the lists.
+void append_round(const hx_ctx *ctx, const BInst &I, unsigned int idx, std::vector<unsigned long long> *cta_items,
+                  std::vector<uint4> *warp_runs);
+
+// Launches the batched kernel for one round of an uploaded work-list.
+hx_status launch_batch_round(const hx_ctx *ctx, const BInst *d_insts, const unsigned long long *d_cta, uint32_t n_cta,
+                             const uint4 *d_runs, uint32_t n_runs, int round, cudaStream_t stream);
+
+// Device bytes a task's buffers occupy (inputs and outputs), for admission.
+size_t task_footprint(const hx_task &t);
+
+}  // namespace hx

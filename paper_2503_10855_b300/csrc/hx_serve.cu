@@ -1,0 +1,483 @@
+// hx_serve.cu -- the serving engine: admission against a device-memory
+// budget, continuous batching into the batched kernel, completion tracking.
+//
+// Hercules's host backend runs independent calls as concurrent tasks and
+// awaits each at its first use (Sec. 4.5); a runner sizes a call's backing
+// memory from its dynamic constants before running it (Sec. 4.2, 4.6).  A
+// server does the same for a stream of requests: it sizes each request from
+// its arguments, admits it when the device-memory budget allows, and keeps
+// the device busy with steps that mix every admitted request's next piece of
+// work, so requests that arrive while others run overlap with them.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <memory>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "hx_batch.cuh"
+
+namespace hx {
+namespace {
+
+double now_s() {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+// Capacities of one continuous-batching step.
+constexpr size_t kStepCtaItems = 1 << 18;   // histogram chunks (256 KiB each)
+constexpr size_t kStepRuns = 1 << 20;       // warp runs
+constexpr size_t kStepPartials = 1 << 22;   // map->reduce tile partials
+constexpr size_t kAccPerInst = kHiBins;     // accumulator words reserved per instance
+
+struct Req {
+    uint64_t id = 0;
+    hx_task task{};
+    double arrival = 0.0;
+    double latency = -1.0;
+    size_t footprint = 0;
+    BInst inst{};            // described at admission
+    int64_t partials = 0, acc_words = 0;
+    int issued_sweeps = 0;   // stencil: sweeps already put in a step
+    bool admitted = false, issued_all = false, done = false;
+    hx_status status = HX_OK;
+};
+
+struct Slot {   // staging for one step: pinned host list + device list and workspace
+    char *h = nullptr;
+    char *d = nullptr;
+    size_t off_cta = 0, off_runs = 0, off_part = 0, off_tick = 0, off_acc = 0, bytes = 0;
+    cudaEvent_t ev = nullptr;
+    bool busy = false;
+};
+
+struct Step {
+    cudaEvent_t ev = nullptr;
+    int slot = -1;             // continuous mode: staging slot to release
+    std::vector<Req *> finishing;
+};
+
+}  // namespace
+}  // namespace hx
+
+struct hx_server {
+    hx_ctx *ctx = nullptr;
+    hx_server_config cfg{};
+    cudaStream_t stream = nullptr;
+    std::mutex mu;
+    std::condition_variable cv_sched, cv_compl, cv_done;
+    std::deque<hx::Req *> queue;              // submitted, not yet admitted
+    std::vector<hx::Req *> active;            // admitted, not fully issued
+    std::unordered_map<uint64_t, std::unique_ptr<hx::Req>> reqs;
+    std::deque<hx::Step> steps;               // issued, not yet completed (in stream order)
+    std::vector<hx::Slot> slots;
+    std::vector<cudaEvent_t> free_events;     // per-launch mode
+    uint64_t next_id = 1;
+    size_t used = 0;
+    int inflight = 0;
+    bool stop = false;
+    hx_server_stats stats{};
+    std::thread sched, compl_thr;
+};
+
+namespace hx {
+namespace {
+
+void admit_locked(hx_server *s) {
+    const size_t budget = s->cfg.hbm_budget_bytes;
+    while (!s->queue.empty()) {
+        Req *r = s->queue.front();
+        const bool fits = budget == 0 || s->used + r->footprint <= budget;
+        if (s->inflight > 0 && (!fits || s->inflight >= s->cfg.max_inflight)) break;
+        s->queue.pop_front();
+        describe_instance(s->ctx, r->task, &r->inst, &r->partials, &r->acc_words);
+        r->admitted = true;
+        s->used += r->footprint;
+        s->inflight += 1;
+        s->stats.admitted += 1;
+        s->stats.footprint_in_flight = s->used;
+        s->stats.peak_footprint = std::max(s->stats.peak_footprint, s->used);
+        s->active.push_back(r);
+    }
+}
+
+// Outputs of requests with no device work (empty map->reduce or histogram):
+// written by small async writes on the server's stream.
+cudaError_t write_trivial(cudaStream_t st, const hx_task &t) {
+    cudaError_t e = cudaSuccess;
+    if (t.kind == HX_TASK_MAP_REDUCE) {
+        e = cudaMemsetAsync(t.u.mr.sum, 0, sizeof(float), st);
+        if (e == cudaSuccess && t.u.mr.sum64) e = cudaMemsetAsync(t.u.mr.sum64, 0, sizeof(double), st);
+    } else if (t.kind == HX_TASK_HISTOGRAM) {
+        e = cudaMemsetAsync(t.u.hi.bins, 0, 256 * sizeof(uint32_t), st);
+        if (e == cudaSuccess && t.u.hi.scan) e = cudaMemsetAsync(t.u.hi.scan, 0, 256 * sizeof(uint32_t), st);
+    }
+    return e;
+}
+
+void fail_requests_locked(hx_server *s, std::vector<Req *> &rs, hx_status st) {
+    for (Req *r : rs) {
+        r->status = st;
+        r->issued_all = true;
+        r->done = true;
+        s->used -= r->footprint;
+        s->inflight -= 1;
+        s->stats.failed += 1;
+        s->stats.completed += 1;
+    }
+    s->stats.footprint_in_flight = s->used;
+    s->cv_done.notify_all();
+}
+
+// Continuous mode: build one step from the admitted requests' next work.
+bool issue_step_locked(hx_server *s) {
+    int slot = -1;
+    for (size_t i = 0; i < s->slots.size(); ++i)
+        if (!s->slots[i].busy) { slot = (int)i; break; }
+    if (slot < 0 || (int)s->steps.size() >= s->cfg.max_steps_in_flight) return false;
+    Slot &sl = s->slots[slot];
+    std::vector<BInst> insts;
+    std::vector<unsigned long long> cta;
+    std::vector<uint4> runs;
+    Step step;
+    int64_t p_used = 0;
+    // Requests that do not fit this step stay in `active` for the next one.
+    for (Req *r : s->active) {
+        if (r->issued_all) continue;
+        const bool full = (int)insts.size() >= s->cfg.max_step_requests;
+        if (!full && r->inst.tiles == 0) {           // nothing to run on the device
+            if (write_trivial(s->stream, r->task) != cudaSuccess) r->status = HX_ERR_CUDA;
+            r->issued_all = true;
+            step.finishing.push_back(r);
+            continue;
+        }
+        const size_t cta0 = cta.size(), runs0 = runs.size();
+        BInst I = r->inst;
+        const unsigned idx = (unsigned)insts.size();
+        if (full || p_used + r->partials > (int64_t)kStepPartials) continue;
+        I.sweep0 = (I.kind == kKindStencil) ? r->issued_sweeps : 0;
+        append_round(s->ctx, I, idx, &cta, &runs);
+        if (cta.size() > kStepCtaItems || runs.size() > kStepRuns) {
+            cta.resize(cta0);
+            runs.resize(runs0);
+            continue;
+        }
+        I.partials = reinterpret_cast<float2 *>(sl.d + sl.off_part) + p_used;
+        I.ticket = reinterpret_cast<unsigned int *>(sl.d + sl.off_tick) + idx;
+        I.acc = reinterpret_cast<unsigned int *>(sl.d + sl.off_acc) + (size_t)idx * kAccPerInst;
+        p_used += r->partials;
+        insts.push_back(I);
+        if (I.kind == kKindStencil) {
+            r->issued_sweeps += 1;
+            if (r->issued_sweeps >= r->inst.iters) {
+                r->issued_all = true;
+                step.finishing.push_back(r);
+            }
+        } else {
+            r->issued_all = true;
+            step.finishing.push_back(r);
+        }
+    }
+    if (insts.empty() && step.finishing.empty()) return false;
+    std::vector<Req *> issued_now = step.finishing;
+    s->active.erase(std::remove_if(s->active.begin(), s->active.end(), [](Req *r) { return r->issued_all; }),
+                    s->active.end());
+    hx_status st = HX_OK;
+    if (!insts.empty()) {
+        memcpy(sl.h, insts.data(), insts.size() * sizeof(BInst));
+        if (!cta.empty()) memcpy(sl.h + sl.off_cta, cta.data(), cta.size() * sizeof(unsigned long long));
+        if (!runs.empty()) memcpy(sl.h + sl.off_runs, runs.data(), runs.size() * sizeof(uint4));
+        const size_t upload = sl.off_runs + runs.size() * sizeof(uint4);
+        cudaError_t e = cudaMemcpyAsync(sl.d, sl.h, upload, cudaMemcpyHostToDevice, s->stream);
+        if (e != cudaSuccess) st = cuda_fail(e, "server: step upload");
+        if (st == HX_OK)
+            st = launch_batch_round(s->ctx, reinterpret_cast<const BInst *>(sl.d),
+                                    reinterpret_cast<const unsigned long long *>(sl.d + sl.off_cta), (uint32_t)cta.size(),
+                                    reinterpret_cast<const uint4 *>(sl.d + sl.off_runs), (uint32_t)runs.size(), 0,
+                                    s->stream);
+        s->stats.launches += 1;
+    }
+    if (st == HX_OK && cudaEventRecord(sl.ev, s->stream) != cudaSuccess) st = HX_ERR_CUDA;
+    if (st != HX_OK) {
+        fail_requests_locked(s, issued_now, st);
+        return true;
+    }
+    sl.busy = true;
+    step.ev = sl.ev;
+    step.slot = slot;
+    s->steps.push_back(std::move(step));
+    s->cv_compl.notify_one();
+    return true;
+}
+
+// Per-launch mode: each admitted request as its own standalone call(s).
+bool issue_per_launch_locked(hx_server *s) {
+    bool any = false;
+    for (Req *r : s->active) {
+        const hx_task &t = r->task;
+        hx_status st = HX_OK;
+        if (t.kind == HX_TASK_MAP_REDUCE)
+            st = hx_map_reduce(s->ctx, t.u.mr.x, t.u.mr.y, t.u.mr.out, t.u.mr.a, t.u.mr.n, t.u.mr.sum, t.u.mr.sum64,
+                               (hx_stream_t)s->stream);
+        else if (t.kind == HX_TASK_STENCIL2D)
+            st = hx_stencil2d(s->ctx, t.u.st.u0, t.u.st.u1, t.u.st.nx, t.u.st.ny, t.u.st.iters, t.u.st.resid, nullptr,
+                              (hx_stream_t)s->stream);
+        else
+            st = hx_histogram(s->ctx, t.u.hi.v, t.u.hi.n, t.u.hi.bins, t.u.hi.scan, (hx_stream_t)s->stream);
+        s->stats.launches += 1;
+        r->issued_all = true;
+        cudaEvent_t ev = nullptr;
+        if (!s->free_events.empty()) {
+            ev = s->free_events.back();
+            s->free_events.pop_back();
+        } else if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+            st = HX_ERR_CUDA;
+        }
+        if (st == HX_OK && cudaEventRecord(ev, s->stream) != cudaSuccess) st = HX_ERR_CUDA;
+        std::vector<Req *> one{r};
+        if (st != HX_OK) {
+            if (ev) s->free_events.push_back(ev);
+            fail_requests_locked(s, one, st);
+        } else {
+            Step step;
+            step.ev = ev;
+            step.finishing = one;
+            s->steps.push_back(std::move(step));
+        }
+        any = true;
+    }
+    s->active.clear();
+    if (any) s->cv_compl.notify_one();
+    return any;
+}
+
+void scheduler_main(hx_server *s) {
+    cudaSetDevice(s->ctx->device);
+    std::unique_lock<std::mutex> lk(s->mu);
+    for (;;) {
+        admit_locked(s);
+        if (s->stop && s->queue.empty() && s->active.empty()) break;
+        bool issued = false;
+        if (!s->active.empty())
+            issued = s->cfg.mode == HX_SERVE_CONTINUOUS ? issue_step_locked(s) : issue_per_launch_locked(s);
+        if (!issued) s->cv_sched.wait_for(lk, std::chrono::microseconds(200));
+    }
+    s->cv_compl.notify_all();
+}
+
+void completer_main(hx_server *s) {
+    cudaSetDevice(s->ctx->device);
+    std::unique_lock<std::mutex> lk(s->mu);
+    for (;;) {
+        while (s->steps.empty()) {
+            if (s->stop && s->queue.empty() && s->active.empty()) return;
+            s->cv_compl.wait_for(lk, std::chrono::milliseconds(5));
+        }
+        cudaEvent_t ev = s->steps.front().ev;
+        lk.unlock();
+        const cudaError_t e = cudaEventSynchronize(ev);
+        const double t = now_s();
+        lk.lock();
+        Step step = std::move(s->steps.front());
+        s->steps.pop_front();
+        for (Req *r : step.finishing) {
+            if (e != cudaSuccess) r->status = HX_ERR_CUDA;
+            if (r->status != HX_OK) s->stats.failed += 1;
+            r->latency = t - r->arrival;
+            r->done = true;
+            s->used -= r->footprint;
+            s->inflight -= 1;
+            s->stats.completed += 1;
+        }
+        s->stats.footprint_in_flight = s->used;
+        if (step.slot >= 0) s->slots[step.slot].busy = false;
+        else s->free_events.push_back(step.ev);
+        s->cv_sched.notify_all();
+        s->cv_done.notify_all();
+    }
+}
+
+hx_status submit_at(hx_server *s, const hx_task *task, double arrival, uint64_t *req_id) {
+    if (!s || !task) return fail(HX_ERR_INVALID, "hx_server_submit: NULL argument");
+    hx_status st = validate_task(*task, 0, "hx_server_submit");
+    if (st != HX_OK) return st;
+    auto r = std::make_unique<Req>();
+    r->task = *task;
+    r->arrival = arrival;
+    r->footprint = task_footprint(*task);
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->stop) return fail(HX_ERR_INVALID, "hx_server_submit: server is stopping");
+    r->id = s->next_id++;
+    if (req_id) *req_id = r->id;
+    s->queue.push_back(r.get());
+    s->reqs[r->id] = std::move(r);
+    s->stats.submitted += 1;
+    s->cv_sched.notify_one();
+    return HX_OK;
+}
+
+}  // namespace
+}  // namespace hx
+
+extern "C" {
+
+hx_status hx_server_create(hx_ctx *ctx, const hx_server_config *cfg, hx_server **out) {
+    using namespace hx;
+    if (!ctx || !cfg || !out) return fail(HX_ERR_INVALID, "hx_server_create: NULL argument");
+    *out = nullptr;
+    if (cfg->mode != HX_SERVE_CONTINUOUS && cfg->mode != HX_SERVE_PER_LAUNCH)
+        return fail(HX_ERR_INVALID, "hx_server_create: unknown mode");
+    if (cfg->max_inflight < 0 || cfg->max_steps_in_flight < 0 || cfg->max_step_requests < 0 ||
+        cfg->max_step_requests > 65536)
+        return fail(HX_ERR_INVALID, "hx_server_create: bad limits");
+    DeviceGuard g(ctx->device);
+    hx_server *s = new (std::nothrow) hx_server();
+    if (!s) return fail(HX_ERR_NOMEM, "hx_server_create: host allocation failed");
+    s->ctx = ctx;
+    s->cfg = *cfg;
+    if (s->cfg.max_inflight == 0) s->cfg.max_inflight = 65536;
+    if (s->cfg.hbm_budget_bytes == 0) s->cfg.hbm_budget_bytes = ctx->hbm_budget;
+    if (s->cfg.max_steps_in_flight == 0) s->cfg.max_steps_in_flight = 2;
+    if (s->cfg.max_step_requests == 0) s->cfg.max_step_requests = 4096;
+    cudaError_t e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        delete s;
+        return cuda_fail(e, "hx_server_create: stream");
+    }
+    if (s->cfg.mode == HX_SERVE_CONTINUOUS) {
+        auto align = [](size_t v) { return (v + 255) & ~(size_t)255; };
+        const size_t K = (size_t)s->cfg.max_step_requests;
+        s->slots.resize((size_t)s->cfg.max_steps_in_flight + 1);
+        for (Slot &sl : s->slots) {
+            sl.off_cta = align(K * sizeof(BInst));
+            sl.off_runs = sl.off_cta + align(kStepCtaItems * sizeof(unsigned long long));
+            sl.off_part = sl.off_runs + align(kStepRuns * sizeof(uint4));
+            sl.off_tick = sl.off_part + align(kStepPartials * sizeof(float2));
+            sl.off_acc = sl.off_tick + align(K * sizeof(unsigned int));
+            sl.bytes = sl.off_acc + align(K * kAccPerInst * sizeof(unsigned int));
+            if (e == cudaSuccess) e = cudaMallocHost(&sl.h, sl.off_part);
+            if (e == cudaSuccess) e = cudaMalloc(&sl.d, sl.bytes);
+            if (e == cudaSuccess) e = cudaMemset(sl.d, 0, sl.bytes);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming);
+        }
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    }
+    if (e != cudaSuccess) {
+        for (Slot &sl : s->slots) {
+            if (sl.h) cudaFreeHost(sl.h);
+            if (sl.d) cudaFree(sl.d);
+            if (sl.ev) cudaEventDestroy(sl.ev);
+        }
+        cudaStreamDestroy(s->stream);
+        delete s;
+        return cuda_fail(e, "hx_server_create: staging");
+    }
+    s->sched = std::thread(scheduler_main, s);
+    s->compl_thr = std::thread(completer_main, s);
+    *out = s;
+    return HX_OK;
+}
+
+void hx_server_destroy(hx_server *s) {
+    if (!s) return;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop = true;
+    }
+    s->cv_sched.notify_all();
+    s->cv_compl.notify_all();
+    if (s->sched.joinable()) s->sched.join();
+    if (s->compl_thr.joinable()) s->compl_thr.join();
+    hx::DeviceGuard g(s->ctx->device);
+    cudaStreamSynchronize(s->stream);
+    for (hx::Slot &sl : s->slots) {
+        if (sl.h) cudaFreeHost(sl.h);
+        if (sl.d) cudaFree(sl.d);
+        if (sl.ev) cudaEventDestroy(sl.ev);
+    }
+    for (cudaEvent_t ev : s->free_events) cudaEventDestroy(ev);
+    cudaStreamDestroy(s->stream);
+    delete s;
+}
+
+hx_status hx_server_submit(hx_server *s, const hx_task *task, uint64_t *req_id) {
+    return hx::submit_at(s, task, hx::now_s(), req_id);
+}
+
+hx_status hx_server_poll(hx_server *s, uint64_t req_id, double *latency_s) {
+    if (!s) return hx::fail(HX_ERR_INVALID, "hx_server_poll: server is NULL");
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->reqs.find(req_id);
+    if (it == s->reqs.end()) return hx::fail(HX_ERR_INVALID, "hx_server_poll: unknown request id");
+    const hx::Req &r = *it->second;
+    if (!r.done) return HX_ERR_BUSY;
+    if (latency_s) *latency_s = r.latency;
+    if (r.status != HX_OK) return hx::fail(r.status, "hx_server_poll: the request's launch failed");
+    return HX_OK;
+}
+
+hx_status hx_server_drain(hx_server *s, double timeout_s) {
+    if (!s) return hx::fail(HX_ERR_INVALID, "hx_server_drain: server is NULL");
+    std::unique_lock<std::mutex> lk(s->mu);
+    const auto deadline = std::chrono::steady_clock::now() + std::chrono::duration<double>(timeout_s);
+    while (s->stats.completed < s->stats.submitted) {
+        if (s->cv_done.wait_until(lk, deadline) == std::cv_status::timeout &&
+            s->stats.completed < s->stats.submitted)
+            return hx::fail(HX_ERR_TIMEOUT, "hx_server_drain: requests still pending at the timeout");
+    }
+    return s->stats.failed ? hx::fail(HX_ERR_CUDA, "hx_server_drain: some launches failed") : HX_OK;
+}
+
+hx_status hx_server_get_stats(hx_server *s, hx_server_stats *out) {
+    if (!s || !out) return hx::fail(HX_ERR_INVALID, "hx_server_get_stats: NULL argument");
+    std::lock_guard<std::mutex> lk(s->mu);
+    *out = s->stats;
+    return HX_OK;
+}
+
+hx_status hx_server_run_trace(hx_server *s, const hx_task *tasks, const double *arrival_s, int32_t n,
+                              double timeout_s, double *latency_s, double *makespan_s) {
+    using namespace hx;
+    if (!s || n < 0 || (n > 0 && (!tasks || !arrival_s || !latency_s)))
+        return fail(HX_ERR_INVALID, "hx_server_run_trace: bad arguments");
+    for (int i = 0; i < n; ++i) {
+        hx_status st = validate_task(tasks[i], i, "hx_server_run_trace");
+        if (st != HX_OK) return st;
+        if (i > 0 && arrival_s[i] < arrival_s[i - 1])
+            return fail(HX_ERR_INVALID, "hx_server_run_trace: arrival times must be non-decreasing");
+    }
+    std::vector<uint64_t> ids(n);
+    const double t0 = now_s() + 1e-3;
+    for (int i = 0; i < n; ++i) {
+        const double target = t0 + arrival_s[i];
+        for (;;) {
+            const double left = target - now_s();
+            if (left <= 0.0) break;
+            if (left > 3e-4) std::this_thread::sleep_for(std::chrono::microseconds(100));
+        }
+        hx_status st = submit_at(s, &tasks[i], target, &ids[i]);
+        if (st != HX_OK) return st;
+    }
+    const double last = n ? t0 + arrival_s[n - 1] : t0;
+    hx_status st = hx_server_drain(s, std::max(0.0, last - now_s()) + timeout_s);
+    double end = t0;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        for (int i = 0; i < n; ++i) {
+            auto it = s->reqs.find(ids[i]);
+            if (it == s->reqs.end()) continue;
+            latency_s[i] = it->second->done ? it->second->latency : -1.0;
+            if (it->second->done) end = std::max(end, it->second->arrival + it->second->latency);
+            if (it->second->done) s->reqs.erase(it);
+        }
+    }
+    if (makespan_s) *makespan_s = end - t0;
+    return st;
+}
+
+}  // extern "C"

@@ -1,0 +1,89 @@
+"""Serving engine: every request's result is the same alone and in the mix
+(bit-identical to its standalone call, and matching the oracle), in both the
+continuous-batching and the per-launch modes; admission respects the budget."""
+
+import numpy as np
+import pytest
+import torch
+
+import workloads
+from tests.test_gpu_batch import Inst, _same
+
+pytestmark = pytest.mark.gpu
+
+
+def _trace(count, rate, seed, hi=1 << 20, iters=5):
+    tr = workloads.serving_trace(count, rate, seed=seed, hi=hi, stencil_iters=iters)
+    for r in tr:
+        r["seed"] &= 0xFFFFFFFF
+    return tr
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_served_results_equal_alone(gpu, mode):
+    hx = gpu
+    trace = _trace(48, 30_000.0, seed=41)
+    insts = [Inst(r) for r in trace]
+    with hx.hx_create(0) as ctx:
+        with hx.Server(ctx, mode=mode) as srv:
+            lat, makespan = srv.run_trace([i.task(hx) for i in insts], [r["arrival_s"] for r in trace])
+            st = srv.stats()
+        assert st["completed"] == len(trace) and st["failed"] == 0
+        assert all(x >= 0.0 for x in lat) and makespan > 0
+        if mode == 0:
+            assert st["launches"] < len(trace)     # requests really were batched together
+        for inst in insts:
+            r = inst.result()
+            _same(r, inst.standalone(hx, ctx))
+            inst.check_oracle(r)
+
+
+def test_admission_respects_budget(gpu):
+    hx = gpu
+    trace = _trace(40, 200_000.0, seed=42, hi=1 << 19, iters=3)
+    insts = [Inst(r) for r in trace]
+    budget = 6 << 20
+    with hx.hx_create(0) as ctx:
+        tasks = [i.task(hx) for i in insts]
+        with hx.Server(ctx, mode=0, hbm_budget_bytes=budget) as srv:
+            srv.run_trace(tasks, [r["arrival_s"] for r in trace])
+            st = srv.stats()
+        biggest = max(_footprint(t) for t in tasks)
+        assert st["peak_footprint"] <= max(budget, biggest)
+        assert st["completed"] == len(trace)
+        for inst in insts:
+            inst.check_oracle(inst.result())
+
+
+def _footprint(t):
+    if t.kind == 0:
+        return t.u.mr.n * 4 * (3 if t.u.mr.out else 2) + 16
+    if t.kind == 1:
+        return t.u.st.nx * t.u.st.ny * 8 + t.u.st.iters * 4
+    return t.u.hi.n + 2048
+
+
+def test_submit_poll_drain(gpu):
+    hx = gpu
+    specs = [{"kind": "map_reduce", "n": 100_003, "a": 1.5, "seed": 1},
+             {"kind": "stencil", "nx": 130, "ny": 77, "iters": 4, "seed": 2},
+             {"kind": "histogram", "n": 65_537, "seed": 3},
+             {"kind": "map_reduce", "n": 0, "a": 1.5, "seed": 4},
+             {"kind": "stencil", "nx": 8, "ny": 8, "iters": 0, "seed": 5}]
+    insts = [Inst(s) for s in specs]
+    with hx.hx_create(0) as ctx:
+        with hx.Server(ctx) as srv:
+            ids = [srv.submit(i.task(hx)) for i in insts]
+            srv.drain(60.0)
+            for rid in ids:
+                done, lat = srv.poll(rid)
+                assert done and lat >= 0.0
+            with pytest.raises(hx.HxError):
+                srv.poll(10**9)
+            x = torch.zeros(8, device="cuda:0")
+            with pytest.raises(hx.HxError):
+                srv.submit(hx.stencil_task(x.view(2, 4), x.view(2, 4), 1, torch.zeros(1, device="cuda:0")))
+        for inst in insts[:3]:
+            inst.check_oracle(inst.result())
+        assert insts[3].s32.item() == 0.0
+        assert torch.equal(insts[4].u0, insts[4].u_init)
