@@ -413,6 +413,9 @@ def bench_hx(args, rank, world, local):
     # ---- batched vs one launch per instance, same instances, same stream
     batched = bench_batched_vs_per_launch(hx, ctx, batch, batch_tasks, stream, reps=10)
 
+    # ---- serving: continuous batching vs one launch per request
+    serving = bench_serving(hx, ctx, dev) if not args.no_serving else None
+
     # ---- end to end through the public API with pinned host buffers
     e2e = bench_e2e(args, hx, ctx, dev, x_h, y_h, u_h, v_h, batch, batch_bufs, BATCH_BYTES)
 
@@ -444,6 +447,7 @@ def bench_hx(args, rank, world, local):
         "kernels": kern,
         "cpu_baseline": cpu,
         "batched": batched,
+        "serving": serving,
         "e2e": e2e,
         "gpu_launches": launches_per_step * K,
         "clocks": clk.summary(),
@@ -455,6 +459,98 @@ def bench_hx(args, rank, world, local):
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+SERVE_RATES = (2000, 5000, 10000, 20000, 50000)
+SERVE_BUDGET = 64 << 30
+
+
+def _serve_floats(r):
+    """fp32 words of device buffers one served request needs (16-byte aligned parts)."""
+    up = lambda k: (k + 3) // 4 * 4  # noqa: E731
+    if r["kind"] == "map_reduce":
+        return 3 * up(r["n"]) + 4
+    if r["kind"] == "stencil":
+        return 2 * up(r["nx"] * r["ny"]) + up(r["iters"])
+    return up((r["n"] + 3) // 4) + 512
+
+
+def _serve_tasks(hx, arena, trace):
+    """hx tasks of a trace, each request's buffers carved from the arena in order."""
+    import torch
+
+    tasks, off = [], 0
+    for r in trace:
+        need = _serve_floats(r)
+        seg = arena[off:off + need]
+        off += need
+        if r["kind"] == "map_reduce":
+            n = r["n"]
+            m = (n + 3) // 4 * 4
+            tasks.append(hx.map_reduce_task(seg[:n], seg[m:m + n], r["a"], seg[3 * m:3 * m + 1],
+                                            out=seg[2 * m:2 * m + n]))
+        elif r["kind"] == "stencil":
+            k = r["nx"] * r["ny"]
+            m = (k + 3) // 4 * 4
+            tasks.append(hx.stencil_task(seg[:k].view(r["ny"], r["nx"]), seg[m:m + k].view(r["ny"], r["nx"]),
+                                         r["iters"], seg[2 * m:2 * m + r["iters"]]))
+        else:
+            n = r["n"]
+            m = ((n + 3) // 4 + 3) // 4 * 4      # fp32 words holding the n bytes, 16-byte aligned
+            bins = seg[m:m + 256].view(torch.int32)
+            scan = seg[m + 256:m + 512].view(torch.int32)
+            tasks.append(hx.histogram_task(seg[:m].view(torch.uint8)[:n], bins, scan))
+    return tasks
+
+
+def bench_serving(hx, ctx, dev, rates=SERVE_RATES, max_requests=4000, window_s=0.25):
+    """Open-loop Poisson serving at several offered rates, continuous batching
+    vs one launch per request, same requests, same device buffers."""
+    import torch
+
+    traces = {lam: workloads.serving_trace(int(min(max_requests, max(300, lam * window_s))), float(lam))
+              for lam in rates}
+    need = max(sum(_serve_floats(r) for r in tr) for tr in traces.values())
+    arena = torch.empty(need, dtype=torch.float32, device=dev)
+    g = torch.Generator(device=dev)
+    g.manual_seed(4)
+    arena.uniform_(-1.0, 1.0, generator=g)
+    points = []
+    for lam in rates:
+        tr = traces[lam]
+        tasks = _serve_tasks(hx, arena, tr)
+        arrivals = [r["arrival_s"] for r in tr]
+        row = {"offered_req_per_s": lam, "requests": len(tr)}
+        for name, mode in (("continuous", hx.HX_SERVE_CONTINUOUS), ("per_launch", hx.HX_SERVE_PER_LAUNCH)):
+            with hx.Server(ctx, mode=mode, hbm_budget_bytes=SERVE_BUDGET) as srv:
+                lat, makespan = srv.run_trace(tasks, arrivals, timeout_s=300.0)
+                st = srv.stats()
+            lat = np.array(lat) * 1e3
+            row[name] = {"req_per_s": round(len(tr) / makespan, 1), "p50_ms": round(float(np.percentile(lat, 50)), 4),
+                         "p99_ms": round(float(np.percentile(lat, 99)), 4), "launches": st["launches"],
+                         "peak_footprint_gb": round(st["peak_footprint"] / 2**30, 3)}
+        points.append(row)
+    del arena
+    torch.cuda.empty_cache()
+    # Equal-p99 comparison: the per-launch server's p99 at the highest rate it
+    # keeps up with (>= 95% of offered) is the latency bound; compare the
+    # highest rate each mode sustains with p99 within that bound.
+    def sustained(mode, bound):
+        ok = [p for p in points if p[mode]["req_per_s"] >= 0.95 * p["offered_req_per_s"] and p[mode]["p99_ms"] <= bound]
+        return max(ok, key=lambda p: p["offered_req_per_s"]) if ok else None
+    keep = [p for p in points if p["per_launch"]["req_per_s"] >= 0.95 * p["offered_req_per_s"]]
+    base = max(keep, key=lambda p: p["offered_req_per_s"]) if keep else points[0]
+    bound = base["per_launch"]["p99_ms"]
+    c = sustained("continuous", bound)
+    pl = sustained("per_launch", bound)
+    eq = {"p99_bound_ms": bound,
+          "per_launch_req_per_s": pl["per_launch"]["req_per_s"] if pl else None,
+          "continuous_req_per_s": c["continuous"]["req_per_s"] if c else None}
+    if eq["per_launch_req_per_s"] and eq["continuous_req_per_s"]:
+        eq["ratio"] = round(eq["continuous_req_per_s"] / eq["per_launch_req_per_s"], 3)
+    return {"mix": "1/3 map->reduce, 1/3 jacobi (20 sweeps, square side ~sqrt(n)), 1/3 histogram+scan; "
+                   "sizes log-uniform 1K-16M elements; Poisson arrivals (seed 4)",
+            "budget_gb": SERVE_BUDGET / 2**30, "points": points, "equal_p99": eq}
 
 
 def bench_batched_vs_per_launch(hx, ctx, batch, tasks, stream, reps=10):
@@ -577,6 +673,7 @@ def main():
     ap.add_argument("--impl", choices=["hx", "reference"], default="hx")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--autotune", action="store_true", help="re-measure the tuning table before timing")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving sweep")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

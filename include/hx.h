@@ -290,9 +290,10 @@ hx_status hx_batch_query(hx_ctx *ctx, uint64_t ticket);
  * Sec. 4.2 and 4.6), and runs them in one of two modes:
  *
  *   HX_SERVE_CONTINUOUS  continuous batching: a scheduler thread repeatedly
- *       forms a step out of every admitted request's next piece of work
- *       (a whole map->reduce or histogram, or the next sweep of a stencil)
- *       and runs the step as one launch of the batched kernel; up to
+ *       forms a step out of every admitted request's next slice of work (up
+ *       to step_quantum_bytes of tiles of a map->reduce or histogram, or of
+ *       the current sweep of a stencil) and runs the step as one launch of
+ *       the batched kernel; up to
  *       max_steps_in_flight steps are queued on the device, so requests that
  *       arrive while a step runs join the next one and their work overlaps
  *       with the requests already running.  Each request computes exactly
@@ -310,12 +311,15 @@ typedef enum hx_serve_mode { HX_SERVE_CONTINUOUS = 0, HX_SERVE_PER_LAUNCH = 1 } 
 
 typedef struct hx_server_config {
     int32_t mode;                 /* hx_serve_mode */
-    int32_t max_inflight;         /* admitted, unfinished requests at most (0: 65536) */
+    int32_t max_inflight;         /* admitted, unfinished requests at most (0: 4096; at most 16384;
+                                   * continuous mode keeps 34 KiB of device workspace per slot) */
     size_t hbm_budget_bytes;      /* admission budget (0: the context's budget; 0 there too: unlimited).
                                    * A request larger than the budget is admitted only when nothing else
                                    * is in flight. */
-    int32_t max_steps_in_flight;  /* continuous mode: steps queued on the device (0: 2) */
+    int32_t max_steps_in_flight;  /* continuous mode: steps queued on the device (0: 4) */
     int32_t max_step_requests;    /* continuous mode: requests per step at most (0: 4096) */
+    size_t step_quantum_bytes;    /* continuous mode: traffic one request contributes to one step at
+                                   * most (0: 32 MiB); larger requests are spread over several steps */
 } hx_server_config;
 
 typedef struct hx_server_stats {
@@ -328,8 +332,9 @@ typedef struct hx_server_stats {
 
 typedef struct hx_server hx_server;
 
-/* Start a server (its threads, its stream and, in continuous mode, about
- * 3 x 60 MiB of device staging per queued step) on ctx's device. */
+/* Start a server (its threads, its stream and, in continuous mode, one
+ * descriptor staging buffer per queued step plus 34 KiB of workspace per
+ * in-flight slot) on ctx's device. */
 hx_status hx_server_create(hx_ctx *ctx, const hx_server_config *cfg, hx_server **out);
 
 /* Wait for in-flight work, stop the threads, free the server. */

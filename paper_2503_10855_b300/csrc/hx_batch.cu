@@ -89,38 +89,57 @@ __device__ __forceinline__ void batch_resolve(const BInst *__restrict__ insts, u
     }
 }
 
+// Index i of the instance with prefix[i] <= j < prefix[i + 1] (instances
+// with no items have equal neighbours and are never returned).
+__device__ __forceinline__ unsigned int find_instance(const uint32_t *__restrict__ prefix, unsigned int n_inst,
+                                                      unsigned int j) {
+    unsigned int lo = 0, hi = n_inst;
+    while (hi - lo > 1) {
+        const unsigned int mid = (lo + hi) >> 1;
+        if (__ldg(prefix + mid) <= j) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
 // Phase 1 runs the CTA items (histogram chunks, CTA c takes items c, c + G,
-// ...); phase 2 the warp runs (warp w takes runs w, w + W, ...).  The static
-// assignment needs no shared counter; runs are small and uniform enough for
-// round-robin to balance.  A warp run is {instance, first tile, tile count};
-// it publishes once: one fence and one ticket increment by the run length.
+// ...); phase 2 the warp runs (warp w takes runs w, w + W, ...).  The work
+// list is not stored: item j belongs to the instance whose prefix range holds
+// j (binary search), and its tiles follow from the instance's slice and run
+// length, so the host only uploads one descriptor per instance.  The static
+// assignment needs no shared counter.  A run publishes once: one fence and
+// one ticket increment by the run length.
 __global__ void __launch_bounds__(kBatchThreads, 4)
-batch_kernel(const BInst *__restrict__ insts, const unsigned long long *__restrict__ cta_items,
-             unsigned int n_cta, const uint4 *__restrict__ warp_runs, unsigned int n_runs, int round) {
+batch_kernel(const BInst *__restrict__ insts, unsigned int n_inst, const uint32_t *__restrict__ cta_prefix,
+             const uint32_t *__restrict__ run_prefix, int round) {
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;");
     extern __shared__ __align__(16) unsigned int sh[];   // kHiSmemBytes when the round has CTA items
     __shared__ unsigned int wtot[kBatchThreads / kWarp];
     __shared__ int s_flag;
     const int lane = threadIdx.x & 31;
+    const unsigned int n_cta = __ldg(cta_prefix + n_inst), n_runs = __ldg(run_prefix + n_inst);
 
     for (unsigned int it = blockIdx.x; it < n_cta; it += gridDim.x) {
-        const unsigned long long item = cta_items[it];
-        batch_hist_item(insts[item >> 32], (int64_t)(item & 0xffffffffull), sh, wtot, &s_flag);
+        const unsigned int i = find_instance(cta_prefix, n_inst, it);
+        const BInst &I = insts[i];
+        batch_hist_item(I, I.t_first + (it - __ldg(cta_prefix + i)), sh, wtot, &s_flag);
     }
 
     constexpr unsigned int kWarpsPerCta = kBatchThreads / kWarp;
     const unsigned int nw = gridDim.x * kWarpsPerCta;
     unsigned int pend_inst = 0xffffffffu, pend_prev = 0u, pend_cnt = 0u;
     for (unsigned int it = blockIdx.x * kWarpsPerCta + (threadIdx.x >> 5); it < n_runs; it += nw) {
-        const uint4 run = warp_runs[it];
-        const BInst &I = insts[run.x];
+        const unsigned int i = find_instance(run_prefix, n_inst, it);
+        const BInst &I = insts[i];
+        const int64_t first = I.t_first + (int64_t)(it - __ldg(run_prefix + i)) * I.run_len;
+        const unsigned int cnt = (unsigned int)min((int64_t)I.run_len, I.t_first + I.t_count - first);
         if (I.kind == kKindMap) {
             const float *x = static_cast<const float *>(I.in0);
             const float *y = static_cast<const float *>(I.in1);
             float *out = static_cast<float *>(I.o0);
-            for (unsigned int k = 0; k < run.z; ++k) {
-                const int64_t tile = (int64_t)run.y + k;
+            for (unsigned int k = 0; k < cnt; ++k) {
+                const int64_t tile = first + k;
                 const ff part = mr_tile(x, y, out, I.a, I.plan, tile, I.vec != 0, lane);
                 if (lane == 0) I.partials[tile] = make_float2(part.hi, part.lo);
             }
@@ -129,8 +148,8 @@ batch_kernel(const BInst *__restrict__ insts, const unsigned long long *__restri
             const float *src = static_cast<const float *>((sweep & 1) ? I.in1 : I.in0);
             float *dst = const_cast<float *>(static_cast<const float *>((sweep & 1) ? I.in0 : I.in1));
             float m = 0.0f;
-            for (unsigned int k = 0; k < run.z; ++k) {
-                const unsigned int tile = run.y + k;
+            for (unsigned int k = 0; k < cnt; ++k) {
+                const unsigned int tile = (unsigned int)(first + k);
                 const int wy = (int)(tile % (unsigned int)I.tiles_y), wx = (int)(tile / (unsigned int)I.tiles_y);
                 const int c_begin = wx * 128, r_begin = wy * kBatchStRows;
                 m = fmaxf(m, I.vec ? stencil_block_vec<kBatchStRows>(src, dst, I.nx, I.ny, c_begin, r_begin)
@@ -142,12 +161,12 @@ batch_kernel(const BInst *__restrict__ insts, const unsigned long long *__restri
         unsigned int prev = 0u;
         if (lane == 0) {
             __threadfence();
-            prev = atomicAdd(I.ticket, run.z);
+            prev = atomicAdd(I.ticket, cnt);
         }
         if (pend_inst != 0xffffffffu) batch_resolve(insts, pend_inst, pend_prev, pend_cnt, round, lane);
-        pend_inst = run.x;
+        pend_inst = i;
         pend_prev = prev;
-        pend_cnt = run.z;
+        pend_cnt = cnt;
     }
     if (pend_inst != 0xffffffffu) batch_resolve(insts, pend_inst, pend_prev, pend_cnt, round, lane);
 }
@@ -167,6 +186,7 @@ void describe_instance(const hx_ctx *ctx, const hx_task &t, BInst *out, int64_t 
         I.tiles = m.n > 0 ? I.plan.tiles : 0;
         I.vec = (((uintptr_t)m.x | (uintptr_t)m.y | (uintptr_t)m.out) & 15u) == 0;
         I.in0 = m.x; I.in1 = m.y; I.o0 = m.out; I.o1 = m.sum; I.o2 = m.sum64;
+        I.run_len = ctx->tune.batch_map_run;
         *partials = I.tiles;
     } else if (t.kind == HX_TASK_STENCIL2D) {
         const auto &s = t.u.st;
@@ -178,29 +198,23 @@ void describe_instance(const hx_ctx *ctx, const hx_task &t, BInst *out, int64_t 
         I.tiles_y = (s.ny + kBatchStRows - 1) / kBatchStRows;
         I.tiles = s.iters > 0 ? (int64_t)I.tiles_x * I.tiles_y : 0;
         I.in0 = s.u0; I.in1 = s.u1; I.o0 = s.resid;
+        I.run_len = ctx->tune.batch_stencil_run;
         *acc_words = 1;
     } else {
         const auto &h = t.u.hi;
         I.n = h.n;
         I.tiles = h.n > 0 ? (h.n + kBHiTile - 1) / kBHiTile : 0;
         I.in0 = h.v; I.o0 = h.bins; I.o1 = h.scan;
+        I.run_len = 1;
         *acc_words = kHiBins;
     }
+    I.t_first = 0;
+    I.t_count = I.tiles;
 }
 
-void append_round(const hx_ctx *ctx, const BInst &I, unsigned int idx, std::vector<unsigned long long> *cta_items,
-                  std::vector<uint4> *warp_runs) {
-    if (I.kind == kKindHist) {
-        for (int64_t k = 0; k < I.tiles; ++k) cta_items->push_back(((unsigned long long)idx << 32) | (unsigned long long)k);
-        return;
-    }
-    const int64_t run = I.kind == kKindMap ? ctx->tune.batch_map_run : ctx->tune.batch_stencil_run;
-    for (int64_t k = 0; k < I.tiles; k += run)
-        warp_runs->push_back(make_uint4(idx, (unsigned)k, (unsigned)std::min<int64_t>(run, I.tiles - k), 0u));
-}
-
-hx_status launch_batch_round(const hx_ctx *ctx, const BInst *d_insts, const unsigned long long *d_cta, uint32_t n_cta,
-                             const uint4 *d_runs, uint32_t n_runs, int round, cudaStream_t stream) {
+hx_status launch_batch_round(const hx_ctx *ctx, const BInst *d_insts, uint32_t n_inst, const uint32_t *d_cta_prefix,
+                             const uint32_t *d_run_prefix, uint32_t n_cta, uint32_t n_runs, int round,
+                             cudaStream_t stream) {
     if (n_cta == 0 && n_runs == 0) return HX_OK;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -214,7 +228,7 @@ hx_status launch_batch_round(const hx_ctx *ctx, const BInst *d_insts, const unsi
     cfg.stream = stream;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    cudaError_t e = cudaLaunchKernelEx(&cfg, batch_kernel, d_insts, d_cta, n_cta, d_runs, n_runs, round);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, batch_kernel, d_insts, n_inst, d_cta_prefix, d_run_prefix, round);
     if (e != cudaSuccess) return cuda_fail(e, "batched kernel launch");
     return HX_OK;
 }
@@ -246,12 +260,11 @@ hx_status batch_setup(hx_ctx *ctx) {
 struct hx_batch {
     hx_ctx *ctx = nullptr;
     int rounds = 0;
-    std::vector<uint32_t> cta_begin;    // rounds + 1 offsets into the CTA item list
-    std::vector<uint32_t> warp_begin;   // rounds + 1 offsets into the warp run list
+    uint32_t n_inst = 0;
+    std::vector<uint32_t> n_cta, n_runs;   // per round: CTA chunks, warp runs
     void *d_mem = nullptr;
     hx::BInst *d_insts = nullptr;
-    unsigned long long *d_cta_items = nullptr;
-    uint4 *d_warp_runs = nullptr;
+    uint32_t *d_prefix = nullptr;          // per round: CTA prefix (n_inst + 1), run prefix (n_inst + 1)
 };
 
 namespace hx {
@@ -320,30 +333,35 @@ extern "C" hx_status hx_batch_plan(hx_ctx *ctx, const hx_task *tasks, int32_t n_
         n_acc += na;
         if (insts[i].kind == kKindStencil) rounds = std::max(rounds, insts[i].iters);
     }
-    // Items, round by round.  Round 0 holds the one-pass instances; stencil
-    // sweep r of each instance goes to round r.
-    std::vector<unsigned long long> cta_items;
-    std::vector<uint4> warp_items;   // runs {instance, first tile, count, 0}
-    std::vector<uint32_t> cta_begin, warp_begin;
+    // Prefix sums of each round's work, round by round.  Round 0 holds the
+    // one-pass instances; stencil sweep r of each instance goes to round r.
+    const size_t stride = (size_t)n_tasks + 1;
+    std::vector<uint32_t> prefix((size_t)rounds * 2 * stride, 0u);
+    std::vector<uint32_t> round_cta(rounds), round_runs(rounds);
     for (int r = 0; r < rounds; ++r) {
-        cta_begin.push_back((uint32_t)cta_items.size());
-        warp_begin.push_back((uint32_t)warp_items.size());
+        uint32_t *cp = prefix.data() + (size_t)r * 2 * stride, *rp = cp + stride;
+        uint64_t c = 0, w = 0;
         for (int i = 0; i < n_tasks; ++i) {
+            cp[i] = (uint32_t)c;
+            rp[i] = (uint32_t)w;
             const BInst &I = insts[i];
             const bool active = (I.kind == kKindStencil) ? (r < I.iters) : (r == 0);
-            if (active) append_round(ctx, I, (unsigned)i, &cta_items, &warp_items);
+            if (active) {
+                c += inst_ctas(I);
+                w += inst_runs(I);
+            }
         }
+        if (c > 0xffffffffull || w > 0xffffffffull) return fail(HX_ERR_INVALID, "hx_batch_plan: too many work items");
+        cp[n_tasks] = (uint32_t)c;
+        rp[n_tasks] = (uint32_t)w;
+        round_cta[r] = (uint32_t)c;
+        round_runs[r] = (uint32_t)w;
     }
-    cta_begin.push_back((uint32_t)cta_items.size());
-    warp_begin.push_back((uint32_t)warp_items.size());
-    if (cta_items.size() > 0xffffffffull || warp_items.size() > 0xffffffffull)
-        return fail(HX_ERR_INVALID, "hx_batch_plan: too many items");
 
-    // One device allocation: insts | CTA items | warp runs | partials | tickets | accumulators.
+    // One device allocation: insts | prefixes | partials | tickets | accumulators.
     auto align = [](size_t v) { return (v + 255) & ~(size_t)255; };
-    const size_t off_items = align(sizeof(BInst) * insts.size());
-    const size_t off_witems = off_items + align(sizeof(unsigned long long) * cta_items.size());
-    const size_t off_part = off_witems + align(sizeof(uint4) * warp_items.size());
+    const size_t off_pre = align(sizeof(BInst) * insts.size());
+    const size_t off_part = off_pre + align(sizeof(uint32_t) * prefix.size());
     const size_t off_tick = off_part + align(sizeof(float2) * n_partials);
     const size_t off_acc = off_tick + align(sizeof(unsigned int) * insts.size());
     const size_t total = off_acc + align(sizeof(unsigned int) * n_acc);
@@ -352,8 +370,9 @@ extern "C" hx_status hx_batch_plan(hx_ctx *ctx, const hx_task *tasks, int32_t n_
     if (!b) return fail(HX_ERR_NOMEM, "hx_batch_plan: host allocation failed");
     b->ctx = ctx;
     b->rounds = rounds;
-    b->cta_begin = cta_begin;
-    b->warp_begin = warp_begin;
+    b->n_inst = (uint32_t)n_tasks;
+    b->n_cta = round_cta;
+    b->n_runs = round_runs;
     cudaError_t e = cudaMalloc(&b->d_mem, total);
     if (e != cudaSuccess) {
         delete b;
@@ -361,8 +380,7 @@ extern "C" hx_status hx_batch_plan(hx_ctx *ctx, const hx_task *tasks, int32_t n_
     }
     char *base = static_cast<char *>(b->d_mem);
     b->d_insts = reinterpret_cast<BInst *>(base);
-    b->d_cta_items = reinterpret_cast<unsigned long long *>(base + off_items);
-    b->d_warp_runs = reinterpret_cast<uint4 *>(base + off_witems);
+    b->d_prefix = reinterpret_cast<uint32_t *>(base + off_pre);
     int64_t pcur = 0, acur = 0;
     for (int i = 0; i < n_tasks; ++i) {
         BInst &I = insts[i];
@@ -381,12 +399,8 @@ extern "C" hx_status hx_batch_plan(hx_ctx *ctx, const hx_task *tasks, int32_t n_
     e = cudaMemset(b->d_mem, 0, total);
     if (e == cudaSuccess && !insts.empty())
         e = cudaMemcpy(b->d_insts, insts.data(), sizeof(BInst) * insts.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess && !cta_items.empty())
-        e = cudaMemcpy(b->d_cta_items, cta_items.data(), sizeof(unsigned long long) * cta_items.size(),
-                       cudaMemcpyHostToDevice);
-    if (e == cudaSuccess && !warp_items.empty())
-        e = cudaMemcpy(b->d_warp_runs, warp_items.data(), sizeof(uint4) * warp_items.size(),
-                       cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !prefix.empty())
+        e = cudaMemcpy(b->d_prefix, prefix.data(), sizeof(uint32_t) * prefix.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         cudaFree(b->d_mem);
         delete b;
@@ -420,11 +434,11 @@ extern "C" hx_status hx_batch_launch(hx_batch *b, hx_stream_t stream) {
     using namespace hx;
     if (!b) return fail(HX_ERR_INVALID, "hx_batch_launch: batch is NULL");
     DeviceGuard g(b->ctx->device);
+    const size_t stride = (size_t)b->n_inst + 1;
     for (int r = 0; r < b->rounds; ++r) {
-        const uint32_t n_cta = b->cta_begin[r + 1] - b->cta_begin[r];
-        const uint32_t n_warp = b->warp_begin[r + 1] - b->warp_begin[r];
-        hx_status st = launch_batch_round(b->ctx, b->d_insts, b->d_cta_items + b->cta_begin[r], n_cta,
-                                          b->d_warp_runs + b->warp_begin[r], n_warp, r, (cudaStream_t)stream);
+        const uint32_t *cp = b->d_prefix + (size_t)r * 2 * stride;
+        hx_status st = launch_batch_round(b->ctx, b->d_insts, b->n_inst, cp, cp + stride, b->n_cta[r], b->n_runs[r],
+                                          r, (cudaStream_t)stream);
         if (st != HX_OK) return st;
     }
     return HX_OK;

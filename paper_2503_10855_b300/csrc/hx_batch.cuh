@@ -27,6 +27,10 @@ struct BInst {
     int64_t tiles;      // items per round
     int tiles_x;        // stencil warp blocks across
     int tiles_y;        // stencil warp blocks down
+    int run_len;        // map / stencil: tiles per warp run
+    int pad2;
+    int64_t t_first;    // this launch's slice: tiles (histogram: chunks) [t_first, t_first + t_count)
+    int64_t t_count;
     MrPlan plan;
     const void *in0;    // map x | stencil u0 | hist v
     const void *in1;    // map y | stencil u1
@@ -45,14 +49,19 @@ hx_status validate_task(const hx_task &t, int idx, const char *who);
 // the workspace it needs: tile partials and accumulator words.
 void describe_instance(const hx_ctx *ctx, const hx_task &t, BInst *out, int64_t *partials, int64_t *acc_words);
 
-// Appends the work items of one round of instance `idx` (the whole instance
-// for map->reduce and histogram, one sweep for a stencil) to the lists.
-void append_round(const hx_ctx *ctx, const BInst &I, unsigned int idx, std::vector<unsigned long long> *cta_items,
-                  std::vector<uint4> *warp_runs);
+// Work items of one launch of instance I (its slice [t_first, t_first +
+// t_count)): warp runs for map->reduce and stencil, CTA chunks for histogram.
+inline uint32_t inst_runs(const BInst &I) {
+    return I.kind == kKindHist ? 0u : (uint32_t)((I.t_count + I.run_len - 1) / I.run_len);
+}
+inline uint32_t inst_ctas(const BInst &I) { return I.kind == kKindHist ? (uint32_t)I.t_count : 0u; }
 
-// Launches the batched kernel for one round of an uploaded work-list.
-hx_status launch_batch_round(const hx_ctx *ctx, const BInst *d_insts, const unsigned long long *d_cta, uint32_t n_cta,
-                             const uint4 *d_runs, uint32_t n_runs, int round, cudaStream_t stream);
+// Launches the batched kernel for one round: n_inst instances, exclusive
+// prefix sums of their CTA chunks and warp runs (n_inst + 1 entries each, on
+// the device), totals n_cta and n_runs.
+hx_status launch_batch_round(const hx_ctx *ctx, const BInst *d_insts, uint32_t n_inst, const uint32_t *d_cta_prefix,
+                             const uint32_t *d_run_prefix, uint32_t n_cta, uint32_t n_runs, int round,
+                             cudaStream_t stream);
 
 // Device bytes a task's buffers occupy (inputs and outputs), for admission.
 size_t task_footprint(const hx_task &t);

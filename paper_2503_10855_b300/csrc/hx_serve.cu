@@ -29,11 +29,12 @@ double now_s() {
     return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
-// Capacities of one continuous-batching step.
-constexpr size_t kStepCtaItems = 1 << 18;   // histogram chunks (256 KiB each)
-constexpr size_t kStepRuns = 1 << 20;       // warp runs
-constexpr size_t kStepPartials = 1 << 22;   // map->reduce tile partials
-constexpr size_t kAccPerInst = kHiBins;     // accumulator words reserved per instance
+// Per-request device workspace, kept from admission to completion so that a
+// request's work can be split over several steps: tile partials, histogram
+// or residual accumulator, arrival ticket.
+constexpr size_t kWsPartials = kMrMaxTiles;
+constexpr size_t kWsAccWords = kHiBins;
+constexpr size_t kWsBytes = ((kWsPartials * sizeof(float2) + (kWsAccWords + 1) * 4) + 255) & ~(size_t)255;
 
 struct Req {
     uint64_t id = 0;
@@ -43,15 +44,17 @@ struct Req {
     size_t footprint = 0;
     BInst inst{};            // described at admission
     int64_t partials = 0, acc_words = 0;
-    int issued_sweeps = 0;   // stencil: sweeps already put in a step
+    int ws = -1;             // workspace slot
+    int sweep = 0;           // stencil: current sweep
+    int64_t issued = 0;      // tiles (chunks) of the current pass already put in a step
     bool admitted = false, issued_all = false, done = false;
     hx_status status = HX_OK;
 };
 
-struct Slot {   // staging for one step: pinned host list + device list and workspace
+struct Slot {   // staging for one step: descriptors and prefix sums, pinned host + device copy
     char *h = nullptr;
     char *d = nullptr;
-    size_t off_cta = 0, off_runs = 0, off_part = 0, off_tick = 0, off_acc = 0, bytes = 0;
+    size_t off_cta = 0, off_run = 0, bytes = 0;
     cudaEvent_t ev = nullptr;
     bool busy = false;
 };
@@ -77,6 +80,8 @@ struct hx_server {
     std::deque<hx::Step> steps;               // issued, not yet completed (in stream order)
     std::vector<hx::Slot> slots;
     std::vector<cudaEvent_t> free_events;     // per-launch mode
+    char *ws_pool = nullptr;                  // continuous mode: max_inflight workspace slots
+    std::vector<int> free_ws;
     uint64_t next_id = 1;
     size_t used = 0;
     int inflight = 0;
@@ -96,6 +101,14 @@ void admit_locked(hx_server *s) {
         if (s->inflight > 0 && (!fits || s->inflight >= s->cfg.max_inflight)) break;
         s->queue.pop_front();
         describe_instance(s->ctx, r->task, &r->inst, &r->partials, &r->acc_words);
+        if (s->cfg.mode == HX_SERVE_CONTINUOUS) {
+            r->ws = s->free_ws.back();
+            s->free_ws.pop_back();
+            char *w = s->ws_pool + (size_t)r->ws * kWsBytes;
+            r->inst.partials = reinterpret_cast<float2 *>(w);
+            r->inst.acc = reinterpret_cast<unsigned int *>(w + kWsPartials * sizeof(float2));
+            r->inst.ticket = r->inst.acc + kWsAccWords;
+        }
         r->admitted = true;
         s->used += r->footprint;
         s->inflight += 1;
@@ -127,6 +140,8 @@ void fail_requests_locked(hx_server *s, std::vector<Req *> &rs, hx_status st) {
         r->done = true;
         s->used -= r->footprint;
         s->inflight -= 1;
+        if (r->ws >= 0) s->free_ws.push_back(r->ws);
+        r->ws = -1;
         s->stats.failed += 1;
         s->stats.completed += 1;
     }
@@ -134,71 +149,76 @@ void fail_requests_locked(hx_server *s, std::vector<Req *> &rs, hx_status st) {
     s->cv_done.notify_all();
 }
 
-// Continuous mode: build one step from the admitted requests' next work.
+// Bytes of traffic one tile (histogram: one chunk) of an instance moves.
+int64_t tile_bytes(const BInst &I) {
+    if (I.kind == kKindMap) return 12 * I.plan.tile_elems;
+    if (I.kind == kKindStencil) return 8 * 128 * kBatchStRows;
+    return kBHiTile;
+}
+
+// Continuous mode: build one step out of the next slice of every admitted
+// request (at most step_quantum_bytes of traffic each; a stencil slice never
+// crosses a sweep boundary), upload its descriptors and prefix sums, launch.
 bool issue_step_locked(hx_server *s) {
     int slot = -1;
     for (size_t i = 0; i < s->slots.size(); ++i)
         if (!s->slots[i].busy) { slot = (int)i; break; }
     if (slot < 0 || (int)s->steps.size() >= s->cfg.max_steps_in_flight) return false;
     Slot &sl = s->slots[slot];
-    std::vector<BInst> insts;
-    std::vector<unsigned long long> cta;
-    std::vector<uint4> runs;
+    BInst *insts = reinterpret_cast<BInst *>(sl.h);
+    uint32_t *cp = reinterpret_cast<uint32_t *>(sl.h + sl.off_cta);
+    uint32_t *rp = reinterpret_cast<uint32_t *>(sl.h + sl.off_run);
+    uint32_t n = 0;
+    uint64_t c = 0, w = 0;
     Step step;
-    int64_t p_used = 0;
-    // Requests that do not fit this step stay in `active` for the next one.
     for (Req *r : s->active) {
         if (r->issued_all) continue;
-        const bool full = (int)insts.size() >= s->cfg.max_step_requests;
-        if (!full && r->inst.tiles == 0) {           // nothing to run on the device
+        if (r->inst.tiles == 0) {                     // nothing to run on the device
             if (write_trivial(s->stream, r->task) != cudaSuccess) r->status = HX_ERR_CUDA;
             r->issued_all = true;
             step.finishing.push_back(r);
             continue;
         }
-        const size_t cta0 = cta.size(), runs0 = runs.size();
+        if ((int)n >= s->cfg.max_step_requests) continue;
         BInst I = r->inst;
-        const unsigned idx = (unsigned)insts.size();
-        if (full || p_used + r->partials > (int64_t)kStepPartials) continue;
-        I.sweep0 = (I.kind == kKindStencil) ? r->issued_sweeps : 0;
-        append_round(s->ctx, I, idx, &cta, &runs);
-        if (cta.size() > kStepCtaItems || runs.size() > kStepRuns) {
-            cta.resize(cta0);
-            runs.resize(runs0);
-            continue;
-        }
-        I.partials = reinterpret_cast<float2 *>(sl.d + sl.off_part) + p_used;
-        I.ticket = reinterpret_cast<unsigned int *>(sl.d + sl.off_tick) + idx;
-        I.acc = reinterpret_cast<unsigned int *>(sl.d + sl.off_acc) + (size_t)idx * kAccPerInst;
-        p_used += r->partials;
-        insts.push_back(I);
-        if (I.kind == kKindStencil) {
-            r->issued_sweeps += 1;
-            if (r->issued_sweeps >= r->inst.iters) {
-                r->issued_all = true;
-                step.finishing.push_back(r);
-            }
-        } else {
+        const int64_t q = std::max<int64_t>(1, (int64_t)s->cfg.step_quantum_bytes / tile_bytes(I));
+        I.t_first = r->issued;
+        I.t_count = std::min<int64_t>(q, I.tiles - r->issued);
+        I.sweep0 = I.kind == kKindStencil ? r->sweep : 0;
+        if (c + inst_ctas(I) > 0xffffffffull || w + inst_runs(I) > 0xffffffffull) continue;
+        cp[n] = (uint32_t)c;
+        rp[n] = (uint32_t)w;
+        c += inst_ctas(I);
+        w += inst_runs(I);
+        insts[n++] = I;
+        r->issued += I.t_count;
+        if (r->issued == I.tiles) {
+            r->issued = 0;
+            if (I.kind == kKindStencil && ++r->sweep < I.iters) continue;
             r->issued_all = true;
             step.finishing.push_back(r);
         }
     }
-    if (insts.empty() && step.finishing.empty()) return false;
+    if (n == 0 && step.finishing.empty()) return false;
+    cp[n] = (uint32_t)c;
+    rp[n] = (uint32_t)w;
     std::vector<Req *> issued_now = step.finishing;
     s->active.erase(std::remove_if(s->active.begin(), s->active.end(), [](Req *r) { return r->issued_all; }),
                     s->active.end());
     hx_status st = HX_OK;
-    if (!insts.empty()) {
-        memcpy(sl.h, insts.data(), insts.size() * sizeof(BInst));
-        if (!cta.empty()) memcpy(sl.h + sl.off_cta, cta.data(), cta.size() * sizeof(unsigned long long));
-        if (!runs.empty()) memcpy(sl.h + sl.off_runs, runs.data(), runs.size() * sizeof(uint4));
-        const size_t upload = sl.off_runs + runs.size() * sizeof(uint4);
-        cudaError_t e = cudaMemcpyAsync(sl.d, sl.h, upload, cudaMemcpyHostToDevice, s->stream);
+    if (n > 0) {
+        // descriptors, then the two prefix arrays (n + 1 entries each) right after them
+        const size_t di = (size_t)n * sizeof(BInst);
+        cudaError_t e = cudaMemcpyAsync(sl.d, sl.h, di, cudaMemcpyHostToDevice, s->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(sl.d + sl.off_cta, sl.h + sl.off_cta, (n + 1) * 4, cudaMemcpyHostToDevice, s->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(sl.d + sl.off_run, sl.h + sl.off_run, (n + 1) * 4, cudaMemcpyHostToDevice, s->stream);
         if (e != cudaSuccess) st = cuda_fail(e, "server: step upload");
         if (st == HX_OK)
-            st = launch_batch_round(s->ctx, reinterpret_cast<const BInst *>(sl.d),
-                                    reinterpret_cast<const unsigned long long *>(sl.d + sl.off_cta), (uint32_t)cta.size(),
-                                    reinterpret_cast<const uint4 *>(sl.d + sl.off_runs), (uint32_t)runs.size(), 0,
+            st = launch_batch_round(s->ctx, reinterpret_cast<const BInst *>(sl.d), n,
+                                    reinterpret_cast<const uint32_t *>(sl.d + sl.off_cta),
+                                    reinterpret_cast<const uint32_t *>(sl.d + sl.off_run), (uint32_t)c, (uint32_t)w, 0,
                                     s->stream);
         s->stats.launches += 1;
     }
@@ -292,6 +312,8 @@ void completer_main(hx_server *s) {
             r->done = true;
             s->used -= r->footprint;
             s->inflight -= 1;
+            if (r->ws >= 0) s->free_ws.push_back(r->ws);
+            r->ws = -1;
             s->stats.completed += 1;
         }
         s->stats.footprint_in_flight = s->used;
@@ -332,18 +354,19 @@ hx_status hx_server_create(hx_ctx *ctx, const hx_server_config *cfg, hx_server *
     *out = nullptr;
     if (cfg->mode != HX_SERVE_CONTINUOUS && cfg->mode != HX_SERVE_PER_LAUNCH)
         return fail(HX_ERR_INVALID, "hx_server_create: unknown mode");
-    if (cfg->max_inflight < 0 || cfg->max_steps_in_flight < 0 || cfg->max_step_requests < 0 ||
-        cfg->max_step_requests > 65536)
+    if (cfg->max_inflight < 0 || cfg->max_inflight > 16384 || cfg->max_steps_in_flight < 0 ||
+        cfg->max_steps_in_flight > 64 || cfg->max_step_requests < 0 || cfg->max_step_requests > 65536)
         return fail(HX_ERR_INVALID, "hx_server_create: bad limits");
     DeviceGuard g(ctx->device);
     hx_server *s = new (std::nothrow) hx_server();
     if (!s) return fail(HX_ERR_NOMEM, "hx_server_create: host allocation failed");
     s->ctx = ctx;
     s->cfg = *cfg;
-    if (s->cfg.max_inflight == 0) s->cfg.max_inflight = 65536;
+    if (s->cfg.max_inflight == 0) s->cfg.max_inflight = 4096;
     if (s->cfg.hbm_budget_bytes == 0) s->cfg.hbm_budget_bytes = ctx->hbm_budget;
-    if (s->cfg.max_steps_in_flight == 0) s->cfg.max_steps_in_flight = 2;
+    if (s->cfg.max_steps_in_flight == 0) s->cfg.max_steps_in_flight = 4;
     if (s->cfg.max_step_requests == 0) s->cfg.max_step_requests = 4096;
+    if (s->cfg.step_quantum_bytes == 0) s->cfg.step_quantum_bytes = (size_t)32 << 20;
     cudaError_t e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
         delete s;
@@ -355,16 +378,16 @@ hx_status hx_server_create(hx_ctx *ctx, const hx_server_config *cfg, hx_server *
         s->slots.resize((size_t)s->cfg.max_steps_in_flight + 1);
         for (Slot &sl : s->slots) {
             sl.off_cta = align(K * sizeof(BInst));
-            sl.off_runs = sl.off_cta + align(kStepCtaItems * sizeof(unsigned long long));
-            sl.off_part = sl.off_runs + align(kStepRuns * sizeof(uint4));
-            sl.off_tick = sl.off_part + align(kStepPartials * sizeof(float2));
-            sl.off_acc = sl.off_tick + align(K * sizeof(unsigned int));
-            sl.bytes = sl.off_acc + align(K * kAccPerInst * sizeof(unsigned int));
-            if (e == cudaSuccess) e = cudaMallocHost(&sl.h, sl.off_part);
+            sl.off_run = sl.off_cta + align((K + 1) * 4);
+            sl.bytes = sl.off_run + align((K + 1) * 4);
+            if (e == cudaSuccess) e = cudaMallocHost(&sl.h, sl.bytes);
             if (e == cudaSuccess) e = cudaMalloc(&sl.d, sl.bytes);
-            if (e == cudaSuccess) e = cudaMemset(sl.d, 0, sl.bytes);
             if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming);
         }
+        const size_t pool = (size_t)s->cfg.max_inflight * kWsBytes;
+        if (e == cudaSuccess) e = cudaMalloc(&s->ws_pool, pool);
+        if (e == cudaSuccess) e = cudaMemset(s->ws_pool, 0, pool);
+        for (int i = s->cfg.max_inflight - 1; i >= 0; --i) s->free_ws.push_back(i);
         if (e == cudaSuccess) e = cudaDeviceSynchronize();
     }
     if (e != cudaSuccess) {
@@ -373,6 +396,7 @@ hx_status hx_server_create(hx_ctx *ctx, const hx_server_config *cfg, hx_server *
             if (sl.d) cudaFree(sl.d);
             if (sl.ev) cudaEventDestroy(sl.ev);
         }
+        if (s->ws_pool) cudaFree(s->ws_pool);
         cudaStreamDestroy(s->stream);
         delete s;
         return cuda_fail(e, "hx_server_create: staging");
@@ -401,6 +425,7 @@ void hx_server_destroy(hx_server *s) {
         if (sl.ev) cudaEventDestroy(sl.ev);
     }
     for (cudaEvent_t ev : s->free_events) cudaEventDestroy(ev);
+    if (s->ws_pool) cudaFree(s->ws_pool);
     cudaStreamDestroy(s->stream);
     delete s;
 }

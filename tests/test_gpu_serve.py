@@ -38,6 +38,23 @@ def test_served_results_equal_alone(gpu, mode):
             inst.check_oracle(r)
 
 
+def test_sliced_requests_equal_alone(gpu):
+    # a 64 KiB quantum spreads every request over many steps (slices of map
+    # tiles, histogram chunks and stencil sweeps)
+    hx = gpu
+    trace = _trace(24, 50_000.0, seed=43, hi=1 << 20, iters=3)
+    insts = [Inst(r) for r in trace]
+    with hx.hx_create(0) as ctx:
+        with hx.Server(ctx, mode=0, step_quantum_bytes=64 << 10, max_steps_in_flight=3) as srv:
+            srv.run_trace([i.task(hx) for i in insts], [r["arrival_s"] for r in trace])
+            st = srv.stats()
+        assert st["launches"] > len(trace)
+        for inst in insts:
+            r = inst.result()
+            _same(r, inst.standalone(hx, ctx))
+            inst.check_oracle(r)
+
+
 def test_admission_respects_budget(gpu):
     hx = gpu
     trace = _trace(40, 200_000.0, seed=42, hi=1 << 19, iters=3)
