@@ -318,8 +318,11 @@ typedef struct hx_server_config {
                                    * is in flight. */
     int32_t max_steps_in_flight;  /* continuous mode: steps queued on the device (0: 4) */
     int32_t max_step_requests;    /* continuous mode: requests per step at most (0: 4096) */
-    size_t step_quantum_bytes;    /* continuous mode: traffic one request contributes to one step at
-                                   * most (0: 32 MiB); larger requests are spread over several steps */
+    size_t step_quantum_bytes;    /* continuous mode: each step aims at step_target_bytes of traffic
+                                   * shared by its requests; a request's slice is that share, but at
+                                   * least step_quantum_bytes (0: 32 MiB).  Larger requests are spread
+                                   * over several steps. */
+    size_t step_target_bytes;     /* continuous mode (0: 512 MiB) */
 } hx_server_config;
 
 typedef struct hx_server_stats {

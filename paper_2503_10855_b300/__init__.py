@@ -418,7 +418,8 @@ HX_SERVE_CONTINUOUS, HX_SERVE_PER_LAUNCH = 0, 1
 
 class ServerConfig(ctypes.Structure):
     _fields_ = [("mode", _I32), ("max_inflight", _I32), ("hbm_budget_bytes", ctypes.c_size_t),
-                ("max_steps_in_flight", _I32), ("max_step_requests", _I32), ("step_quantum_bytes", ctypes.c_size_t)]
+                ("max_steps_in_flight", _I32), ("max_step_requests", _I32), ("step_quantum_bytes", ctypes.c_size_t),
+                ("step_target_bytes", ctypes.c_size_t)]
 
 
 class ServerStats(ctypes.Structure):
@@ -452,9 +453,9 @@ class Server:
 
     def __init__(self, ctx: Context, mode: int = HX_SERVE_CONTINUOUS, hbm_budget_bytes: int = 0,
                  max_inflight: int = 0, max_steps_in_flight: int = 0, max_step_requests: int = 0,
-                 step_quantum_bytes: int = 0):
+                 step_quantum_bytes: int = 0, step_target_bytes: int = 0):
         cfg = ServerConfig(mode, max_inflight, hbm_budget_bytes, max_steps_in_flight, max_step_requests,
-                           step_quantum_bytes)
+                           step_quantum_bytes, step_target_bytes)
         h = _P()
         _check(_lib.hx_server_create(ctx.handle, ctypes.byref(cfg), ctypes.byref(h)), "hx_server_create")
         self.ctx = ctx

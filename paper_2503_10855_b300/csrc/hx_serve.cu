@@ -54,7 +54,7 @@ struct Req {
 struct Slot {   // staging for one step: descriptors and prefix sums, pinned host + device copy
     char *h = nullptr;
     char *d = nullptr;
-    size_t off_cta = 0, off_run = 0, bytes = 0;
+    size_t bytes = 0;
     cudaEvent_t ev = nullptr;
     bool busy = false;
 };
@@ -165,12 +165,21 @@ bool issue_step_locked(hx_server *s) {
         if (!s->slots[i].busy) { slot = (int)i; break; }
     if (slot < 0 || (int)s->steps.size() >= s->cfg.max_steps_in_flight) return false;
     Slot &sl = s->slots[slot];
+    // Staging layout, uploaded with one copy: descriptors, then the CTA and
+    // run prefix arrays (n + 1 entries each), placed after the step is built.
     BInst *insts = reinterpret_cast<BInst *>(sl.h);
-    uint32_t *cp = reinterpret_cast<uint32_t *>(sl.h + sl.off_cta);
-    uint32_t *rp = reinterpret_cast<uint32_t *>(sl.h + sl.off_run);
+    std::vector<uint32_t> cpv, rpv;
+    cpv.reserve(s->active.size() + 1);
+    rpv.reserve(s->active.size() + 1);
     uint32_t n = 0;
     uint64_t c = 0, w = 0;
     Step step;
+    // Slice size: the step aims at step_target_bytes of traffic shared by the
+    // requests in it, but each gets at least step_quantum_bytes.
+    size_t n_work = 0;
+    for (Req *r : s->active) n_work += (!r->issued_all && r->inst.tiles > 0) ? 1 : 0;
+    n_work = std::min<size_t>(std::max<size_t>(n_work, 1), (size_t)s->cfg.max_step_requests);
+    const size_t quantum = std::max(s->cfg.step_quantum_bytes, s->cfg.step_target_bytes / n_work);
     for (Req *r : s->active) {
         if (r->issued_all) continue;
         if (r->inst.tiles == 0) {                     // nothing to run on the device
@@ -181,13 +190,13 @@ bool issue_step_locked(hx_server *s) {
         }
         if ((int)n >= s->cfg.max_step_requests) continue;
         BInst I = r->inst;
-        const int64_t q = std::max<int64_t>(1, (int64_t)s->cfg.step_quantum_bytes / tile_bytes(I));
+        const int64_t q = std::max<int64_t>(1, (int64_t)quantum / tile_bytes(I));
         I.t_first = r->issued;
         I.t_count = std::min<int64_t>(q, I.tiles - r->issued);
         I.sweep0 = I.kind == kKindStencil ? r->sweep : 0;
         if (c + inst_ctas(I) > 0xffffffffull || w + inst_runs(I) > 0xffffffffull) continue;
-        cp[n] = (uint32_t)c;
-        rp[n] = (uint32_t)w;
+        cpv.push_back((uint32_t)c);
+        rpv.push_back((uint32_t)w);
         c += inst_ctas(I);
         w += inst_runs(I);
         insts[n++] = I;
@@ -200,25 +209,23 @@ bool issue_step_locked(hx_server *s) {
         }
     }
     if (n == 0 && step.finishing.empty()) return false;
-    cp[n] = (uint32_t)c;
-    rp[n] = (uint32_t)w;
+    cpv.push_back((uint32_t)c);
+    rpv.push_back((uint32_t)w);
+    const size_t off_cta = ((size_t)n * sizeof(BInst) + 15) & ~(size_t)15;
+    const size_t off_run = off_cta + (((size_t)(n + 1) * 4 + 15) & ~(size_t)15);
+    memcpy(sl.h + off_cta, cpv.data(), (n + 1) * 4);
+    memcpy(sl.h + off_run, rpv.data(), (n + 1) * 4);
     std::vector<Req *> issued_now = step.finishing;
     s->active.erase(std::remove_if(s->active.begin(), s->active.end(), [](Req *r) { return r->issued_all; }),
                     s->active.end());
     hx_status st = HX_OK;
     if (n > 0) {
-        // descriptors, then the two prefix arrays (n + 1 entries each) right after them
-        const size_t di = (size_t)n * sizeof(BInst);
-        cudaError_t e = cudaMemcpyAsync(sl.d, sl.h, di, cudaMemcpyHostToDevice, s->stream);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(sl.d + sl.off_cta, sl.h + sl.off_cta, (n + 1) * 4, cudaMemcpyHostToDevice, s->stream);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(sl.d + sl.off_run, sl.h + sl.off_run, (n + 1) * 4, cudaMemcpyHostToDevice, s->stream);
+        cudaError_t e = cudaMemcpyAsync(sl.d, sl.h, off_run + (n + 1) * 4, cudaMemcpyHostToDevice, s->stream);
         if (e != cudaSuccess) st = cuda_fail(e, "server: step upload");
         if (st == HX_OK)
             st = launch_batch_round(s->ctx, reinterpret_cast<const BInst *>(sl.d), n,
-                                    reinterpret_cast<const uint32_t *>(sl.d + sl.off_cta),
-                                    reinterpret_cast<const uint32_t *>(sl.d + sl.off_run), (uint32_t)c, (uint32_t)w, 0,
+                                    reinterpret_cast<const uint32_t *>(sl.d + off_cta),
+                                    reinterpret_cast<const uint32_t *>(sl.d + off_run), (uint32_t)c, (uint32_t)w, 0,
                                     s->stream);
         s->stats.launches += 1;
     }
@@ -367,6 +374,7 @@ hx_status hx_server_create(hx_ctx *ctx, const hx_server_config *cfg, hx_server *
     if (s->cfg.max_steps_in_flight == 0) s->cfg.max_steps_in_flight = 4;
     if (s->cfg.max_step_requests == 0) s->cfg.max_step_requests = 4096;
     if (s->cfg.step_quantum_bytes == 0) s->cfg.step_quantum_bytes = (size_t)32 << 20;
+    if (s->cfg.step_target_bytes == 0) s->cfg.step_target_bytes = (size_t)512 << 20;
     cudaError_t e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
         delete s;
@@ -377,9 +385,7 @@ hx_status hx_server_create(hx_ctx *ctx, const hx_server_config *cfg, hx_server *
         const size_t K = (size_t)s->cfg.max_step_requests;
         s->slots.resize((size_t)s->cfg.max_steps_in_flight + 1);
         for (Slot &sl : s->slots) {
-            sl.off_cta = align(K * sizeof(BInst));
-            sl.off_run = sl.off_cta + align((K + 1) * 4);
-            sl.bytes = sl.off_run + align((K + 1) * 4);
+            sl.bytes = align(K * sizeof(BInst)) + 2 * align((K + 1) * 4);
             if (e == cudaSuccess) e = cudaMallocHost(&sl.h, sl.bytes);
             if (e == cudaSuccess) e = cudaMalloc(&sl.d, sl.bytes);
             if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming);

@@ -45,7 +45,8 @@ def test_sliced_requests_equal_alone(gpu):
     trace = _trace(24, 50_000.0, seed=43, hi=1 << 20, iters=3)
     insts = [Inst(r) for r in trace]
     with hx.hx_create(0) as ctx:
-        with hx.Server(ctx, mode=0, step_quantum_bytes=64 << 10, max_steps_in_flight=3) as srv:
+        with hx.Server(ctx, mode=0, step_quantum_bytes=64 << 10, step_target_bytes=64 << 10,
+                       max_steps_in_flight=3) as srv:
             srv.run_trace([i.task(hx) for i in insts], [r["arrival_s"] for r in trace])
             st = srv.stats()
         assert st["launches"] > len(trace)
