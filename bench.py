@@ -97,6 +97,31 @@ def apply_tuning(hx, ctx, args) -> str:
     return "built-in defaults"
 
 
+def kernel_sources_sha256() -> str:
+    import glob
+    import hashlib
+
+    pkg = os.path.join(ROOT, "paper_2503_10855_b300", "csrc")
+    files = sorted(glob.glob(os.path.join(pkg, "*.cu")) + glob.glob(os.path.join(pkg, "*.cuh")))
+    files.append(os.path.join(ROOT, "include", "hx.h"))
+    h = hashlib.sha256()
+    for f in files:
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def measured_traffic():
+    """DRAM bytes per launch from the committed ncu capture, if it was taken
+    on the current kernel sources (else {}: the counters are stale)."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.txt")) as f:
+            doc = json.load(f)
+    except (OSError, ValueError):
+        return {}
+    return doc.get("kernels", {}) if doc.get("sources_sha256") == kernel_sources_sha256() else {}
+
+
 def _dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -405,6 +430,9 @@ def bench_hx(args, rank, world, local):
         kern[name] = {"ms": round(avg_ms, 5), "algorithmic_bytes": byts, "GB/s": round(gbs, 1),
                       "frac_of_measured_hbm": round(gbs / peak, 4), "launches": launches}
     kern["jacobi"]["note"] = "2 x 16 MiB grids are L2-resident after the first sweep"
+    traffic = measured_traffic()   # per launch (jacobi: per sweep)
+    for name in kern:
+        kern[name]["dram_bytes_per_launch"] = traffic.get(name)
     dom = max(comps, key=lambda k: comp_ms[k])
     dom_per_launch_ms = comp_ms[dom] / K / kern[dom]["launches"]
     dom_bytes_per_launch = kern[dom]["algorithmic_bytes"] / kern[dom]["launches"]
@@ -443,7 +471,8 @@ def bench_hx(args, rank, world, local):
         "frac_of_nominal_8tbs": round(value / world / 8000.0, 4),
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                     "traffic": None},
+                     "traffic": traffic.get(dom),
+                     "algorithmic_bytes_per_launch": dom_bytes_per_launch},
         "kernels": kern,
         "cpu_baseline": cpu,
         "batched": batched,
