@@ -4,15 +4,15 @@
 // parallel fork-joins as concurrent tasks (Sec. 4.5; the AsyncCall attribute
 // of Sec. 3.4).  On one GPU that becomes a device work-list: every instance
 // is cut into the same tiles its standalone call would use, the tiles of all
-// instances are listed as work items, and resident workers take them in a
-// fixed round-robin order.  Map->reduce tiles and stencil blocks form WARP
-// runs (a warp computes and reduces a run of consecutive tiles of one
-// instance on its own, with no block barrier); histogram chunks are CTA items
-// (the CTA's warps share one set of shared-memory bins) and run first.
-// Per-instance arrival tickets let the last run of an instance do its final
-// combine, so no worker ever waits for another.  A stencil instance with several sweeps contributes
-// one sweep per round; rounds are consecutive launches chained with
-// programmatic dependent launch.
+// instances are described once and resident workers take their work items.
+// Map->reduce tiles and stencil blocks form WARP runs (a warp computes and
+// reduces a run of consecutive tiles of one instance on its own, with no
+// block barrier); histogram chunks are CTA items (the CTA's warps share one
+// set of shared-memory counters) and run first.  Per-instance arrival
+// tickets let the last run of an instance do its final combine, so no worker
+// ever waits for another.  A stencil instance with several sweeps
+// contributes one sweep per round; rounds are consecutive launches chained
+// with programmatic dependent launch.
 #include <algorithm>
 #include <cstring>
 #include <new>
@@ -103,15 +103,16 @@ __device__ __forceinline__ unsigned int find_instance(const uint32_t *__restrict
 }
 
 // Phase 1 runs the CTA items (histogram chunks, CTA c takes items c, c + G,
-// ...); phase 2 the warp runs (warp w takes runs w, w + W, ...).  The work
-// list is not stored: item j belongs to the instance whose prefix range holds
-// j (binary search), and its tiles follow from the instance's slice and run
-// length, so the host only uploads one descriptor per instance.  The static
-// assignment needs no shared counter.  A run publishes once: one fence and
-// one ticket increment by the run length.
-__global__ void __launch_bounds__(kBatchThreads, 4)
+// ...); phase 2 the warp runs, fetched one at a time from a counter (each
+// warp prefetches its next index while it works, and runs are large, so the
+// counter sees a few thousand atomics per launch).  The work list is not
+// stored: item j belongs to the instance whose prefix range holds j (binary
+// search), and its tiles follow from the instance's slice and run length, so
+// the host only uploads one descriptor per instance.  A run publishes once:
+// one fence and one ticket increment by the run length.
+__global__ void __launch_bounds__(kBatchThreads, 2)
 batch_kernel(const BInst *__restrict__ insts, unsigned int n_inst, const uint32_t *__restrict__ cta_prefix,
-             const uint32_t *__restrict__ run_prefix, int round) {
+             const uint32_t *__restrict__ run_prefix, int round, unsigned int *ctrl) {
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;");
     extern __shared__ __align__(16) unsigned int sh[];   // kHiSmemBytes when the round has CTA items
@@ -126,10 +127,16 @@ batch_kernel(const BInst *__restrict__ insts, unsigned int n_inst, const uint32_
         batch_hist_item(I, I.t_first + (it - __ldg(cta_prefix + i)), sh, wtot, &s_flag);
     }
 
-    constexpr unsigned int kWarpsPerCta = kBatchThreads / kWarp;
-    const unsigned int nw = gridDim.x * kWarpsPerCta;
+    // Warp runs are taken dynamically: lane 0 fetches the next run index
+    // from ctrl[0] while the current run is processed (runs differ in cost,
+    // a static assignment leaves warps idle at the end).
     unsigned int pend_inst = 0xffffffffu, pend_prev = 0u, pend_cnt = 0u;
-    for (unsigned int it = blockIdx.x * kWarpsPerCta + (threadIdx.x >> 5); it < n_runs; it += nw) {
+    unsigned int it = 0u;
+    if (lane == 0) it = atomicAdd(&ctrl[0], 1u);
+    it = __shfl_sync(0xffffffffu, it, 0);
+    while (it < n_runs) {
+        unsigned int next = 0u;
+        if (lane == 0) next = atomicAdd(&ctrl[0], 1u);
         const unsigned int i = find_instance(run_prefix, n_inst, it);
         const BInst &I = insts[i];
         const int64_t first = I.t_first + (int64_t)(it - __ldg(run_prefix + i)) * I.run_len;
@@ -138,7 +145,7 @@ batch_kernel(const BInst *__restrict__ insts, unsigned int n_inst, const uint32_
             const float *x = static_cast<const float *>(I.in0);
             const float *y = static_cast<const float *>(I.in1);
             float *out = static_cast<float *>(I.o0);
-            for (unsigned int k = 0; k < cnt; ++k) {
+            for (int64_t k = 0; k < cnt; ++k) {
                 const int64_t tile = first + k;
                 const ff part = mr_tile(x, y, out, I.a, I.plan, tile, I.vec != 0, lane);
                 if (lane == 0) I.partials[tile] = make_float2(part.hi, part.lo);
@@ -167,8 +174,18 @@ batch_kernel(const BInst *__restrict__ insts, unsigned int n_inst, const uint32_
         pend_inst = i;
         pend_prev = prev;
         pend_cnt = cnt;
+        it = __shfl_sync(0xffffffffu, next, 0);
     }
     if (pend_inst != 0xffffffffu) batch_resolve(insts, pend_inst, pend_prev, pend_cnt, round, lane);
+    // The last CTA to finish resets the run counter for the next launch.
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(&ctrl[1], 1u) == gridDim.x - 1) {
+            ctrl[0] = 0u;
+            ctrl[1] = 0u;
+        }
+    }
 }
 
 void describe_instance(const hx_ctx *ctx, const hx_task &t, BInst *out, int64_t *partials, int64_t *acc_words) {
@@ -214,7 +231,7 @@ void describe_instance(const hx_ctx *ctx, const hx_task &t, BInst *out, int64_t 
 
 hx_status launch_batch_round(const hx_ctx *ctx, const BInst *d_insts, uint32_t n_inst, const uint32_t *d_cta_prefix,
                              const uint32_t *d_run_prefix, uint32_t n_cta, uint32_t n_runs, int round,
-                             cudaStream_t stream) {
+                             unsigned int *d_ctrl, cudaStream_t stream) {
     if (n_cta == 0 && n_runs == 0) return HX_OK;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -228,7 +245,7 @@ hx_status launch_batch_round(const hx_ctx *ctx, const BInst *d_insts, uint32_t n
     cfg.stream = stream;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    cudaError_t e = cudaLaunchKernelEx(&cfg, batch_kernel, d_insts, n_inst, d_cta_prefix, d_run_prefix, round);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, batch_kernel, d_insts, n_inst, d_cta_prefix, d_run_prefix, round, d_ctrl);
     if (e != cudaSuccess) return cuda_fail(e, "batched kernel launch");
     return HX_OK;
 }
@@ -265,6 +282,7 @@ struct hx_batch {
     void *d_mem = nullptr;
     hx::BInst *d_insts = nullptr;
     uint32_t *d_prefix = nullptr;          // per round: CTA prefix (n_inst + 1), run prefix (n_inst + 1)
+    unsigned int *d_ctrl = nullptr;        // run counter + finished-CTA counter (reset by each launch)
 };
 
 namespace hx {
@@ -364,7 +382,8 @@ extern "C" hx_status hx_batch_plan(hx_ctx *ctx, const hx_task *tasks, int32_t n_
     const size_t off_part = off_pre + align(sizeof(uint32_t) * prefix.size());
     const size_t off_tick = off_part + align(sizeof(float2) * n_partials);
     const size_t off_acc = off_tick + align(sizeof(unsigned int) * insts.size());
-    const size_t total = off_acc + align(sizeof(unsigned int) * n_acc);
+    const size_t off_ctrl = off_acc + align(sizeof(unsigned int) * n_acc);
+    const size_t total = off_ctrl + 256;
     DeviceGuard g(ctx->device);
     hx_batch *b = new (std::nothrow) hx_batch();
     if (!b) return fail(HX_ERR_NOMEM, "hx_batch_plan: host allocation failed");
@@ -381,6 +400,7 @@ extern "C" hx_status hx_batch_plan(hx_ctx *ctx, const hx_task *tasks, int32_t n_
     char *base = static_cast<char *>(b->d_mem);
     b->d_insts = reinterpret_cast<BInst *>(base);
     b->d_prefix = reinterpret_cast<uint32_t *>(base + off_pre);
+    b->d_ctrl = reinterpret_cast<unsigned int *>(base + off_ctrl);
     int64_t pcur = 0, acur = 0;
     for (int i = 0; i < n_tasks; ++i) {
         BInst &I = insts[i];
@@ -438,7 +458,7 @@ extern "C" hx_status hx_batch_launch(hx_batch *b, hx_stream_t stream) {
     for (int r = 0; r < b->rounds; ++r) {
         const uint32_t *cp = b->d_prefix + (size_t)r * 2 * stride;
         hx_status st = launch_batch_round(b->ctx, b->d_insts, b->n_inst, cp, cp + stride, b->n_cta[r], b->n_runs[r],
-                                          r, (cudaStream_t)stream);
+                                          r, b->d_ctrl, (cudaStream_t)stream);
         if (st != HX_OK) return st;
     }
     return HX_OK;

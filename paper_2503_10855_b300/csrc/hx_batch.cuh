@@ -58,10 +58,12 @@ inline uint32_t inst_ctas(const BInst &I) { return I.kind == kKindHist ? (uint32
 
 // Launches the batched kernel for one round: n_inst instances, exclusive
 // prefix sums of their CTA chunks and warp runs (n_inst + 1 entries each, on
-// the device), totals n_cta and n_runs.
+// the device), totals n_cta and n_runs; d_ctrl: two zeroed words the kernel
+// uses as its run counter and leaves zeroed (launches sharing d_ctrl must be
+// ordered, e.g. on one stream).
 hx_status launch_batch_round(const hx_ctx *ctx, const BInst *d_insts, uint32_t n_inst, const uint32_t *d_cta_prefix,
                              const uint32_t *d_run_prefix, uint32_t n_cta, uint32_t n_runs, int round,
-                             cudaStream_t stream);
+                             unsigned int *d_ctrl, cudaStream_t stream);
 
 // Device bytes a task's buffers occupy (inputs and outputs), for admission.
 size_t task_footprint(const hx_task &t);

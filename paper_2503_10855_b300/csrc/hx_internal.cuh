@@ -159,17 +159,21 @@ __device__ __forceinline__ ff mr_thread_partial(const float *__restrict__ x,
     ff acc = {0.0f, 0.0f};
     const bool full = base + p.tile_elems <= p.n;
     if (full && aligned) {
+        // Two groups of kMrUnroll vectors per operand in flight: the loads of
+        // group g + 1 are issued before group g is computed.
         const float4 *x4 = reinterpret_cast<const float4 *>(x + base);
         const float4 *y4 = reinterpret_cast<const float4 *>(y + base);
         float4 *o4 = reinterpret_cast<float4 *>(out + base);
-        for (int u0 = 0; u0 < p.vecs_per_thread; u0 += kMrUnroll) {
-            float4 xv[kMrUnroll], yv[kMrUnroll];
+        float4 xa[kMrUnroll], ya[kMrUnroll], xb[kMrUnroll], yb[kMrUnroll];
+        auto load = [&](float4 *xv, float4 *yv, int u0) {
 #pragma unroll
             for (int k = 0; k < kMrUnroll; ++k) {
                 const int64_t vi = (int64_t)(u0 + k) * nthreads + t;
                 xv[k] = ld_stream4(x4 + vi);
                 yv[k] = ld_stream4(y4 + vi);
             }
+        };
+        auto consume = [&](const float4 *xv, const float4 *yv, int u0) {
 #pragma unroll
             for (int k = 0; k < kMrUnroll; ++k) {
                 float4 o;
@@ -183,6 +187,15 @@ __device__ __forceinline__ ff mr_thread_partial(const float *__restrict__ x,
                 acc = ff_add_f(acc, o.z);
                 acc = ff_add_f(acc, o.w);
             }
+        };
+        const int V = p.vecs_per_thread;
+        load(xa, ya, 0);
+        for (int u0 = 0; u0 < V; u0 += 2 * kMrUnroll) {
+            if (u0 + kMrUnroll < V) load(xb, yb, u0 + kMrUnroll);
+            consume(xa, ya, u0);
+            if (u0 + kMrUnroll >= V) break;
+            if (u0 + 2 * kMrUnroll < V) load(xa, ya, u0 + 2 * kMrUnroll);
+            consume(xb, yb, u0 + kMrUnroll);
         }
     } else {
         for (int u = 0; u < p.vecs_per_thread; ++u) {

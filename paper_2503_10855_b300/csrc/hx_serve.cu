@@ -80,7 +80,8 @@ struct hx_server {
     std::deque<hx::Step> steps;               // issued, not yet completed (in stream order)
     std::vector<hx::Slot> slots;
     std::vector<cudaEvent_t> free_events;     // per-launch mode
-    char *ws_pool = nullptr;                  // continuous mode: max_inflight workspace slots
+    char *ws_pool = nullptr;                  // continuous mode: max_inflight workspace slots (+ run counter)
+    unsigned int *ctrl = nullptr;
     std::vector<int> free_ws;
     uint64_t next_id = 1;
     size_t used = 0;
@@ -226,7 +227,7 @@ bool issue_step_locked(hx_server *s) {
             st = launch_batch_round(s->ctx, reinterpret_cast<const BInst *>(sl.d), n,
                                     reinterpret_cast<const uint32_t *>(sl.d + off_cta),
                                     reinterpret_cast<const uint32_t *>(sl.d + off_run), (uint32_t)c, (uint32_t)w, 0,
-                                    s->stream);
+                                    s->ctrl, s->stream);
         s->stats.launches += 1;
     }
     if (st == HX_OK && cudaEventRecord(sl.ev, s->stream) != cudaSuccess) st = HX_ERR_CUDA;
@@ -391,8 +392,9 @@ hx_status hx_server_create(hx_ctx *ctx, const hx_server_config *cfg, hx_server *
             if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming);
         }
         const size_t pool = (size_t)s->cfg.max_inflight * kWsBytes;
-        if (e == cudaSuccess) e = cudaMalloc(&s->ws_pool, pool);
-        if (e == cudaSuccess) e = cudaMemset(s->ws_pool, 0, pool);
+        if (e == cudaSuccess) e = cudaMalloc(&s->ws_pool, pool + 256);
+        if (e == cudaSuccess) e = cudaMemset(s->ws_pool, 0, pool + 256);
+        s->ctrl = reinterpret_cast<unsigned int *>(s->ws_pool + pool);
         for (int i = s->cfg.max_inflight - 1; i >= 0; --i) s->free_ws.push_back(i);
         if (e == cudaSuccess) e = cudaDeviceSynchronize();
     }

@@ -265,7 +265,8 @@ hx_status hx_autotune(hx_ctx *ctx, int32_t max_log2, hx_stream_t stream) {
             ctx->tune.stencil_rows[c] = rows;
             ctx->tune.stencil_rows[c + 1 < HX_TUNE_CLASSES ? c + 1 : c] = rows;
             const float ms = time_median(s, reps, [&](int) {
-                return hx_stencil2d(ctx, pool, pool + pts, side, side, 2, res, nullptr, stream);
+                // 8 chained sweeps: the steady state of an iterated stencil
+                return hx_stencil2d(ctx, pool, pool + pts, side, side, 8, res, nullptr, stream);
             }, &st);
             if (st == HX_OK && ms < best) { best = ms; best_r = rows; }
         }
