@@ -56,6 +56,9 @@ def _get():
             f.restype = ctypes.c_int
         lib.hxo_histogram_u8.argtypes = [P, ctypes.c_int64, P, P]
         lib.hxo_histogram_u8.restype = None
+        I = ctypes.c_int
+        lib.hxo_fork_reduce.argtypes = [I, P, I, I, I, P, P, I, P, P, P, P, P]
+        lib.hxo_fork_reduce.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -118,3 +121,59 @@ def histogram(v: np.ndarray):
     scan = np.zeros(256, dtype=np.uint32)
     _get().hxo_histogram_u8(_ptr(v), v.size, _ptr(bins), _ptr(scan))
     return bins, scan
+
+
+# Op codes and monoid codes of the fork-join nest interpreter (hxo_fork_reduce).
+NEST_OPS = {"in": 1, "const": 2, "index": 3, "add": 4, "sub": 5, "mul": 6, "div": 7,
+            "fma": 8, "neg": 9, "abs": 10, "min": 11, "max": 12, "sqrt": 13}
+NEST_MONOIDS = {"sum": 0, "max": 1, "min": 2, "prod": 3, "argmax": 4, "argmin": 5}
+
+
+def _encode_program(program):
+    codes = []
+    for item in program:
+        name, arg = (item, 0) if isinstance(item, str) else item
+        codes += [NEST_OPS[name] if isinstance(name, str) else int(name), int(arg)]
+    return np.asarray(codes, dtype=np.int32)
+
+
+def fork_reduce(program, inputs, dims, reduce_dims, monoid="sum", consts=(), want_out=True):
+    """Sequential evaluation of a fork-join nest (see ``hxo_fork_reduce``).
+
+    ``program``: postfix list of op names or (name, arg) pairs.  ``inputs``:
+    float32 numpy arrays whose shape is ``dims``; each one's own element
+    strides (transposes, ``np.broadcast_to`` views) give the addressing.
+    Returns (out or None, result, index or None): ``out`` has shape ``dims``,
+    ``result`` (float64) and ``index`` (int64) the shape of the outer
+    ``ndim - reduce_dims`` dimensions.
+    """
+    dims = tuple(int(d) for d in dims)
+    ndim = len(dims)
+    ops = _encode_program(program)
+    arrs, strides = [], np.zeros((max(len(inputs), 1), 3), dtype=np.int64)
+    for k, a in enumerate(inputs):
+        assert a.dtype == np.float32 and a.shape == dims, (a.dtype, a.shape, dims)
+        arrs.append(a)
+        for d in range(ndim):
+            strides[k, d] = a.strides[d] // 4
+    ptrs = (ctypes.c_void_p * max(len(arrs), 1))(*[ctypes.c_void_p(a.ctypes.data) for a in arrs])
+    c = np.zeros(8, dtype=np.float32)
+    c[:len(consts)] = consts
+    outer_shape = dims[:ndim - reduce_dims]
+    n_outer = int(np.prod(outer_shape, dtype=np.int64))
+    out = np.zeros(dims, dtype=np.float32) if want_out else None
+    result = np.zeros(max(n_outer, 1), dtype=np.float64)
+    index = np.zeros(max(n_outer, 1), dtype=np.int64)
+    dims_a = np.asarray(dims + (1,) * (3 - ndim), dtype=np.int64)
+    rc = _get().hxo_fork_reduce(ndim, _ptr(dims_a), reduce_dims, NEST_MONOIDS[monoid],
+                                len(ops) // 2, _ptr(ops) if ops.size else ctypes.c_void_p(0),
+                                _ptr(c), len(arrs), ptrs, _ptr(strides),
+                                _ptr(out) if want_out and out.size else ctypes.c_void_p(0),
+                                _ptr(result), _ptr(index))
+    if rc:
+        raise ValueError("oracle fork_reduce: malformed nest")
+    if reduce_dims == 0:
+        return out, None, None
+    result = result[:n_outer].reshape(outer_shape)
+    index = index[:n_outer].reshape(outer_shape) if monoid.startswith("arg") else None
+    return out, result, index

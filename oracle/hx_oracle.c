@@ -185,3 +185,178 @@ void hxo_histogram_u8(const uint8_t *v, int64_t n, uint32_t *bins,
         }
     }
 }
+
+/* ---------------------------------------------------------------------------
+ * Generic fork-join nest: a fork of up to three factors whose body is a small
+ * straight-line map program, feeding a reduce over the innermost
+ * `reduce_dims` fork dimensions under one of six monoids.
+ *
+ * Fork (Sec. 3.3): factors dims[0..ndim), dimension 0 outermost; thread
+ * (i0, i1, i2) has the flat ID f = (i0*dims[1] + i1)*dims[2] + i2 (missing
+ * dimensions dropped).  The outer m = ndim - reduce_dims dimensions index the
+ * independent reductions ("segments"); the inner ones are folded.  With
+ * O = dims[0]*...*dims[m-1] and I = dims[m]*...*dims[ndim-1], segment s holds
+ * the threads s*I .. s*I + I - 1, and the reduce of segment s starts at the
+ * monoid's identity and folds the segment's values for r = 0, 1, ..., I-1:
+ * the increasing thread-ID order of Sec. 3.3.  reduce_dims == 0 means no
+ * reduce: only the map values are produced.
+ *
+ * Map program: a postfix (stack) program over single-precision values, every
+ * operation rounded to fp32 as IEEE 754 single does it (the C float
+ * operators, sqrtf and fmaf are correctly rounded):
+ *   1 IN k     push in[k][sum_d i_d*strides[k*3+d]]    (element strides)
+ *   2 CONST k  push consts[k]
+ *   3 INDEX d  push (float)i_d
+ *   4 ADD  5 SUB  6 MUL  7 DIV    pop b, pop a, push a op b
+ *   8 FMA      pop c, b, a, push fmaf(a, b, c) (one rounding)
+ *   9 NEG  10 ABS  13 SQRT        pop a, push -a / fabsf(a) / sqrtf(a)
+ *  11 MIN  12 MAX                 pop b, pop a, push the smaller / larger
+ *                                 (a NaN operand yields the other one)
+ * The program must leave exactly one value; the stack holds at most 8.
+ *
+ * Monoids (Sec. 3.4 MonoidReduce), folded left in thread-ID order:
+ *   0 sum   acc = acc + v in double, init 0
+ *   1 max   acc = v if v > acc, init -inf (NaN never taken; equal values keep
+ *           the earlier one except that +0 replaces -0)
+ *   2 min   acc = v if v < acc, init +inf (-0 replaces +0)
+ *   3 prod  acc = acc * v in double, init 1
+ *   4 argmax, 5 argmin: (value, index) of the first thread, in thread-ID
+ *           order, whose value is the largest / smallest non-NaN value;
+ *           index = r, the position inside the segment; init (-inf / +inf,
+ *           -1), and index -1 remains when every value is NaN or I == 0.
+ * result[s] is the folded value (sum and prod as double, the rest exactly
+ * the fp32 value widened); result_index[s] the index for argmax / argmin.
+ *
+ * out (nullable) receives every thread's map value at its flat ID.  Returns 0,
+ * or 1 for a malformed program or arguments.
+ */
+#define HXO_MAX_STACK 8
+
+static int hxo_eval(int n_ops, const int32_t *ops, const float *consts,
+                    const float *const *in, const int64_t *strides,
+                    const int64_t *idx, int ndim, float *value)
+{
+    float st[HXO_MAX_STACK];
+    int sp = 0;
+    for (int k = 0; k < n_ops; ++k) {
+        int code = ops[2 * k], arg = ops[2 * k + 1];
+        float a, b, c;
+        switch (code) {
+        case 1: {
+            int64_t off = 0;
+            for (int d = 0; d < ndim; ++d) off += idx[d] * strides[arg * 3 + d];
+            if (sp >= HXO_MAX_STACK) return 1;
+            st[sp++] = in[arg][off];
+            break;
+        }
+        case 2:
+            if (sp >= HXO_MAX_STACK) return 1;
+            st[sp++] = consts[arg];
+            break;
+        case 3:
+            if (sp >= HXO_MAX_STACK || arg < 0 || arg >= ndim) return 1;
+            st[sp++] = (float)idx[arg];
+            break;
+        case 4: case 5: case 6: case 7: case 11: case 12:
+            if (sp < 2) return 1;
+            b = st[--sp];
+            a = st[--sp];
+            if (code == 4) st[sp++] = a + b;
+            else if (code == 5) st[sp++] = a - b;
+            else if (code == 6) st[sp++] = a * b;
+            else if (code == 7) st[sp++] = a / b;
+            else if (code == 11) st[sp++] = isnan(a) ? b : (isnan(b) ? a : (b < a ? b : a));
+            else st[sp++] = isnan(a) ? b : (isnan(b) ? a : (b > a ? b : a));
+            break;
+        case 8:
+            if (sp < 3) return 1;
+            c = st[--sp];
+            b = st[--sp];
+            a = st[--sp];
+            st[sp++] = fmaf(a, b, c);
+            break;
+        case 9: case 10: case 13:
+            if (sp < 1) return 1;
+            a = st[--sp];
+            st[sp++] = code == 9 ? -a : (code == 10 ? fabsf(a) : sqrtf(a));
+            break;
+        default:
+            return 1;
+        }
+    }
+    if (sp != 1) return 1;
+    *value = st[0];
+    return 0;
+}
+
+int hxo_fork_reduce(int ndim, const int64_t *dims, int reduce_dims, int monoid,
+                    int n_ops, const int32_t *ops, const float *consts,
+                    int n_in, const float *const *in, const int64_t *strides,
+                    float *out, double *result, int64_t *result_index)
+{
+    if (ndim < 1 || ndim > 3 || reduce_dims < 0 || reduce_dims > ndim) return 1;
+    if (reduce_dims > 0 && (monoid < 0 || monoid > 5 || !result)) return 1;
+    if (reduce_dims > 0 && monoid >= 4 && !result_index) return 1;
+    for (int d = 0; d < ndim; ++d)
+        if (dims[d] < 0) return 1;
+    /* the program must be well formed even when the fork is empty */
+    int depth = 0;
+    for (int k = 0; k < n_ops; ++k) {
+        int code = ops[2 * k], arg = ops[2 * k + 1];
+        if (code == 1 && (arg < 0 || arg >= n_in || !in[arg])) return 1;
+        if (code == 2 && (arg < 0 || arg >= 8)) return 1;
+        if (code == 3 && (arg < 0 || arg >= ndim)) return 1;
+        if (code >= 1 && code <= 3) depth += 1;
+        else if ((code >= 4 && code <= 7) || code == 11 || code == 12) depth -= 1;
+        else if (code == 8) depth -= 2;
+        else if (code != 9 && code != 10 && code != 13) return 1;
+        if (depth < 1 || depth > HXO_MAX_STACK) return 1;
+    }
+    if (depth != 1) return 1;
+    int m = ndim - reduce_dims;
+    int64_t outer = 1, inner = 1;
+    for (int d = 0; d < m; ++d) outer *= dims[d];
+    for (int d = m; d < ndim; ++d) inner *= dims[d];
+    for (int64_t s = 0; s < outer; ++s) {
+        double acc = 0.0;
+        float best = 0.0f;
+        int64_t best_i = -1;
+        switch (monoid) {
+        case 0: acc = 0.0; break;
+        case 1: case 4: best = -INFINITY; break;
+        case 2: case 5: best = INFINITY; break;
+        case 3: acc = 1.0; break;
+        }
+        for (int64_t r = 0; r < inner; ++r) {
+            int64_t f = s * inner + r, rem = f, idx[3] = {0, 0, 0};
+            for (int d = ndim - 1; d >= 0; --d) {
+                idx[d] = rem % dims[d];
+                rem /= dims[d];
+            }
+            float v;
+            if (hxo_eval(n_ops, ops, consts, in, strides, idx, ndim, &v)) return 1;
+            if (out) out[f] = v;
+            if (reduce_dims == 0) continue;
+            switch (monoid) {
+            case 0: acc = acc + (double)v; break;
+            case 3: acc = acc * (double)v; break;
+            case 1:
+                if (v > best || (v == 0.0f && best == 0.0f && signbit(best) && !signbit(v))) best = v;
+                break;
+            case 2:
+                if (v < best || (v == 0.0f && best == 0.0f && !signbit(best) && signbit(v))) best = v;
+                break;
+            case 4:
+                if (!isnan(v) && (best_i < 0 || v > best)) { best = v; best_i = r; }
+                break;
+            case 5:
+                if (!isnan(v) && (best_i < 0 || v < best)) { best = v; best_i = r; }
+                break;
+            }
+        }
+        if (reduce_dims == 0) continue;
+        result[s] = (monoid == 0 || monoid == 3) ? acc : (double)best;
+        if (monoid >= 4) result_index[s] = best_i;
+    }
+    return 0;
+}

@@ -13,6 +13,7 @@ import subprocess
 import pytest
 
 import oracle
+from tests import test_oracle_nest_pins as npins
 from tests import test_oracle_pins as pins
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "hx_oracle.c")
@@ -25,6 +26,18 @@ STENCIL_PINS = [pins.test_jacobi_golden_corner_spike, pins.test_jacobi_interior_
                 pins.test_jacobi_residual_is_max_step_change]
 HIST_PINS = [pins.test_histogram_golden_tiny, pins.test_histogram_matches_bincount_and_cumsum,
              pins.test_histogram_closed_forms]
+
+NEST_PINS = [*(lambda op=op: npins.test_nest_binary_ops_match_numpy_single(op) for op in npins.BINARY),
+             *(lambda op=op: npins.test_nest_unary_ops_match_numpy_single(op) for op in npins.UNARY),
+             npins.test_nest_const_and_operand_order, npins.test_nest_fma_is_one_rounding,
+             npins.test_nest_row_sums_match_numpy, npins.test_nest_row_prods_match_numpy,
+             lambda: npins.test_nest_row_extrema_match_numpy("max", npins.np.max),
+             lambda: npins.test_nest_row_extrema_match_numpy("min", npins.np.min),
+             lambda: npins.test_nest_row_arg_extrema_match_numpy("argmax", npins.np.argmax),
+             lambda: npins.test_nest_row_arg_extrema_match_numpy("argmin", npins.np.argmin),
+             npins.test_nest_3d_partial_reductions_match_numpy, npins.test_nest_strided_and_broadcast_inputs,
+             npins.test_nest_index_op_matches_index_grid, npins.test_nest_fold_order_is_thread_id_order,
+             npins.test_nest_nan_and_empty_rules, npins.test_nest_signed_zero_rules]
 
 MUTANTS = {
     "map_transposed": ("double v = a * (double)x[i] + (double)y[i];",
@@ -51,6 +64,24 @@ MUTANTS = {
                             "run = run + bins[k];\n            excl_scan[k] = run;", HIST_PINS),
     "hist_drop_first": ("for (int64_t i = 0; i < n; ++i) bins[v[i]]",
                         "for (int64_t i = 1; i < n; ++i) bins[v[i]]", HIST_PINS),
+    "nest_sub_swapped": ("else if (code == 5) st[sp++] = a - b;", "else if (code == 5) st[sp++] = b - a;",
+                         NEST_PINS),
+    "nest_fma_two_roundings": ("st[sp++] = fmaf(a, b, c);", "st[sp++] = a * b + c;", NEST_PINS),
+    "nest_argmax_last_tie": ("if (!isnan(v) && (best_i < 0 || v > best)) { best = v; best_i = r; }",
+                             "if (!isnan(v) && (best_i < 0 || v >= best)) { best = v; best_i = r; }", NEST_PINS),
+    "nest_dims_reversed": ("for (int d = ndim - 1; d >= 0; --d) {\n                idx[d] = rem % dims[d];",
+                           "for (int d = 0; d < ndim; ++d) {\n                idx[d] = rem % dims[d];", NEST_PINS),
+    "nest_strides_reversed": ("off += idx[d] * strides[arg * 3 + d];",
+                              "off += idx[d] * strides[arg * 3 + (ndim - 1 - d)];", NEST_PINS),
+    "nest_max_init_zero": ("case 1: case 4: best = -INFINITY; break;", "case 1: case 4: best = 0.0f; break;",
+                           NEST_PINS),
+    "nest_sum_in_float": ("case 0: acc = acc + (double)v; break;", "case 0: acc = (float)(acc + (double)v); break;",
+                          NEST_PINS),
+    "nest_prod_init_zero": ("case 3: acc = 1.0; break;\n        }\n        for (int64_t r",
+                            "case 3: acc = 0.0; break;\n        }\n        for (int64_t r", NEST_PINS),
+    "nest_index_off_by_one": ("st[sp++] = (float)idx[arg];", "st[sp++] = (float)(idx[arg] + 1);", NEST_PINS),
+    "nest_min_keeps_pos_zero": ("if (v < best || (v == 0.0f && best == 0.0f && !signbit(best) && signbit(v))) best = v;",
+                                "if (v < best) best = v;", NEST_PINS),
 }
 
 
@@ -72,7 +103,7 @@ def test_pins_catch_mutant(tmp_path, monkeypatch, name):
     real = oracle._get()
     mutant = _load_mutant(tmp_path, name, old, new)
     for fn in ("hxo_map_reduce_f64", "hxo_monoid_reduce_f64", "hxo_jacobi_f64",
-               "hxo_jacobi_f32", "hxo_histogram_u8"):
+               "hxo_jacobi_f32", "hxo_histogram_u8", "hxo_fork_reduce"):
         getattr(mutant, fn).argtypes = getattr(real, fn).argtypes
         getattr(mutant, fn).restype = getattr(real, fn).restype
     monkeypatch.setattr(oracle, "_lib", mutant)
@@ -80,6 +111,6 @@ def test_pins_catch_mutant(tmp_path, monkeypatch, name):
     for t in tests:
         try:
             t()
-        except AssertionError:
+        except (AssertionError, ValueError):
             failures += 1
     assert failures > 0, f"no pin caught mutant {name}"
