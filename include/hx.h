@@ -169,6 +169,125 @@ hx_status hx_stencil2d(hx_ctx *ctx, float *u0, float *u1, int32_t nx, int32_t ny
 hx_status hx_histogram(hx_ctx *ctx, const uint8_t *v, int64_t n, uint32_t *d_bins,
                        uint32_t *d_excl_scan, hx_stream_t stream);
 
+/* ------------------------------------------------------------------ generic nests
+ * A fork-join nest in general form (Sec. 3.3): a fork of factors
+ * dims[0..ndim) (dimension 0 outermost, 1 <= ndim <= 3) whose threads each
+ * evaluate a small map program, and a reduce that folds the innermost
+ * `reduce_dims` dimensions under a monoid (the MonoidReduce attribute of
+ * Sec. 3.4).  Thread (i0, i1, i2) has flat ID f = (i0*dims[1] + i1)*dims[2]
+ * + i2.  The outer ndim - reduce_dims dimensions index independent
+ * "segments": with O = product of the outer factors and I = product of the
+ * reduced ones, segment s is threads s*I .. s*I + I - 1 and yields one
+ * result.  reduce_dims == 0 is a pure map (a fork with no reduce).
+ *
+ * The map program is postfix over single-precision values; every operation
+ * rounds once to fp32 (IEEE add, sub, mul, div, sqrt, fma; no contraction):
+ *   HX_OP_IN k     push in[k][sum_d i_d * strides[k][d]]  (element strides,
+ *                  any sign; 0 broadcasts along that dimension)
+ *   HX_OP_CONST k  push consts[k]          HX_OP_INDEX d  push (float)i_d
+ *   HX_OP_ADD / SUB / MUL / DIV  pop b, pop a, push a op b
+ *   HX_OP_FMA      pop c, b, a, push fmaf(a, b, c)
+ *   HX_OP_NEG / ABS / SQRT       pop a, push -a, |a|, sqrt(a)
+ *   HX_OP_MIN / MAX  pop b, pop a, push the smaller / larger (a NaN
+ *                  operand yields the other operand)
+ * At most 32 ops and 8 stack slots; the program must leave one value.
+ *
+ * Monoids (results per segment):
+ *   SUM, PROD   float-float accumulation; result = the pair rounded to
+ *               fp32, result64 = hi + lo in double.  Against an exact
+ *               left fold the error is far below fp32 rounding.
+ *   MAX, MIN    exact; NaN values are skipped; +0 beats -0 for MAX and -0
+ *               beats +0 for MIN; an empty segment gives -inf / +inf.
+ *   ARGMAX, ARGMIN  the first thread (in thread-ID order) holding the
+ *               largest / smallest non-NaN value: result = that value,
+ *               result_index = its position r inside the segment (0..I-1);
+ *               (-inf / +inf, -1) when the segment is empty or all NaN.
+ * Every result is deterministic: the combination order depends only on the
+ * sizes, the tree, the chunk and the tuning table.
+ *
+ * Reduction schedule (`tree`), after the paper's reduction-tree schedule
+ * (Sec. 5.2: chunk, reassociate the monoid, fission) and its lowering of
+ * reductions to warp primitives (Sec. 4.4):
+ *   HX_TREE_WARP   chunks of `chunk` elements per group of lanes, shuffle
+ *                  butterfly inside the group, chunk partials combined by
+ *                  the last group to arrive (default; chunk 0 = tuned).
+ *   HX_TREE_CHUNK  one thread per contiguous chunk (default 64 elements),
+ *                  sequential fold; the last thread folds the partials.
+ *   HX_TREE_SEQ    one thread folds a whole segment (the loop as written).
+ *
+ * The library generates the kernel for a nest's shape (program, monoid,
+ * tree, dimension split, addressing mode of each input) from its own
+ * template and compiles it for sm_103a with NVRTC on first use (a fraction
+ * of a second); kernels are cached for the life of the process.
+ *
+ *   in[k]      device float pointers (4-byte aligned) of the inputs the
+ *              program reads; strides[k][d] in elements.
+ *   out        device, O*I floats at flat IDs, or NULL; required when
+ *              reduce_dims == 0.  It may alias an input only if both have
+ *              the same layout.
+ *   result     device, O floats (required when reduce_dims > 0).
+ *   result64   device, O doubles, or NULL.
+ *   result_index  device, O int64 (required for ARGMAX / ARGMIN).
+ * A pointer the nest never touches may be NULL: inputs and out when the
+ * fork has no threads, the results when it has no segments (O == 0).
+ * Errors: HX_ERR_INVALID for a malformed descriptor (nothing launched);
+ * HX_ERR_CUDA with the compiler log in hx_last_error() if the generated
+ * kernel fails to compile.  O*I <= 2^60. */
+#define HX_NEST_MAX_DIMS 3
+#define HX_NEST_MAX_OPS 32
+#define HX_NEST_MAX_INPUTS 4
+#define HX_NEST_MAX_CONSTS 8
+#define HX_NEST_MAX_STACK 8
+
+typedef enum hx_nest_opcode {
+    HX_OP_IN = 1, HX_OP_CONST = 2, HX_OP_INDEX = 3,
+    HX_OP_ADD = 4, HX_OP_SUB = 5, HX_OP_MUL = 6, HX_OP_DIV = 7, HX_OP_FMA = 8,
+    HX_OP_NEG = 9, HX_OP_ABS = 10, HX_OP_MIN = 11, HX_OP_MAX = 12, HX_OP_SQRT = 13
+} hx_nest_opcode;
+
+typedef enum hx_monoid {
+    HX_MONOID_SUM = 0, HX_MONOID_MAX = 1, HX_MONOID_MIN = 2, HX_MONOID_PROD = 3,
+    HX_MONOID_ARGMAX = 4, HX_MONOID_ARGMIN = 5
+} hx_monoid;
+
+typedef enum hx_tree { HX_TREE_WARP = 0, HX_TREE_CHUNK = 1, HX_TREE_SEQ = 2 } hx_tree;
+
+typedef struct hx_nest_op {
+    int32_t code;   /* hx_nest_opcode */
+    int32_t arg;    /* input slot, constant slot or dimension */
+} hx_nest_op;
+
+typedef struct hx_nest {
+    int32_t ndim;
+    int32_t reduce_dims;
+    int32_t monoid;                 /* hx_monoid, ignored when reduce_dims == 0 */
+    int32_t tree;                   /* hx_tree */
+    int64_t dims[HX_NEST_MAX_DIMS];
+    int64_t chunk;                  /* elements per chunk, 0 = default / tuned */
+    int32_t n_ops;
+    int32_t pad_;
+    hx_nest_op ops[HX_NEST_MAX_OPS];
+    float consts[HX_NEST_MAX_CONSTS];
+    const float *in[HX_NEST_MAX_INPUTS];
+    int64_t strides[HX_NEST_MAX_INPUTS][HX_NEST_MAX_DIMS];
+    float *out;
+    float *result;
+    double *result64;
+    int64_t *result_index;
+} hx_nest;
+
+/* Run the nest on `stream` (asynchronous; uses the stream's workspace slot). */
+hx_status hx_fork_reduce(hx_ctx *ctx, const hx_nest *nest, hx_stream_t stream);
+
+/* Validate the nest and compile its kernel now (no device needed), so that
+ * the first hx_fork_reduce does not pay for compilation. */
+hx_status hx_nest_prepare(const hx_nest *nest);
+
+/* The CUDA source generated for the nest's shape (for inspection): copies
+ * at most cap-1 bytes plus a terminating NUL into buf (if buf and cap are
+ * non-zero) and stores the full length in *len (if len is non-NULL). */
+hx_status hx_nest_source(const hx_nest *nest, char *buf, size_t cap, size_t *len);
+
 /* ------------------------------------------------------------------ tuning
  * The paper leaves tile, chunk and vector choices to a hand-written schedule
  * per target (Sec. 2.2: fork-chunk, fork-tile, fork-reshape; Sec. 5.2: the
@@ -184,6 +303,11 @@ hx_status hx_histogram(hx_ctx *ctx, const uint8_t *v, int64_t n, uint32_t *d_bin
  *   hist_threads[c]  histogram CTA width (256, 512 or 1024), n in class c.
  *   stencil_rows[c]  rows per warp block of a standalone sweep (4, 8 or
  *                    16), class of nx*ny; results do not depend on it.
+ *   nest_lane_elems[c]  elements per lane of one warp-tree chunk of a
+ *                    generic nest whose segments hold n elements, n in class
+ *                    c (a multiple of 8 in [8, 512]; raised automatically so
+ *                    that a nest never needs more than 16384 chunk partials).
+ *                    Like map_vecs it fixes the summation tree.
  *   batch_map_run, batch_stencil_run: tiles per warp run in batches.
  * Size class c holds sizes in [2^c, 2^(c+1)); sizes 0 and 1 are class 0.
  * A context starts from the built-in defaults, or from the JSON file named
@@ -193,6 +317,7 @@ typedef struct hx_tune_table {
     int32_t map_vecs[HX_TUNE_CLASSES];
     int32_t hist_threads[HX_TUNE_CLASSES];
     int32_t stencil_rows[HX_TUNE_CLASSES];
+    int32_t nest_lane_elems[HX_TUNE_CLASSES];
     int32_t batch_map_run;
     int32_t batch_stencil_run;
 } hx_tune_table;

@@ -186,6 +186,127 @@ def hx_histogram(ctx: Context, v, bins=None, scan=None, want_scan: bool = True, 
     return bins, scan
 
 
+# ------------------------------------------------------------------ generic nests
+HX_NEST_MAX_DIMS, HX_NEST_MAX_OPS, HX_NEST_MAX_INPUTS, HX_NEST_MAX_CONSTS = 3, 32, 4, 8
+NEST_OPS = {"in": 1, "const": 2, "index": 3, "add": 4, "sub": 5, "mul": 6, "div": 7,
+            "fma": 8, "neg": 9, "abs": 10, "min": 11, "max": 12, "sqrt": 13}
+MONOIDS = {"sum": 0, "max": 1, "min": 2, "prod": 3, "argmax": 4, "argmin": 5}
+TREES = {"warp": 0, "chunk": 1, "seq": 2}
+
+
+class NestOp(ctypes.Structure):
+    _fields_ = [("code", _I32), ("arg", _I32)]
+
+
+class Nest(ctypes.Structure):
+    """Mirror of ``hx_nest`` (see include/hx.h)."""
+
+    _fields_ = [("ndim", _I32), ("reduce_dims", _I32), ("monoid", _I32), ("tree", _I32),
+                ("dims", _I64 * HX_NEST_MAX_DIMS), ("chunk", _I64), ("n_ops", _I32), ("pad_", _I32),
+                ("ops", NestOp * HX_NEST_MAX_OPS), ("consts", ctypes.c_float * HX_NEST_MAX_CONSTS),
+                ("inputs", _P * HX_NEST_MAX_INPUTS),
+                ("strides", (_I64 * HX_NEST_MAX_DIMS) * HX_NEST_MAX_INPUTS),
+                ("out", _P), ("result", _P), ("result64", _P), ("result_index", _P)]
+
+
+_NP = ctypes.POINTER(Nest)
+_lib.hx_fork_reduce.argtypes = [_P, _NP, _P]
+_lib.hx_fork_reduce.restype = ctypes.c_int
+_lib.hx_nest_prepare.argtypes = [_NP]
+_lib.hx_nest_prepare.restype = ctypes.c_int
+_lib.hx_nest_source.argtypes = [_NP, ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]
+_lib.hx_nest_source.restype = ctypes.c_int
+
+
+def make_nest(program, inputs, dims, reduce_dims, monoid="sum", consts=(), out=None, result=None,
+              result64=None, result_index=None, tree="warp", chunk=0) -> Nest:
+    """Fill an ``hx_nest``.  ``program``: postfix list of op names or (name, arg)
+    pairs (or raw integer codes).  ``inputs``: float32 tensors whose shape is
+    ``dims``; each one's own element strides are its addressing (transposes,
+    ``expand`` views with stride 0).  Outputs are tensors or None."""
+    import torch
+
+    nest = Nest()
+    dims = tuple(int(d) for d in dims)
+    nest.ndim = len(dims)
+    nest.reduce_dims = int(reduce_dims)
+    nest.monoid = MONOIDS[monoid] if isinstance(monoid, str) else int(monoid)
+    nest.tree = TREES[tree] if isinstance(tree, str) else int(tree)
+    nest.chunk = int(chunk)
+    for d, v in enumerate(dims[:HX_NEST_MAX_DIMS]):
+        nest.dims[d] = v
+    if len(program) > HX_NEST_MAX_OPS:
+        raise ValueError("a nest program holds at most 32 ops")
+    nest.n_ops = len(program)
+    for k, item in enumerate(program):
+        name, arg = (item, 0) if isinstance(item, (str, int)) else item
+        nest.ops[k].code = NEST_OPS[name] if isinstance(name, str) else int(name)
+        nest.ops[k].arg = int(arg)
+    for k, c in enumerate(consts):
+        nest.consts[k] = float(c)
+    if len(inputs) > HX_NEST_MAX_INPUTS:
+        raise ValueError("a nest reads at most 4 inputs")
+    for k, t in enumerate(inputs):
+        if t is None:
+            continue
+        if not isinstance(t, torch.Tensor) or t.dtype != torch.float32:
+            raise TypeError(f"input {k} must be a float32 tensor")
+        if tuple(t.shape) != dims:
+            raise ValueError(f"input {k} has shape {tuple(t.shape)}, the fork is {dims}")
+        nest.inputs[k] = t.data_ptr()
+        for d in range(len(dims)):
+            nest.strides[k][d] = t.stride(d)
+    for name, t, dt in (("out", out, torch.float32), ("result", result, torch.float32),
+                        ("result64", result64, torch.float64), ("result_index", result_index, torch.int64)):
+        if t is not None:
+            if t.dtype != dt or not t.is_contiguous():
+                raise TypeError(f"{name} must be a contiguous {dt} tensor")
+            setattr(nest, name, t.data_ptr())
+    return nest
+
+
+def hx_nest_prepare(nest: Nest) -> None:
+    _check(_lib.hx_nest_prepare(ctypes.byref(nest)), "hx_nest_prepare")
+
+
+def hx_nest_source(nest: Nest) -> str:
+    n = ctypes.c_size_t()
+    _check(_lib.hx_nest_source(ctypes.byref(nest), None, 0, ctypes.byref(n)), "hx_nest_source")
+    buf = ctypes.create_string_buffer(n.value + 1)
+    _check(_lib.hx_nest_source(ctypes.byref(nest), buf, n.value + 1, None), "hx_nest_source")
+    return buf.value.decode()
+
+
+def hx_fork_reduce(ctx: Context, nest: Nest, stream=None) -> None:
+    _check(_lib.hx_fork_reduce(ctx.handle, ctypes.byref(nest), _stream_handle(stream)), "hx_fork_reduce")
+
+
+def fork_reduce(ctx: Context, program, inputs, dims, reduce_dims, monoid="sum", consts=(), want_out=False,
+                want_result64=False, tree="warp", chunk=0, device=None, stream=None):
+    """Run a nest, allocating its outputs; returns (out, result, result_index, result64).
+
+    ``out`` has shape ``dims``; the results have the shape of the outer
+    ``ndim - reduce_dims`` dimensions (None where not requested)."""
+    import torch
+
+    dims = tuple(int(d) for d in dims)
+    if device is None:
+        device = next((t.device for t in inputs if t is not None), torch.device("cuda", ctx.device))
+    outer = dims[:len(dims) - reduce_dims] if reduce_dims else None
+    out = torch.empty(dims, dtype=torch.float32, device=device) if (want_out or not reduce_dims) else None
+    result = result64 = index = None
+    if reduce_dims:
+        result = torch.empty(outer, dtype=torch.float32, device=device)
+        if want_result64:
+            result64 = torch.empty(outer, dtype=torch.float64, device=device)
+        m = MONOIDS[monoid] if isinstance(monoid, str) else int(monoid)
+        if m >= 4:
+            index = torch.empty(outer, dtype=torch.int64, device=device)
+    nest = make_nest(program, inputs, dims, reduce_dims, monoid, consts, out, result, result64, index, tree, chunk)
+    hx_fork_reduce(ctx, nest, stream)
+    return out, result, index, result64
+
+
 # ------------------------------------------------------------------ batches
 HX_TASK_MAP_REDUCE, HX_TASK_STENCIL2D, HX_TASK_HISTOGRAM = 0, 1, 2
 
@@ -350,12 +471,14 @@ class TuneTable(ctypes.Structure):
     """Mirror of ``hx_tune_table``: per-size-class choices (see include/hx.h)."""
 
     _fields_ = [("map_vecs", _I32 * HX_TUNE_CLASSES), ("hist_threads", _I32 * HX_TUNE_CLASSES),
-                ("stencil_rows", _I32 * HX_TUNE_CLASSES), ("batch_map_run", _I32),
+                ("stencil_rows", _I32 * HX_TUNE_CLASSES), ("nest_lane_elems", _I32 * HX_TUNE_CLASSES),
+                ("batch_map_run", _I32),
                 ("batch_stencil_run", _I32)]
 
     def as_dict(self) -> dict:
         return {"map_vecs": list(self.map_vecs), "hist_threads": list(self.hist_threads),
-                "stencil_rows": list(self.stencil_rows), "batch_map_run": self.batch_map_run,
+                "stencil_rows": list(self.stencil_rows), "nest_lane_elems": list(self.nest_lane_elems),
+                "batch_map_run": self.batch_map_run,
                 "batch_stencil_run": self.batch_stencil_run}
 
 

@@ -76,15 +76,20 @@ hx_status hx_create(hx_ctx **out, int device, size_t hbm_budget_bytes) {
         return hx::cuda_fail(e, "hx_create: SM count");
     }
     const size_t bytes = sizeof(hx::WsSlot) * HX_MAX_STREAMS;
+    const size_t nest_bytes = sizeof(hx::NestWs) * HX_MAX_STREAMS;
     e = cudaMalloc(&ctx->ws, bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->nest_ws, nest_bytes);
     if (e != cudaSuccess) {
+        if (ctx->ws) cudaFree(ctx->ws);
         delete ctx;
         return hx::cuda_fail(e, "hx_create: workspace cudaMalloc");
     }
     e = cudaMemset(ctx->ws, 0, bytes);
+    if (e == cudaSuccess) e = cudaMemset(ctx->nest_ws, 0, nest_bytes);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         cudaFree(ctx->ws);
+        cudaFree(ctx->nest_ws);
         delete ctx;
         return hx::cuda_fail(e, "hx_create: workspace clear");
     }
@@ -92,6 +97,7 @@ hx_status hx_create(hx_ctx **out, int device, size_t hbm_budget_bytes) {
     if (st == HX_OK) st = hx::batch_setup(ctx);
     if (st != HX_OK) {
         cudaFree(ctx->ws);
+        cudaFree(ctx->nest_ws);
         delete ctx;
         return st;
     }
@@ -111,6 +117,7 @@ void hx_destroy(hx_ctx *ctx) {
         ctx->pending.clear();
     }
     if (ctx->ws) cudaFree(ctx->ws);
+    if (ctx->nest_ws) cudaFree(ctx->nest_ws);
     delete ctx;
 }
 

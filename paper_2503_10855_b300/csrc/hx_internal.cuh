@@ -53,6 +53,14 @@ struct WsSlot {
 };
 static_assert(sizeof(WsSlot) % 256 == 0, "slot alignment");
 
+// Per-stream workspace of the generic fork-join nests: chunk partials and
+// per-segment arrival tickets (tickets are zero between calls).
+constexpr int kNestCap = 16384;
+struct NestWs {
+    float4 part[kNestCap];
+    unsigned int tick[kNestCap];
+};
+
 // ---------------------------------------------------------------- plans
 struct MrPlan {
     int64_t n;
@@ -473,6 +481,7 @@ struct hx_ctx {
     int num_sms = 0;
     size_t hbm_budget = 0;
     hx::WsSlot *ws = nullptr;   // HX_MAX_STREAMS slots
+    hx::NestWs *nest_ws = nullptr;  // HX_MAX_STREAMS slots, same index as ws
     hx_stream_t slot_stream[HX_MAX_STREAMS] = {};
     bool slot_used[HX_MAX_STREAMS] = {};
     hx_tune_table tune = {};             // per-size-class choices (see hx.h)

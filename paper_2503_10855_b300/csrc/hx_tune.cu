@@ -100,6 +100,7 @@ void hx_tune_table_default(hx_tune_table *t) {
         t->map_vecs[c] = hx::kMrMinVecs;
         t->hist_threads[c] = 512;
         t->stencil_rows[c] = hx::kStRows;
+        t->nest_lane_elems[c] = 16;
     }
     t->batch_map_run = 8;
     t->batch_stencil_run = 16;
@@ -112,6 +113,8 @@ hx_status hx_tune_table_check(const hx_tune_table *t) {
         if (!allowed_vecs(t->map_vecs[c])) return fail(HX_ERR_INVALID, "tune table: map_vecs must be a multiple of 4 in [4, 1024]");
         if (!allowed_threads(t->hist_threads[c])) return fail(HX_ERR_INVALID, "tune table: hist_threads must be 256, 512 or 1024");
         if (!allowed_rows(t->stencil_rows[c])) return fail(HX_ERR_INVALID, "tune table: stencil_rows must be 4, 8 or 16");
+        const int le = t->nest_lane_elems[c];
+        if (le < 8 || le > 512 || le % 8) return fail(HX_ERR_INVALID, "tune table: nest_lane_elems must be a multiple of 8 in [8, 512]");
     }
     if (t->batch_map_run < 1 || t->batch_map_run > 64) return fail(HX_ERR_INVALID, "tune table: batch_map_run must be in [1, 64]");
     if (t->batch_stencil_run < 1 || t->batch_stencil_run > 256)
@@ -135,6 +138,7 @@ hx_status hx_tune_table_save(const hx_tune_table *t, const char *path) {
     arr("map_vecs", t->map_vecs);
     arr("hist_threads", t->hist_threads);
     arr("stencil_rows", t->stencil_rows);
+    arr("nest_lane_elems", t->nest_lane_elems);
     fprintf(f, "  \"batch_map_run\": %d,\n  \"batch_stencil_run\": %d\n}\n", t->batch_map_run, t->batch_stencil_run);
     const bool ok = fclose(f) == 0;
     return ok ? HX_OK : fail(HX_ERR_INVALID, "hx_tune_table_save: write failed");
@@ -154,7 +158,8 @@ hx_status hx_tune_table_load(hx_tune_table *t, const char *path) {
     hx_tune_table_default(&tmp);
     std::vector<long> v;
     struct { const char *key; int32_t *dst; } arrays[] = {
-        {"map_vecs", tmp.map_vecs}, {"hist_threads", tmp.hist_threads}, {"stencil_rows", tmp.stencil_rows}};
+        {"map_vecs", tmp.map_vecs}, {"hist_threads", tmp.hist_threads}, {"stencil_rows", tmp.stencil_rows},
+        {"nest_lane_elems", tmp.nest_lane_elems}};
     for (auto &a : arrays) {
         if (!json_ints(text, a.key, &v) || v.size() != HX_TUNE_CLASSES)
             return fail(HX_ERR_INVALID, std::string("hx_tune_table_load: bad or missing ") + a.key);

@@ -1,0 +1,213 @@
+"""Generic fork-join nests on the GPU against the oracle's sequential nest.
+
+Map values (``out``) are compared bit for bit: both sides round every op once
+to fp32.  Max / min / argmax / argmin are exact.  Sums and products are
+float-float on the GPU and a double left fold in the oracle; the bound is
+1e-5 of the condition (sum of |v|, resp. |prod|) for the fp32 result and
+1e-9 for the double one.  The nests span several chunks and ragged tails,
+all three reduction trees, strided / broadcast / reversed inputs, index ops
+and empty segments.
+"""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+TREES = ["warp", "chunk", "seq"]
+MONOIDS = ["sum", "max", "min", "prod", "argmax", "argmin"]
+
+
+def _np(shape, seed, lo=-1.0, scale=1.0):
+    n = int(np.prod(shape))
+    x = workloads.uniform_pm1_f32(seed, n) if n else np.zeros(0, np.float32)
+    return (x.reshape(shape) * np.float32(scale) + np.float32(lo + 1.0)).astype(np.float32)
+
+
+def _check(hx, ctx, program, arrays, view, dims, rd, monoid, consts=(), tree="warp", chunk=0, want_out=True):
+    """Run one nest on the GPU (inputs = view(device copies)) and the oracle
+    (inputs = view(numpy arrays)); compare."""
+    np_in = view([a for a in arrays])
+    dev = [torch.from_numpy(a).cuda() for a in arrays]
+    t_in = view(dev)
+    out, res, idx, res64 = hx.fork_reduce(ctx, program, t_in, dims, rd, monoid, consts, want_out=want_out,
+                                          want_result64=rd > 0, tree=tree, chunk=chunk)
+    torch.cuda.synchronize()
+    ref_out, ref, ref_idx = oracle.fork_reduce(program, np_in, dims, rd, monoid, consts, want_out=True)
+    if out is not None:
+        np.testing.assert_array_equal(out.cpu().numpy().view(np.uint32), ref_out.view(np.uint32))
+    if rd == 0:
+        return out
+    got = res.cpu().numpy().astype(np.float64)
+    got64 = res64.cpu().numpy()
+    if monoid in ("sum", "prod"):
+        vals = ref_out.reshape(ref.shape + (-1,)).astype(np.float64)
+        cond = np.abs(vals).sum(axis=-1) if monoid == "sum" else np.abs(ref)
+        cond = np.maximum(cond, np.finfo(np.float32).tiny)
+        assert np.all(np.abs(got - ref) <= 1e-5 * cond), (np.max(np.abs(got - ref) / cond))
+        assert np.all(np.abs(got64 - ref) <= 1e-9 * cond), (np.max(np.abs(got64 - ref) / cond))
+    else:
+        np.testing.assert_array_equal(got, ref)
+        np.testing.assert_array_equal(np.signbit(got), np.signbit(ref))
+        np.testing.assert_array_equal(got64, ref)
+    if monoid.startswith("arg"):
+        np.testing.assert_array_equal(idx.cpu().numpy(), ref_idx)
+    return res
+
+
+ident = lambda xs: xs   # noqa: E731
+
+
+@pytest.mark.parametrize("tree", TREES)
+@pytest.mark.parametrize("monoid", MONOIDS)
+@pytest.mark.parametrize("n", [0, 1, 31, 33, 1000, 4097, 100_003])
+def test_full_reduce_1d(gpu, tree, monoid, n):
+    hx = gpu
+    x = _np((n,), 101, lo=-1.0)
+    if monoid == "prod":
+        x = (np.float32(1.0) + x * np.float32(1e-3)).astype(np.float32)
+    with hx.hx_create(0) as ctx:
+        _check(hx, ctx, [("in", 0)], [x], ident, (n,), 1, monoid, tree=tree)
+
+
+@pytest.mark.parametrize("tree", TREES)
+@pytest.mark.parametrize("monoid", MONOIDS)
+@pytest.mark.parametrize("rows,cols", [(129, 5), (64, 31), (33, 1000), (3, 70_001)])
+def test_row_reduce_fused_map(gpu, tree, monoid, rows, cols):
+    # |x - y| * c + y over rows (the max-gradient shape of EDGE, Sec. 5.2)
+    hx = gpu
+    x = _np((rows, cols), 102)
+    y = _np((rows, cols), 103)
+    prog = [("in", 0), ("in", 1), "sub", "abs", ("const", 0), ("in", 1), "fma"]
+    consts = [0.75]
+    if monoid == "prod":
+        prog = [("in", 0), ("const", 1), "mul", ("const", 2), "add"]   # 1 + x/1024: well conditioned
+        consts = [0.75, 1.0 / 1024, 1.0]
+    with hx.hx_create(0) as ctx:
+        _check(hx, ctx, prog, [x, y], ident, (rows, cols), 1, monoid, consts, tree=tree)
+
+
+@pytest.mark.parametrize("monoid", MONOIDS)
+@pytest.mark.parametrize("rd", [1, 2, 3])
+def test_3d_permuted_and_broadcast(gpu, monoid, rd):
+    hx = gpu
+    a = _np((7, 9, 33), 104)                      # viewed as (33, 7, 9): a permutation
+    b = _np((9,), 105)                            # broadcast along dims 0 and 1
+    view = lambda xs: [xs[0].transpose(2, 0, 1) if isinstance(xs[0], np.ndarray) else xs[0].permute(2, 0, 1),  # noqa: E731
+                       (np.broadcast_to(xs[1], (33, 7, 9)) if isinstance(xs[1], np.ndarray)
+                        else xs[1].expand(33, 7, 9))]
+    prog = [("in", 0), ("in", 1), "mul", ("index", 2), ("const", 0), "mul", "add"]
+    if monoid == "prod":
+        prog = [("in", 0), ("const", 1), "mul", ("const", 2), "add"]
+    with hx.hx_create(0) as ctx:
+        _check(hx, ctx, prog, [a, b], view, (33, 7, 9), rd, monoid, [0.125, 1.0 / 256, 1.0])
+
+
+@pytest.mark.parametrize("tree", TREES)
+def test_index_only_program_and_map_only(gpu, tree):
+    hx = gpu
+    with hx.hx_create(0) as ctx:
+        dims = (37, 61)
+        out, _, _, _ = hx.fork_reduce(ctx, [("index", 0), ("const", 0), ("index", 1), "fma"], [], dims, 0,
+                                      consts=[61.0], tree=tree, device="cuda:0")
+        np.testing.assert_array_equal(out.cpu().numpy().ravel(), np.arange(37 * 61, dtype=np.float32))
+        # argmax of -|j - i| is the diagonal
+        _, res, idx, _ = hx.fork_reduce(ctx, [("index", 1), ("index", 0), "sub", "abs", "neg"], [], (50, 50), 1,
+                                        "argmax", tree=tree, device="cuda:0")
+        assert torch.equal(idx.cpu(), torch.arange(50))
+        x = _np((300, 301), 106)
+        _check(hx, ctx, [("in", 0), "abs", "sqrt", ("in", 0), "div"], [x], ident, (300, 301), 0, "sum", tree=tree)
+
+
+def test_reversed_strides_through_the_abi(gpu):
+    hx = gpu
+    n = 10_001
+    x = _np((n,), 107)
+    with hx.hx_create(0) as ctx:
+        t = torch.from_numpy(x).cuda()
+        res = torch.empty((), dtype=torch.float32, device="cuda:0")
+        idx = torch.empty((), dtype=torch.int64, device="cuda:0")
+        out = torch.empty(n, dtype=torch.float32, device="cuda:0")
+        nest = hx.make_nest([("in", 0)], [t], (n,), 1, "argmax", out=out, result=res, result_index=idx)
+        nest.inputs[0] = t.data_ptr() + 4 * (n - 1)     # walk x backwards: stride -1
+        nest.strides[0][0] = -1
+        hx.hx_fork_reduce(ctx, nest)
+        torch.cuda.synchronize()
+        _, ref, ref_idx = oracle.fork_reduce([("in", 0)], [x[::-1]], (n,), 1, "argmax")
+        np.testing.assert_array_equal(out.cpu().numpy(), x[::-1])
+        assert float(res) == float(ref) and int(idx) == int(ref_idx)
+
+
+def test_ties_nans_signed_zeros(gpu):
+    hx = gpu
+    nan = np.float32("nan")
+    x = _np((6, 1000), 108)
+    x[0, 10] = x[0, 900] = np.float32(7.0)
+    x[1, :] = nan
+    x[2, ::3] = nan
+    x[3, :] = np.float32(-0.0)
+    x[3, 500] = np.float32(0.0)
+    x[4, :] = np.float32(0.0)
+    x[4, 777] = np.float32(-0.0)
+    x[5, 5] = x[5, 995] = np.float32(-9.0)
+    with hx.hx_create(0) as ctx:
+        for tree in TREES:
+            for monoid in ("max", "min", "argmax", "argmin"):
+                _check(hx, ctx, [("in", 0)], [x], ident, x.shape, 1, monoid, tree=tree)
+
+
+@pytest.mark.parametrize("chunk", [256, 1000, 4096])
+def test_explicit_chunks_and_determinism(gpu, chunk):
+    hx = gpu
+    x = _np((4, 200_000), 109)
+    with hx.hx_create(0) as ctx:
+        r1 = _check(hx, ctx, [("in", 0), ("in", 0), "mul"], [x], ident, x.shape, 1, "sum", chunk=chunk)
+        r2 = _check(hx, ctx, [("in", 0), ("in", 0), "mul"], [x], ident, x.shape, 1, "sum", chunk=chunk)
+        assert torch.equal(r1, r2)
+
+
+def test_large_full_reduce_caps_partials(gpu):
+    # 2^26 elements: more chunks than the workspace holds, so the chunk grows
+    hx = gpu
+    n = (1 << 26) + 7
+    x = workloads.uniform_pm1_f32(110, n)
+    with hx.hx_create(0) as ctx:
+        for monoid in ("sum", "argmax"):
+            _check(hx, ctx, [("in", 0), "abs"], [x], ident, (n,), 1, monoid, want_out=False)
+
+
+def test_empty_segments_give_identities(gpu):
+    hx = gpu
+    with hx.hx_create(0) as ctx:
+        x = torch.zeros((5, 0), device="cuda:0")
+        for monoid, ident_v in (("sum", 0.0), ("prod", 1.0), ("max", -np.inf), ("min", np.inf)):
+            _, res, _, _ = hx.fork_reduce(ctx, [("in", 0)], [x], (5, 0), 1, monoid)
+            assert torch.equal(res.cpu(), torch.full((5,), ident_v))
+        _, res, idx, _ = hx.fork_reduce(ctx, [("in", 0)], [x], (5, 0), 1, "argmin")
+        assert torch.equal(idx.cpu(), torch.full((5,), -1))
+        # outer extent 0: nothing to do, nothing written
+        hx.fork_reduce(ctx, [("in", 0)], [torch.zeros((0, 4), device="cuda:0")], (0, 4), 1, "sum")
+
+
+def test_streams_use_separate_workspace(gpu):
+    hx = gpu
+    x = _np((1 << 20,), 111)
+    y = _np((1 << 20,), 112)
+    with hx.hx_create(0) as ctx:
+        tx, ty = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
+        s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+        torch.cuda.synchronize()
+        outs = []
+        for _ in range(4):
+            for s, t in ((s1, tx), (s2, ty)):
+                with torch.cuda.stream(s):
+                    outs.append(hx.fork_reduce(ctx, [("in", 0)], [t], t.shape, 1, "sum", stream=s)[1])
+        torch.cuda.synchronize()
+        for k, r in enumerate(outs):
+            assert torch.equal(r, outs[k % 2])
+        ref_x = oracle.fork_reduce([("in", 0)], [x], x.shape, 1, "sum")[1]
+        assert abs(float(outs[0]) - float(ref_x)) <= 1e-5 * np.abs(x).astype(np.float64).sum()
