@@ -459,6 +459,11 @@ def bench_hx(args, rank, world, local):
     # ---- serving: continuous batching vs one launch per request
     serving = bench_serving(hx, ctx, dev) if not args.no_serving else None
 
+    # ---- generic nests and the reduction-tree ablation
+    nests = None
+    if not args.no_nests:
+        nests = {"workloads": bench_nests(hx, ctx, dev, peak), "tree_ablation": bench_tree_ablation(hx, ctx, dev)}
+
     # ---- end to end through the public API with pinned host buffers
     e2e = bench_e2e(args, hx, ctx, dev, x_h, y_h, u_h, v_h, batch, batch_bufs, BATCH_BYTES)
 
@@ -498,6 +503,7 @@ def bench_hx(args, rank, world, local):
         "cpu_baseline": cpu,
         "batched": batched,
         "serving": serving,
+        "nests": nests,
         "e2e": e2e,
         "gpu_launches": launches_per_step * K,
         "clocks": clk.summary(),
@@ -601,6 +607,87 @@ def bench_serving(hx, ctx, dev, rates=SERVE_RATES, max_requests=4000, window_s=0
     return {"mix": "1/3 map->reduce, 1/3 jacobi (20 sweeps, square side ~sqrt(n)), 1/3 histogram+scan; "
                    "sizes log-uniform 1K-16M elements; Poisson arrivals (seed 4)",
             "budget_gb": SERVE_BUDGET / 2**30, "points": points, "equal_p99": eq}
+
+
+def _time_ms(fn, reps, warm=2):
+    """Mean ms of fn() over reps calls, CUDA events on the current stream."""
+    import torch
+
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        fn()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def bench_nests(hx, ctx, dev, peak, reps=20):
+    """Generic fork-join nests (map program + monoid reduce) at HBM scale.
+
+    Every input is at least 512 MiB (far above the 126 MB L2), so each call
+    streams from HBM.  Algorithmic bytes = inputs read once + outputs written."""
+    import torch
+
+    F = 4
+    g = torch.Generator(device=dev).manual_seed(5)
+    rows = cols = 16384
+    big = torch.rand(1 << 28, device=dev, generator=g) * 2 - 1
+    x27, y27 = big[: 1 << 27], big[1 << 27:]
+    mat = big.view(rows, cols)
+    out27 = torch.empty(1 << 27, device=dev)
+    res = torch.empty(1 << 24, device=dev)
+    idx = torch.empty(1, dtype=torch.int64, device=dev)
+    cases = [
+        ("sum of 2^28 fp32", [("in", 0)], [big], (1 << 28,), 1, "sum", None, res[:1], None, 4 << 28),
+        ("row sums 16384 x 16384", [("in", 0)], [mat], (rows, cols), 1, "sum", None, res[:rows], None,
+         F * rows * cols + F * rows),
+        ("max over 2^24 rows of 8", [("in", 0)], [big[: 1 << 27].view(1 << 24, 8)], (1 << 24, 8), 1, "max",
+         None, res, None, F * (1 << 27) + F * (1 << 24)),
+        ("argmax |x - y| over 2^27", [("in", 0), ("in", 1), "sub", "abs"], [x27, y27], (1 << 27,), 1, "argmax",
+         None, res[:1], idx, 8 << 27),
+        ("map out = fma(x, 1.5, y) over 2^27", [("in", 0), ("const", 0), ("in", 1), "fma"], [x27, y27],
+         (1 << 27,), 0, "sum", out27, None, None, 12 << 27),
+        ("3-D sum over dims 1,2 of a 1024 x 512 x 512 permuted view", [("in", 0)],
+         [big.view(512, 1024, 512).permute(1, 0, 2)], (1024, 512, 512), 2, "sum", None, res[:1024], None,
+         F * (1 << 28) + F * 1024),
+    ]
+    rows_out = []
+    for name, prog, ins, dims, rd, monoid, out, result, index, nbytes in cases:
+        nest = hx.make_nest(prog, ins, dims, rd, monoid, consts=[1.5], out=out, result=result,
+                            result_index=index)
+        hx.hx_nest_prepare(nest)
+        ms = _time_ms(lambda: hx.hx_fork_reduce(ctx, nest), reps)
+        gbs = nbytes / (ms * 1e-3) / 1e9
+        rows_out.append({"nest": name, "ms": round(ms, 4), "algorithmic_bytes": nbytes, "GB/s": round(gbs, 1),
+                         "frac_of_measured_hbm": round(gbs / peak, 4)})
+    del big, out27, res
+    torch.cuda.empty_cache()
+    return rows_out
+
+
+def bench_tree_ablation(hx, ctx, dev, n=1 << 20, reps=5):
+    """The EDGE experiment of Sec. 5.2 as a kernel-level ablation: one large
+    max reduction (max |x| over a 1024 x 1024 image) as the sequential loop,
+    as the two-level chunk tree, and as the warp-shuffle tree."""
+    import torch
+
+    g = torch.Generator(device=dev).manual_seed(6)
+    x = torch.rand(n, device=dev, generator=g) * 2 - 1
+    res = torch.empty(1, device=dev)
+    ms = {}
+    for tree in ("seq", "chunk", "warp"):
+        nest = hx.make_nest([("in", 0), "abs"], [x], (n,), 1, "max", result=res, tree=tree)
+        hx.hx_nest_prepare(nest)
+        ms[tree] = _time_ms(lambda: hx.hx_fork_reduce(ctx, nest), reps if tree == "seq" else 50)
+    return {"reduction": f"max |x| over {n} fp32 (one segment)", "seq_ms": round(ms["seq"], 4),
+            "chunk_tree_ms": round(ms["chunk"], 4), "warp_tree_ms": round(ms["warp"], 4),
+            "chunk_tree_speedup": round(ms["seq"] / ms["chunk"], 2),
+            "warp_tree_speedup": round(ms["seq"] / ms["warp"], 2),
+            "paper_edge_end_to_end": {"tree": 6.22, "tree_plus_warp": 9.77}}
 
 
 def bench_batched_vs_per_launch(hx, ctx, batch, tasks, stream, reps=10):
@@ -724,6 +811,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--autotune", action="store_true", help="re-measure the tuning table before timing")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving sweep")
+    ap.add_argument("--no-nests", action="store_true", help="skip the generic-nest section")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
