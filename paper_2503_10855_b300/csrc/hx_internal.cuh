@@ -53,12 +53,20 @@ struct WsSlot {
 };
 static_assert(sizeof(WsSlot) % 256 == 0, "slot alignment");
 
-// Per-stream workspace of the generic fork-join nests: chunk partials and
-// per-segment arrival tickets (tickets are zero between calls).
-constexpr int kNestCap = 16384;
+// Per-stream workspace of the generic fork-join nests: chunk partials (one
+// per chunk), group partials (one per 32 chunks of a segment) and arrival
+// tickets, which are zero between calls.  A chunk plan keeps segments x
+// chunks <= kNestCap; with more than 32 chunks per segment there are fewer
+// than kNestCap / 32 segments, which bounds the group arrays.
+constexpr int kNestCap = 65536;
+constexpr int kNestTick = kNestCap / 2;
+constexpr int kNestCap2 = 4096;
+constexpr int kNestTick2 = 2048;
 struct NestWs {
     float4 part[kNestCap];
-    unsigned int tick[kNestCap];
+    float4 part2[kNestCap2];
+    unsigned int tick[kNestTick];
+    unsigned int tick2[kNestTick2];
 };
 
 // ---------------------------------------------------------------- plans

@@ -6,25 +6,31 @@
 // Like the Hercules GPU backend (Sec. 4.4), the library turns the nest into a
 // CUDA kernel: the map program becomes one fused expression, pasted into the
 // hand-written kernel template below together with the nest's shape
-// (dimension counts, monoid, reduction schedule, addressing mode of every
+// (dimension split, monoid, reduction schedule, addressing mode of every
 // input), and the result is compiled for sm_103a with NVRTC.  Sizes, strides,
 // constants and pointers are launch arguments, so one compiled kernel serves
 // every nest of the same shape; compiled kernels are cached process-wide by
 // their source text.
 //
-// Reduction schedules (Sec. 5.2, the reduction-tree macro and warp reductions):
-//   HX_TREE_WARP   chunks of a segment go to groups of G lanes (G = 32, or the
-//                  next power of two >= the segment length when that is below
-//                  32); lanes stride through the chunk, fold their elements
-//                  in order, combine with a shuffle butterfly; chunk partials
-//                  are combined by the group that arrives last (ticket).
+// Reduction schedules (Sec. 5.2: the reduction-tree macro -- chunk,
+// monoid-reassociate, fork-fission -- and the lowering of reductions to warp
+// primitives):
+//   HX_TREE_WARP   a segment is cut into chunks; a group of G lanes (G = 32,
+//                  fewer for short segments) takes a chunk in "slots" of 4
+//                  consecutive elements, lane l taking slots l, l+G, ...; each
+//                  lane folds its elements in increasing order, the group
+//                  combines lanes with a shuffle butterfly.  Chunk partials
+//                  form a 3-level tree (chunks -> groups of 32 chunks ->
+//                  segment), each level finished by the last arrival (ticket).
 //   HX_TREE_CHUNK  the two-level tree of the reduction-tree macro: one thread
 //                  folds each contiguous chunk sequentially, the last thread
 //                  to finish folds the chunk partials sequentially.
 //   HX_TREE_SEQ    the untransformed loop: one thread folds a whole segment.
 // Sums and products accumulate in float-float (hi, lo) pairs; extrema are
-// exact.  The combination order depends only on the nest's sizes, schedule
-// and chunk, so results are bit-identical from run to run.
+// exact.  The combination order depends only on the nest's sizes, schedule,
+// chunk and tuning table -- not on pointer alignment (the float4 and scalar
+// load paths assign the same elements to the same lanes) -- so results are
+// bit-identical from run to run.
 #include <nvrtc.h>
 
 #include <cstdarg>
@@ -39,33 +45,49 @@
 namespace {
 
 constexpr int kNestBlock = 256;
-constexpr int kNestU = 8;   // elements per lane in flight (warp tree)
 
 // ---------------------------------------------------------------- device template
-// Everything the generated kernels share.  MONOID (-1 = map only), TREE, G and
-// the HAS_* flags are #defined by the generated header in front of it.
+// Everything the generated kernels share.  MONOID (-1 = map only), TREE, G, U,
+// VEC and the HAS_* flags are #defined by the generated header in front of
+// it; the generated part also supplies struct Seg, seg_setup(), struct Buf,
+// load_group(), map_elem() and map_at().
 const char *kPrelude = R"CUDA(
 typedef long long i64;
+typedef unsigned long long u64;
 struct NestParams {
     const float *in[4];
     i64 st[4][3];
-    i64 lin[4];     // stride of an input addressed linearly inside a segment
+    i64 lin[4];         // stride of an input addressed linearly inside a segment
     float c[8];
     i64 dims[3];
-    i64 outer, inner, chunk, nchunks, n_items;
+    unsigned dm[3];     // n / dims[d] == (n * dm[d]) >> ds[d] for 0 <= n < 2^31
+    unsigned ds[3];
+    i64 outer, inner, chunk, nchunks, ngroups, n_items;
     float *out;
     float *res;
     double *res64;
     i64 *res_idx;
-    float4 *part;
-    unsigned *tick;
+    float4 *part;       // one partial per chunk
+    float4 *part2;      // one partial per group of 32 chunks
+    unsigned *tick;     // chunk arrivals per (segment, group)
+    unsigned *tick2;    // group arrivals per segment
 };
+
+// Quotient by a fork factor, by multiplication (Granlund and Montgomery,
+// "Division by invariant integers using multiplication", 1994, Thm. 4.2 with
+// N = 31): exact for 0 <= n < 2^31.
+__device__ __forceinline__ unsigned hx_div(const NestParams &p, int d, unsigned n) {
+    return (unsigned)(((u64)n * p.dm[d]) >> p.ds[d]);
+}
 
 __device__ __forceinline__ float hx_minnum(float a, float b) {
     return isnan(a) ? b : (isnan(b) ? a : (b < a ? b : a));
 }
 __device__ __forceinline__ float hx_maxnum(float a, float b) {
     return isnan(a) ? b : (isnan(b) ? a : (b > a ? b : a));
+}
+__device__ __forceinline__ float hx_comp(const float4 &v, int q) {
+    return q == 0 ? v.x : (q == 1 ? v.y : (q == 2 ? v.z : v.w));
 }
 #define HX_NEG_INF __int_as_float(0xff800000)
 #define HX_POS_INF __int_as_float(0x7f800000)
@@ -76,9 +98,10 @@ struct Acc { float hi, lo; };
 struct Acc { float v; };
 #elif MONOID >= 4
 struct Acc { float v; i64 i; };
+#else
+struct Acc { int unused; };
 #endif
 
-#if MONOID >= 0
 __device__ __forceinline__ Acc acc_init() {
 #if MONOID == 0
     return Acc{0.0f, 0.0f};
@@ -90,8 +113,10 @@ __device__ __forceinline__ Acc acc_init() {
     return Acc{HX_POS_INF};
 #elif MONOID == 4
     return Acc{HX_NEG_INF, -1};
-#else
+#elif MONOID == 5
     return Acc{HX_POS_INF, -1};
+#else
+    return Acc{0};
 #endif
 }
 
@@ -117,11 +142,12 @@ __device__ __forceinline__ void acc_fold(Acc &a, float v, i64 r) {
     if (v < a.v || (v == 0.0f && a.v == 0.0f && !signbit(a.v) && signbit(v))) a.v = v;
 #elif MONOID == 4
     if (!isnan(v) && (a.i < 0 || v > a.v)) { a.v = v; a.i = r; }
-#else
+#elif MONOID == 5
     if (!isnan(v) && (a.i < 0 || v < a.v)) { a.v = v; a.i = r; }
 #endif
 }
 
+#if MONOID >= 0
 // Combine two partial results.  Commutative bit for bit (the exact TwoSum /
 // TwoProd error terms do not depend on operand order; extrema break ties by
 // the smaller thread index), so both lanes of a butterfly pair agree.
@@ -153,18 +179,26 @@ __device__ __forceinline__ Acc acc_combine(Acc a, Acc b) {
 #endif
 }
 
+template <int W>
 __device__ __forceinline__ Acc acc_shfl(unsigned mask, Acc a, int k) {
     Acc o = a;
 #if MONOID == 0 || MONOID == 3
-    o.hi = __shfl_xor_sync(mask, a.hi, k, G);
-    o.lo = __shfl_xor_sync(mask, a.lo, k, G);
+    o.hi = __shfl_xor_sync(mask, a.hi, k, W);
+    o.lo = __shfl_xor_sync(mask, a.lo, k, W);
 #elif MONOID == 1 || MONOID == 2
-    o.v = __shfl_xor_sync(mask, a.v, k, G);
+    o.v = __shfl_xor_sync(mask, a.v, k, W);
 #else
-    o.v = __shfl_xor_sync(mask, a.v, k, G);
-    o.i = __shfl_xor_sync(mask, a.i, k, G);
+    o.v = __shfl_xor_sync(mask, a.v, k, W);
+    o.i = __shfl_xor_sync(mask, a.i, k, W);
 #endif
     return o;
+}
+
+template <int W>
+__device__ __forceinline__ Acc acc_butterfly(unsigned mask, Acc a) {
+#pragma unroll
+    for (int k = W / 2; k >= 1; k >>= 1) a = acc_combine(a, acc_shfl<W>(mask, a, k));
+    return a;
 }
 
 union PartBits { float4 f4; struct { float a, b; i64 i; } s; };
@@ -212,20 +246,40 @@ __device__ __forceinline__ void write_result(const NestParams &p, i64 s, Acc a) 
 #endif
 #endif
 }
-
-// Chunk partial of item (s, c); the last chunk of segment s to arrive folds
-// all of the segment's partials in chunk order.  Called by one thread.
-__device__ __forceinline__ bool publish_partial(const NestParams &p, i64 s, i64 item, Acc a) {
-    part_store(p.part + item, a);
-    __threadfence();
-    return atomicAdd(p.tick + s, 1u) == (unsigned)(p.nchunks - 1);
-}
 #endif  // MONOID >= 0
 )CUDA";
 
-// The kernel bodies.  OUTER_SETUP(s), LOAD(j, r) / MAP(j, r) and the
-// per-element index setup INNER_IDX(r) are generated per nest.
+// Warp-tree kernel (TREE == 0).  Double-buffered: the loads of the next U
+// slots per lane are issued before the current ones are folded.
 const char *kWarpBody = R"CUDA(
+__device__ __forceinline__ void proc_group(const NestParams &p, const Seg &g, const Buf &b, i64 t0, Acc &acc) {
+#pragma unroll
+    for (int j = 0; j < U; ++j) {
+        const i64 t = t0 + (i64)j * G;
+        if (t < g.nslot) {
+            const i64 r0 = g.r_begin + 4 * t;
+            float vq[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) vq[q] = (VEC || r0 + q < g.r_end) ? map_elem(p, g, b, j, q, r0 + q) : 0.0f;
+#if HAS_OUT
+            float *o = p.out + g.s * p.inner + r0;
+            if (VEC) {
+                *(float4 *)o = make_float4(vq[0], vq[1], vq[2], vq[3]);
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (r0 + q < g.r_end) o[q] = vq[q];
+            }
+#endif
+#if MONOID >= 0
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (VEC || r0 + q < g.r_end) acc_fold(acc, vq[q], r0 + q);
+#endif
+        }
+    }
+}
+
 extern "C" __global__ void __launch_bounds__(256) hx_nest_kernel(const NestParams p) {
     const int lane = threadIdx.x & 31;
     const int gl = lane & (G - 1);
@@ -233,96 +287,107 @@ extern "C" __global__ void __launch_bounds__(256) hx_nest_kernel(const NestParam
     const i64 per_cta = 256 / G;
     for (i64 item = (i64)blockIdx.x * per_cta + threadIdx.x / G; item < p.n_items;
          item += (i64)gridDim.x * per_cta) {
-        const i64 s = item / p.nchunks;
-        const i64 r_begin = (item - s * p.nchunks) * p.chunk;
-        const i64 r_end = min(p.inner, r_begin + p.chunk);
-        OUTER_SETUP
-#if MONOID >= 0
+        Seg g;
+        g.s = p.nchunks == 1 ? item : item / p.nchunks;
+        const i64 c = item - g.s * p.nchunks;
+        g.r_begin = c * p.chunk;
+        g.r_end = min(p.inner, g.r_begin + p.chunk);
+        g.nslot = (g.r_end - g.r_begin + 3) >> 2;
+        seg_setup(p, g);
         Acc acc = acc_init();
-#endif
-        for (i64 r0 = r_begin + gl; r0 < r_end; r0 += (i64)G * U) {
-            LOAD_DECL
-#pragma unroll
-            for (int j = 0; j < U; ++j) {
-                const i64 r = r0 + (i64)j * G;
-                if (r < r_end) {
-                    LOAD_BODY
-                }
-            }
-#pragma unroll
-            for (int j = 0; j < U; ++j) {
-                const i64 r = r0 + (i64)j * G;
-                if (r < r_end) {
-                    MAP_BODY
-#if HAS_OUT
-                    p.out[s * p.inner + r] = v;
-#endif
-#if MONOID >= 0
-                    acc_fold(acc, v, r);
-#endif
-                }
-            }
+        Buf ba, bb;
+        load_group(p, g, ba, gl);
+        for (i64 t0 = gl; t0 < g.nslot; t0 += 2 * G * U) {
+            load_group(p, g, bb, t0 + G * U);
+            proc_group(p, g, ba, t0, acc);
+            load_group(p, g, ba, t0 + 2 * G * U);
+            proc_group(p, g, bb, t0 + G * U, acc);
         }
 #if MONOID >= 0
-#pragma unroll
-        for (int k = G / 2; k >= 1; k >>= 1) acc = acc_combine(acc, acc_shfl(gmask, acc, k));
+        acc = acc_butterfly<G>(gmask, acc);
         if (p.nchunks == 1) {
-            if (gl == 0) write_result(p, s, acc);
-        } else {
-            // nchunks > 1 only with G == 32: the whole warp shares the item
-            unsigned last = 0;
-            if (lane == 0) last = publish_partial(p, s, item, acc) ? 1u : 0u;
-            last = __shfl_sync(0xffffffffu, last, 0);
-            if (last) {
-                __threadfence();
-                Acc t = acc_init();
-                for (i64 q = lane; q < p.nchunks; q += 32) t = acc_combine(t, part_load(p.part + s * p.nchunks + q));
-#pragma unroll
-                for (int k = 16; k >= 1; k >>= 1) t = acc_combine(t, acc_shfl(0xffffffffu, t, k));
-                if (lane == 0) {
-                    write_result(p, s, t);
-                    p.tick[s] = 0u;
-                }
+            if (gl == 0) write_result(p, g.s, acc);
+            continue;
+        }
+        // Several chunks per segment happen only with G == 32: the whole warp
+        // shares the item.  Level 1: the last chunk of its group of 32 folds
+        // the group's partials.
+        const i64 grp = c >> 5;
+        const int gsize = (int)min((i64)32, p.nchunks - grp * 32);
+        unsigned *t1 = p.tick + g.s * p.ngroups + grp;
+        unsigned last = 0;
+        if (lane == 0) {
+            part_store(p.part + item, acc);
+            __threadfence();
+            last = atomicAdd(t1, 1u) == (unsigned)(gsize - 1) ? 1u : 0u;
+        }
+        if (!__shfl_sync(0xffffffffu, last, 0)) continue;
+        __threadfence();
+        Acc t = lane < gsize ? part_load(p.part + g.s * p.nchunks + grp * 32 + lane) : acc_init();
+        t = acc_butterfly<32>(0xffffffffu, t);
+        if (p.ngroups == 1) {
+            if (lane == 0) {
+                write_result(p, g.s, t);
+                *t1 = 0u;
             }
+            continue;
+        }
+        // Level 2: the last group of the segment folds the group partials.
+        last = 0;
+        if (lane == 0) {
+            *t1 = 0u;
+            part_store(p.part2 + g.s * p.ngroups + grp, t);
+            __threadfence();
+            last = atomicAdd(p.tick2 + g.s, 1u) == (unsigned)(p.ngroups - 1) ? 1u : 0u;
+        }
+        if (!__shfl_sync(0xffffffffu, last, 0)) continue;
+        __threadfence();
+        Acc u = acc_init();
+        for (i64 q = lane; q < p.ngroups; q += 32) u = acc_combine(u, part_load(p.part2 + g.s * p.ngroups + q));
+        u = acc_butterfly<32>(0xffffffffu, u);
+        if (lane == 0) {
+            write_result(p, g.s, u);
+            p.tick2[g.s] = 0u;
         }
 #endif
     }
 }
 )CUDA";
 
+// One thread per item: HX_TREE_CHUNK (items = chunks of a segment) or
+// HX_TREE_SEQ (items = segments).  Sequential fold in thread-ID order; the
+// last chunk of a segment folds the chunk partials in chunk order.
 const char *kThreadBody = R"CUDA(
-// One thread per item: HX_TREE_CHUNK (items = chunks) or HX_TREE_SEQ (items =
-// segments, nchunks == 1).  Sequential fold in thread-ID order.
 extern "C" __global__ void __launch_bounds__(256) hx_nest_kernel(const NestParams p) {
     for (i64 item = (i64)blockIdx.x * 256 + threadIdx.x; item < p.n_items; item += (i64)gridDim.x * 256) {
-        const i64 s = item / p.nchunks;
-        const i64 r_begin = (item - s * p.nchunks) * p.chunk;
-        const i64 r_end = min(p.inner, r_begin + p.chunk);
-        OUTER_SETUP
-#if MONOID >= 0
+        Seg g;
+        g.s = p.nchunks == 1 ? item : item / p.nchunks;
+        g.r_begin = (item - g.s * p.nchunks) * p.chunk;
+        g.r_end = min(p.inner, g.r_begin + p.chunk);
+        g.nslot = 0;
+        seg_setup(p, g);
         Acc acc = acc_init();
-#endif
-        for (i64 r = r_begin; r < r_end; ++r) {
-            const int j = 0;
-            LOAD_DECL
-            LOAD_BODY
-            MAP_BODY
+#pragma unroll 4
+        for (i64 r = g.r_begin; r < g.r_end; ++r) {
+            const float v = map_at(p, g, r);
 #if HAS_OUT
-            p.out[s * p.inner + r] = v;
+            p.out[g.s * p.inner + r] = v;
 #endif
-#if MONOID >= 0
             acc_fold(acc, v, r);
-#endif
         }
 #if MONOID >= 0
         if (p.nchunks == 1) {
-            write_result(p, s, acc);
-        } else if (publish_partial(p, s, item, acc)) {
+            write_result(p, g.s, acc);
+            continue;
+        }
+        part_store(p.part + item, acc);
+        __threadfence();
+        if (atomicAdd(p.tick + g.s, 1u) == (unsigned)(p.nchunks - 1)) {
             __threadfence();
             Acc t = acc_init();
-            for (i64 q = 0; q < p.nchunks; ++q) t = acc_combine(t, part_load(p.part + s * p.nchunks + q));
-            write_result(p, s, t);
-            p.tick[s] = 0u;
+            for (i64 q = 0; q < p.nchunks; ++q) t = acc_combine(t, part_load(p.part + g.s * p.nchunks + q));
+            write_result(p, g.s, t);
+            p.tick[g.s] = 0u;
         }
 #endif
     }
@@ -338,20 +403,25 @@ struct NestArgs {
     int64_t lin[4];
     float c[8];
     int64_t dims[3];
-    int64_t outer, inner, chunk, nchunks, n_items;
+    uint32_t dm[3];
+    uint32_t ds[3];
+    int64_t outer, inner, chunk, nchunks, ngroups, n_items;
     float *out;
     float *res;
     double *res64;
     int64_t *res_idx;
     float4 *part;
+    float4 *part2;
     unsigned *tick;
+    unsigned *tick2;
 };
-static_assert(sizeof(NestArgs) == 304, "NestParams layout");
+static_assert(sizeof(NestArgs) == 352, "NestParams layout");
 
 struct Shape {
-    int ndim, m;          // fork dims; dims addressed per segment (outer)
+    int ndim, m;          // fork dims; outer dims (those indexing segments)
     int monoid;           // -1: map only
     int tree, G, U;
+    bool vec;             // float4 loads / stores (aligned, unit-stride, inner % 4 == 0)
     bool has_out, has_res64, use32;
     bool used[HX_NEST_MAX_INPUTS];
     bool linear[HX_NEST_MAX_INPUTS];
@@ -458,33 +528,6 @@ bool linear_stride(const hx_nest *n, int m, int k, int64_t *S) {
     return true;
 }
 
-Shape shape_of(const hx_nest *n) {
-    Shape sh{};
-    sh.ndim = n->ndim;
-    int64_t outer, inner;
-    extents(n, &outer, &inner, &sh.m);
-    sh.monoid = n->reduce_dims == 0 ? -1 : n->monoid;
-    sh.tree = n->tree;
-    sh.U = kNestU;
-    sh.G = 32;
-    if (n->tree == HX_TREE_WARP && inner < 32) {
-        sh.G = 1;
-        while (sh.G < inner) sh.G *= 2;
-    }
-    sh.has_out = n->out != nullptr;
-    sh.has_res64 = n->reduce_dims > 0 && n->result64 != nullptr;
-    sh.use32 = inner < ((int64_t)1 << 31);
-    for (int k = 0; k < n->n_ops; ++k) {
-        if (n->ops[k].code == HX_OP_IN) sh.used[n->ops[k].arg] = true;
-        if (n->ops[k].code == HX_OP_INDEX) sh.index_used[n->ops[k].arg] = true;
-    }
-    for (int k = 0; k < HX_NEST_MAX_INPUTS; ++k) {
-        int64_t S;
-        sh.linear[k] = linear_stride(n, sh.m, k, &S);
-    }
-    return sh;
-}
-
 std::string fmt(const char *f, ...) __attribute__((format(printf, 1, 2)));
 std::string fmt(const char *f, ...) {
     char buf[512];
@@ -495,18 +538,88 @@ std::string fmt(const char *f, ...) {
     return buf;
 }
 
-// The map program as one C expression over x<k>[j] (loaded inputs), p.c[k]
-// and the fork indices i<d>.
-std::string map_expression(const hx_nest *n) {
+Shape shape_of(const hx_nest *n) {
+    Shape sh{};
+    sh.ndim = n->ndim;
+    int64_t outer, inner;
+    extents(n, &outer, &inner, &sh.m);
+    sh.monoid = n->reduce_dims == 0 ? -1 : n->monoid;
+    sh.tree = n->tree;
+    int n_used = 0;
+    for (int k = 0; k < n->n_ops; ++k) {
+        if (n->ops[k].code == HX_OP_IN && !sh.used[n->ops[k].arg]) {
+            sh.used[n->ops[k].arg] = true;
+            ++n_used;
+        }
+        if (n->ops[k].code == HX_OP_INDEX) sh.index_used[n->ops[k].arg] = true;
+    }
+    sh.U = n_used <= 2 ? 4 : 2;
+    sh.G = 32;
+    if (n->tree == HX_TREE_WARP) {
+        const int64_t per_lane = 4 * sh.U;   // elements a lane loads per buffer
+        const int64_t want = (inner + per_lane - 1) / per_lane;
+        sh.G = 1;
+        while (sh.G < 32 && sh.G < want) sh.G *= 2;
+    }
+    sh.has_out = n->out != nullptr;
+    sh.has_res64 = n->reduce_dims > 0 && n->result64 != nullptr;
+    sh.use32 = inner < ((int64_t)1 << 31);
+    // float4 slots: every slot of 4 consecutive threads must be 4 contiguous,
+    // 16-byte aligned floats of every input (and of out).  That holds for a
+    // linear input of stride 1, and for a strided one whose innermost
+    // dimension has stride 1 and an extent divisible by 4, when the base and
+    // all other strides are multiples of 4 floats.
+    bool vec = n->tree == HX_TREE_WARP && inner % 4 == 0 && ((uintptr_t)n->out & 15) == 0;
+    const int last = n->ndim - 1;
+    for (int k = 0; k < HX_NEST_MAX_INPUTS; ++k) {
+        int64_t S = 0;
+        sh.linear[k] = linear_stride(n, sh.m, k, &S);
+        if (!sh.used[k]) continue;
+        bool ok = ((uintptr_t)n->in[k] & 15) == 0;
+        if (sh.linear[k]) {
+            ok = ok && (S == 1 || inner <= 1);
+        } else {
+            ok = ok && n->strides[k][last] == 1 && n->dims[last] % 4 == 0;
+            for (int d = sh.m; d < last; ++d) ok = ok && n->strides[k][d] % 4 == 0;
+        }
+        for (int d = 0; d < sh.m; ++d) ok = ok && n->strides[k][d] % 4 == 0;
+        vec = vec && ok;
+    }
+    sh.vec = vec;
+    return sh;
+}
+
+// Declarations i<m> .. i<ndim-1> of the inner indices of thread r of a
+// segment (multiplicative division when the segment has < 2^31 threads).
+std::string inner_indices(const Shape &sh, const char *r) {
+    const int last = sh.ndim - 1;
+    if (sh.m == last) return fmt(" const i64 i%d = (%s);", last, r);
+    std::string code;
+    if (sh.use32) {
+        code += fmt(" unsigned rr = (unsigned)(%s);", r);
+        for (int d = last; d > sh.m; --d)
+            code += fmt(" const unsigned q%d = hx_div(p, %d, rr); const i64 i%d = (i64)(rr - q%d * (unsigned)p.dims[%d]);"
+                        " rr = q%d;", d, d, d, d, d, d);
+    } else {
+        code += fmt(" i64 rr = (%s);", r);
+        for (int d = last; d > sh.m; --d) code += fmt(" const i64 i%d = rr %% p.dims[%d]; rr /= p.dims[%d];", d, d, d);
+    }
+    code += fmt(" const i64 i%d = (i64)rr;", sh.m);
+    return code;
+}
+
+// The map program as one C expression.  style 0: inputs are slot components
+// hx_comp(b.x<k>[j], q); style 1: scalars x<k>.
+std::string map_expression(const hx_nest *n, const Shape &sh, int style) {
     std::string st[HX_NEST_MAX_STACK];
     int sp = 0;
     for (int k = 0; k < n->n_ops; ++k) {
         const int code = n->ops[k].code, arg = n->ops[k].arg;
         std::string a, b, c;
         switch (code) {
-        case HX_OP_IN: st[sp++] = fmt("x%d[j]", arg); break;
+        case HX_OP_IN: st[sp++] = style == 0 ? fmt("hx_comp(b.x%d[j], q)", arg) : fmt("x%d", arg); break;
         case HX_OP_CONST: st[sp++] = fmt("p.c[%d]", arg); break;
-        case HX_OP_INDEX: st[sp++] = fmt("(float)i%d", arg); break;
+        case HX_OP_INDEX: st[sp++] = arg < sh.m ? fmt("(float)g.i%d", arg) : fmt("(float)i%d", arg); break;
         case HX_OP_NEG: st[sp - 1] = "(-" + st[sp - 1] + ")"; break;
         case HX_OP_ABS: st[sp - 1] = "fabsf(" + st[sp - 1] + ")"; break;
         case HX_OP_SQRT: st[sp - 1] = "sqrtf(" + st[sp - 1] + ")"; break;
@@ -525,81 +638,82 @@ std::string map_expression(const hx_nest *n) {
     return st[0];
 }
 
-// Index of dimension d inside the segment, from r (the segment-local thread
-// index), for the inner dims [m, ndim).
-std::string inner_indices(const Shape &sh, bool need[HX_NEST_MAX_DIMS]) {
-    std::string code;
-    const int last = sh.ndim - 1;
-    bool any = false;
-    for (int d = sh.m; d <= last; ++d) any = any || need[d];
-    if (!any) return code;
-    if (sh.m == last) return fmt("const i64 i%d = r;", last);
-    const char *ty = sh.use32 ? "unsigned" : "i64";
-    code += fmt("%s rr = (%s)r;", ty, ty);
-    for (int d = last; d > sh.m; --d) {
-        code += fmt(" const i64 i%d = (i64)(rr %% (%s)p.dims[%d]); rr /= (%s)p.dims[%d];", d, ty, d, ty, d);
-    }
-    code += fmt(" const i64 i%d = (i64)rr;", sh.m);
-    return code;
-}
-
 std::string generate(const hx_nest *n, const Shape &sh) {
     std::string src = "// libhx fork-join nest kernel (generated)\n";
-    src += fmt("#define MONOID %d\n#define TREE %d\n#define G %d\n#define U %d\n", sh.monoid, sh.tree, sh.G,
-               sh.tree == HX_TREE_WARP ? sh.U : 1);
+    src += fmt("#define MONOID %d\n#define TREE %d\n#define G %d\n#define U %d\n#define VEC %d\n", sh.monoid, sh.tree,
+               sh.G, sh.U, sh.vec ? 1 : 0);
     src += fmt("#define HAS_OUT %d\n#define HAS_RES64 %d\n", sh.has_out ? 1 : 0, sh.has_res64 ? 1 : 0);
-    // outer indices and per-input segment base offsets
-    std::string outer = "";
-    if (sh.m > 0) {
-        outer += "i64 so = s;";
-        for (int d = sh.m - 1; d >= 1; --d)
-            outer += fmt(" const i64 i%d = so %% p.dims[%d]; so /= p.dims[%d];", d, d, d);
-        outer += " const i64 i0 = so;";
-    }
-    bool need_inner[HX_NEST_MAX_DIMS] = {};
-    for (int d = sh.m; d < sh.ndim; ++d) need_inner[d] = sh.index_used[d];
-    std::string load_decl, load_body;
-    for (int k = 0; k < HX_NEST_MAX_INPUTS; ++k) {
-        if (!sh.used[k]) continue;
-        std::string base = "0";
-        for (int d = 0; d < sh.m; ++d) base += fmt(" + i%d * p.st[%d][%d]", d, k, d);
-        outer += fmt(" const float *b%d = p.in[%d] + (%s);", k, k, base.c_str());
-        load_decl += fmt(" float x%d[U];", k);
-        if (!sh.linear[k])
-            for (int d = sh.m; d < sh.ndim; ++d) need_inner[d] = true;
-    }
-    // loads: linear inputs use r directly, the others the inner indices
-    bool lin_need[HX_NEST_MAX_DIMS] = {};
-    bool any_nonlin = false;
-    for (int k = 0; k < HX_NEST_MAX_INPUTS; ++k)
-        if (sh.used[k] && !sh.linear[k]) any_nonlin = true;
-    if (any_nonlin) {
-        for (int d = sh.m; d < sh.ndim; ++d) lin_need[d] = true;
-        load_body += "{ " + inner_indices(sh, lin_need);
-    } else {
-        load_body += "{";
-    }
-    for (int k = 0; k < HX_NEST_MAX_INPUTS; ++k) {
-        if (!sh.used[k]) continue;
-        std::string off;
-        if (sh.linear[k]) {
-            off = fmt("r * p.lin[%d]", k);
-        } else {
-            off = "0";
-            for (int d = sh.m; d < sh.ndim; ++d) off += fmt(" + i%d * p.st[%d][%d]", d, k, d);
-        }
-        load_body += fmt(" x%d[j] = __ldg(b%d + (%s));", k, k, off.c_str());
-    }
-    load_body += " }";
-    bool idx_need[HX_NEST_MAX_DIMS] = {};
-    for (int d = sh.m; d < sh.ndim; ++d) idx_need[d] = sh.index_used[d];
-    std::string map_body = inner_indices(sh, idx_need) + " const float v = " + map_expression(n) + ";";
-    if (load_decl.empty()) load_decl = " ";
-    src += "#define OUTER_SETUP " + (outer.empty() ? std::string(" ") : outer) + "\n";
-    src += "#define LOAD_DECL" + load_decl + "\n";
-    src += "#define LOAD_BODY " + load_body + "\n";
-    src += "#define MAP_BODY " + map_body + "\n";
     src += kPrelude;
+    bool inner_index_used = false;
+    for (int d = sh.m; d < sh.ndim; ++d) inner_index_used = inner_index_used || sh.index_used[d];
+
+    // segment: outer indices and per-input base pointers
+    std::string seg = "struct Seg {\n    i64 s, r_begin, r_end, nslot;\n";
+    std::string setup = "__device__ __forceinline__ void seg_setup(const NestParams &p, Seg &g) {\n";
+    if (sh.m > 0) {
+        seg += "    i64";
+        for (int d = 0; d < sh.m; ++d) seg += fmt("%s i%d", d ? "," : "", d);
+        seg += ";\n";
+        setup += "    i64 so = g.s;\n";
+        for (int d = sh.m - 1; d >= 1; --d) setup += fmt("    g.i%d = so %% p.dims[%d]; so /= p.dims[%d];\n", d, d, d);
+        setup += "    g.i0 = so;\n";
+    }
+    std::string buf = "struct Buf {\n";
+    bool any_in = false;
+    for (int k = 0; k < HX_NEST_MAX_INPUTS; ++k) {
+        if (!sh.used[k]) continue;
+        any_in = true;
+        seg += fmt("    const float *b%d;\n", k);
+        std::string base = "0";
+        for (int d = 0; d < sh.m; ++d) base += fmt(" + g.i%d * p.st[%d][%d]", d, k, d);
+        setup += fmt("    g.b%d = p.in[%d] + (%s);\n", k, k, base.c_str());
+        buf += fmt("    float4 x%d[U];\n", k);
+    }
+    if (!any_in) buf += "    int unused;\n";
+    src += seg + "};\n" + setup + "}\n" + buf + "};\n";
+
+    // element offset of thread r of the segment in input k
+    for (int k = 0; k < HX_NEST_MAX_INPUTS; ++k) {
+        if (!sh.used[k]) continue;
+        src += fmt("__device__ __forceinline__ i64 off%d(const NestParams &p, i64 r) {", k);
+        if (sh.linear[k]) {
+            src += fmt(" return r * p.lin[%d]; }\n", k);
+        } else {
+            src += inner_indices(sh, "r") + " return 0";
+            for (int d = sh.m; d < sh.ndim; ++d) src += fmt(" + i%d * p.st[%d][%d]", d, k, d);
+            src += "; }\n";
+        }
+    }
+    // load U slots of 4 elements per lane
+    src += "__device__ __forceinline__ void load_group(const NestParams &p, const Seg &g, Buf &b, i64 t0) {\n"
+           "#pragma unroll\n    for (int j = 0; j < U; ++j) {\n        const i64 t = t0 + (i64)j * G;\n"
+           "        if (t < g.nslot) {\n            const i64 r = g.r_begin + 4 * t;\n";
+    for (int k = 0; k < HX_NEST_MAX_INPUTS; ++k) {
+        if (!sh.used[k]) continue;
+        if (sh.vec) {
+            // a linear float4 input has stride 1: its offset is r itself
+            if (sh.linear[k]) src += fmt("            b.x%d[j] = __ldg((const float4 *)(g.b%d + r));\n", k, k);
+            else src += fmt("            b.x%d[j] = __ldg((const float4 *)(g.b%d + off%d(p, r)));\n", k, k, k);
+        } else {
+            src += fmt("            b.x%d[j].x = __ldg(g.b%d + off%d(p, r));\n", k, k, k);
+            static const char comp[] = "xyzw";
+            for (int q = 1; q < 4; ++q)
+                src += fmt("            b.x%d[j].%c = (r + %d < g.r_end) ? __ldg(g.b%d + off%d(p, r + %d)) : 0.0f;\n", k,
+                           comp[q], q, k, k, q);
+        }
+    }
+    src += "        }\n    }\n}\n";
+    // map value of element (slot j, component q) = thread r
+    src += "__device__ __forceinline__ float map_elem(const NestParams &p, const Seg &g, const Buf &b, int j, int q,"
+           " i64 r) {";
+    if (inner_index_used) src += inner_indices(sh, "r");
+    src += " return " + map_expression(n, sh, 0) + "; }\n";
+    // map value of thread r, loading its inputs (sequential trees)
+    src += "__device__ __forceinline__ float map_at(const NestParams &p, const Seg &g, i64 r) {";
+    if (inner_index_used) src += inner_indices(sh, "r");
+    for (int k = 0; k < HX_NEST_MAX_INPUTS; ++k)
+        if (sh.used[k]) src += fmt(" const float x%d = __ldg(g.b%d + off%d(p, r));", k, k, k);
+    src += " return " + map_expression(n, sh, 1) + "; }\n";
     src += sh.tree == HX_TREE_WARP ? kWarpBody : kThreadBody;
     return src;
 }
@@ -660,34 +774,50 @@ hx_status load(Compiled *c) {
     return HX_OK;
 }
 
-// Work split of a nest: elements per item and items per segment.
+// Work split of a nest: elements per item (chunk), items per segment, and
+// groups of 32 chunks per segment (warp tree).
 struct Split {
-    int64_t chunk, nchunks;
+    int64_t chunk, nchunks, ngroups;
 };
 
-Split split_of(const hx_nest *n, const hx_tune_table *tune, int64_t outer, int64_t inner, const Shape &sh) {
+hx_status split_of(const hx_nest *n, const hx_tune_table *tune, int64_t outer, int64_t inner, const Shape &sh,
+                   Split *out) {
     const int64_t cap = hx::kNestCap;
-    int64_t chunk;
-    if (n->tree == HX_TREE_SEQ) return Split{inner > 0 ? inner : 1, 1};
-    // sub-warp groups (segments shorter than 32) take a whole segment each:
-    // the ticket path below assumes the full warp shares a chunk
-    if (n->tree == HX_TREE_WARP && sh.G < 32) return Split{inner > 0 ? inner : 1, 1};
-    if (n->chunk > 0) {
-        chunk = n->chunk;
-    } else if (n->tree == HX_TREE_WARP) {
-        chunk = (int64_t)sh.G * (tune ? tune->nest_lane_elems[hx::size_class(inner)] : 16);
-    } else {
-        chunk = 64;
+    const int64_t whole = inner > 0 ? inner : 1;
+    Split sp{whole, 1, 1};
+    if (n->tree == HX_TREE_SEQ) {
+        *out = sp;
+        return HX_OK;
     }
-    if (inner <= chunk || (sh.monoid >= 0 && outer > cap / 2)) return Split{inner > 0 ? inner : 1, 1};
+    int64_t chunk;
+    if (n->chunk > 0) chunk = n->chunk;
+    else if (n->tree == HX_TREE_WARP) chunk = (int64_t)sh.G * (tune ? tune->nest_lane_elems[hx::size_class(inner)] : 16);
+    else chunk = 64;
+    if (n->tree == HX_TREE_WARP) chunk = (chunk + 3) / 4 * 4;   // whole slots
+    // groups narrower than a warp take whole segments (the chunk tree below
+    // relies on the full warp sharing a chunk)
+    if ((n->tree == HX_TREE_WARP && sh.G < 32) || inner <= chunk || (sh.monoid >= 0 && outer > cap / 2)) {
+        *out = sp;
+        return HX_OK;
+    }
     int64_t nchunks = (inner + chunk - 1) / chunk;
     if (sh.monoid >= 0 && outer * nchunks > cap) {
         nchunks = cap / outer;
         chunk = (inner + nchunks - 1) / nchunks;
-        if (n->tree == HX_TREE_WARP) chunk = (chunk + 32 * kNestU - 1) / (32 * kNestU) * (32 * kNestU);
+        if (n->tree == HX_TREE_WARP) chunk = (chunk + 511) / 512 * 512;
         nchunks = (inner + chunk - 1) / chunk;
     }
-    return Split{chunk, nchunks};
+    sp.chunk = chunk;
+    sp.nchunks = nchunks;
+    sp.ngroups = n->tree == HX_TREE_WARP ? (nchunks + 31) / 32 : 1;
+    if (sh.monoid >= 0) {
+        // workspace bounds (see NestWs): these hold by construction
+        const bool ok = outer * nchunks <= cap && outer * sp.ngroups <= hx::kNestTick &&
+                        (sp.ngroups == 1 || (outer * sp.ngroups <= hx::kNestCap2 && outer <= hx::kNestTick2));
+        if (!ok) return hx::fail(HX_ERR_NOMEM, "hx_nest: chunk plan exceeds the workspace");
+    }
+    *out = sp;
+    return HX_OK;
 }
 
 hx_status prepare(const hx_nest *n, const hx_tune_table *tune, Compiled **c, Shape *sh, Split *sp, int64_t *outer,
@@ -697,8 +827,21 @@ hx_status prepare(const hx_nest *n, const hx_tune_table *tune, Compiled **c, Sha
     int m;
     extents(n, outer, inner, &m);
     *sh = shape_of(n);
-    *sp = split_of(n, tune, *outer, *inner, *sh);
+    st = split_of(n, tune, *outer, *inner, *sh, sp);
+    if (st != HX_OK) return st;
     return compile(generate(n, *sh), c);
+}
+
+// Multiplier and shift for quotients by d of 31-bit numerators: l =
+// ceil(log2 d), m = ceil(2^(31+l) / d) < 2^32 (Granlund and Montgomery 1994,
+// Thm. 4.2: m*d - 2^(31+l) < d <= 2^l).
+void magic(int64_t d, uint32_t *m, uint32_t *s) {
+    if (d < 1 || d >= ((int64_t)1 << 31)) d = 1;   // unused: the kernel divides in 64 bits then
+    int l = 0;
+    while (((int64_t)1 << l) < d) ++l;
+    const uint64_t two = (uint64_t)1 << (31 + l);
+    *m = (uint32_t)((two + (uint64_t)d - 1) / (uint64_t)d);
+    *s = 31 + l;
 }
 
 }  // namespace
@@ -708,9 +851,6 @@ extern "C" {
 hx_status hx_nest_source(const hx_nest *nest, char *buf, size_t cap, size_t *len) {
     hx_status st = validate(nest);
     if (st != HX_OK) return st;
-    int64_t outer, inner;
-    int m;
-    extents(nest, &outer, &inner, &m);
     const std::string src = generate(nest, shape_of(nest));
     if (len) *len = src.size();
     if (buf && cap) {
@@ -753,22 +893,26 @@ hx_status hx_fork_reduce(hx_ctx *ctx, const hx_nest *nest, hx_stream_t stream) {
         if (sh.linear[k]) linear_stride(nest, sh.m, k, &a.lin[k]);
     }
     for (int k = 0; k < HX_NEST_MAX_CONSTS; ++k) a.c[k] = nest->consts[k];
-    for (int d = 0; d < 3; ++d) a.dims[d] = d < nest->ndim ? nest->dims[d] : 1;
+    for (int d = 0; d < 3; ++d) {
+        a.dims[d] = d < nest->ndim ? nest->dims[d] : 1;
+        magic(a.dims[d], &a.dm[d], &a.ds[d]);
+    }
     a.outer = outer;
     a.inner = inner;
     a.chunk = sp.chunk;
     a.nchunks = sp.nchunks;
+    a.ngroups = sp.ngroups;
     a.n_items = outer * sp.nchunks;
     a.out = nest->out;
     a.res = nest->result;
     a.res64 = nest->result64;
     a.res_idx = nest->result_index;
     a.part = ws->part;
+    a.part2 = ws->part2;
     a.tick = ws->tick;
+    a.tick2 = ws->tick2;
 
-    int64_t threads;
-    if (sh.tree == HX_TREE_WARP) threads = a.n_items * sh.G;
-    else threads = a.n_items;
+    const int64_t threads = sh.tree == HX_TREE_WARP ? a.n_items * sh.G : a.n_items;
     int64_t blocks = (threads + kNestBlock - 1) / kNestBlock;
     const int64_t max_blocks = (int64_t)ctx->num_sms * (2048 / kNestBlock);
     if (blocks > max_blocks) blocks = max_blocks;

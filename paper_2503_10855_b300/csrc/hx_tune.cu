@@ -236,6 +236,37 @@ hx_status hx_autotune(hx_ctx *ctx, int32_t max_log2, hx_stream_t stream) {
     }
     for (int c = map_top + 1; c < HX_TUNE_CLASSES; ++c) t.map_vecs[c] = t.map_vecs[map_top];
 
+    // generic nests: warp-tree chunk length per class, timed on the plain
+    // sum of one contiguous array (above 2^26 the partial cap decides)
+    for (int c = 10; c <= map_top && st == HX_OK; ++c) {
+        const int64_t n = (int64_t)1 << c;
+        const size_t stride = ((size_t)n + 63) & ~(size_t)63;
+        const size_t regions = std::max<size_t>(1, pool_elems / stride);
+        hx_nest nest{};
+        nest.ndim = 1;
+        nest.reduce_dims = 1;
+        nest.monoid = HX_MONOID_SUM;
+        nest.tree = HX_TREE_WARP;
+        nest.dims[0] = n;
+        nest.n_ops = 1;
+        nest.ops[0].code = HX_OP_IN;
+        nest.strides[0][0] = 1;
+        nest.result = res;
+        float best = 1e30f;
+        int best_le = t.nest_lane_elems[c];
+        for (int le : {8, 16, 32, 64, 128}) {
+            ctx->tune.nest_lane_elems[c] = le;
+            const float ms = time_median(s, reps, [&](int r) {
+                nest.in[0] = pool + (r % regions) * stride;
+                return hx_fork_reduce(ctx, &nest, stream);
+            }, &st);
+            if (st == HX_OK && ms < best) { best = ms; best_le = le; }
+        }
+        t.nest_lane_elems[c] = best_le;
+        ctx->tune.nest_lane_elems[c] = best_le;
+    }
+    for (int c = map_top + 1; c < HX_TUNE_CLASSES; ++c) t.nest_lane_elems[c] = t.nest_lane_elems[map_top];
+
     // histogram CTA width per class
     const int hist_top = std::min<int>(max_log2, 28);
     const size_t pool_bytes = pool_elems * sizeof(float);

@@ -211,3 +211,49 @@ def test_streams_use_separate_workspace(gpu):
             assert torch.equal(r, outs[k % 2])
         ref_x = oracle.fork_reduce([("in", 0)], [x], x.shape, 1, "sum")[1]
         assert abs(float(outs[0]) - float(ref_x)) <= 1e-5 * np.abs(x).astype(np.float64).sum()
+
+
+def test_alignment_does_not_change_bits(gpu):
+    # the same rows, once 16-byte aligned (float4 path) and once shifted by
+    # one element (scalar path): identical lane assignment, identical bits
+    hx = gpu
+    x = torch.from_numpy(_np((4, 4096), 113)).cuda()
+    buf = torch.zeros(4 * 4096 + 4, device="cuda:0")
+    with hx.hx_create(0) as ctx:
+        res = []
+        for off in (0, 1):
+            v = buf[off:off + 4 * 4096].view(4, 4096)
+            v.copy_(x)
+            for monoid in ("sum", "prod", "argmax"):
+                src = hx.hx_nest_source(hx.make_nest([("in", 0)], [v], (4, 4096), 1, monoid,
+                                                     result=torch.empty(4, device="cuda:0"),
+                                                     result_index=torch.empty(4, dtype=torch.int64, device="cuda:0")))
+                assert ("#define VEC 1" in src) == (off == 0)
+                _, r, i, r64 = hx.fork_reduce(ctx, [("in", 0), ("const", 0), "mul", ("const", 1), "add"], [v],
+                                              (4, 4096), 1, monoid, consts=[1.0 / 64, 1.0], want_result64=True)
+                res.append((r.clone(), r64.clone(), None if i is None else i.clone()))
+        torch.cuda.synchronize()
+        for a, b in zip(res[:3], res[3:]):
+            assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
+            if a[2] is not None:
+                assert torch.equal(a[2], b[2])
+
+
+@pytest.mark.parametrize("monoid", ["sum", "argmin"])
+def test_strided_float4_slots(gpu, monoid):
+    # (5, 6, 12) viewed as (6, 5, 12): the inner dims (5, 12) are strided
+    # (72, 1) but every slot of 4 threads is 4 aligned contiguous floats
+    hx = gpu
+    a = _np((5, 6, 12), 114)
+    view = lambda xs: [xs[0].transpose(1, 0, 2) if isinstance(xs[0], np.ndarray) else xs[0].permute(1, 0, 2)]  # noqa: E731
+    with hx.hx_create(0) as ctx:
+        t = torch.from_numpy(a).cuda().permute(1, 0, 2)
+        src = hx.hx_nest_source(hx.make_nest([("in", 0)], [t], (6, 5, 12), 2, monoid,
+                                             result=torch.empty(6, device="cuda:0"),
+                                             result_index=torch.empty(6, dtype=torch.int64, device="cuda:0")))
+        assert "#define VEC 1" in src and "p.lin[0]" not in src
+        _check(hx, ctx, [("in", 0), ("index", 2), ("const", 0), "mul", "add"], [a], view, (6, 5, 12), 2, monoid,
+               [0.5])
+        big = _np((64, 96, 128), 115)
+        view2 = lambda xs: [xs[0].transpose(1, 0, 2) if isinstance(xs[0], np.ndarray) else xs[0].permute(1, 0, 2)]  # noqa: E731
+        _check(hx, ctx, [("in", 0), "abs"], [big], view2, (96, 64, 128), 2, monoid)

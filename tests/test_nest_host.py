@@ -73,13 +73,20 @@ def test_generated_source_fuses_the_program():
     n = hx.make_nest([("in", 0), ("const", 0), ("in", 1), "fma", ("in", 1), "max"], [x, y], (8, 16), 1, "sum",
                      result=torch.zeros(8))
     src = hx.hx_nest_source(n)
-    assert "hx_maxnum(fmaf(x0[j], p.c[0], x1[j]), x1[j])" in src
+    assert "hx_maxnum(fmaf(hx_comp(b.x0[j], q), p.c[0], hx_comp(b.x1[j], q)), hx_comp(b.x1[j], q))" in src
+    assert "return fmaf(x0, p.c[0], x1)" not in src            # the sequential form has its own expression
     assert "p.lin[0]" in src and "p.lin[1]" in src          # row-major rows are linear segments
+    assert "#define VEC 1" in src                              # aligned unit-stride rows load float4
     # a transposed input over a full reduce does not collapse: per-dim offsets
     t = torch.zeros(16, 8).T
     src = hx.hx_nest_source(hx.make_nest([("in", 0)], [t], (8, 16), 2, "max", result=torch.zeros(1)))
-    assert "p.lin[0]" not in src and "p.st[0][1]" in src
-    # narrow segments use sub-warp groups
+    assert "p.lin[0]" not in src and "p.st[0][1]" in src and "hx_div(p, 1, rr)" in src
+    assert "#define VEC 0" in src
+    # short segments use sub-warp groups: one lane per 5-element row, four
+    # lanes per 64-element row
     src = hx.hx_nest_source(hx.make_nest([("in", 0)], [torch.zeros(64, 5)], (64, 5), 1, "sum",
                                          result=torch.zeros(64)))
-    assert "#define G 8" in src
+    assert "#define G 1" in src
+    src = hx.hx_nest_source(hx.make_nest([("in", 0)], [torch.zeros(8, 64)], (8, 64), 1, "sum",
+                                         result=torch.zeros(8)))
+    assert "#define G 4" in src

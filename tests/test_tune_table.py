@@ -15,6 +15,7 @@ def test_default_table_is_valid():
     assert set(d["hist_threads"]) <= {256, 512, 1024}
     assert set(d["stencil_rows"]) <= {4, 8, 16}
     assert all(v % 4 == 0 for v in d["map_vecs"])
+    assert all(v % 8 == 0 and 8 <= v <= 512 for v in d["nest_lane_elems"])
 
 
 def test_json_round_trip(tmp_path):
@@ -23,6 +24,7 @@ def test_json_round_trip(tmp_path):
         t.map_vecs[c] = 4 * (1 + c % 4)
         t.hist_threads[c] = (256, 512, 1024)[c % 3]
         t.stencil_rows[c] = (4, 8, 16)[c % 3]
+        t.nest_lane_elems[c] = 8 * (1 + c % 5)
     t.batch_map_run, t.batch_stencil_run = 5, 33
     path = tmp_path / "tune.json"
     hx.hx_tune_table_save(t, str(path))
@@ -32,7 +34,8 @@ def test_json_round_trip(tmp_path):
     assert u.as_dict() == t.as_dict()
 
 
-@pytest.mark.parametrize("field,value", [("map_vecs", 6), ("hist_threads", 300), ("stencil_rows", 5)])
+@pytest.mark.parametrize("field,value", [("map_vecs", 6), ("hist_threads", 300), ("stencil_rows", 5),
+                                         ("nest_lane_elems", 12), ("nest_lane_elems", 1024)])
 def test_invalid_entries_rejected(tmp_path, field, value):
     t = hx.hx_tune_table_default()
     getattr(t, field)[3] = value
