@@ -56,6 +56,11 @@ def _get():
             f.restype = ctypes.c_int
         lib.hxo_histogram_u8.argtypes = [P, ctypes.c_int64, P, P]
         lib.hxo_histogram_u8.restype = None
+        I32 = ctypes.c_int32
+        lib.hxo_srad_f64.argtypes = [P, I32, I32, I32, ctypes.c_double, I32, I32, I32, I32, P, P]
+        lib.hxo_srad_f64.restype = ctypes.c_int
+        lib.hxo_srad_f32.argtypes = [P, I32, I32, I32, ctypes.c_float, I32, I32, I32, I32, P, P]
+        lib.hxo_srad_f32.restype = ctypes.c_int
         I = ctypes.c_int
         lib.hxo_fork_reduce.argtypes = [I, P, I, I, I, P, P, I, P, P, P, P, P]
         lib.hxo_fork_reduce.restype = ctypes.c_int
@@ -177,3 +182,19 @@ def fork_reduce(program, inputs, dims, reduce_dims, monoid="sum", consts=(), wan
     result = result[:n_outer].reshape(outer_shape)
     index = index[:n_outer].reshape(outer_shape) if monoid.startswith("arg") else None
     return out, result, index
+
+
+def srad(J0: np.ndarray, iters: int, lam: float, roi, precision: str = "f64"):
+    """SRAD-style iteration (see ``hxo_srad_f64``): returns (J after ``iters``
+    iterations, q0sq per iteration).  ``roi`` = (r0, r1, c0, c1), half-open."""
+    assert J0.ndim == 2
+    ny, nx = J0.shape
+    dt = np.float64 if precision == "f64" else np.float32
+    src = np.ascontiguousarray(J0, dtype=dt)
+    out = np.empty_like(src)
+    q0 = np.zeros(max(iters, 1), dtype=dt)
+    fn = _get().hxo_srad_f64 if precision == "f64" else _get().hxo_srad_f32
+    r0, r1, c0, c1 = (int(v) for v in roi)
+    if fn(_ptr(src), nx, ny, iters, lam, r0, r1, c0, c1, _ptr(out), _ptr(q0)):
+        raise ValueError("oracle srad: bad arguments")
+    return out, q0[:iters]

@@ -360,3 +360,108 @@ int hxo_fork_reduce(int ndim, const int64_t *dims, int reduce_dims, int monoid,
     }
     return 0;
 }
+
+/* ---------------------------------------------------------------------------
+ * SRAD-style fused nest: speckle reducing anisotropic diffusion, iterated.
+ *
+ * The paper evaluates SRAD (Sec. 6), whose GPU schedule fuses two large loops
+ * and turns a large sum reduction into a 3-layer reduction tree (Sec. 5.1,
+ * Sec. 5.2).  It does not print SRAD's arithmetic; the steps below are the
+ * published SRAD scheme (Yu and Acton, "Speckle reducing anisotropic
+ * diffusion", IEEE TIP 2002), written as one outer sequential loop with
+ * three fork-joins per iteration:
+ *
+ *  1. reduce: over the region of interest rows [r0, r1) x cols [c0, c1), in
+ *     row-major order, S1 = sum J, S2 = sum J^2 (double); with N pixels,
+ *     mean = S1/N, var = S2/N - mean^2, q0sq = var / mean^2 (the speckle
+ *     scale of iteration t);
+ *  2. fork over pixels: with clamp-to-edge neighbours and Jc = J[i][j],
+ *     dN = J[i-1][j] - Jc, dS = J[i+1][j] - Jc, dW = J[i][j-1] - Jc,
+ *     dE = J[i][j+1] - Jc,
+ *     G2 = ((dN*dN + dS*dS) + (dW*dW + dE*dE)) / (Jc*Jc)
+ *     L  = ((dN + dS) + (dW + dE)) / Jc
+ *     num = 0.5*G2 - 0.0625*(L*L),  den = 1 + 0.25*L,  qsq = num / (den*den)
+ *     c = 1 / (1 + (qsq - q0sq) / (q0sq * (1 + q0sq))), clamped to [0, 1]
+ *     (a NaN c stays NaN);
+ *  3. fork over pixels: D = (c[i][j]*dN + c[i+1][j]*dS) + (c[i][j]*dW +
+ *     c[i][j+1]*dE) (neighbour indices clamped), J'[i][j] = Jc + (0.25*lambda)*D.
+ *
+ * Intensities must be nonzero (the scheme divides by J); a homogeneous ROI
+ * (q0sq == 0) makes the coefficient 0/0 and the result NaN, as the formula
+ * says.  q0sq_out[t] receives iteration t's speckle scale.  The f32 variant
+ * evaluates steps 2 and 3 in single precision in the order written (every
+ * operation rounded to fp32); its ROI sums are the double sums of the fp32
+ * values, and q0sq is computed in double and rounded to fp32 once.
+ * Returns 0, or 1 for bad arguments / failed scratch allocation.
+ */
+#define HXO_SRAD_BODY(T, HALF, SIXTEENTH, QUARTER, ONE, ZERO)                         \
+    size_t npts = (size_t)nx * (size_t)ny;                                            \
+    if (nx < 1 || ny < 1 || r0 < 0 || r1 > ny || r0 >= r1 || c0 < 0 || c1 > nx ||     \
+        c0 >= c1 || iters < 0)                                                         \
+        return 1;                                                                      \
+    T *cur = (T *)malloc(npts * sizeof(T));                                           \
+    T *nxt = (T *)malloc(npts * sizeof(T));                                           \
+    T *cc = (T *)malloc(npts * sizeof(T));                                            \
+    if (!cur || !nxt || !cc) { free(cur); free(nxt); free(cc); return 1; }            \
+    memcpy(cur, J0, npts * sizeof(T));                                                \
+    const T k = QUARTER * lambda;                                                     \
+    for (int32_t t = 0; t < iters; ++t) {                                             \
+        double s1 = 0.0, s2 = 0.0;                                                    \
+        for (int64_t i = r0; i < r1; ++i)                                             \
+            for (int64_t j = c0; j < c1; ++j) {                                       \
+                double v = (double)cur[i * nx + j];                                   \
+                s1 = s1 + v;                                                          \
+                s2 = s2 + v * v;                                                      \
+            }                                                                         \
+        double npix = (double)(r1 - r0) * (double)(c1 - c0);                          \
+        double mean = s1 / npix;                                                      \
+        double var = s2 / npix - mean * mean;                                         \
+        const T q0sq = (T)(var / (mean * mean));                                      \
+        q0sq_out[t] = q0sq;                                                           \
+        for (int64_t i = 0; i < ny; ++i)                                              \
+            for (int64_t j = 0; j < nx; ++j) {                                        \
+                T Jc = cur[i * nx + j];                                               \
+                T dN = cur[clampi(i - 1, 0, ny - 1) * nx + j] - Jc;                   \
+                T dS = cur[clampi(i + 1, 0, ny - 1) * nx + j] - Jc;                   \
+                T dW = cur[i * nx + clampi(j - 1, 0, nx - 1)] - Jc;                   \
+                T dE = cur[i * nx + clampi(j + 1, 0, nx - 1)] - Jc;                   \
+                T G2 = ((dN * dN + dS * dS) + (dW * dW + dE * dE)) / (Jc * Jc);       \
+                T L = ((dN + dS) + (dW + dE)) / Jc;                                   \
+                T num = HALF * G2 - SIXTEENTH * (L * L);                              \
+                T den = ONE + QUARTER * L;                                            \
+                T qsq = num / (den * den);                                            \
+                T c = ONE / (ONE + (qsq - q0sq) / (q0sq * (ONE + q0sq)));             \
+                if (c < ZERO) c = ZERO;                                               \
+                else if (c > ONE) c = ONE;                                            \
+                cc[i * nx + j] = c;                                                   \
+            }                                                                         \
+        for (int64_t i = 0; i < ny; ++i)                                              \
+            for (int64_t j = 0; j < nx; ++j) {                                        \
+                T Jc = cur[i * nx + j];                                               \
+                int64_t is = clampi(i + 1, 0, ny - 1), je = clampi(j + 1, 0, nx - 1); \
+                T dN = cur[clampi(i - 1, 0, ny - 1) * nx + j] - Jc;                   \
+                T dS = cur[is * nx + j] - Jc;                                         \
+                T dW = cur[i * nx + clampi(j - 1, 0, nx - 1)] - Jc;                   \
+                T dE = cur[i * nx + je] - Jc;                                         \
+                T cN = cc[i * nx + j], cS = cc[is * nx + j];                          \
+                T cW = cc[i * nx + j], cE = cc[i * nx + je];                          \
+                T D = (cN * dN + cS * dS) + (cW * dW + cE * dE);                      \
+                nxt[i * nx + j] = Jc + k * D;                                         \
+            }                                                                         \
+        T *tmp = cur; cur = nxt; nxt = tmp;                                           \
+    }                                                                                 \
+    memcpy(J_out, cur, npts * sizeof(T));                                             \
+    free(cur); free(nxt); free(cc);                                                   \
+    return 0;
+
+int hxo_srad_f64(const double *J0, int32_t nx, int32_t ny, int32_t iters, double lambda,
+                 int32_t r0, int32_t r1, int32_t c0, int32_t c1, double *J_out, double *q0sq_out)
+{
+    HXO_SRAD_BODY(double, 0.5, 0.0625, 0.25, 1.0, 0.0)
+}
+
+int hxo_srad_f32(const float *J0, int32_t nx, int32_t ny, int32_t iters, float lambda,
+                 int32_t r0, int32_t r1, int32_t c0, int32_t c1, float *J_out, float *q0sq_out)
+{
+    HXO_SRAD_BODY(float, 0.5f, 0.0625f, 0.25f, 1.0f, 0.0f)
+}

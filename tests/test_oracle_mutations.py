@@ -15,6 +15,7 @@ import pytest
 import oracle
 from tests import test_oracle_nest_pins as npins
 from tests import test_oracle_pins as pins
+from tests import test_oracle_srad_pins as spins
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "hx_oracle.c")
 
@@ -38,6 +39,14 @@ NEST_PINS = [*(lambda op=op: npins.test_nest_binary_ops_match_numpy_single(op) f
              npins.test_nest_3d_partial_reductions_match_numpy, npins.test_nest_strided_and_broadcast_inputs,
              npins.test_nest_index_op_matches_index_grid, npins.test_nest_fold_order_is_thread_id_order,
              npins.test_nest_nan_and_empty_rules, npins.test_nest_signed_zero_rules]
+
+SRAD_PINS = [lambda: spins.test_srad_conserves_mass(0.5, (17, 23)), spins.test_srad_transpose_symmetry,
+             lambda: spins.test_srad_maximum_principle(1.0),
+             lambda: spins.test_srad_is_jacobi_relaxation_where_c_clamps_to_one(0.5),
+             spins.test_srad_speckle_scale_matches_numpy,
+             *(lambda a=a, b=b: spins.test_srad_checkerboard_closed_form(a, b)
+               for a, b in ((2.0, 1.0), (1.0, 3.0), (1.5, 1.25))),
+             spins.test_srad_homogeneous_cases]
 
 MUTANTS = {
     "map_transposed": ("double v = a * (double)x[i] + (double)y[i];",
@@ -80,6 +89,21 @@ MUTANTS = {
     "nest_prod_init_zero": ("case 3: acc = 1.0; break;\n        }\n        for (int64_t r",
                             "case 3: acc = 0.0; break;\n        }\n        for (int64_t r", NEST_PINS),
     "nest_index_off_by_one": ("st[sp++] = (float)idx[arg];", "st[sp++] = (float)(idx[arg] + 1);", NEST_PINS),
+    "srad_cS_self": ("T cN = cc[i * nx + j], cS = cc[is * nx + j];", "T cN = cc[i * nx + j], cS = cc[i * nx + j];",
+                     SRAD_PINS),
+    "srad_cE_self": ("T cW = cc[i * nx + j], cE = cc[i * nx + je];", "T cW = cc[i * nx + j], cE = cc[i * nx + j];",
+                     SRAD_PINS),
+    "srad_step_half": ("const T k = QUARTER * lambda;", "const T k = HALF * lambda;", SRAD_PINS),
+    "srad_var_n_minus_1": ("double var = s2 / npix - mean * mean;", "double var = s2 / (npix - 1.0) - mean * mean;",
+                           SRAD_PINS),
+    "srad_num_sign": ("T num = HALF * G2 - SIXTEENTH * (L * L);", "T num = HALF * G2 + SIXTEENTH * (L * L);",
+                      SRAD_PINS),
+    "srad_den_sign": ("T den = ONE + QUARTER * L;", "T den = ONE - QUARTER * L;", SRAD_PINS),
+    "srad_no_upper_clamp": ("else if (c > ONE) c = ONE;", "else if (c > ONE) c = c;", SRAD_PINS),
+    "srad_G2_over_J": ("(dW * dW + dE * dE)) / (Jc * Jc);", "(dW * dW + dE * dE)) / Jc;", SRAD_PINS),
+    "srad_roi_rows_from_zero": ("for (int64_t i = r0; i < r1; ++i)", "for (int64_t i = 0; i < r1; ++i)", SRAD_PINS),
+    "srad_dS_from_north": ("T dS = cur[is * nx + j] - Jc;", "T dS = cur[clampi(i - 1, 0, ny - 1) * nx + j] - Jc;",
+                           SRAD_PINS),
     "nest_min_keeps_pos_zero": ("if (v < best || (v == 0.0f && best == 0.0f && !signbit(best) && signbit(v))) best = v;",
                                 "if (v < best) best = v;", NEST_PINS),
 }
@@ -103,7 +127,7 @@ def test_pins_catch_mutant(tmp_path, monkeypatch, name):
     real = oracle._get()
     mutant = _load_mutant(tmp_path, name, old, new)
     for fn in ("hxo_map_reduce_f64", "hxo_monoid_reduce_f64", "hxo_jacobi_f64",
-               "hxo_jacobi_f32", "hxo_histogram_u8", "hxo_fork_reduce"):
+               "hxo_jacobi_f32", "hxo_histogram_u8", "hxo_fork_reduce", "hxo_srad_f64", "hxo_srad_f32"):
         getattr(mutant, fn).argtypes = getattr(real, fn).argtypes
         getattr(mutant, fn).restype = getattr(real, fn).restype
     monkeypatch.setattr(oracle, "_lib", mutant)
