@@ -169,6 +169,43 @@ hx_status hx_stencil2d(hx_ctx *ctx, float *u0, float *u1, int32_t nx, int32_t ny
 hx_status hx_histogram(hx_ctx *ctx, const uint8_t *v, int64_t n, uint32_t *d_bins,
                        uint32_t *d_excl_scan, hx_stream_t stream);
 
+/* ------------------------------------------------------------------ SRAD-style fused nest
+ * Speckle reducing anisotropic diffusion, iterated: per iteration a reduce
+ * (the speckle scale q0^2 = var/mean^2 of a region of interest) feeds two
+ * stencil fork-joins (diffusion coefficient, then flux update).  The paper's
+ * SRAD schedule fuses the two large loops (Sec. 5.1) and builds a GPU-only
+ * reduction tree for the large sum (Sec. 5.2).  The arithmetic is the
+ * published SRAD scheme; with clamp-to-edge neighbours and Jc = J[i][j]:
+ *   dN = J[i-1][j]-Jc, dS = J[i+1][j]-Jc, dW = J[i][j-1]-Jc, dE = J[i][j+1]-Jc
+ *   G2 = ((dN*dN + dS*dS) + (dW*dW + dE*dE)) / (Jc*Jc),
+ *   L = ((dN + dS) + (dW + dE)) / Jc,
+ *   qsq = (0.5*G2 - 0.0625*L*L) / ((1 + 0.25*L)^2),
+ *   c = clamp(1 / (1 + (qsq - q0sq) / (q0sq*(1 + q0sq))), 0, 1),
+ *   J' = Jc + (0.25*lambda) * ((c[i][j]*dN + c[i+1][j]*dS) + (c[i][j]*dW + c[i][j+1]*dE)),
+ * every operation in fp32 in that order (no contraction); q0sq is formed in
+ * double from float-float region sums (S1 = sum J, S2 = sum J^2 over rows
+ * [r0, r1) x cols [c0, c1); mean = S1/N, var = S2/N - mean^2) and rounded
+ * to fp32 once.
+ *
+ *   J0, J1   device, ny x nx fp32 row-major; J0 holds the input image
+ *            (nonzero intensities: the scheme divides by J).  Iterations
+ *            ping-pong J0 -> J1 -> J0 ...; *result_in_J1 (host, nullable)
+ *            is 1 when the result is in J1 (iters odd).
+ *   C        device scratch, ny x nx fp32, used by the unfused path only
+ *            (may be NULL when fused != 0).
+ *   d_q0sq   device, iters floats: the speckle scale each iteration used.
+ *   fused    1: one kernel per iteration (coefficients recomputed in shared
+ *            memory per tile, the next iteration's region sums accumulated by
+ *            the same pass); 0: region reduce, coefficient and update as
+ *            three kernels per iteration.  Both give bit-identical results.
+ *   1 <= nx, ny <= 65536, nx*ny <= 2^31; the region must be non-empty and
+ *   inside the image and span at most 65536 tiles of 16 x 128 pixels.
+ * A homogeneous region (q0sq == 0) makes the coefficient 0/0: the image
+ * becomes NaN, as the formula says. */
+hx_status hx_srad(hx_ctx *ctx, float *J0, float *J1, float *C, int32_t nx, int32_t ny, int32_t iters,
+                  float lambda, int32_t r0, int32_t r1, int32_t c0, int32_t c1, float *d_q0sq,
+                  int32_t fused, int32_t *result_in_J1, hx_stream_t stream);
+
 /* ------------------------------------------------------------------ generic nests
  * A fork-join nest in general form (Sec. 3.3): a fork of factors
  * dims[0..ndim) (dimension 0 outermost, 1 <= ndim <= 3) whose threads each

@@ -186,6 +186,36 @@ def hx_histogram(ctx: Context, v, bins=None, scan=None, want_scan: bool = True, 
     return bins, scan
 
 
+# ------------------------------------------------------------------ SRAD-style nest
+_lib.hx_srad.argtypes = [_P, _P, _P, _P, _I32, _I32, _I32, ctypes.c_float, _I32, _I32, _I32, _I32, _P, _I32,
+                         ctypes.POINTER(_I32), _P]
+_lib.hx_srad.restype = ctypes.c_int
+
+
+def hx_srad(ctx: Context, J0, J1, iters: int, lam: float, roi, q0sq=None, fused: bool = True, C=None, stream=None):
+    """``iters`` SRAD iterations ping-ponging J0 <-> J1 (both ny x nx fp32).
+
+    ``roi`` = (r0, r1, c0, c1), half-open.  Returns (result tensor, q0sq)
+    where q0sq[t] is the speckle scale iteration t used.  The unfused path
+    needs a scratch ``C`` of the image's shape (allocated when omitted)."""
+    import torch
+
+    if J0.dim() != 2 or J0.shape != J1.shape:
+        raise ValueError("J0 and J1 must be 2-D of the same shape")
+    ny, nx = J0.shape
+    if q0sq is None:
+        q0sq = torch.empty(max(iters, 1), dtype=torch.float32, device=J0.device)
+    if not fused and C is None:
+        C = torch.empty_like(J0)
+    r0, r1, c0, c1 = (int(v) for v in roi)
+    in_j1 = _I32(0)
+    _check(_lib.hx_srad(ctx.handle, _dev_ptr(J0, torch.float32, "J0"), _dev_ptr(J1, torch.float32, "J1"),
+                        _dev_ptr(C, torch.float32, "C") if C is not None else _P(0), nx, ny, iters, float(lam),
+                        r0, r1, c0, c1, _dev_ptr(q0sq, torch.float32, "q0sq", iters), 1 if fused else 0,
+                        ctypes.byref(in_j1), _stream_handle(stream)), "hx_srad")
+    return (J1 if in_j1.value else J0), q0sq
+
+
 # ------------------------------------------------------------------ generic nests
 HX_NEST_MAX_DIMS, HX_NEST_MAX_OPS, HX_NEST_MAX_INPUTS, HX_NEST_MAX_CONSTS = 3, 32, 4, 8
 NEST_OPS = {"in": 1, "const": 2, "index": 3, "add": 4, "sub": 5, "mul": 6, "div": 7,

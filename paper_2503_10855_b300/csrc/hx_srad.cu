@@ -1,0 +1,312 @@
+// hx_srad.cu -- the SRAD-style fused nest: speckle reducing anisotropic
+// diffusion, iterated.  Each iteration is a global reduce (the speckle scale
+// q0^2 of a region of interest) feeding two stencil fork-joins (the
+// diffusion coefficient c, then the flux update of the image).  The paper's
+// SRAD schedule fuses the two large loops to remove global-memory traffic
+// (Sec. 5.1) and turns the large sum into a GPU-only reduction tree
+// (Sec. 5.2).  Here:
+//
+//   fused (one kernel per iteration): a CTA loads its 16 x 128 output tile
+//   of J plus a halo into shared memory, computes c for the tile and one
+//   extra row and column (the south / east neighbours' coefficients) into
+//   shared memory, writes J', and accumulates the region-of-interest sums of
+//   J' (float-float) for the NEXT iteration's q0^2 -- the reduce is fused
+//   into the loop that produces its input.  Tile partials are combined by
+//   the last region tile to arrive, in tile order; it writes q0^2[t+1].
+//   HBM traffic: J read once (halo rows come from L2) and J' written once.
+//
+//   unfused (three kernels per iteration, the loop nest as written):
+//   region reduce -> q0^2[t], coefficient kernel (J -> C), update kernel
+//   (J, C -> J').
+//
+// Both evaluate every expression in single precision in one fixed order (no
+// contraction), so the two paths give bit-identical images; q0^2 is formed
+// in double from the float-float sums and rounded once.  Iterations chain
+// with programmatic dependent launch.
+#include "hx_internal.cuh"
+
+namespace hx {
+namespace {
+
+constexpr int kTX = 128;          // tile columns
+constexpr int kTY = 16;           // tile rows
+constexpr int kThreads = 256;
+constexpr int kJsW = kTX + 4;     // J tile: rows i0-1 .. i0+TY+1, cols j0-1 .. j0+TX+1 (+1 pad)
+constexpr int kJsH = kTY + 3;
+constexpr int kCsW = kTX + 2;     // c tile: rows i0 .. i0+TY, cols j0 .. j0+TX (+1 pad)
+constexpr int kCsH = kTY + 1;
+
+struct SradArgs {
+    int nx, ny;
+    int r0, r1, c0, c1;           // region of interest, half-open
+    int tx0, ty0, ntx;            // first region tile and region tiles per row
+    int roi_tiles;
+    float k;                      // 0.25 * lambda
+};
+
+__device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+// Diffusion coefficient of a pixel from its value and its four neighbour
+// differences (the SRAD expression, fp32, fixed order).
+__device__ __forceinline__ float srad_coeff(float Jc, float dN, float dS, float dW, float dE, float q0sq) {
+    const float G2 = ((dN * dN + dS * dS) + (dW * dW + dE * dE)) / (Jc * Jc);
+    const float L = ((dN + dS) + (dW + dE)) / Jc;
+    const float num = 0.5f * G2 - 0.0625f * (L * L);
+    const float den = 1.0f + 0.25f * L;
+    const float qsq = num / (den * den);
+    float c = 1.0f / (1.0f + (qsq - q0sq) / (q0sq * (1.0f + q0sq)));
+    if (c < 0.0f) c = 0.0f;
+    else if (c > 1.0f) c = 1.0f;
+    return c;
+}
+
+__device__ __forceinline__ float srad_update(float Jc, float dN, float dS, float dW, float dE, float cN, float cS,
+                                             float cW, float cE, float k) {
+    const float D = (cN * dN + cS * dS) + (cW * dW + cE * dE);
+    return Jc + k * D;
+}
+
+// Region sums of one thread: S1 += v, S2 += v*v (the square kept exact as a
+// float-float product).
+struct RoiAcc {
+    ff s1, s2;
+};
+__device__ __forceinline__ void roi_add(RoiAcc &a, float v) {
+    a.s1 = ff_add_f(a.s1, v);
+    const float p = v * v;
+    a.s2 = ff_add(a.s2, ff{p, fmaf(v, v, -p)});
+}
+
+// CTA-wide combine of the threads' region sums (warp butterflies, then the
+// warps in order), published as the tile's partial; the last region tile to
+// arrive folds all partials in tile order and writes q0^2.  Fixed order
+// throughout, so q0^2 depends only on the image and the region.
+__device__ void roi_publish(RoiAcc a, const SradArgs &p, int roi_tile, NestWs *ws, float *q0sq_out) {
+    __shared__ float4 red[kThreads / 32];
+    __shared__ unsigned last;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    a.s1 = warp_sum(a.s1);
+    a.s2 = warp_sum(a.s2);
+    if (lane == 0) red[warp] = make_float4(a.s1.hi, a.s1.lo, a.s2.hi, a.s2.lo);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ff s1 = {0.0f, 0.0f}, s2 = {0.0f, 0.0f};
+        for (int w = 0; w < kThreads / 32; ++w) {
+            s1 = ff_add(s1, ff{red[w].x, red[w].y});
+            s2 = ff_add(s2, ff{red[w].z, red[w].w});
+        }
+        ws->part[roi_tile] = make_float4(s1.hi, s1.lo, s2.hi, s2.lo);
+        __threadfence();
+        last = atomicAdd(&ws->tick[0], 1u) == (unsigned)(p.roi_tiles - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    RoiAcc t = {{0.0f, 0.0f}, {0.0f, 0.0f}};
+    for (int q = threadIdx.x; q < p.roi_tiles; q += kThreads) {
+        const float4 v = __ldcg(&ws->part[q]);
+        t.s1 = ff_add(t.s1, ff{v.x, v.y});
+        t.s2 = ff_add(t.s2, ff{v.z, v.w});
+    }
+    t.s1 = warp_sum(t.s1);
+    t.s2 = warp_sum(t.s2);
+    __syncthreads();
+    if (lane == 0) red[warp] = make_float4(t.s1.hi, t.s1.lo, t.s2.hi, t.s2.lo);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ff s1 = {0.0f, 0.0f}, s2 = {0.0f, 0.0f};
+        for (int w = 0; w < kThreads / 32; ++w) {
+            s1 = ff_add(s1, ff{red[w].x, red[w].y});
+            s2 = ff_add(s2, ff{red[w].z, red[w].w});
+        }
+        const double npix = (double)(p.r1 - p.r0) * (double)(p.c1 - p.c0);
+        const double mean = ff_to_double(s1) / npix;
+        const double var = ff_to_double(s2) / npix - mean * mean;
+        *q0sq_out = (float)(var / (mean * mean));
+        ws->tick[0] = 0u;
+    }
+}
+
+// Region sums of J itself (iteration 0, and every iteration of the unfused
+// path).  One CTA per region tile, same tile geometry and order as the
+// fused kernel.
+__global__ void __launch_bounds__(kThreads) srad_stats_kernel(const float *__restrict__ J, SradArgs p, NestWs *ws,
+                                                              float *q0sq_out) {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;");
+    const int roi_tile = blockIdx.x;
+    const int i0 = (p.ty0 + roi_tile / p.ntx) * kTY, j0 = (p.tx0 + roi_tile % p.ntx) * kTX;
+    RoiAcc a = {{0.0f, 0.0f}, {0.0f, 0.0f}};
+    for (int idx = threadIdx.x; idx < kTY * kTX; idx += kThreads) {
+        const int i = i0 + idx / kTX, j = j0 + idx % kTX;
+        if (i >= p.r0 && i < p.r1 && j >= p.c0 && j < p.c1) roi_add(a, J[(size_t)i * p.nx + j]);
+    }
+    roi_publish(a, p, roi_tile, ws, q0sq_out);
+}
+
+// One fused iteration: coefficient in shared memory, update, and the next
+// iteration's region sums.  q0sq_next == nullptr on the last iteration.
+__global__ void __launch_bounds__(kThreads) srad_fused_kernel(const float *__restrict__ J, float *__restrict__ Jn,
+                                                              SradArgs p, const float *q0sq_t, NestWs *ws,
+                                                              float *q0sq_next) {
+    __shared__ float Js[kJsH][kJsW];
+    __shared__ float Cs[kCsH][kCsW];
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;");
+    const int i0 = blockIdx.y * kTY, j0 = blockIdx.x * kTX;
+    const int nx = p.nx, ny = p.ny;
+    const float q0sq = *q0sq_t;
+    // J tile with a halo of 1 above / left and 2 below / right, clamped to
+    // the image (the clamp-to-edge neighbours)
+    for (int idx = threadIdx.x; idx < kJsH * (kTX + 3); idx += kThreads) {
+        const int r = idx / (kTX + 3), c = idx - r * (kTX + 3);
+        const int gi = clampi(i0 - 1 + r, 0, ny - 1), gj = clampi(j0 - 1 + c, 0, nx - 1);
+        Js[r][c] = __ldg(J + (size_t)gi * nx + gj);
+    }
+    __syncthreads();
+    // coefficient of rows i0 .. i0+TY and cols j0 .. j0+TX (inside the image)
+    for (int idx = threadIdx.x; idx < kCsH * (kTX + 1); idx += kThreads) {
+        const int r = idx / (kTX + 1), c = idx - r * (kTX + 1);
+        if (i0 + r < ny && j0 + c < nx) {
+            const float Jc = Js[r + 1][c + 1];
+            Cs[r][c] = srad_coeff(Jc, Js[r][c + 1] - Jc, Js[r + 2][c + 1] - Jc, Js[r + 1][c] - Jc,
+                                  Js[r + 1][c + 2] - Jc, q0sq);
+        }
+    }
+    __syncthreads();
+    const bool in_roi_rows = i0 < p.r1 && i0 + kTY > p.r0;
+    const bool in_roi = q0sq_next && in_roi_rows && j0 < p.c1 && j0 + kTX > p.c0;
+    RoiAcc a = {{0.0f, 0.0f}, {0.0f, 0.0f}};
+    for (int idx = threadIdx.x; idx < kTY * kTX; idx += kThreads) {
+        const int r = idx / kTX, c = idx - r * kTX;
+        const int i = i0 + r, j = j0 + c;
+        if (i < ny && j < nx) {
+            const float Jc = Js[r + 1][c + 1];
+            const int rs = i + 1 < ny ? r + 1 : r, ce = j + 1 < nx ? c + 1 : c;
+            const float v = srad_update(Jc, Js[r][c + 1] - Jc, Js[r + 2][c + 1] - Jc, Js[r + 1][c] - Jc,
+                                        Js[r + 1][c + 2] - Jc, Cs[r][c], Cs[rs][c], Cs[r][c], Cs[r][ce], p.k);
+            Jn[(size_t)i * nx + j] = v;
+            if (in_roi && i >= p.r0 && i < p.r1 && j >= p.c0 && j < p.c1) roi_add(a, v);
+        }
+    }
+    if (in_roi) {
+        const int roi_tile = (blockIdx.y - p.ty0) * p.ntx + (blockIdx.x - p.tx0);
+        roi_publish(a, p, roi_tile, ws, q0sq_next);
+    }
+}
+
+// Unfused: the coefficient of every pixel into C.
+__global__ void __launch_bounds__(kThreads) srad_coeff_kernel(const float *__restrict__ J, float *__restrict__ C,
+                                                              SradArgs p, const float *q0sq_t) {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;");
+    const int j = blockIdx.x * kTX + (threadIdx.x & (kTX - 1));
+    const int i = blockIdx.y * (kThreads / kTX) + (threadIdx.x / kTX);
+    if (i >= p.ny || j >= p.nx) return;
+    const int nx = p.nx;
+    const float Jc = J[(size_t)i * nx + j];
+    const float dN = J[(size_t)clampi(i - 1, 0, p.ny - 1) * nx + j] - Jc;
+    const float dS = J[(size_t)clampi(i + 1, 0, p.ny - 1) * nx + j] - Jc;
+    const float dW = J[(size_t)i * nx + clampi(j - 1, 0, nx - 1)] - Jc;
+    const float dE = J[(size_t)i * nx + clampi(j + 1, 0, nx - 1)] - Jc;
+    C[(size_t)i * nx + j] = srad_coeff(Jc, dN, dS, dW, dE, *q0sq_t);
+}
+
+// Unfused: the flux update from J and C.
+__global__ void __launch_bounds__(kThreads) srad_update_kernel(const float *__restrict__ J,
+                                                               const float *__restrict__ C, float *__restrict__ Jn,
+                                                               SradArgs p) {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;");
+    const int j = blockIdx.x * kTX + (threadIdx.x & (kTX - 1));
+    const int i = blockIdx.y * (kThreads / kTX) + (threadIdx.x / kTX);
+    if (i >= p.ny || j >= p.nx) return;
+    const int nx = p.nx;
+    const size_t is = (size_t)clampi(i + 1, 0, p.ny - 1), je = (size_t)clampi(j + 1, 0, nx - 1);
+    const float Jc = J[(size_t)i * nx + j];
+    const float dN = J[(size_t)clampi(i - 1, 0, p.ny - 1) * nx + j] - Jc;
+    const float dS = J[is * nx + j] - Jc;
+    const float dW = J[(size_t)i * nx + clampi(j - 1, 0, nx - 1)] - Jc;
+    const float dE = J[(size_t)i * nx + je] - Jc;
+    const float c = C[(size_t)i * nx + j];
+    Jn[(size_t)i * nx + j] = srad_update(Jc, dN, dS, dW, dE, c, C[is * nx + j], c, C[(size_t)i * nx + je], p.k);
+}
+
+}  // namespace
+}  // namespace hx
+
+extern "C" hx_status hx_srad(hx_ctx *ctx, float *J0, float *J1, float *C, int32_t nx, int32_t ny, int32_t iters,
+                             float lambda, int32_t r0, int32_t r1, int32_t c0, int32_t c1, float *d_q0sq,
+                             int32_t fused, int32_t *result_in_J1, hx_stream_t stream) {
+    using namespace hx;
+    if (!ctx) return fail(HX_ERR_INVALID, "hx_srad: ctx is NULL");
+    if (nx < 1 || ny < 1 || nx > 65536 || ny > 65536 || (int64_t)nx * ny > ((int64_t)1 << 31))
+        return fail(HX_ERR_INVALID, "hx_srad: image size out of range");
+    if (iters < 0 || iters > (1 << 20)) return fail(HX_ERR_INVALID, "hx_srad: iters out of range");
+    if (r0 < 0 || r1 > ny || r0 >= r1 || c0 < 0 || c1 > nx || c0 >= c1)
+        return fail(HX_ERR_INVALID, "hx_srad: region of interest empty or outside the image");
+    if (!J0 || !J1) return fail(HX_ERR_INVALID, "hx_srad: image pointer is NULL");
+    if (iters > 0 && !d_q0sq) return fail(HX_ERR_INVALID, "hx_srad: d_q0sq is NULL");
+    if (!fused && iters > 0 && !C) return fail(HX_ERR_INVALID, "hx_srad: the unfused path needs C");
+    if ((((uintptr_t)J0 | (uintptr_t)J1 | (uintptr_t)C | (uintptr_t)d_q0sq) & 3u) != 0)
+        return fail(HX_ERR_INVALID, "hx_srad: pointers must be 4-byte aligned");
+    const size_t bytes = (size_t)nx * ny * sizeof(float);
+    auto overlap = [bytes](const float *a, const float *b) {
+        return a && b && (uintptr_t)a < (uintptr_t)b + bytes && (uintptr_t)b < (uintptr_t)a + bytes;
+    };
+    if (overlap(J0, J1) || (!fused && (overlap(J0, C) || overlap(J1, C))))
+        return fail(HX_ERR_INVALID, "hx_srad: image buffers overlap");
+    SradArgs p;
+    p.nx = nx;
+    p.ny = ny;
+    p.r0 = r0;
+    p.r1 = r1;
+    p.c0 = c0;
+    p.c1 = c1;
+    p.tx0 = c0 / kTX;
+    p.ty0 = r0 / kTY;
+    p.ntx = (c1 - 1) / kTX - p.tx0 + 1;
+    const int nty = (r1 - 1) / kTY - p.ty0 + 1;
+    p.roi_tiles = p.ntx * nty;
+    p.k = 0.25f * lambda;
+    if (p.roi_tiles > kNestCap) return fail(HX_ERR_NOMEM, "hx_srad: region of interest spans too many tiles");
+    if (result_in_J1) *result_in_J1 = iters & 1;
+    if (iters == 0) return HX_OK;
+    DeviceGuard g(ctx->device);
+    WsSlot *slot = nullptr;
+    hx_status st = slot_for(ctx, stream, &slot);
+    if (st != HX_OK) return st;
+    NestWs *ws = ctx->nest_ws + (slot - ctx->ws);
+
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.blockDim = dim3(kThreads);
+    cfg.stream = (cudaStream_t)stream;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const dim3 tiles((nx + kTX - 1) / kTX, (ny + kTY - 1) / kTY);
+    const dim3 rows_grid((nx + kTX - 1) / kTX, (ny + kThreads / kTX - 1) / (kThreads / kTX));
+    cudaError_t e;
+    for (int t = 0; t < iters; ++t) {
+        const float *src = (t & 1) ? J1 : J0;
+        float *dst = (t & 1) ? J0 : J1;
+        if (t == 0 || !fused) {
+            cfg.gridDim = dim3(p.roi_tiles);
+            e = cudaLaunchKernelEx(&cfg, srad_stats_kernel, src, p, ws, d_q0sq + t);
+            if (e != cudaSuccess) return cuda_fail(e, "hx_srad: stats launch");
+        }
+        if (fused) {
+            cfg.gridDim = tiles;
+            float *next = t + 1 < iters ? d_q0sq + t + 1 : nullptr;
+            e = cudaLaunchKernelEx(&cfg, srad_fused_kernel, src, dst, p, (const float *)(d_q0sq + t), ws, next);
+        } else {
+            cfg.gridDim = rows_grid;
+            e = cudaLaunchKernelEx(&cfg, srad_coeff_kernel, src, C, p, (const float *)(d_q0sq + t));
+            if (e == cudaSuccess) e = cudaLaunchKernelEx(&cfg, srad_update_kernel, src, (const float *)C, dst, p);
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "hx_srad: launch");
+    }
+    return HX_OK;
+}

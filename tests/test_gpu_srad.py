@@ -1,0 +1,97 @@
+"""SRAD-style fused nest on the GPU against the oracle.
+
+The GPU evaluates the coefficient and the update in fp32 in the oracle's
+order (no contraction), and forms q0^2 in double from float-float region
+sums; the oracle forms it in double from sequential double sums.  Both round
+q0^2 to fp32 once, so per-iteration q0^2 and the images are compared bit for
+bit with the f32 oracle, and within 2e-5 (relative, normwise) with the f64
+one.  The fused path (one kernel per iteration) and the unfused one (three
+kernels) must agree bit for bit.
+"""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+def _run(hx, ctx, J, iters, lam, roi, fused):
+    J0 = torch.from_numpy(J).cuda()
+    J1 = torch.empty_like(J0)
+    out, q0 = hx.hx_srad(ctx, J0, J1, iters, lam, roi, fused=fused)
+    torch.cuda.synchronize()
+    return out.cpu().numpy(), q0[:iters].cpu().numpy()
+
+
+CASES = [((17, 23), (0, 17, 0, 23)), ((16, 128), (3, 9, 5, 100)), ((33, 257), (0, 33, 0, 257)),
+         ((130, 300), (17, 129, 130, 299)), ((1, 200), (0, 1, 10, 190)), ((200, 1), (5, 150, 0, 1)),
+         ((512, 512), (0, 128, 0, 128))]
+
+
+@pytest.mark.parametrize("shape,roi", CASES)
+@pytest.mark.parametrize("iters", [1, 3])
+def test_srad_matches_oracle(gpu, shape, roi, iters):
+    hx = gpu
+    J = workloads.srad_image(*shape)
+    lam = 0.5
+    ref32, q32 = oracle.srad(J, iters, lam, roi, "f32")
+    ref64, _ = oracle.srad(J, iters, lam, roi, "f64")
+    with hx.hx_create(0) as ctx:
+        fused, qf = _run(hx, ctx, J, iters, lam, roi, True)
+        unfused, qu = _run(hx, ctx, J, iters, lam, roi, False)
+    np.testing.assert_array_equal(qf.view(np.uint32), q32.view(np.uint32))
+    np.testing.assert_array_equal(fused.view(np.uint32), ref32.view(np.uint32))
+    np.testing.assert_array_equal(unfused.view(np.uint32), fused.view(np.uint32))
+    np.testing.assert_array_equal(qu.view(np.uint32), qf.view(np.uint32))
+    assert np.max(np.abs(fused - ref64)) <= 2e-5 * np.max(np.abs(ref64))
+
+
+def test_srad_zero_iterations_and_homogeneous_region(gpu):
+    hx = gpu
+    with hx.hx_create(0) as ctx:
+        J = workloads.srad_image(20, 30)
+        out, _ = _run(hx, ctx, J, 0, 0.5, (0, 20, 0, 30), True)
+        np.testing.assert_array_equal(out, J)
+        flat = np.full((20, 30), 1.75, dtype=np.float32)
+        for fused in (True, False):
+            out, q0 = _run(hx, ctx, flat, 2, 0.5, (0, 20, 0, 30), fused)
+            assert q0[0] == 0.0 and np.all(np.isnan(out))
+
+
+def test_srad_rejects_bad_arguments(gpu):
+    hx = gpu
+    with hx.hx_create(0) as ctx:
+        J0 = torch.ones(16, 16, device="cuda:0")
+        J1 = torch.empty_like(J0)
+        for roi in ((0, 0, 0, 16), (0, 17, 0, 16), (4, 2, 0, 16), (0, 16, -1, 3)):
+            with pytest.raises(hx.HxError):
+                hx.hx_srad(ctx, J0, J1, 1, 0.5, roi)
+        with pytest.raises(hx.HxError):
+            hx.hx_srad(ctx, J0, J0, 1, 0.5, (0, 16, 0, 16))          # in place
+        with pytest.raises(hx.HxError):
+            hx.hx_srad(ctx, J0, J1, 1, 0.5, (0, 16, 0, 16), fused=False, C=J1)
+
+
+def test_srad_full_size_one_iteration(gpu):
+    # the bench's image size: 8192 x 8192, Rodinia-style 128 x 128 region
+    hx = gpu
+    ny = nx = 8192
+    roi = (0, 128, 0, 128)
+    J = workloads.srad_image(ny, nx)
+    ref32, q32 = oracle.srad(J, 1, 0.5, roi, "f32")
+    with hx.hx_create(0) as ctx:
+        J0 = torch.from_numpy(J).cuda()
+        J1 = torch.empty_like(J0)
+        out, q0 = hx.hx_srad(ctx, J0, J1, 1, 0.5, roi)
+        torch.cuda.synchronize()
+        assert q0[0].item() == float(q32[0])
+        got = out.cpu().numpy()
+        np.testing.assert_array_equal(got.view(np.uint32), ref32.view(np.uint32))
+        # flux conservation at any size (fp32 rounding per pixel only)
+        tot_in = float(np.sum(J, dtype=np.float64))
+        tot_out = float(out.double().sum().item())
+        assert abs(tot_out - tot_in) <= 1e-6 * tot_in

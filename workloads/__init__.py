@@ -52,6 +52,7 @@ SEED_STENCIL = 1
 SEED_HISTOGRAM = 2
 SEED_BATCH = 3
 SEED_SERVING = 4
+SEED_SRAD = 7
 
 _CHUNK = 1 << 22
 
@@ -128,6 +129,14 @@ def map_reduce_inputs(n: int, seed: int = SEED_MAP_REDUCE):
 def stencil_grid(ny: int, nx: int, seed: int = SEED_STENCIL) -> np.ndarray:
     """Row-major ny x nx grid, uniform on [0, 1)."""
     return uniform01_f32(seed, ny * nx).reshape(ny, nx)
+
+
+def srad_image(ny: int, nx: int, seed: int = SEED_SRAD) -> np.ndarray:
+    """Positive fp32 intensity image exp(u), u uniform on [0, 1) (values in
+    [1, e)): the exponentiated-image input of SRAD-style diffusion.  exp is
+    taken in double and rounded to fp32 once."""
+    u = uniform01_f32(seed, ny * nx).astype(np.float64)
+    return np.exp(u).astype(np.float32).reshape(ny, nx)
 
 
 def histogram_mixture_u8(n: int, seed: int = SEED_HISTOGRAM) -> np.ndarray:
