@@ -462,7 +462,8 @@ def bench_hx(args, rank, world, local):
     # ---- generic nests and the reduction-tree ablation
     nests = None
     if not args.no_nests:
-        nests = {"workloads": bench_nests(hx, ctx, dev, peak), "tree_ablation": bench_tree_ablation(hx, ctx, dev)}
+        nests = {"workloads": bench_nests(hx, ctx, dev, peak), "tree_ablation": bench_tree_ablation(hx, ctx, dev),
+                 "srad": bench_srad(hx, ctx, dev, peak)}
 
     # ---- end to end through the public API with pinned host buffers
     e2e = bench_e2e(args, hx, ctx, dev, x_h, y_h, u_h, v_h, batch, batch_bufs, BATCH_BYTES)
@@ -688,6 +689,47 @@ def bench_tree_ablation(hx, ctx, dev, n=1 << 20, reps=5):
             "chunk_tree_speedup": round(ms["seq"] / ms["chunk"], 2),
             "warp_tree_speedup": round(ms["seq"] / ms["warp"], 2),
             "paper_edge_end_to_end": {"tree": 6.22, "tree_plus_warp": 9.77}}
+
+
+def bench_srad(hx, ctx, dev, peak, ny=8192, nx=8192, iters=10, reps=3):
+    """SRAD-style nest on an 8192 x 8192 image (256 MiB, far above L2), 10
+    iterations, lambda 0.5, 128 x 128 region of interest: the fused path
+    (one kernel per iteration) against the unfused loop nest (region reduce,
+    coefficient, update).  Each repetition restarts from the same image.
+    Algorithmic bytes: 8 per pixel and iteration (read J, write J')."""
+    import torch
+
+    import workloads
+
+    src = torch.from_numpy(workloads.srad_image(ny, nx)).to(dev)
+    J0, J1, C = torch.empty_like(src), torch.empty_like(src), torch.empty_like(src)
+    q0 = torch.empty(iters, device=dev)
+    roi = (0, 128, 0, 128)
+    out = {}
+    for fused in (True, False):
+        ms = []
+        for r in range(reps + 1):
+            J0.copy_(src)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            hx.hx_srad(ctx, J0, J1, iters, 0.5, roi, q0sq=q0, fused=fused, C=C)
+            b.record()
+            torch.cuda.synchronize()
+            if r:
+                ms.append(a.elapsed_time(b))
+        out["fused" if fused else "unfused"] = sorted(ms)[len(ms) // 2]
+    npx = ny * nx
+    per_it = {k: v / iters for k, v in out.items()}
+    gbs = 8 * npx / (per_it["fused"] * 1e-3) / 1e9
+    del src, J0, J1, C
+    torch.cuda.empty_cache()
+    return {"image": f"{ny} x {nx} fp32, {iters} iterations, lambda 0.5, region 128 x 128",
+            "fused_ms_per_iteration": round(per_it["fused"], 4),
+            "unfused_ms_per_iteration": round(per_it["unfused"], 4),
+            "fusion_speedup": round(per_it["unfused"] / per_it["fused"], 3),
+            "fused_mpix_per_s": round(npx / (per_it["fused"] * 1e-3) / 1e6, 1),
+            "fused_algorithmic_GB/s": round(gbs, 1), "fused_frac_of_measured_hbm": round(gbs / peak, 4),
+            "launches_per_iteration": {"fused": 1, "unfused": 3}}
 
 
 def bench_batched_vs_per_launch(hx, ctx, batch, tasks, stream, reps=10):

@@ -47,14 +47,17 @@ struct SradArgs {
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
 // Diffusion coefficient of a pixel from its value and its four neighbour
-// differences (the SRAD expression, fp32, fixed order).
-__device__ __forceinline__ float srad_coeff(float Jc, float dN, float dS, float dW, float dE, float q0sq) {
-    const float G2 = ((dN * dN + dS * dS) + (dW * dW + dE * dE)) / (Jc * Jc);
-    const float L = ((dN + dS) + (dW + dE)) / Jc;
+// differences: the SRAD expression 1/(1 + (num/den^2 - q0sq)/(q0sq(1+q0sq)))
+// multiplied through by den^2, so that a pixel costs two divisions (iq =
+// 1/(q0sq(1+q0sq)) is per launch).  fp32, fixed order.
+__device__ __forceinline__ float srad_coeff(float Jc, float dN, float dS, float dW, float dE, float q0sq, float iq) {
+    const float r = 1.0f / Jc;
+    const float G2 = (((dN * dN + dS * dS) + (dW * dW + dE * dE)) * r) * r;
+    const float L = ((dN + dS) + (dW + dE)) * r;
     const float num = 0.5f * G2 - 0.0625f * (L * L);
     const float den = 1.0f + 0.25f * L;
-    const float qsq = num / (den * den);
-    float c = 1.0f / (1.0f + (qsq - q0sq) / (q0sq * (1.0f + q0sq)));
+    const float den2 = den * den;
+    float c = den2 / (den2 + (num - q0sq * den2) * iq);
     if (c < 0.0f) c = 0.0f;
     else if (c > 1.0f) c = 1.0f;
     return c;
@@ -155,13 +158,15 @@ __global__ void __launch_bounds__(kThreads) srad_fused_kernel(const float *__res
     asm volatile("griddepcontrol.launch_dependents;");
     const int i0 = blockIdx.y * kTY, j0 = blockIdx.x * kTX;
     const int nx = p.nx, ny = p.ny;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const float q0sq = *q0sq_t;
+    const float iq = 1.0f / (q0sq * (1.0f + q0sq));
     // J tile with a halo of 1 above / left and 2 below / right, clamped to
-    // the image (the clamp-to-edge neighbours)
-    for (int idx = threadIdx.x; idx < kJsH * (kTX + 3); idx += kThreads) {
-        const int r = idx / (kTX + 3), c = idx - r * (kTX + 3);
-        const int gi = clampi(i0 - 1 + r, 0, ny - 1), gj = clampi(j0 - 1 + c, 0, nx - 1);
-        Js[r][c] = __ldg(J + (size_t)gi * nx + gj);
+    // the image (the clamp-to-edge neighbours): warp w loads rows w, w+8, ...
+    for (int r = warp; r < kJsH; r += kThreads / 32) {
+        const float *row = J + (size_t)clampi(i0 - 1 + r, 0, ny - 1) * nx;
+#pragma unroll
+        for (int c = lane; c < kTX + 3; c += 32) Js[r][c] = __ldg(row + clampi(j0 - 1 + c, 0, nx - 1));
     }
     __syncthreads();
     // coefficient of rows i0 .. i0+TY and cols j0 .. j0+TX (inside the image)
@@ -170,15 +175,15 @@ __global__ void __launch_bounds__(kThreads) srad_fused_kernel(const float *__res
         if (i0 + r < ny && j0 + c < nx) {
             const float Jc = Js[r + 1][c + 1];
             Cs[r][c] = srad_coeff(Jc, Js[r][c + 1] - Jc, Js[r + 2][c + 1] - Jc, Js[r + 1][c] - Jc,
-                                  Js[r + 1][c + 2] - Jc, q0sq);
+                                  Js[r + 1][c + 2] - Jc, q0sq, iq);
         }
     }
     __syncthreads();
     const bool in_roi_rows = i0 < p.r1 && i0 + kTY > p.r0;
     const bool in_roi = q0sq_next && in_roi_rows && j0 < p.c1 && j0 + kTX > p.c0;
     RoiAcc a = {{0.0f, 0.0f}, {0.0f, 0.0f}};
-    for (int idx = threadIdx.x; idx < kTY * kTX; idx += kThreads) {
-        const int r = idx / kTX, c = idx - r * kTX;
+    const int c = threadIdx.x & (kTX - 1);
+    for (int r = threadIdx.x / kTX; r < kTY; r += kThreads / kTX) {
         const int i = i0 + r, j = j0 + c;
         if (i < ny && j < nx) {
             const float Jc = Js[r + 1][c + 1];
@@ -209,7 +214,8 @@ __global__ void __launch_bounds__(kThreads) srad_coeff_kernel(const float *__res
     const float dS = J[(size_t)clampi(i + 1, 0, p.ny - 1) * nx + j] - Jc;
     const float dW = J[(size_t)i * nx + clampi(j - 1, 0, nx - 1)] - Jc;
     const float dE = J[(size_t)i * nx + clampi(j + 1, 0, nx - 1)] - Jc;
-    C[(size_t)i * nx + j] = srad_coeff(Jc, dN, dS, dW, dE, *q0sq_t);
+    const float q0sq = *q0sq_t;
+    C[(size_t)i * nx + j] = srad_coeff(Jc, dN, dS, dW, dE, q0sq, 1.0f / (q0sq * (1.0f + q0sq)));
 }
 
 // Unfused: the flux update from J and C.

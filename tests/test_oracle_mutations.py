@@ -101,7 +101,7 @@ MUTANTS = {
     "srad_den_sign": ("T den = ONE + QUARTER * L;", "T den = ONE - QUARTER * L;", SRAD_PINS),
     "srad_no_upper_clamp": ("else if (c > ONE) c = ONE;", "else if (c > ONE) c = c;", SRAD_PINS),
     "srad_G2_over_J": ("(dW * dW + dE * dE)) / (Jc * Jc);", "(dW * dW + dE * dE)) / Jc;", SRAD_PINS),
-    "srad_roi_rows_from_zero": ("for (int64_t i = r0; i < r1; ++i)", "for (int64_t i = 0; i < r1; ++i)", SRAD_PINS),
+    "srad_roi_rows_from_zero": ("for (int64_t i = r0; i < r1; i++)", "for (int64_t i = 0; i < r1; i++)", SRAD_PINS),
     "srad_dS_from_north": ("T dS = cur[is * nx + j] - Jc;", "T dS = cur[clampi(i - 1, 0, ny - 1) * nx + j] - Jc;",
                            SRAD_PINS),
     "nest_min_keeps_pos_zero": ("if (v < best || (v == 0.0f && best == 0.0f && !signbit(best) && signbit(v))) best = v;",
