@@ -665,6 +665,7 @@ def bench_nests(hx, ctx, dev, peak, reps=20):
         gbs = nbytes / (ms * 1e-3) / 1e9
         rows_out.append({"nest": name, "ms": round(ms, 4), "algorithmic_bytes": nbytes, "GB/s": round(gbs, 1),
                          "frac_of_measured_hbm": round(gbs / peak, 4)})
+    rows_out[0]["dram_bytes_per_launch"] = measured_traffic().get("nest_sum_2p28")
     del big, out27, res
     torch.cuda.empty_cache()
     return rows_out
@@ -729,6 +730,8 @@ def bench_srad(hx, ctx, dev, peak, ny=8192, nx=8192, iters=10, reps=3):
             "fusion_speedup": round(per_it["unfused"] / per_it["fused"], 3),
             "fused_mpix_per_s": round(npx / (per_it["fused"] * 1e-3) / 1e6, 1),
             "fused_algorithmic_GB/s": round(gbs, 1), "fused_frac_of_measured_hbm": round(gbs / peak, 4),
+            "fused_dram_bytes_per_iteration": measured_traffic().get("srad_fused"),
+            "bound": "issue (two IEEE fp32 divisions per pixel in the coefficient)",
             "launches_per_iteration": {"fused": 1, "unfused": 3}}
 
 
