@@ -386,6 +386,11 @@ int hxo_fork_reduce(int ndim, const int64_t *dims, int reduce_dims, int monoid,
  *  3. fork over pixels: D = (c[i][j]*dN + c[i+1][j]*dS) + (c[i][j]*dW +
  *     c[i][j+1]*dE) (neighbour indices clamped), J'[i][j] = Jc + (0.25*lambda)*D.
  *
+ * Parity: conservation, symmetry, the maximum principle, the Jacobi limit,
+ * the ROI statistics and a checkerboard closed form for qsq pin this nest;
+ * the mapping from qsq to c is parity unpinned (the tests can only restate
+ * it).
+ *
  * Intensities must be nonzero (the scheme divides by J); a homogeneous ROI
  * (q0sq == 0) makes the coefficient 0/0 and the result NaN, as the formula
  * says.  q0sq_out[t] receives iteration t's speckle scale.  The f32 variant
