@@ -374,7 +374,7 @@ hx_status hx_tune_set(hx_ctx *ctx, const hx_tune_table *t);
 
 /* Measure the candidates for every size class up to 2^max_log2 elements
  * (10 <= max_log2 <= 30) on this context's device and store the fastest in
- * the context's table.  Allocates and frees about 1.5 GiB of temporary
+ * the context's table.  Allocates and frees about 3.5 GiB of temporary
  * device memory, synchronises `stream`, takes a few seconds. */
 hx_status hx_autotune(hx_ctx *ctx, int32_t max_log2, hx_stream_t stream);
 

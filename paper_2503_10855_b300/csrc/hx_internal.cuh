@@ -33,7 +33,7 @@ constexpr int kMrWarpsPerCta = 4;    // standalone launch: tiles per CTA
 // class; kStRows is the default).
 constexpr int kStRows = 8;
 constexpr int kStWarps = 4;          // warps per CTA, stacked vertically
-constexpr int kBatchStRows = 4;      // rows per warp block inside the batched kernel
+constexpr int kBatchStRows = 8;      // rows per warp block inside the batched kernel
 
 // histogram: 256 bins; per-CTA shared counters replicated per slot (below).
 constexpr int kHiBins = 256;

@@ -9,6 +9,7 @@
 // every batch plan reads it, so a standalone call and a batch made from the
 // same context always agree bit for bit.
 #include <algorithm>
+#include <cmath>
 #include <cerrno>
 #include <cstdio>
 #include <cstdlib>
@@ -103,7 +104,7 @@ void hx_tune_table_default(hx_tune_table *t) {
         t->nest_lane_elems[c] = 16;
     }
     t->batch_map_run = 8;
-    t->batch_stencil_run = 16;
+    t->batch_stencil_run = 8;
 }
 
 hx_status hx_tune_table_check(const hx_tune_table *t) {
@@ -313,44 +314,65 @@ hx_status hx_autotune(hx_ctx *ctx, int32_t max_log2, hx_stream_t stream) {
     }
     for (int c = st_top + 2; c < HX_TUNE_CLASSES; ++c) t.stencil_rows[c] = t.stencil_rows[st_top];
 
-    // batch run lengths: a mixed batch of 48 map->reduce (2^20) and 48
-    // stencil (512^2, ragged and aligned) instances
+    // batch run lengths, timed on a batch shaped like the standard 512-instance
+    // mix: 256 map->reduce instances with sizes spread log-uniformly over
+    // 2^10..2^22 and 256 one-sweep stencils with sides log-uniform over
+    // 32..2048, half of them ragged (element path), interleaved.  Run length
+    // trades per-run overhead against the tail, so the batch must be as large
+    // as real ones: it gets its own buffer (about 2.7 GB, freed afterwards).
+    float *bpool = nullptr;
+    size_t bpool_elems = 0;
+    std::vector<hx_task> tasks;
     if (st == HX_OK) {
-        const int64_t mn = (int64_t)1 << 20;
-        const int side = 512;
-        std::vector<hx_task> tasks;
-        size_t off = 0;
-        for (int i = 0; i < 48; ++i) {
-            hx_task tk;
-            memset(&tk, 0, sizeof tk);
-            tk.kind = HX_TASK_MAP_REDUCE;
-            tk.u.mr.x = pool + off;
-            tk.u.mr.y = pool + off + mn;
-            tk.u.mr.out = pool + off + 2 * mn;
-            tk.u.mr.sum = res + i;
-            tk.u.mr.a = 1.5f;
-            tk.u.mr.n = mn;
-            off += 3 * mn;
-            tasks.push_back(tk);
+        std::vector<int64_t> mns;
+        std::vector<int> sides;
+        for (int i = 0; i < 256; ++i) {
+            const double u = (i + 0.5) / 256.0;
+            const int64_t mn = (int64_t)std::llround(std::exp2(10.0 + 12.0 * u));
+            int side = (int)std::llround(std::exp2(5.0 + 6.0 * u));
+            side = (i & 1) ? (side | 1) : (side + 3) / 4 * 4;
+            mns.push_back(mn);
+            sides.push_back(side);
+            bpool_elems += 3 * (((size_t)mn + 3) / 4 * 4) + (2 * (size_t)side * side + 3) / 4 * 4;
         }
-        for (int i = 0; i < 48; ++i) {
-            const int nx = side - (i & 1) * 3;   // half ragged (element path), half aligned
-            hx_task tk;
-            memset(&tk, 0, sizeof tk);
-            tk.kind = HX_TASK_STENCIL2D;
-            tk.u.st.u0 = pool + off;
-            tk.u.st.u1 = pool + off + (size_t)side * side;
-            tk.u.st.resid = res + 1024 + i;
-            tk.u.st.nx = nx;
-            tk.u.st.ny = side;
-            tk.u.st.iters = 1;
-            off += 2 * (size_t)side * side;
-            tasks.push_back(tk);
+        e = cudaMalloc(&bpool, bpool_elems * sizeof(float));
+        if (e != cudaSuccess) st = cuda_fail(e, "hx_autotune: batch pool cudaMalloc");
+        if (st == HX_OK) {
+            tune_fill_f32<<<ctx->num_sms * 8, 256, 0, s>>>(bpool, (int64_t)bpool_elems, 777u);
+            size_t off = 0;
+            for (int i = 0; i < 256; ++i) {
+                const int64_t mn = mns[i];
+                const int side = sides[i];
+                const size_t mn4 = ((size_t)mn + 3) / 4 * 4;   // 16-byte aligned arrays
+                hx_task tk;
+                memset(&tk, 0, sizeof tk);
+                tk.kind = HX_TASK_MAP_REDUCE;
+                tk.u.mr.x = bpool + off;
+                tk.u.mr.y = bpool + off + mn4;
+                tk.u.mr.out = bpool + off + 2 * mn4;
+                tk.u.mr.sum = res + i;
+                tk.u.mr.a = 1.5f;
+                tk.u.mr.n = mn;
+                off += 3 * mn4;
+                tasks.push_back(tk);
+                memset(&tk, 0, sizeof tk);
+                tk.kind = HX_TASK_STENCIL2D;
+                tk.u.st.u0 = bpool + off;
+                tk.u.st.u1 = bpool + off + (size_t)side * side;
+                tk.u.st.resid = res + 1024 + i;
+                tk.u.st.nx = side;
+                tk.u.st.ny = side;
+                tk.u.st.iters = 1;
+                off += (2 * (size_t)side * side + 3) / 4 * 4;
+                tasks.push_back(tk);
+            }
         }
+    }
+    if (st == HX_OK) {
         float best = 1e30f;
         int best_m = t.batch_map_run, best_s = t.batch_stencil_run;
-        for (int mr : {4, 8, 16}) {
-            for (int sr : {8, 16, 32}) {
+        for (int mr : {2, 4, 8}) {
+            for (int sr : {4, 8, 16}) {
                 ctx->tune.batch_map_run = mr;
                 ctx->tune.batch_stencil_run = sr;
                 hx_batch *b = nullptr;
@@ -366,6 +388,7 @@ hx_status hx_autotune(hx_ctx *ctx, int32_t max_log2, hx_stream_t stream) {
         t.batch_stencil_run = best_s;
     }
     cudaStreamSynchronize(s);
+    if (bpool) cudaFree(bpool);
     cudaFree(pool);
     cudaFree(res);
     if (st != HX_OK) {
