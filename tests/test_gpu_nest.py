@@ -257,3 +257,59 @@ def test_strided_float4_slots(gpu, monoid):
         big = _np((64, 96, 128), 115)
         view2 = lambda xs: [xs[0].transpose(1, 0, 2) if isinstance(xs[0], np.ndarray) else xs[0].permute(1, 0, 2)]  # noqa: E731
         _check(hx, ctx, [("in", 0), "abs"], [big], view2, (96, 64, 128), 2, monoid)
+
+
+@pytest.mark.slow
+def test_bench_workloads_full_size(gpu):
+    # the six nests bench.py times, at their sizes, against the oracle (whole
+    # arrays where the oracle takes seconds, sampled rows / segments otherwise)
+    hx = gpu
+    dev = torch.device("cuda:0")
+    big = workloads.uniform_pm1_f32_torch(120, 1 << 28, dev)
+    x27, y27 = big[: 1 << 27], big[1 << 27:]
+    rng = np.random.default_rng(0)
+    with hx.hx_create(0) as ctx:
+        # sum of 2^28 and argmax |x - y| over 2^27: whole arrays
+        _, s, _, s64 = hx.fork_reduce(ctx, [("in", 0)], [big], (1 << 28,), 1, "sum", want_result64=True)
+        _, m, mi, _ = hx.fork_reduce(ctx, [("in", 0), ("in", 1), "sub", "abs"], [x27, y27], (1 << 27,), 1, "argmax")
+        torch.cuda.synchronize()
+        host = big.cpu().numpy()
+        _, ref, _ = oracle.fork_reduce([("in", 0)], [host], host.shape, 1, "sum", want_out=False)
+        cond = float(np.abs(host).astype(np.float64).sum())
+        assert abs(float(s) - float(ref)) <= 1e-5 * cond and abs(float(s64) - float(ref)) <= 1e-9 * cond
+        hx27, hy27 = host[: 1 << 27], host[1 << 27:]
+        _, rm, ri = oracle.fork_reduce([("in", 0), ("in", 1), "sub", "abs"], [hx27, hy27], hx27.shape, 1, "argmax",
+                                       want_out=False)
+        assert float(m) == float(rm) and int(mi) == int(ri)
+        # row sums of 16384 x 16384: 64 sampled rows
+        mat = big.view(16384, 16384)
+        _, rs, _, _ = hx.fork_reduce(ctx, [("in", 0)], [mat], mat.shape, 1, "sum")
+        rows = rng.choice(16384, 64, replace=False)
+        sub = host.reshape(16384, 16384)[rows]
+        _, rref, _ = oracle.fork_reduce([("in", 0)], [sub], sub.shape, 1, "sum", want_out=False)
+        got = rs.cpu().numpy()[rows].astype(np.float64)
+        assert np.all(np.abs(got - rref) <= 1e-5 * np.abs(sub).astype(np.float64).sum(axis=1))
+        # max over 2^24 rows of 8: 100000 sampled rows, exact
+        r8 = big[: 1 << 27].view(1 << 24, 8)
+        _, mx, _, _ = hx.fork_reduce(ctx, [("in", 0)], [r8], r8.shape, 1, "max")
+        rows = rng.choice(1 << 24, 100_000, replace=False)
+        sub = host[: 1 << 27].reshape(1 << 24, 8)[rows]
+        _, mref, _ = oracle.fork_reduce([("in", 0)], [sub], sub.shape, 1, "max", want_out=False)
+        np.testing.assert_array_equal(mx.cpu().numpy()[rows].astype(np.float64), mref)
+        # fused map over 2^27: sampled elements, bit for bit
+        out, _, _, _ = hx.fork_reduce(ctx, [("in", 0), ("const", 0), ("in", 1), "fma"], [x27, y27], (1 << 27,), 0,
+                                      consts=[1.5])
+        idx = rng.choice(1 << 27, 1 << 20, replace=False)
+        oref, _, _ = oracle.fork_reduce([("in", 0), ("const", 0), ("in", 1), "fma"],
+                                        [np.ascontiguousarray(hx27[idx]), np.ascontiguousarray(hy27[idx])],
+                                        (idx.size,), 0, consts=[1.5])
+        np.testing.assert_array_equal(out.cpu().numpy()[idx].view(np.uint32), oref.view(np.uint32))
+        # 3-D sum over dims 1, 2 of the permuted 1024 x 512 x 512 view: 8 sampled segments
+        v3 = big.view(512, 1024, 512).permute(1, 0, 2)
+        _, r3, _, _ = hx.fork_reduce(ctx, [("in", 0)], [v3], v3.shape, 2, "sum")
+        segs = rng.choice(1024, 8, replace=False)
+        h3 = host.reshape(512, 1024, 512)
+        for sgm in segs:
+            blk = np.ascontiguousarray(h3[:, sgm, :])
+            _, bref, _ = oracle.fork_reduce([("in", 0)], [blk], blk.shape, 2, "sum", want_out=False)
+            assert abs(float(r3[sgm]) - float(bref)) <= 1e-5 * float(np.abs(blk).astype(np.float64).sum())
