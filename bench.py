@@ -459,6 +459,9 @@ def bench_hx(args, rank, world, local):
     # ---- serving: continuous batching vs one launch per request
     serving = bench_serving(hx, ctx, dev) if not args.no_serving else None
 
+    # ---- size sweeps of the step's kernels
+    sweeps = bench_sweeps(hx, ctx, dev, peak) if not args.no_sweeps else None
+
     # ---- generic nests and the reduction-tree ablation
     nests = None
     if not args.no_nests:
@@ -505,6 +508,7 @@ def bench_hx(args, rank, world, local):
         "batched": batched,
         "serving": serving,
         "nests": nests,
+        "sweeps": sweeps,
         "e2e": e2e,
         "gpu_launches": launches_per_step * K,
         "clocks": clk.summary(),
@@ -735,6 +739,81 @@ def bench_srad(hx, ctx, dev, peak, ny=8192, nx=8192, iters=10, reps=3):
             "launches_per_iteration": {"fused": 1, "unfused": 3}}
 
 
+def bench_sweeps(hx, ctx, dev, peak):
+    """Size sweeps (each point timed over rotating inputs that together exceed
+    the 126 MB L2, so every call streams from HBM): map->reduce 2^20..2^28,
+    Jacobi 2048^2 / 8192^2 / 16384^2 x 20 sweeps (the larger grids do not fit
+    in L2, so their algorithmic GB/s is HBM traffic), and the histogram at
+    2^24..2^30 mixture bytes plus two adversarial 2^26 inputs (every byte the
+    same value; a ramp 0, 1, ..., 255, 0, ...)."""
+    import torch
+
+    import workloads
+
+    def per_call_ms(fn, n_sets, reps):
+        for k in range(2):
+            fn(k % n_sets)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for k in range(reps):
+            fn(k % n_sets)
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    out = {"map_reduce": [], "jacobi_x20": [], "histogram": []}
+    s32 = torch.empty(1, device=dev)
+    for lg in (20, 22, 24, 26, 28):
+        n = 1 << lg
+        n_sets = max(1, (512 << 20) // (12 * n))
+        xs = [workloads.uniform_pm1_f32_torch(0, n, dev, 2, 0) for _ in range(1)]
+        x, y = xs[0], workloads.uniform_pm1_f32_torch(0, n, dev, 2, 1)
+        sets = [(x.clone(), y.clone(), torch.empty_like(x)) for _ in range(n_sets)]
+        del x, y, xs
+        ms = per_call_ms(lambda k: hx.hx_map_reduce(ctx, sets[k][0], sets[k][1], 1.5, out=sets[k][2], sum_out=s32),
+                         n_sets, max(8, 2 * n_sets))
+        gbs = 12 * n / (ms * 1e-3) / 1e9
+        out["map_reduce"].append({"n": f"2^{lg}", "ms": round(ms, 5), "GB/s": round(gbs, 1),
+                                  "frac_of_measured_hbm": round(gbs / peak, 4)})
+        del sets
+        torch.cuda.empty_cache()
+    for side in (2048, 8192, 16384):
+        u0 = torch.from_numpy(workloads.stencil_grid(side, side)).to(dev) if side <= 8192 else \
+            workloads.uniform01_f32_torch(1, side * side, dev).view(side, side)
+        u1 = torch.empty_like(u0)
+        res = torch.empty(20, device=dev)
+        ms = per_call_ms(lambda k: hx.hx_stencil2d(ctx, u0, u1, 20, resid=res), 1, 3)
+        gbs = 8 * side * side * 20 / (ms * 1e-3) / 1e9
+        out["jacobi_x20"].append({"grid": f"{side}^2", "ms": round(ms, 4), "algorithmic_GB/s": round(gbs, 1),
+                                  "frac_of_measured_hbm": round(gbs / peak, 4),
+                                  "resident": "L2" if side <= 2048 else "HBM"})
+        del u0, u1
+        torch.cuda.empty_cache()
+    bins = torch.empty(256, dtype=torch.int32, device=dev)
+    scan = torch.empty_like(bins)
+    cases = [(f"mixture 2^{lg}", lg, None) for lg in (24, 26, 28, 30)]
+    cases += [("one value 2^26", 26, "one"), ("ramp 2^26", 26, "ramp")]
+    for name, lg, kind in cases:
+        n = 1 << lg
+        if kind is None:
+            v0 = torch.from_numpy(workloads.histogram_mixture_u8(min(n, 1 << 26))).to(dev)
+            v0 = v0.repeat(n // v0.numel())
+        elif kind == "one":
+            v0 = torch.full((n,), 7, dtype=torch.uint8, device=dev)
+        else:
+            v0 = (torch.arange(n, device=dev) % 256).to(torch.uint8)
+        n_sets = max(1, (512 << 20) // n)
+        sets = [v0] + [v0.clone() for _ in range(n_sets - 1)]
+        ms = per_call_ms(lambda k: hx.hx_histogram(ctx, sets[k], bins, scan), n_sets, max(8, 2 * n_sets))
+        gbs = n / (ms * 1e-3) / 1e9
+        out["histogram"].append({"input": name, "ms": round(ms, 5), "GB/s": round(gbs, 1),
+                                 "frac_of_measured_hbm": round(gbs / peak, 4)})
+        del sets, v0
+        torch.cuda.empty_cache()
+    return out
+
+
 def bench_batched_vs_per_launch(hx, ctx, batch, tasks, stream, reps=10):
     """requests/s of the 512 instances as one batch vs one launch per instance.
 
@@ -857,6 +936,7 @@ def main():
     ap.add_argument("--autotune", action="store_true", help="re-measure the tuning table before timing")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving sweep")
     ap.add_argument("--no-nests", action="store_true", help="skip the generic-nest section")
+    ap.add_argument("--no-sweeps", action="store_true", help="skip the size sweeps")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
