@@ -486,7 +486,7 @@ def bench_hx(args, rank, world, local):
         "metric": "achieved HBM GB/s (algorithmic bytes / time) of the fork-join hot path",
         "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": K, "warmup": args.warmup,
         "ms_per_step": round(ms_per_step, 5), "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32 (fp64 reduce combine), u8/u32",
+        "vs_baseline": None, "dtype": "f32 (float-float sums), u8/u32",
         "data": "synthetic (seeded SplitMix64), inputs resident in HBM",
         "config": {
             "workload": "fork-join step: map->reduce N=2^20 a=1.5 + jacobi 2048x2048 x20 sweeps "

@@ -68,6 +68,9 @@ struct NestWs {
     unsigned int tick[kNestTick];
     unsigned int tick2[kNestTick2];
 };
+// A run of Jacobi sweeps stores one partial maximum per CTA and sweep in
+// NestWs::part (as floats) before a residual kernel folds them.
+constexpr int64_t kStPartCap = 4 * (int64_t)kNestCap;
 
 // ---------------------------------------------------------------- plans
 struct MrPlan {

@@ -16,14 +16,17 @@
 
 namespace hx {
 
-// A CTA covers one 128-column (or 32-column) strip and kStWarps warp blocks
-// stacked vertically; CTAs run row band by row band.  The CTA folds its
-// warps' maxima in shared memory and publishes once: one atomic max and one
-// arrival ticket per CTA, the last CTA writes the residual.
-template <bool VEC, int R>
+// A CTA covers one 128-column strip and kStWarps warp blocks stacked
+// vertically; CTAs run row band by row band.  The CTA folds its warps' maxima
+// in shared memory and publishes once.  PART: it stores its maximum at
+// part[cta] and a residual kernel reduces the sweep's partials later (no
+// same-address atomics in the sweep: at 2048^2 those cost 30 % of a sweep);
+// otherwise one atomic max and one arrival ticket per CTA, and the last CTA
+// writes the residual.
+template <bool VEC, int R, bool PART>
 __global__ void __launch_bounds__(kStWarps * kWarp)
 stencil_kernel(const float *__restrict__ src, float *__restrict__ dst, int nx, int ny,
-               WsSlot *ws, float *d_resid_t) {
+               WsSlot *ws, float *d_resid_t, float *part) {
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;");
     __shared__ float wmax[kStWarps];
@@ -41,6 +44,10 @@ stencil_kernel(const float *__restrict__ src, float *__restrict__ dst, int nx, i
     if (threadIdx.x == 0) {
         float bm = wmax[0];
         for (int i = 1; i < kStWarps; ++i) bm = fmaxf(bm, wmax[i]);
+        if (PART) {
+            part[blockIdx.y * gridDim.x + blockIdx.x] = bm;
+            return;
+        }
         atomicMax(&ws->st_max_bits, __float_as_uint(bm));
         __threadfence();
         if (atomicAdd(&ws->st_ticket, 1u) == gridDim.x * gridDim.y - 1) {
@@ -48,6 +55,24 @@ stencil_kernel(const float *__restrict__ src, float *__restrict__ dst, int nx, i
             *d_resid_t = __uint_as_float(atomicExch(&ws->st_max_bits, 0u));
             ws->st_ticket = 0u;
         }
+    }
+}
+
+// Residuals of a run of sweeps: CTA t folds the p partial maxima of sweep
+// t (max is exact, so the order does not matter) into resid[t].
+__global__ void __launch_bounds__(256) stencil_resid_kernel(const float *__restrict__ part, int p, float *resid) {
+    __shared__ float wmax[256 / kWarp];
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;");
+    const float *q = part + (size_t)blockIdx.x * p;
+    float m = 0.0f;
+    for (int i = threadIdx.x; i < p; i += 256) m = fmaxf(m, __ldcg(q + i));
+    m = warp_max(m);
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < 256 / kWarp; ++w) m = fmaxf(m, wmax[w]);
+        resid[blockIdx.x] = m;
     }
 }
 
@@ -79,11 +104,23 @@ extern "C" hx_status hx_stencil2d(hx_ctx *ctx, float *u0, float *u1, int32_t nx,
     const int width = 128;   // both paths: 32 lanes x 4 columns
     const int rows = ctx->tune.stencil_rows[size_class((int64_t)nx * ny)];
     dim3 grid((nx + width - 1) / width, (ny + kStWarps * rows - 1) / (kStWarps * rows));
-    using KernelFn = void (*)(const float *, float *, int, int, WsSlot *, float *);
+    // Partial maxima per sweep go to the stream's nest workspace (free while
+    // this call runs: calls on one stream are serial), up to kStPartCap per
+    // run of sweeps; grids with more CTAs than that use the atomic path.
+    const int64_t p = (int64_t)grid.x * grid.y;
+    const bool use_part = p <= kStPartCap;
+    float *part = reinterpret_cast<float *>(ctx->nest_ws[ws - ctx->ws].part);
+    using KernelFn = void (*)(const float *, float *, int, int, WsSlot *, float *, float *);
     KernelFn fn;
-    if (rows == 4) fn = vec ? stencil_kernel<true, 4> : stencil_kernel<false, 4>;
-    else if (rows == 16) fn = vec ? stencil_kernel<true, 16> : stencil_kernel<false, 16>;
-    else fn = vec ? stencil_kernel<true, 8> : stencil_kernel<false, 8>;
+    if (use_part) {
+        if (rows == 4) fn = vec ? stencil_kernel<true, 4, true> : stencil_kernel<false, 4, true>;
+        else if (rows == 16) fn = vec ? stencil_kernel<true, 16, true> : stencil_kernel<false, 16, true>;
+        else fn = vec ? stencil_kernel<true, 8, true> : stencil_kernel<false, 8, true>;
+    } else {
+        if (rows == 4) fn = vec ? stencil_kernel<true, 4, false> : stencil_kernel<false, 4, false>;
+        else if (rows == 16) fn = vec ? stencil_kernel<true, 16, false> : stencil_kernel<false, 16, false>;
+        else fn = vec ? stencil_kernel<true, 8, false> : stencil_kernel<false, 8, false>;
+    }
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
@@ -94,11 +131,23 @@ extern "C" hx_status hx_stencil2d(hx_ctx *ctx, float *u0, float *u1, int32_t nx,
     cfg.stream = (cudaStream_t)stream;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    for (int t = 0; t < iters; ++t) {
-        const float *src = (t & 1) ? u1 : u0;
-        float *dst = (t & 1) ? u0 : u1;
-        cudaError_t e = cudaLaunchKernelEx(&cfg, fn, src, dst, (int)nx, (int)ny, ws, d_resid + t);
-        if (e != cudaSuccess) return cuda_fail(e, "hx_stencil2d: launch");
+    const int per_run = use_part ? (int)(kStPartCap / p) : iters;
+    for (int t0 = 0; t0 < iters; t0 += per_run) {
+        const int t1 = t0 + per_run < iters ? t0 + per_run : iters;
+        for (int t = t0; t < t1; ++t) {
+            const float *src = (t & 1) ? u1 : u0;
+            float *dst = (t & 1) ? u0 : u1;
+            cudaError_t e = cudaLaunchKernelEx(&cfg, fn, src, dst, (int)nx, (int)ny, ws, d_resid + t,
+                                               part + (size_t)(t - t0) * p);
+            if (e != cudaSuccess) return cuda_fail(e, "hx_stencil2d: launch");
+        }
+        if (use_part) {
+            cudaLaunchConfig_t rc = cfg;
+            rc.gridDim = dim3((unsigned)(t1 - t0));
+            rc.blockDim = dim3(256);
+            cudaError_t e = cudaLaunchKernelEx(&rc, stencil_resid_kernel, (const float *)part, (int)p, d_resid + t0);
+            if (e != cudaSuccess) return cuda_fail(e, "hx_stencil2d: residual launch");
+        }
     }
     return HX_OK;
 }
