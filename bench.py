@@ -384,33 +384,37 @@ def bench_hx(args, rank, world, local):
             for c in comps:
                 issue(c, s)
     stream.synchronize()
-    graphs = []
+    # the timed step: one CUDA graph per buffer set holding the whole step
+    # (programmatic dependent launch chains across the components); the
+    # per-component breakdown comes from a second pass with one graph per
+    # component and events between them
+    step_graphs, comp_graphs = [], []
     for s in sets:
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            for c in comps:
+                issue(c, s)
+        step_graphs.append(g)
         gs = {}
         for c in comps:
-            g = torch.cuda.CUDAGraph()
-            with torch.cuda.graph(g, stream=stream):
+            gc = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(gc, stream=stream):
                 issue(c, s)
-            gs[c] = g
-        graphs.append(gs)
-    launches_per_step = 1 + ST_ITERS + 1 + batch.rounds
-
-    def run_step(i, ev=None):
-        gs = graphs[i % n_sets]
-        for j, c in enumerate(comps):
-            if ev is not None:
-                ev[j].record(stream)
-            gs[c].replay()
-        if ev is not None:
-            ev[len(comps)].record(stream)
+            gs[c] = gc
+        comp_graphs.append(gs)
+    # launches per step: map->reduce 1, or 2 when its tile partials are
+    # folded by a separate launch (at most 1024 tiles); 20 sweeps + their
+    # residual fold; the histogram; the batch's rounds
+    vecs = hx.hx_tune_get(ctx).map_vecs[MR_N.bit_length() - 1]
+    mr_tiles = -(-MR_N // (128 * vecs))
+    launches_per_step = (2 if mr_tiles <= 1024 else 1) + ST_ITERS + 1 + 1 + batch.rounds
 
     with torch.cuda.stream(stream):
         for i in range(args.warmup):
-            run_step(i)
+            step_graphs[i % n_sets].replay()
     stream.synchronize()
 
     K = args.steps
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(len(comps) + 1)] for _ in range(K)]
     t_start = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
     if dist:
@@ -420,18 +424,30 @@ def bench_hx(args, rank, world, local):
         wall0 = time.perf_counter()
         t_start.record(stream)
         for i in range(K):
-            run_step(i, evs[i])
+            step_graphs[i % n_sets].replay()
         t_end.record(stream)
         torch.cuda.synchronize()
         wall = time.perf_counter() - wall0
     if dist:
         dist.barrier()
     total_ms = t_start.elapsed_time(t_end)
+    total_ms = max_over_ranks(total_ms, dist, dev)
+
+    # per-component times (not part of the timed region)
+    K2 = min(K, 200)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(len(comps) + 1)] for _ in range(K2)]
+    with torch.cuda.stream(stream):
+        for i in range(K2):
+            gs = comp_graphs[i % n_sets]
+            for j, c in enumerate(comps):
+                evs[i][j].record(stream)
+                gs[c].replay()
+            evs[i][len(comps)].record(stream)
+    torch.cuda.synchronize()
     comp_ms = {c: 0.0 for c in comps}
     for e in evs:
         for j, c in enumerate(comps):
-            comp_ms[c] += e[j].elapsed_time(e[j + 1])
-    total_ms = max_over_ranks(total_ms, dist, dev)
+            comp_ms[c] += e[j].elapsed_time(e[j + 1]) * K / K2   # scaled to K steps
 
     peak, peak_kind = _peaks()
     ms_per_step = total_ms / K
