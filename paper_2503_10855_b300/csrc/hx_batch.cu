@@ -8,11 +8,13 @@
 // Map->reduce tiles and stencil blocks form WARP runs (a warp computes and
 // reduces a run of consecutive tiles of one instance on its own, with no
 // block barrier); histogram chunks are CTA items (the CTA's warps share one
-// set of shared-memory counters) and run first.  Per-instance arrival
-// tickets let the last run of an instance do its final combine, so no worker
-// ever waits for another.  A stencil instance with several sweeps
-// contributes one sweep per round; rounds are consecutive launches chained
-// with programmatic dependent launch.
+// set of shared-memory counters) and run first.  Work items only store their
+// partial results (map tile partials; atomic max / add into the instance's
+// accumulator for stencils and histograms): no fences, no arrival tickets.
+// A second launch, chained with programmatic dependent launch, runs the
+// final combine of every instance the launch completed, one warp each, so no
+// worker ever waits for another.  A stencil instance with several sweeps
+// contributes one sweep per round; rounds are consecutive launches.
 #include <algorithm>
 #include <cstring>
 #include <new>
@@ -23,13 +25,10 @@
 namespace hx {
 
 // One histogram chunk counted by the whole CTA into its shared counters
-// (dynamic shared memory, kHiSmemBytes), merged into the instance's bins;
-// the CTA that merges the instance's last chunk publishes bins and scan.
-__device__ __forceinline__ void batch_hist_item(const BInst &I, int64_t tile, unsigned int *sh,
-                                                unsigned int *wtot, int *flag) {
+// (dynamic shared memory, kHiSmemBytes) and added into the instance's bins.
+__device__ __forceinline__ void batch_hist_item(const BInst &I, int64_t tile, unsigned int *sh) {
     hist_zero(sh);
     __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned int slot = hist_slot_offset();
     const uint8_t *v = static_cast<const uint8_t *>(I.in0);
     const int64_t s = tile * kBHiTile;
@@ -42,51 +41,8 @@ __device__ __forceinline__ void batch_hist_item(const BInst &I, int64_t tile, un
     if (threadIdx.x < head) hist_count_byte(sh, slot, v[s + threadIdx.x]);
     if (threadIdx.x < tail) hist_count_byte(sh, slot, v[e - tail + threadIdx.x]);
     __syncthreads();
-    if (hist_merge(sh, I.acc)) __threadfence();
+    hist_merge(sh, I.acc);
     __syncthreads();
-    if (threadIdx.x == 0) *flag = atomicAdd(I.ticket, 1u) == (unsigned int)(I.tiles - 1);
-    __syncthreads();
-    if (*flag) {
-        __threadfence();
-        const unsigned int c = atomicExch(I.acc + threadIdx.x, 0u);   // 256 threads == 256 bins
-        static_cast<uint32_t *>(I.o0)[threadIdx.x] = c;
-        unsigned int incl = c;
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            const unsigned int t = __shfl_up_sync(0xffffffffu, incl, off);
-            if (lane >= off) incl += t;
-        }
-        if (lane == 31) wtot[warp] = incl;
-        __syncthreads();
-        unsigned int before = 0u;
-        for (int w = 0; w < warp; ++w) before += wtot[w];
-        if (I.o1) static_cast<uint32_t *>(I.o1)[threadIdx.x] = before + incl - c;
-        if (threadIdx.x == 0) *I.ticket = 0u;
-    }
-    __syncthreads();
-}
-
-// The arrival ticket of a warp run is resolved one run later (or after the
-// warp's last run), so the atomic's round trip overlaps useful work.  The
-// warp whose run completes an instance runs the instance's final combine.
-__device__ __forceinline__ void batch_resolve(const BInst *__restrict__ insts, unsigned int inst,
-                                              unsigned int prev, unsigned int cnt, int round, int lane) {
-    prev = __shfl_sync(0xffffffffu, prev, 0);
-    const BInst &I = insts[inst];
-    if ((int64_t)prev + cnt != I.tiles) return;
-    __threadfence();
-    if (I.kind == kKindMap) {
-        const ff sf = mr_final(I.partials, I.plan.tiles, lane);
-        if (lane == 0) {
-            const double s = ff_to_double(sf);
-            *static_cast<float *>(I.o1) = (float)s;
-            if (I.o2) *static_cast<double *>(I.o2) = s;
-            *I.ticket = 0u;
-        }
-    } else if (lane == 0) {
-        static_cast<float *>(I.o0)[I.sweep0 + round] = __uint_as_float(atomicExch(I.acc, 0u));
-        *I.ticket = 0u;
-    }
 }
 
 // Index i of the instance with prefix[i] <= j < prefix[i + 1] (instances
@@ -108,29 +64,25 @@ __device__ __forceinline__ unsigned int find_instance(const uint32_t *__restrict
 // counter sees a few thousand atomics per launch).  The work list is not
 // stored: item j belongs to the instance whose prefix range holds j (binary
 // search), and its tiles follow from the instance's slice and run length, so
-// the host only uploads one descriptor per instance.  A run publishes once:
-// one fence and one ticket increment by the run length.
+// the host only uploads one descriptor per instance.
 __global__ void __launch_bounds__(kBatchThreads, 2)
 batch_kernel(const BInst *__restrict__ insts, unsigned int n_inst, const uint32_t *__restrict__ cta_prefix,
              const uint32_t *__restrict__ run_prefix, int round, unsigned int *ctrl) {
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;");
     extern __shared__ __align__(16) unsigned int sh[];   // kHiSmemBytes when the round has CTA items
-    __shared__ unsigned int wtot[kBatchThreads / kWarp];
-    __shared__ int s_flag;
     const int lane = threadIdx.x & 31;
     const unsigned int n_cta = __ldg(cta_prefix + n_inst), n_runs = __ldg(run_prefix + n_inst);
 
     for (unsigned int it = blockIdx.x; it < n_cta; it += gridDim.x) {
         const unsigned int i = find_instance(cta_prefix, n_inst, it);
         const BInst &I = insts[i];
-        batch_hist_item(I, I.t_first + (it - __ldg(cta_prefix + i)), sh, wtot, &s_flag);
+        batch_hist_item(I, I.t_first + (it - __ldg(cta_prefix + i)), sh);
     }
 
     // Warp runs are taken dynamically: lane 0 fetches the next run index
     // from ctrl[0] while the current run is processed (runs differ in cost,
     // a static assignment leaves warps idle at the end).
-    unsigned int pend_inst = 0xffffffffu, pend_prev = 0u, pend_cnt = 0u;
     unsigned int it = 0u;
     if (lane == 0) it = atomicAdd(&ctrl[0], 1u);
     it = __shfl_sync(0xffffffffu, it, 0);
@@ -165,25 +117,62 @@ batch_kernel(const BInst *__restrict__ insts, unsigned int n_inst, const uint32_
             m = warp_max(m);
             if (lane == 0) atomicMax(I.acc, __float_as_uint(m));
         }
-        unsigned int prev = 0u;
-        if (lane == 0) {
-            __threadfence();
-            prev = atomicAdd(I.ticket, cnt);
-        }
-        if (pend_inst != 0xffffffffu) batch_resolve(insts, pend_inst, pend_prev, pend_cnt, round, lane);
-        pend_inst = i;
-        pend_prev = prev;
-        pend_cnt = cnt;
         it = __shfl_sync(0xffffffffu, next, 0);
     }
-    if (pend_inst != 0xffffffffu) batch_resolve(insts, pend_inst, pend_prev, pend_cnt, round, lane);
-    // The last CTA to finish resets the run counter for the next launch.
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        if (atomicAdd(&ctrl[1], 1u) == gridDim.x - 1) {
-            ctrl[0] = 0u;
-            ctrl[1] = 0u;
+}
+
+// The final combine of every instance this launch completed (it had work
+// items in the launch and its slice reached its last tile), one warp per
+// instance, after the batched kernel has finished (programmatic dependent
+// launch waits for the whole grid): the sum of a map->reduce instance from
+// its tile partials in the standalone call's fixed order, the residual of a
+// stencil sweep, the bins and scan of a histogram.  Accumulators are left at
+// zero for the next use; the run counter is reset for the next launch.
+__global__ void __launch_bounds__(kBatchThreads)
+batch_final_kernel(const BInst *__restrict__ insts, unsigned int n_inst, const uint32_t *__restrict__ cta_prefix,
+                   const uint32_t *__restrict__ run_prefix, int round, unsigned int *ctrl) {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;");
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctrl[0] = 0u;
+    const int lane = threadIdx.x & 31;
+    const unsigned int i = blockIdx.x * (kBatchThreads / kWarp) + (threadIdx.x >> 5);
+    if (i >= n_inst) return;
+    const unsigned int work = (__ldg(cta_prefix + i + 1) - __ldg(cta_prefix + i)) +
+                              (__ldg(run_prefix + i + 1) - __ldg(run_prefix + i));
+    const BInst &I = insts[i];
+    if (work == 0 || I.t_first + I.t_count != I.tiles) return;
+    if (I.kind == kKindMap) {
+        const ff sf = mr_final(I.partials, I.plan.tiles, lane);
+        if (lane == 0) {
+            const double s = ff_to_double(sf);
+            *static_cast<float *>(I.o1) = (float)s;
+            if (I.o2) *static_cast<double *>(I.o2) = s;
+        }
+    } else if (I.kind == kKindStencil) {
+        if (lane == 0) static_cast<float *>(I.o0)[I.sweep0 + round] = __uint_as_float(atomicExch(I.acc, 0u));
+    } else {
+        // lane l owns bins 8l .. 8l+7: local prefix, then a shuffle scan of
+        // the lane totals
+        unsigned int c[8], tot = 0u;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            c[k] = atomicExch(I.acc + 8 * lane + k, 0u);
+            static_cast<uint32_t *>(I.o0)[8 * lane + k] = c[k];
+            tot += c[k];
+        }
+        unsigned int incl = tot;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const unsigned int t = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += t;
+        }
+        if (I.o1) {
+            unsigned int run = incl - tot;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                static_cast<uint32_t *>(I.o1)[8 * lane + k] = run;
+                run += c[k];
+            }
         }
     }
 }
@@ -247,6 +236,10 @@ hx_status launch_batch_round(const hx_ctx *ctx, const BInst *d_insts, uint32_t n
     cfg.numAttrs = 1;
     cudaError_t e = cudaLaunchKernelEx(&cfg, batch_kernel, d_insts, n_inst, d_cta_prefix, d_run_prefix, round, d_ctrl);
     if (e != cudaSuccess) return cuda_fail(e, "batched kernel launch");
+    cfg.gridDim = dim3((n_inst + kBatchThreads / kWarp - 1) / (kBatchThreads / kWarp));
+    cfg.dynamicSmemBytes = 0;
+    e = cudaLaunchKernelEx(&cfg, batch_final_kernel, d_insts, n_inst, d_cta_prefix, d_run_prefix, round, d_ctrl);
+    if (e != cudaSuccess) return cuda_fail(e, "batched final launch");
     return HX_OK;
 }
 
@@ -376,12 +369,11 @@ extern "C" hx_status hx_batch_plan(hx_ctx *ctx, const hx_task *tasks, int32_t n_
         round_runs[r] = (uint32_t)w;
     }
 
-    // One device allocation: insts | prefixes | partials | tickets | accumulators.
+    // One device allocation: insts | prefixes | partials | accumulators | run counter.
     auto align = [](size_t v) { return (v + 255) & ~(size_t)255; };
     const size_t off_pre = align(sizeof(BInst) * insts.size());
     const size_t off_part = off_pre + align(sizeof(uint32_t) * prefix.size());
-    const size_t off_tick = off_part + align(sizeof(float2) * n_partials);
-    const size_t off_acc = off_tick + align(sizeof(unsigned int) * insts.size());
+    const size_t off_acc = off_part + align(sizeof(float2) * n_partials);
     const size_t off_ctrl = off_acc + align(sizeof(unsigned int) * n_acc);
     const size_t total = off_ctrl + 256;
     DeviceGuard g(ctx->device);
@@ -404,7 +396,6 @@ extern "C" hx_status hx_batch_plan(hx_ctx *ctx, const hx_task *tasks, int32_t n_
     int64_t pcur = 0, acur = 0;
     for (int i = 0; i < n_tasks; ++i) {
         BInst &I = insts[i];
-        I.ticket = reinterpret_cast<unsigned int *>(base + off_tick) + i;
         if (I.kind == kKindMap) {
             I.partials = reinterpret_cast<float2 *>(base + off_part) + pcur;
             pcur += I.tiles;

@@ -38,7 +38,6 @@ struct BInst {
     void *o1;           // map sum | hist scan
     void *o2;           // map sum64
     float2 *partials;   // map tile partials (hi, lo)
-    unsigned int *ticket;
     unsigned int *acc;  // stencil: max bits (1); hist: 256 bins
 };
 
@@ -56,10 +55,11 @@ inline uint32_t inst_runs(const BInst &I) {
 }
 inline uint32_t inst_ctas(const BInst &I) { return I.kind == kKindHist ? (uint32_t)I.t_count : 0u; }
 
-// Launches the batched kernel for one round: n_inst instances, exclusive
-// prefix sums of their CTA chunks and warp runs (n_inst + 1 entries each, on
-// the device), totals n_cta and n_runs; d_ctrl: two zeroed words the kernel
-// uses as its run counter and leaves zeroed (launches sharing d_ctrl must be
+// Launches the batched kernel for one round (n_inst instances, exclusive
+// prefix sums of their CTA chunks and warp runs, n_inst + 1 entries each on
+// the device, totals n_cta and n_runs) and after it the final-combine kernel
+// for the instances the round completes.  d_ctrl: a zeroed word the kernels
+// use as the run counter and leave zeroed (launches sharing d_ctrl must be
 // ordered, e.g. on one stream).
 hx_status launch_batch_round(const hx_ctx *ctx, const BInst *d_insts, uint32_t n_inst, const uint32_t *d_cta_prefix,
                              const uint32_t *d_run_prefix, uint32_t n_cta, uint32_t n_runs, int round,

@@ -31,10 +31,10 @@ double now_s() {
 
 // Per-request device workspace, kept from admission to completion so that a
 // request's work can be split over several steps: tile partials, histogram
-// or residual accumulator, arrival ticket.
+// or residual accumulator.
 constexpr size_t kWsPartials = kMrMaxTiles;
 constexpr size_t kWsAccWords = kHiBins;
-constexpr size_t kWsBytes = ((kWsPartials * sizeof(float2) + (kWsAccWords + 1) * 4) + 255) & ~(size_t)255;
+constexpr size_t kWsBytes = ((kWsPartials * sizeof(float2) + kWsAccWords * 4) + 255) & ~(size_t)255;
 
 struct Req {
     uint64_t id = 0;
@@ -108,7 +108,6 @@ void admit_locked(hx_server *s) {
             char *w = s->ws_pool + (size_t)r->ws * kWsBytes;
             r->inst.partials = reinterpret_cast<float2 *>(w);
             r->inst.acc = reinterpret_cast<unsigned int *>(w + kWsPartials * sizeof(float2));
-            r->inst.ticket = r->inst.acc + kWsAccWords;
         }
         r->admitted = true;
         s->used += r->footprint;
