@@ -767,13 +767,21 @@ def bench_sweeps(hx, ctx, dev, peak):
     import workloads
 
     def per_call_ms(fn, n_sets, reps):
-        for k in range(2):
-            fn(k % n_sets)
+        # the calls go into one CUDA graph (device time, not host launch
+        # overhead), replayed after a warm-up
+        for k in range(n_sets):
+            fn(k)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        s = torch.cuda.Stream()
+        with torch.cuda.graph(g, stream=s):
+            for k in range(reps):
+                fn(k % n_sets)
+        g.replay()
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
-        for k in range(reps):
-            fn(k % n_sets)
+        g.replay()
         b.record()
         torch.cuda.synchronize()
         return a.elapsed_time(b) / reps
