@@ -386,8 +386,10 @@ hx_status hx_autotune(hx_ctx *ctx, int32_t max_log2, hx_stream_t stream);
  * (instance, tile) items that resident CTAs pull from an atomic counter.
  * Every item runs the same tile code as the standalone calls above and the
  * tile plan of an instance depends only on its own sizes, so each result is
- * bit-identical to the standalone call's.  The last tile of an instance to
- * finish runs its final combine (no CTA ever waits for another).
+ * bit-identical to the standalone call's.  Work items only store partial
+ * results; a second launch chained after the batched one runs the final
+ * combine of every instance the launch completed (no CTA ever waits for
+ * another).
  *
  * A stencil task with iters > 1 is executed as rounds: round r runs sweep r
  * of every stencil instance that has one (plus, in round 0, all map->reduce

@@ -2,16 +2,18 @@
 // residual reduce.
 //
 // One sweep is a 2-D fork over the grid (Sec. 3.3) tiled into warp blocks of
-// R rows x 128 columns (R tuned per size class), stacked kStWarps to a CTA; a warp loads its rows and halo columns up front
-// into registers and takes horizontal neighbours from the adjacent lanes, so
-// each input point is read from memory about once per sweep.  The max of
-// |u' - u| is the fused reduction (loop fusion, Sec. 5.1; max reduction tree,
-// Sec. 5.2): warp shuffle max, a shared-memory max over the CTA's warps, one
-// atomic max per CTA into the workspace (max is exact and order
-// independent), and the last CTA to arrive publishes it.  Sweeps form a
-// sequential loop (Sec. 4.4 rule 1): one launch each, chained with
-// programmatic dependent launch so that a sweep's CTAs are already resident
-// when the previous sweep drains.
+// R rows x 128 columns (R tuned per size class), stacked kStWarps to a CTA;
+// a warp loads its rows and halo columns up front into registers and takes
+// horizontal neighbours from the adjacent lanes, so each input point is read
+// from memory about once per sweep.  The max of |u' - u| is the fused
+// reduction (loop fusion, Sec. 5.1; max reduction tree, Sec. 5.2): warp
+// shuffle max, a shared-memory max over the CTA's warps, then one partial per
+// CTA, folded for a run of sweeps by a small residual kernel (max is exact
+// and order independent); grids with more CTAs than the workspace holds use
+// one atomic max per CTA and let the last CTA to arrive publish it instead.
+// Sweeps form a sequential loop (Sec. 4.4 rule 1): one launch each, chained
+// with programmatic dependent launch so that a sweep's CTAs are already
+// resident when the previous sweep drains.
 #include "hx_internal.cuh"
 
 namespace hx {
