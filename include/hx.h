@@ -457,7 +457,7 @@ hx_status hx_batch_query(hx_ctx *ctx, uint64_t ticket);
  *       forms a step out of every admitted request's next slice of work (up
  *       to step_quantum_bytes of tiles of a map->reduce or histogram, or of
  *       the current sweep of a stencil) and runs the step as one launch of
- *       the batched kernel; up to
+ *       the batched kernel (plus its final-combine launch); up to
  *       max_steps_in_flight steps are queued on the device, so requests that
  *       arrive while a step runs join the next one and their work overlaps
  *       with the requests already running.  Each request computes exactly
