@@ -75,6 +75,16 @@ hx_status hx_create(hx_ctx **out, int device, size_t hbm_budget_bytes);
  * stream work issued through it is still running.  NULL is accepted. */
 void hx_destroy(hx_ctx *ctx);
 
+/* Test hook for failure handling without a GPU fault: of the calls on this
+ * context that would launch device work (hx_map_reduce, hx_stencil2d,
+ * hx_histogram, each round of a batch launch or served step,
+ * hx_fork_reduce, hx_srad), the next `after` run normally and the `count`
+ * after those fail with HX_ERR_CUDA ("injected launch failure") before
+ * launching anything.  The context stays usable; a server fails every
+ * request that had work in the failed step and recycles its workspace.
+ * count == 0 clears the hook; negative arguments are HX_ERR_INVALID. */
+hx_status hx_debug_inject_launch_failures(hx_ctx *ctx, int32_t after, int32_t count);
+
 /* ------------------------------------------------------------------ map->reduce
  * One fork of factor n (Sec. 3.3): thread i computes
  *     out[i] = fmaf(a, x[i], y[i])            (one rounding, fp32)
@@ -517,7 +527,9 @@ hx_status hx_server_submit(hx_server *s, const hx_task *task, uint64_t *req_id);
 hx_status hx_server_poll(hx_server *s, uint64_t req_id, double *latency_s);
 
 /* Block until every submitted request has completed, at most timeout_s
- * seconds (HX_ERR_TIMEOUT otherwise). */
+ * seconds (HX_ERR_TIMEOUT otherwise).  HX_ERR_CUDA when a request completed
+ * with a failed launch since the previous drain returned (hx_server_poll
+ * tells which); HX_OK otherwise. */
 hx_status hx_server_drain(hx_server *s, double timeout_s);
 
 hx_status hx_server_get_stats(hx_server *s, hx_server_stats *out);

@@ -94,6 +94,16 @@ class Context:
         self.close()
 
 
+_lib.hx_debug_inject_launch_failures.argtypes = [_P, _I32, _I32]
+_lib.hx_debug_inject_launch_failures.restype = ctypes.c_int
+
+
+def hx_debug_inject_launch_failures(ctx: "Context", count: int, after: int = 0) -> None:
+    """Test hook: after ``after`` more launching calls on ``ctx``, ``count`` calls fail with HX_ERR_CUDA."""
+    _check(_lib.hx_debug_inject_launch_failures(ctx.handle, int(after), int(count)),
+           "hx_debug_inject_launch_failures")
+
+
 def hx_create(device: int = 0, hbm_budget_bytes: int = 0) -> Context:
     return Context(device, hbm_budget_bytes)
 

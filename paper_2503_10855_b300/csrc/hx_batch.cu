@@ -222,6 +222,7 @@ hx_status launch_batch_round(const hx_ctx *ctx, const BInst *d_insts, uint32_t n
                              const uint32_t *d_run_prefix, uint32_t n_cta, uint32_t n_runs, int round,
                              unsigned int *d_ctrl, cudaStream_t stream) {
     if (n_cta == 0 && n_runs == 0) return HX_OK;
+    if (take_injected_failure(ctx)) return fail(HX_ERR_CUDA, "batched launch: injected launch failure (test hook)");
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;

@@ -105,6 +105,15 @@ hx_status hx_create(hx_ctx **out, int device, size_t hbm_budget_bytes) {
     return HX_OK;
 }
 
+hx_status hx_debug_inject_launch_failures(hx_ctx *ctx, int32_t after, int32_t count) {
+    if (!ctx) return hx::fail(HX_ERR_INVALID, "hx_debug_inject_launch_failures: ctx is NULL");
+    if (after < 0 || count < 0) return hx::fail(HX_ERR_INVALID, "hx_debug_inject_launch_failures: negative count");
+    std::lock_guard<std::mutex> lk(ctx->inject_mu);
+    ctx->inject_after = after;
+    ctx->inject_count = count;
+    return HX_OK;
+}
+
 void hx_destroy(hx_ctx *ctx) {
     if (!ctx) return;
     hx::DeviceGuard g(ctx->device);

@@ -87,6 +87,7 @@ extern "C" hx_status hx_histogram(hx_ctx *ctx, const uint8_t *v, int64_t n, uint
     WsSlot *ws = nullptr;
     hx_status st = slot_for(ctx, stream, &ws);
     if (st != HX_OK) return st;
+    if (take_injected_failure(ctx)) return fail(HX_ERR_CUDA, "hx_histogram: injected launch failure (test hook)");
     int head = (int)((16 - ((uintptr_t)v & 15u)) & 15u);
     if (head > n) head = (int)n;
     const int64_t nvec = (n - head) / 16;

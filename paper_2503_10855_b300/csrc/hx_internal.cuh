@@ -10,6 +10,7 @@
 
 #include <cstdio>
 #include <map>
+#include <mutex>
 #include <string>
 #include <utility>
 
@@ -498,6 +499,11 @@ struct hx_ctx {
     hx_tune_table tune = {};             // per-size-class choices (see hx.h)
     int hist_ctas_per_sm[3] = {1, 1, 1}; // resident CTAs per SM for widths 256, 512, 1024
     int batch_ctas_per_sm[2] = {1, 1};   // batched kernel without / with histogram counters
+    // test hook: after `inject_after` more launching calls, `inject_count`
+    // calls fail before launching
+    mutable std::mutex inject_mu;
+    mutable int inject_after = 0;
+    mutable int inject_count = 0;
     // hx_batch_submit bookkeeping: ticket -> (plan, completion event)
     uint64_t next_ticket = 1;
     std::map<uint64_t, std::pair<hx_batch *, cudaEvent_t>> pending;
@@ -515,6 +521,20 @@ inline int size_class(int64_t n) {
     return c;
 }
 hx_status batch_setup(hx_ctx *ctx);
+
+// Consumes one injected launch failure (hx_debug_inject_launch_failures):
+// true when the calling entry point must fail with HX_ERR_CUDA before it
+// launches anything.
+inline bool take_injected_failure(const hx_ctx *ctx) {
+    std::lock_guard<std::mutex> lk(ctx->inject_mu);
+    if (ctx->inject_count <= 0) return false;
+    if (ctx->inject_after > 0) {
+        --ctx->inject_after;
+        return false;
+    }
+    --ctx->inject_count;
+    return true;
+}
 
 struct DeviceGuard {
     int prev = -1;

@@ -78,6 +78,7 @@ extern "C" hx_status hx_map_reduce(hx_ctx *ctx, const float *x, const float *y, 
     WsSlot *ws = nullptr;
     hx_status st = slot_for(ctx, stream, &ws);
     if (st != HX_OK) return st;
+    if (take_injected_failure(ctx)) return fail(HX_ERR_CUDA, "hx_map_reduce: injected launch failure (test hook)");
     if (n == 0) {
         map_reduce_empty_kernel<<<1, 1, 0, (cudaStream_t)stream>>>(d_sum, d_sum64);
     } else {

@@ -884,6 +884,8 @@ hx_status hx_fork_reduce(hx_ctx *ctx, const hx_nest *nest, hx_stream_t stream) {
     if (st != HX_OK) return st;
     st = load(c);
     if (st != HX_OK) return st;
+    if (hx::take_injected_failure(ctx))
+        return hx::fail(HX_ERR_CUDA, "hx_fork_reduce: injected launch failure (test hook)");
     hx::NestWs *ws = ctx->nest_ws + (slot - ctx->ws);
 
     NestArgs a{};

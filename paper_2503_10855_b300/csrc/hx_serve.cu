@@ -81,6 +81,7 @@ struct hx_server {
     std::vector<hx::Slot> slots;
     std::vector<cudaEvent_t> free_events;     // per-launch mode
     char *ws_pool = nullptr;                  // continuous mode: max_inflight workspace slots (+ run counter)
+    uint64_t failed_at_drain = 0;             // stats.failed when the last drain returned
     unsigned int *ctrl = nullptr;
     std::vector<int> free_ws;
     uint64_t next_id = 1;
@@ -135,12 +136,20 @@ cudaError_t write_trivial(cudaStream_t st, const hx_task &t) {
 
 void fail_requests_locked(hx_server *s, std::vector<Req *> &rs, hx_status st) {
     for (Req *r : rs) {
+        if (r->done) continue;
         r->status = st;
         r->issued_all = true;
         r->done = true;
         s->used -= r->footprint;
         s->inflight -= 1;
-        if (r->ws >= 0) s->free_ws.push_back(r->ws);
+        if (r->ws >= 0) {
+            // the request's final combine may never run: clear its
+            // accumulators (ordered after its steps already on the stream)
+            // before the slot serves another request
+            char *w = s->ws_pool + (size_t)r->ws * kWsBytes;
+            cudaMemsetAsync(w + kWsPartials * sizeof(float2), 0, kWsAccWords * 4, s->stream);
+            s->free_ws.push_back(r->ws);
+        }
         r->ws = -1;
         s->stats.failed += 1;
         s->stats.completed += 1;
@@ -174,6 +183,7 @@ bool issue_step_locked(hx_server *s) {
     uint32_t n = 0;
     uint64_t c = 0, w = 0;
     Step step;
+    std::vector<Req *> in_step;   // every request with work (or an output) in this step
     // Slice size: the step aims at step_target_bytes of traffic shared by the
     // requests in it, but each gets at least step_quantum_bytes.
     size_t n_work = 0;
@@ -186,6 +196,7 @@ bool issue_step_locked(hx_server *s) {
             if (write_trivial(s->stream, r->task) != cudaSuccess) r->status = HX_ERR_CUDA;
             r->issued_all = true;
             step.finishing.push_back(r);
+            in_step.push_back(r);
             continue;
         }
         if ((int)n >= s->cfg.max_step_requests) continue;
@@ -200,6 +211,7 @@ bool issue_step_locked(hx_server *s) {
         c += inst_ctas(I);
         w += inst_runs(I);
         insts[n++] = I;
+        in_step.push_back(r);
         r->issued += I.t_count;
         if (r->issued == I.tiles) {
             r->issued = 0;
@@ -215,7 +227,6 @@ bool issue_step_locked(hx_server *s) {
     const size_t off_run = off_cta + (((size_t)(n + 1) * 4 + 15) & ~(size_t)15);
     memcpy(sl.h + off_cta, cpv.data(), (n + 1) * 4);
     memcpy(sl.h + off_run, rpv.data(), (n + 1) * 4);
-    std::vector<Req *> issued_now = step.finishing;
     s->active.erase(std::remove_if(s->active.begin(), s->active.end(), [](Req *r) { return r->issued_all; }),
                     s->active.end());
     hx_status st = HX_OK;
@@ -231,7 +242,11 @@ bool issue_step_locked(hx_server *s) {
     }
     if (st == HX_OK && cudaEventRecord(sl.ev, s->stream) != cudaSuccess) st = HX_ERR_CUDA;
     if (st != HX_OK) {
-        fail_requests_locked(s, issued_now, st);
+        // every request with work in the failed step fails, finished or not:
+        // a sliced request missing this slice would compute a wrong result
+        fail_requests_locked(s, in_step, st);
+        s->active.erase(std::remove_if(s->active.begin(), s->active.end(), [](Req *r) { return r->done; }),
+                        s->active.end());
         return true;
     }
     sl.busy = true;
@@ -462,7 +477,9 @@ hx_status hx_server_drain(hx_server *s, double timeout_s) {
             s->stats.completed < s->stats.submitted)
             return hx::fail(HX_ERR_TIMEOUT, "hx_server_drain: requests still pending at the timeout");
     }
-    return s->stats.failed ? hx::fail(HX_ERR_CUDA, "hx_server_drain: some launches failed") : HX_OK;
+    const bool new_failures = s->stats.failed > s->failed_at_drain;
+    s->failed_at_drain = s->stats.failed;
+    return new_failures ? hx::fail(HX_ERR_CUDA, "hx_server_drain: some requests' launches failed") : HX_OK;
 }
 
 hx_status hx_server_get_stats(hx_server *s, hx_server_stats *out) {

@@ -282,6 +282,7 @@ extern "C" hx_status hx_srad(hx_ctx *ctx, float *J0, float *J1, float *C, int32_
     WsSlot *slot = nullptr;
     hx_status st = slot_for(ctx, stream, &slot);
     if (st != HX_OK) return st;
+    if (take_injected_failure(ctx)) return fail(HX_ERR_CUDA, "hx_srad: injected launch failure (test hook)");
     NestWs *ws = ctx->nest_ws + (slot - ctx->ws);
 
     cudaLaunchAttribute attr[1];

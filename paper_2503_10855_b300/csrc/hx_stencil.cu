@@ -101,6 +101,7 @@ extern "C" hx_status hx_stencil2d(hx_ctx *ctx, float *u0, float *u1, int32_t nx,
     WsSlot *ws = nullptr;
     hx_status st = slot_for(ctx, stream, &ws);
     if (st != HX_OK) return st;
+    if (take_injected_failure(ctx)) return fail(HX_ERR_CUDA, "hx_stencil2d: injected launch failure (test hook)");
 
     const bool vec = (nx % 4 == 0) && ((((uintptr_t)u0 | (uintptr_t)u1) & 15u) == 0);
     const int width = 128;   // both paths: 32 lanes x 4 columns
