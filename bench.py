@@ -792,25 +792,32 @@ def bench_sweeps(hx, ctx, dev, peak):
 
     import workloads
 
+    # one stream for every capture (the context keeps a workspace slot per
+    # distinct stream)
+    sweep_stream = torch.cuda.Stream(device=dev)
+
     def per_call_ms(fn, n_sets, reps):
         # the calls go into one CUDA graph (device time, not host launch
-        # overhead), replayed after a warm-up
+        # overhead); after three warm-up replays, five timed replays with
+        # events on the replay stream; the median replay
         for k in range(n_sets):
             fn(k)
         torch.cuda.synchronize()
         g = torch.cuda.CUDAGraph()
-        s = torch.cuda.Stream()
+        s = sweep_stream
         with torch.cuda.graph(g, stream=s):
             for k in range(reps):
                 fn(k % n_sets)
-        g.replay()
+        with torch.cuda.stream(s):
+            for _ in range(3):
+                g.replay()
+            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(5)]
+            for a, b in evs:
+                a.record(s)
+                g.replay()
+                b.record(s)
         torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record()
-        g.replay()
-        b.record()
-        torch.cuda.synchronize()
-        return a.elapsed_time(b) / reps
+        return statistics.median(a.elapsed_time(b) for a, b in evs) / reps
 
     out = {"map_reduce": [], "jacobi_x20": [], "histogram": []}
     s32 = torch.empty(1, device=dev)

@@ -100,7 +100,7 @@ batch_kernel(const BInst *__restrict__ insts, unsigned int n_inst, const uint32_
             for (int64_t k = 0; k < cnt; ++k) {
                 const int64_t tile = first + k;
                 const ff part = mr_tile(x, y, out, I.a, I.plan, tile, I.vec != 0, lane);
-                if (lane == 0) I.partials[tile] = make_float2(part.hi, part.lo);
+                if (lane == 0) st_keep2(I.partials + tile, make_float2(part.hi, part.lo));
             }
         } else {
             const int sweep = I.sweep0 + round;

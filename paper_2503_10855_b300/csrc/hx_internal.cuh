@@ -114,6 +114,15 @@ __device__ __forceinline__ void st_stream4(float4 *p, float4 v) {
     asm volatile("st.global.cs.v4.f32 [%0], {%1,%2,%3,%4};"
                  :: "l"(p), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w) : "memory");
 }
+// Store of a tile partial, which the final combine reads back after the
+// streams of the same launch have passed through L2: written with L2
+// evict-last priority so those streams do not push it out to DRAM.
+__device__ __forceinline__ void st_keep2(float2 *p, float2 v) {
+    uint64_t pol;
+    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    asm volatile("st.global.L2::cache_hint.v2.f32 [%0], {%1,%2}, %3;"
+                 :: "l"(p), "f"(v.x), "f"(v.y), "l"(pol) : "memory");
+}
 
 // ---------------------------------------------------------------- trees
 // Sums are carried as unevaluated pairs hi + lo of fp32 numbers (the
@@ -245,12 +254,22 @@ __device__ __forceinline__ ff mr_tile(const float *__restrict__ x, const float *
 
 // Final combine of `tiles` tile partials in a fixed order, by one warp: lane
 // l folds partials l, l+32, l+64, ... then the butterfly.  Same value in
-// every lane.
+// every lane.  The loads of kMrFinalDepth partials are issued before they
+// are folded (a lane folds up to 128 partials: one L2 round trip per group
+// of 32 instead of one per partial); the fold order is unchanged.
+constexpr int kMrFinalDepth = 32;
 __device__ __forceinline__ ff mr_final(const float2 *partials, int64_t tiles, int lane) {
     ff acc = {0.0f, 0.0f};
-    for (int64_t i = lane; i < tiles; i += kWarp) {
-        const float2 q = __ldcg(partials + i);
-        acc = ff_add(acc, ff{q.x, q.y});
+    for (int64_t i0 = lane; i0 < tiles; i0 += (int64_t)kWarp * kMrFinalDepth) {
+        float2 q[kMrFinalDepth];
+#pragma unroll
+        for (int k = 0; k < kMrFinalDepth; ++k) {
+            const int64_t i = i0 + (int64_t)k * kWarp;
+            q[k] = i < tiles ? __ldcg(partials + i) : make_float2(0.0f, 0.0f);
+        }
+#pragma unroll
+        for (int k = 0; k < kMrFinalDepth; ++k)
+            if (i0 + (int64_t)k * kWarp < tiles) acc = ff_add(acc, ff{q[k].x, q[k].y});
     }
     return warp_sum(acc);
 }
@@ -265,7 +284,7 @@ __device__ __forceinline__ void mr_warp_item(const float *__restrict__ x, const 
     const ff part = mr_tile(x, y, out, a, p, tile, aligned, lane);
     unsigned int prev = 0u;
     if (lane == 0) {
-        partials[tile] = make_float2(part.hi, part.lo);
+        st_keep2(partials + tile, make_float2(part.hi, part.lo));
         __threadfence();
         prev = atomicAdd(ticket, 1u);
     }

@@ -30,7 +30,7 @@ map_reduce_kernel(const float *__restrict__ x, const float *__restrict__ y, floa
     if (tile >= p.tiles) return;
     if (DEFER) {
         const ff part = mr_tile(x, y, out, a, p, tile, aligned, threadIdx.x & 31);
-        if ((threadIdx.x & 31) == 0) ws->mr_partial[tile] = make_float2(part.hi, part.lo);
+        if ((threadIdx.x & 31) == 0) st_keep2(ws->mr_partial + tile, make_float2(part.hi, part.lo));
     } else {
         mr_warp_item(x, y, out, a, p, tile, aligned, ws->mr_partial, &ws->mr_ticket, d_sum, d_sum64);
     }
