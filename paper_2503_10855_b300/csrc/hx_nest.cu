@@ -147,6 +147,29 @@ __device__ __forceinline__ void acc_fold(Acc &a, float v, i64 r) {
 #endif
 }
 
+// Fold for the few values of one load group (warp tree).  For sums this is a
+// step of Ogita, Rump and Oishi's cascaded summation (Sum2, 2005): hi takes
+// the plain fp32 sum and lo collects the exact TwoSum errors, without the
+// renormalisation of every step; acc_settle renormalises the pair once per
+// group, so lo never gathers more than 4 U errors.  Other monoids fold as
+// acc_fold does.
+__device__ __forceinline__ void acc_fold_run(Acc &a, float v, i64 r) {
+#if MONOID == 0
+    float s = a.hi + v, bb = s - a.hi;
+    a.lo += (a.hi - (s - bb)) + (v - bb);
+    a.hi = s;
+#else
+    acc_fold(a, v, r);
+#endif
+}
+__device__ __forceinline__ void acc_settle(Acc &a) {
+#if MONOID == 0
+    float s = a.hi + a.lo, bb = s - a.hi;
+    a.lo = (a.hi - (s - bb)) + (a.lo - bb);     // exact: hi + lo unchanged
+    a.hi = s;
+#endif
+}
+
 #if MONOID >= 0
 // Combine two partial results.  Commutative bit for bit (the exact TwoSum /
 // TwoProd error terms do not depend on operand order; extrema break ties by
@@ -203,6 +226,16 @@ __device__ __forceinline__ Acc acc_butterfly(unsigned mask, Acc a) {
 
 union PartBits { float4 f4; struct { float a, b; i64 i; } s; };
 
+// Partials are read back by the last arrival of their group, possibly after
+// much of the launch's input has streamed through L2: stored with L2
+// evict-last priority.
+__device__ __forceinline__ void st_keep4(float4 *dst, float4 v) {
+    unsigned long long pol;
+    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1,%2,%3,%4}, %5;"
+                 :: "l"(dst), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "l"(pol) : "memory");
+}
+
 __device__ __forceinline__ void part_store(float4 *dst, Acc a) {
     PartBits u;
     u.f4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
@@ -213,7 +246,7 @@ __device__ __forceinline__ void part_store(float4 *dst, Acc a) {
 #else
     u.s.a = a.v; u.s.i = a.i;
 #endif
-    *dst = u.f4;
+    st_keep4(dst, u.f4);
 }
 
 __device__ __forceinline__ Acc part_load(const float4 *src) {
@@ -274,10 +307,101 @@ __device__ __forceinline__ void proc_group(const NestParams &p, const Seg &g, co
 #if MONOID >= 0
 #pragma unroll
             for (int q = 0; q < 4; ++q)
-                if (VEC || r0 + q < g.r_end) acc_fold(acc, vq[q], r0 + q);
+                if (VEC || r0 + q < g.r_end) acc_fold_run(acc, vq[q], r0 + q);
 #endif
         }
     }
+#if MONOID >= 0
+    acc_settle(acc);
+#endif
+}
+
+#if MONOID >= 0
+// Last step of a segment in a group narrower than a warp: the group's lanes
+// combine their partials, and the group's first lane writes the result.
+__device__ __forceinline__ void group_result(const NestParams &p, i64 s, Acc acc, unsigned gmask, int gl) {
+    acc = acc_butterfly<G>(gmask, acc);
+    if (gl == 0) write_result(p, s, acc);
+}
+#endif
+
+#if MONOID >= 0 && G == 32
+// Reduction tree of one item once its lanes have folded their slots: the
+// butterfly, then for a segment of several chunks the last-arrival levels.
+__device__ __forceinline__ void item_tree(const NestParams &p, const Seg &g, i64 item, Acc acc, int lane) {
+    acc = acc_butterfly<32>(0xffffffffu, acc);
+    if (p.nchunks == 1) {
+        if (lane == 0) write_result(p, g.s, acc);
+        return;
+    }
+    // Level 1: the last chunk of its group of 32 folds the group's partials.
+    const i64 c = item - g.s * p.nchunks;
+    const i64 grp = c >> 5;
+    const int gsize = (int)min((i64)32, p.nchunks - grp * 32);
+    unsigned *t1 = p.tick + g.s * p.ngroups + grp;
+    unsigned last = 0;
+    if (lane == 0) {
+        part_store(p.part + item, acc);
+        __threadfence();
+        last = atomicAdd(t1, 1u) == (unsigned)(gsize - 1) ? 1u : 0u;
+    }
+    if (!__shfl_sync(0xffffffffu, last, 0)) return;
+    __threadfence();
+    Acc t = lane < gsize ? part_load(p.part + g.s * p.nchunks + grp * 32 + lane) : acc_init();
+    t = acc_butterfly<32>(0xffffffffu, t);
+    if (p.ngroups == 1) {
+        if (lane == 0) {
+            write_result(p, g.s, t);
+            *t1 = 0u;
+        }
+        return;
+    }
+    // Level 2: the last group of the segment folds the group partials.
+    last = 0;
+    if (lane == 0) {
+        *t1 = 0u;
+        part_store(p.part2 + g.s * p.ngroups + grp, t);
+        __threadfence();
+        last = atomicAdd(p.tick2 + g.s, 1u) == (unsigned)(p.ngroups - 1) ? 1u : 0u;
+    }
+    if (!__shfl_sync(0xffffffffu, last, 0)) return;
+    __threadfence();
+    // lane l folds group partials l, l + 32, ... in order; the loads of 4 of
+    // them are issued before they are folded
+    Acc u = acc_init();
+    const float4 *gp = p.part2 + g.s * p.ngroups;
+    for (i64 q0 = lane; q0 < p.ngroups; q0 += 32 * 4) {
+        Acc v[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) v[k] = q0 + 32 * k < p.ngroups ? part_load(gp + q0 + 32 * k) : acc_init();
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (q0 + 32 * k < p.ngroups) u = acc_combine(u, v[k]);
+    }
+    u = acc_butterfly<32>(0xffffffffu, u);
+    if (lane == 0) {
+        write_result(p, g.s, u);
+        p.tick2[g.s] = 0u;
+    }
+}
+#endif
+
+// Item `item` (chunk item % nchunks of segment item / nchunks).
+__device__ __forceinline__ void seg_item(const NestParams &p, Seg &g, i64 item) {
+    g.s = p.nchunks == 1 ? item : item / p.nchunks;
+    g.r_begin = (item - g.s * p.nchunks) * p.chunk;
+    g.r_end = min(p.inner, g.r_begin + p.chunk);
+    g.nslot = (g.r_end - g.r_begin + 3) >> 2;
+    seg_setup(p, g);
+}
+
+// Segment s as one item (the whole inner extent).
+__device__ __forceinline__ void seg_whole(const NestParams &p, Seg &g, i64 s) {
+    g.s = s;
+    g.r_begin = 0;
+    g.r_end = p.inner;
+    g.nslot = (p.inner + 3) >> 2;
+    seg_setup(p, g);
 }
 
 extern "C" __global__ void __launch_bounds__(256) hx_nest_kernel(const NestParams p) {
@@ -285,15 +409,53 @@ extern "C" __global__ void __launch_bounds__(256) hx_nest_kernel(const NestParam
     const int gl = lane & (G - 1);
     const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
     const i64 per_cta = 256 / G;
+#if G < 32
+    // Groups narrower than a warp take whole segments, and G lanes x U slots
+    // cover a segment's inner extent, so one load group holds a segment: the
+    // loads of the group's next segment are issued before the current one is
+    // folded (two segments in flight per lane).
+    const i64 stride = (i64)gridDim.x * per_cta;
+    i64 item = (i64)blockIdx.x * per_cta + threadIdx.x / G;
+    Seg ga, gb;
+    Buf ba, bb;
+    if (item < p.n_items) {
+        seg_whole(p, ga, item);
+        load_group(p, ga, ba, gl);
+    }
+    while (item < p.n_items) {
+        const i64 i1 = item + stride;
+        if (i1 < p.n_items) {
+            seg_whole(p, gb, i1);
+            load_group(p, gb, bb, gl);
+        }
+        {
+            Acc acc = acc_init();
+            proc_group(p, ga, ba, gl, acc);
+#if MONOID >= 0
+            group_result(p, ga.s, acc, gmask, gl);
+#endif
+        }
+        if (i1 >= p.n_items) break;
+        const i64 i2 = i1 + stride;
+        if (i2 < p.n_items) {
+            seg_whole(p, ga, i2);
+            load_group(p, ga, ba, gl);
+        }
+        {
+            Acc acc = acc_init();
+            proc_group(p, gb, bb, gl, acc);
+#if MONOID >= 0
+            group_result(p, gb.s, acc, gmask, gl);
+#endif
+        }
+        item = i2;
+    }
+#else
+    // G == 32: the whole warp shares an item (a chunk of a segment).
     for (i64 item = (i64)blockIdx.x * per_cta + threadIdx.x / G; item < p.n_items;
          item += (i64)gridDim.x * per_cta) {
         Seg g;
-        g.s = p.nchunks == 1 ? item : item / p.nchunks;
-        const i64 c = item - g.s * p.nchunks;
-        g.r_begin = c * p.chunk;
-        g.r_end = min(p.inner, g.r_begin + p.chunk);
-        g.nslot = (g.r_end - g.r_begin + 3) >> 2;
-        seg_setup(p, g);
+        seg_item(p, g, item);
         Acc acc = acc_init();
         Buf ba, bb;
         load_group(p, g, ba, gl);
@@ -304,53 +466,10 @@ extern "C" __global__ void __launch_bounds__(256) hx_nest_kernel(const NestParam
             proc_group(p, g, bb, t0 + G * U, acc);
         }
 #if MONOID >= 0
-        acc = acc_butterfly<G>(gmask, acc);
-        if (p.nchunks == 1) {
-            if (gl == 0) write_result(p, g.s, acc);
-            continue;
-        }
-        // Several chunks per segment happen only with G == 32: the whole warp
-        // shares the item.  Level 1: the last chunk of its group of 32 folds
-        // the group's partials.
-        const i64 grp = c >> 5;
-        const int gsize = (int)min((i64)32, p.nchunks - grp * 32);
-        unsigned *t1 = p.tick + g.s * p.ngroups + grp;
-        unsigned last = 0;
-        if (lane == 0) {
-            part_store(p.part + item, acc);
-            __threadfence();
-            last = atomicAdd(t1, 1u) == (unsigned)(gsize - 1) ? 1u : 0u;
-        }
-        if (!__shfl_sync(0xffffffffu, last, 0)) continue;
-        __threadfence();
-        Acc t = lane < gsize ? part_load(p.part + g.s * p.nchunks + grp * 32 + lane) : acc_init();
-        t = acc_butterfly<32>(0xffffffffu, t);
-        if (p.ngroups == 1) {
-            if (lane == 0) {
-                write_result(p, g.s, t);
-                *t1 = 0u;
-            }
-            continue;
-        }
-        // Level 2: the last group of the segment folds the group partials.
-        last = 0;
-        if (lane == 0) {
-            *t1 = 0u;
-            part_store(p.part2 + g.s * p.ngroups + grp, t);
-            __threadfence();
-            last = atomicAdd(p.tick2 + g.s, 1u) == (unsigned)(p.ngroups - 1) ? 1u : 0u;
-        }
-        if (!__shfl_sync(0xffffffffu, last, 0)) continue;
-        __threadfence();
-        Acc u = acc_init();
-        for (i64 q = lane; q < p.ngroups; q += 32) u = acc_combine(u, part_load(p.part2 + g.s * p.ngroups + q));
-        u = acc_butterfly<32>(0xffffffffu, u);
-        if (lane == 0) {
-            write_result(p, g.s, u);
-            p.tick2[g.s] = 0u;
-        }
+        item_tree(p, g, item, acc, lane);
 #endif
     }
+#endif  // G < 32
 }
 )CUDA";
 
@@ -723,6 +842,7 @@ struct Compiled {
     std::string cubin;
     cudaLibrary_t lib = nullptr;
     cudaKernel_t kernel = nullptr;
+    int ctas_per_sm = 1;   // resident CTAs of kNestBlock threads per SM
 };
 
 std::mutex g_mu;
@@ -769,8 +889,14 @@ hx_status load(Compiled *c) {
     if (c->kernel) return HX_OK;
     cudaError_t e = cudaLibraryLoadData(&c->lib, c->cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
     if (e != cudaSuccess) return hx::cuda_fail(e, "hx_nest: cudaLibraryLoadData");
-    e = cudaLibraryGetKernel(&c->kernel, c->lib, "hx_nest_kernel");
+    cudaKernel_t k = nullptr;
+    e = cudaLibraryGetKernel(&k, c->lib, "hx_nest_kernel");
     if (e != cudaSuccess) return hx::cuda_fail(e, "hx_nest: cudaLibraryGetKernel");
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void *)k, kNestBlock, 0);
+    if (e != cudaSuccess) return hx::cuda_fail(e, "hx_nest: occupancy query");
+    c->ctas_per_sm = occ > 0 ? occ : 1;
+    c->kernel = k;
     return HX_OK;
 }
 
@@ -818,6 +944,24 @@ hx_status split_of(const hx_nest *n, const hx_tune_table *tune, int64_t outer, i
     }
     *out = sp;
     return HX_OK;
+}
+
+// A warp-tree reduction whose chunks outnumber the warps the device holds at
+// once gets longer chunks instead: one chunk per resident warp (at least one
+// per segment), a multiple of 512 elements.  Each warp then streams one long
+// chunk, and the tree above the chunks (arrival tickets, group partials)
+// shrinks by the same factor.  Explicit chunk lengths are kept.
+void one_wave(const hx_nest *n, const Shape &sh, int64_t outer, int64_t inner, int64_t warps, Split *sp) {
+    if (n->tree != HX_TREE_WARP || sh.G != 32 || sh.monoid < 0 || n->chunk > 0) return;
+    if (outer * sp->nchunks <= warps) return;
+    int64_t per_seg = warps / outer;
+    if (per_seg < 1) per_seg = 1;
+    if (per_seg >= sp->nchunks) return;
+    int64_t chunk = (inner + per_seg - 1) / per_seg;
+    chunk = (chunk + 511) / 512 * 512;
+    sp->chunk = chunk;
+    sp->nchunks = (inner + chunk - 1) / chunk;
+    sp->ngroups = (sp->nchunks + 31) / 32;
 }
 
 hx_status prepare(const hx_nest *n, const hx_tune_table *tune, Compiled **c, Shape *sh, Split *sp, int64_t *outer,
@@ -884,6 +1028,7 @@ hx_status hx_fork_reduce(hx_ctx *ctx, const hx_nest *nest, hx_stream_t stream) {
     if (st != HX_OK) return st;
     st = load(c);
     if (st != HX_OK) return st;
+    one_wave(nest, sh, outer, inner, (int64_t)ctx->num_sms * c->ctas_per_sm * (kNestBlock / 32), &sp);
     if (hx::take_injected_failure(ctx))
         return hx::fail(HX_ERR_CUDA, "hx_fork_reduce: injected launch failure (test hook)");
     hx::NestWs *ws = ctx->nest_ws + (slot - ctx->ws);
