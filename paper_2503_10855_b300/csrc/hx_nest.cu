@@ -679,6 +679,13 @@ Shape shape_of(const hx_nest *n) {
         const int64_t want = (inner + per_lane - 1) / per_lane;
         sh.G = 1;
         while (sh.G < 32 && sh.G < want) sh.G *= 2;
+        // a group narrower than a warp loads a whole segment at once: no more
+        // slots per lane than the segment has (registers for more segments
+        // in flight)
+        if (sh.G < 32) {
+            const int64_t u = ((inner + 3) / 4 + sh.G - 1) / sh.G;
+            if (u < sh.U) sh.U = u < 1 ? 1 : (int)u;
+        }
     }
     sh.has_out = n->out != nullptr;
     sh.has_res64 = n->reduce_dims > 0 && n->result64 != nullptr;
@@ -1061,7 +1068,10 @@ hx_status hx_fork_reduce(hx_ctx *ctx, const hx_nest *nest, hx_stream_t stream) {
 
     const int64_t threads = sh.tree == HX_TREE_WARP ? a.n_items * sh.G : a.n_items;
     int64_t blocks = (threads + kNestBlock - 1) / kNestBlock;
-    const int64_t max_blocks = (int64_t)ctx->num_sms * (2048 / kNestBlock);
+    // whole waves of resident CTAs, up to 2048 threads per SM (a partial
+    // last wave would run the items' tail at low occupancy)
+    const int waves = c->ctas_per_sm >= 2048 / kNestBlock ? 1 : (2048 / kNestBlock) / c->ctas_per_sm;
+    const int64_t max_blocks = (int64_t)ctx->num_sms * c->ctas_per_sm * waves;
     if (blocks > max_blocks) blocks = max_blocks;
     if (blocks < 1) blocks = 1;
     void *args[] = {&a};
