@@ -31,9 +31,9 @@ namespace {
 constexpr int kTX = 128;          // tile columns
 constexpr int kTY = 16;           // tile rows
 constexpr int kThreads = 256;
-constexpr int kJsW = kTX + 4;     // J tile: rows i0-1 .. i0+TY+1, cols j0-1 .. j0+TX+1 (+1 pad)
+constexpr int kJsW = kTX + 8;     // J tile: rows i0-1 .. i0+TY+1, cols j0-1 .. j0+TX+1 at x = 3 .. 133
 constexpr int kJsH = kTY + 3;
-constexpr int kCsW = kTX + 2;     // c tile: rows i0 .. i0+TY, cols j0 .. j0+TX (+1 pad)
+constexpr int kCsW = kTX + 8;     // c tile: rows i0 .. i0+TY, cols j0 .. j0+TX at x = 4 .. 132
 constexpr int kCsH = kTY + 1;
 
 struct SradArgs {
@@ -149,11 +149,19 @@ __global__ void __launch_bounds__(kThreads) srad_stats_kernel(const float *__res
 
 // One fused iteration: coefficient in shared memory, update, and the next
 // iteration's region sums.  q0sq_next == nullptr on the last iteration.
+//
+// Shared tiles keep image column j0 + x - 4 at index x, so the tile's 128
+// columns start on a 16-byte boundary (x = 4): J at x = 3 .. 133, c at
+// x = 4 .. 132.  A tile whose halo lies inside the image, outside the
+// region of interest, takes the vector path when rows are 16-byte aligned
+// (vec): float4 loads and stores, four pixels per thread step.  Every other
+// tile takes the element path with clamped loads.  Both evaluate the same
+// per-pixel expressions on the same operands, so they agree bit for bit.
 __global__ void __launch_bounds__(kThreads) srad_fused_kernel(const float *__restrict__ J, float *__restrict__ Jn,
                                                               SradArgs p, const float *q0sq_t, NestWs *ws,
-                                                              float *q0sq_next) {
-    __shared__ float Js[kJsH][kJsW];
-    __shared__ float Cs[kCsH][kCsW];
+                                                              float *q0sq_next, int vec) {
+    __shared__ __align__(16) float Js[kJsH][kJsW];
+    __shared__ __align__(16) float Cs[kCsH][kCsW];
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;");
     const int i0 = blockIdx.y * kTY, j0 = blockIdx.x * kTX;
@@ -161,35 +169,89 @@ __global__ void __launch_bounds__(kThreads) srad_fused_kernel(const float *__res
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const float q0sq = *q0sq_t;
     const float iq = 1.0f / (q0sq * (1.0f + q0sq));
-    // J tile with a halo of 1 above / left and 2 below / right, clamped to
-    // the image (the clamp-to-edge neighbours): warp w loads rows w, w+8, ...
+    const bool in_roi_rows = i0 < p.r1 && i0 + kTY > p.r0;
+    const bool roi_tile = in_roi_rows && j0 < p.c1 && j0 + kTX > p.c0;
+    const bool in_roi = q0sq_next && roi_tile;
+    const bool fast = vec && !roi_tile && i0 >= 1 && i0 + kTY + 1 < ny && j0 >= 1 && j0 + kTX + 1 < nx;
+    if (fast) {
+        // rows i0-1 .. i0+TY+1: a warp loads a row's 128 columns as float4,
+        // three lanes its halo columns
+        for (int r = warp; r < kJsH; r += kThreads / 32) {
+            const float *row = J + (size_t)(i0 - 1 + r) * nx + j0;
+            *reinterpret_cast<float4 *>(&Js[r][4 + 4 * lane]) = __ldg(reinterpret_cast<const float4 *>(row) + lane);
+            if (lane < 3) Js[r][lane == 0 ? 3 : 131 + lane] = __ldg(row + (lane == 0 ? -1 : 127 + lane));
+        }
+        __syncthreads();
+        // coefficients: 17 rows x 32 groups of 4 columns, then column 128
+        for (int w = threadIdx.x; w < kCsH * 32 + kCsH; w += kThreads) {
+            if (w < kCsH * 32) {
+                const int r = w >> 5, x = 4 + 4 * (w & 31);
+                const float4 c4 = *reinterpret_cast<const float4 *>(&Js[r + 1][x]);
+                const float4 n4 = *reinterpret_cast<const float4 *>(&Js[r][x]);
+                const float4 s4 = *reinterpret_cast<const float4 *>(&Js[r + 2][x]);
+                const float wv = Js[r + 1][x - 1], ev = Js[r + 1][x + 4];
+                float4 o;
+                o.x = srad_coeff(c4.x, n4.x - c4.x, s4.x - c4.x, wv - c4.x, c4.y - c4.x, q0sq, iq);
+                o.y = srad_coeff(c4.y, n4.y - c4.y, s4.y - c4.y, c4.x - c4.y, c4.z - c4.y, q0sq, iq);
+                o.z = srad_coeff(c4.z, n4.z - c4.z, s4.z - c4.z, c4.y - c4.z, c4.w - c4.z, q0sq, iq);
+                o.w = srad_coeff(c4.w, n4.w - c4.w, s4.w - c4.w, c4.z - c4.w, ev - c4.w, q0sq, iq);
+                *reinterpret_cast<float4 *>(&Cs[r][x]) = o;
+            } else {
+                const int r = w - kCsH * 32;
+                const float Jc = Js[r + 1][132];
+                Cs[r][132] = srad_coeff(Jc, Js[r][132] - Jc, Js[r + 2][132] - Jc, Js[r + 1][131] - Jc,
+                                        Js[r + 1][133] - Jc, q0sq, iq);
+            }
+        }
+        __syncthreads();
+        // update: 16 rows x 32 groups of 4 columns, two groups per thread
+        for (int w = threadIdx.x; w < kTY * 32; w += kThreads) {
+            const int r = w >> 5, x = 4 + 4 * (w & 31);
+            const float4 c4 = *reinterpret_cast<const float4 *>(&Js[r + 1][x]);
+            const float4 n4 = *reinterpret_cast<const float4 *>(&Js[r][x]);
+            const float4 s4 = *reinterpret_cast<const float4 *>(&Js[r + 2][x]);
+            const float wv = Js[r + 1][x - 1], ev = Js[r + 1][x + 4];
+            const float4 k4 = *reinterpret_cast<const float4 *>(&Cs[r][x]);
+            const float4 ks = *reinterpret_cast<const float4 *>(&Cs[r + 1][x]);
+            const float ke = Cs[r][x + 4];
+            float4 o;
+            o.x = srad_update(c4.x, n4.x - c4.x, s4.x - c4.x, wv - c4.x, c4.y - c4.x, k4.x, ks.x, k4.x, k4.y, p.k);
+            o.y = srad_update(c4.y, n4.y - c4.y, s4.y - c4.y, c4.x - c4.y, c4.z - c4.y, k4.y, ks.y, k4.y, k4.z, p.k);
+            o.z = srad_update(c4.z, n4.z - c4.z, s4.z - c4.z, c4.y - c4.z, c4.w - c4.z, k4.z, ks.z, k4.z, k4.w, p.k);
+            o.w = srad_update(c4.w, n4.w - c4.w, s4.w - c4.w, c4.z - c4.w, ev - c4.w, k4.w, ks.w, k4.w, ke, p.k);
+            *reinterpret_cast<float4 *>(Jn + (size_t)(i0 + r) * nx + j0 + (x - 4)) = o;
+        }
+        return;
+    }
+    // Element path.  J tile with a halo of 1 above / left and 2 below /
+    // right, clamped to the image (the clamp-to-edge neighbours): warp w
+    // loads rows w, w+8, ...
     for (int r = warp; r < kJsH; r += kThreads / 32) {
         const float *row = J + (size_t)clampi(i0 - 1 + r, 0, ny - 1) * nx;
 #pragma unroll
-        for (int c = lane; c < kTX + 3; c += 32) Js[r][c] = __ldg(row + clampi(j0 - 1 + c, 0, nx - 1));
+        for (int c = lane; c < kTX + 3; c += 32) Js[r][3 + c] = __ldg(row + clampi(j0 - 1 + c, 0, nx - 1));
     }
     __syncthreads();
     // coefficient of rows i0 .. i0+TY and cols j0 .. j0+TX (inside the image)
     for (int idx = threadIdx.x; idx < kCsH * (kTX + 1); idx += kThreads) {
         const int r = idx / (kTX + 1), c = idx - r * (kTX + 1);
         if (i0 + r < ny && j0 + c < nx) {
-            const float Jc = Js[r + 1][c + 1];
-            Cs[r][c] = srad_coeff(Jc, Js[r][c + 1] - Jc, Js[r + 2][c + 1] - Jc, Js[r + 1][c] - Jc,
-                                  Js[r + 1][c + 2] - Jc, q0sq, iq);
+            const float Jc = Js[r + 1][c + 4];
+            Cs[r][c + 4] = srad_coeff(Jc, Js[r][c + 4] - Jc, Js[r + 2][c + 4] - Jc, Js[r + 1][c + 3] - Jc,
+                                      Js[r + 1][c + 5] - Jc, q0sq, iq);
         }
     }
     __syncthreads();
-    const bool in_roi_rows = i0 < p.r1 && i0 + kTY > p.r0;
-    const bool in_roi = q0sq_next && in_roi_rows && j0 < p.c1 && j0 + kTX > p.c0;
     RoiAcc a = {{0.0f, 0.0f}, {0.0f, 0.0f}};
     const int c = threadIdx.x & (kTX - 1);
     for (int r = threadIdx.x / kTX; r < kTY; r += kThreads / kTX) {
         const int i = i0 + r, j = j0 + c;
         if (i < ny && j < nx) {
-            const float Jc = Js[r + 1][c + 1];
+            const float Jc = Js[r + 1][c + 4];
             const int rs = i + 1 < ny ? r + 1 : r, ce = j + 1 < nx ? c + 1 : c;
-            const float v = srad_update(Jc, Js[r][c + 1] - Jc, Js[r + 2][c + 1] - Jc, Js[r + 1][c] - Jc,
-                                        Js[r + 1][c + 2] - Jc, Cs[r][c], Cs[rs][c], Cs[r][c], Cs[r][ce], p.k);
+            const float v = srad_update(Jc, Js[r][c + 4] - Jc, Js[r + 2][c + 4] - Jc, Js[r + 1][c + 3] - Jc,
+                                        Js[r + 1][c + 5] - Jc, Cs[r][c + 4], Cs[rs][c + 4], Cs[r][c + 4],
+                                        Cs[r][ce + 4], p.k);
             Jn[(size_t)i * nx + j] = v;
             if (in_roi && i >= p.r0 && i < p.r1 && j >= p.c0 && j < p.c1) roi_add(a, v);
         }
@@ -294,6 +356,8 @@ extern "C" hx_status hx_srad(hx_ctx *ctx, float *J0, float *J1, float *C, int32_
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     const dim3 tiles((nx + kTX - 1) / kTX, (ny + kTY - 1) / kTY);
+    // float4 rows: 16-byte aligned images whose rows are whole float4s
+    const int vec = nx % 4 == 0 && (((uintptr_t)J0 | (uintptr_t)J1) & 15u) == 0;
     const dim3 rows_grid((nx + kTX - 1) / kTX, (ny + kThreads / kTX - 1) / (kThreads / kTX));
     cudaError_t e;
     for (int t = 0; t < iters; ++t) {
@@ -307,7 +371,7 @@ extern "C" hx_status hx_srad(hx_ctx *ctx, float *J0, float *J1, float *C, int32_
         if (fused) {
             cfg.gridDim = tiles;
             float *next = t + 1 < iters ? d_q0sq + t + 1 : nullptr;
-            e = cudaLaunchKernelEx(&cfg, srad_fused_kernel, src, dst, p, (const float *)(d_q0sq + t), ws, next);
+            e = cudaLaunchKernelEx(&cfg, srad_fused_kernel, src, dst, p, (const float *)(d_q0sq + t), ws, next, vec);
         } else {
             cfg.gridDim = rows_grid;
             e = cudaLaunchKernelEx(&cfg, srad_coeff_kernel, src, C, p, (const float *)(d_q0sq + t));

@@ -6,7 +6,9 @@ sums; the oracle forms it in double from sequential double sums.  Both round
 q0^2 to fp32 once, so per-iteration q0^2 and the images are compared bit for
 bit with the f32 oracle, and within 2e-5 (relative, normwise) with the f64
 one.  The fused path (one kernel per iteration) and the unfused one (three
-kernels) must agree bit for bit.
+kernels) must agree bit for bit; so must the fused kernel's vector path
+(interior tiles, 16-byte rows) and its element path (edge and region tiles,
+and images whose rows are not whole float4s).
 """
 
 import numpy as np
@@ -29,7 +31,9 @@ def _run(hx, ctx, J, iters, lam, roi, fused):
 
 CASES = [((17, 23), (0, 17, 0, 23)), ((16, 128), (3, 9, 5, 100)), ((33, 257), (0, 33, 0, 257)),
          ((130, 300), (17, 129, 130, 299)), ((1, 200), (0, 1, 10, 190)), ((200, 1), (5, 150, 0, 1)),
-         ((512, 512), (0, 128, 0, 128))]
+         ((512, 512), (0, 128, 0, 128)),
+         # interior tiles on the vector path around region tiles on the element path
+         ((100, 404), (40, 60, 150, 250))]
 
 
 @pytest.mark.parametrize("shape,roi", CASES)
@@ -95,3 +99,25 @@ def test_srad_full_size_one_iteration(gpu):
         tot_in = float(np.sum(J, dtype=np.float64))
         tot_out = float(out.double().sum().item())
         assert abs(tot_out - tot_in) <= 1e-6 * tot_in
+
+
+def test_srad_vector_and_element_paths_agree(gpu):
+    # the same image with 16-byte aligned rows (vector path on interior tiles)
+    # and at a 4-byte offset (element path everywhere)
+    hx = gpu
+    ny, nx = 96, 520
+    roi = (0, 16, 0, 128)
+    J = workloads.srad_image(ny, nx)
+    ref32, _ = oracle.srad(J, 3, 0.5, roi, "f32")
+    with hx.hx_create(0) as ctx:
+        outs = []
+        for off in (0, 1):
+            buf = torch.empty(2 * ny * nx + 8, device="cuda:0")
+            J0 = buf[off: off + ny * nx].view(ny, nx)
+            J1 = buf[ny * nx + 4 + off: ny * nx + 4 + off + ny * nx].view(ny, nx)
+            J0.copy_(torch.from_numpy(J))
+            out, _ = hx.hx_srad(ctx, J0, J1, 3, 0.5, roi)
+            torch.cuda.synchronize()
+            outs.append(out.cpu().numpy())
+    np.testing.assert_array_equal(outs[0].view(np.uint32), ref32.view(np.uint32))
+    np.testing.assert_array_equal(outs[1].view(np.uint32), ref32.view(np.uint32))
