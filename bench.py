@@ -605,7 +605,7 @@ def bench_hx(args, rank, world, local):
     return 0
 
 
-SERVE_RATES = (2000, 5000, 10000, 20000, 50000)
+SERVE_RATES = (2000, 5000, 10000, 12000, 15000, 20000, 30000, 40000, 50000)
 SERVE_BUDGET = 64 << 30
 
 
@@ -670,19 +670,27 @@ def bench_serving(hx, ctx, dev, rates=SERVE_RATES, max_requests=4000, window_s=0
                 lat, makespan = srv.run_trace(tasks, arrivals, timeout_s=300.0)
                 st = srv.stats()
             lat = np.array(lat) * 1e3
-            row[name] = {"req_per_s": round(len(tr) / makespan, 1), "p50_ms": round(float(np.percentile(lat, 50)), 4),
+            # a queue that keeps up has stationary latency: the last tenth of
+            # the requests (in arrival order) waits no longer than about the
+            # first tenth; a growing backlog shows up as a rising tail
+            k = max(1, len(lat) // 10)
+            head, tail = float(np.median(lat[:k])), float(np.median(lat[-k:]))
+            rate = len(tr) / makespan
+            row[name] = {"req_per_s": round(rate, 1), "p50_ms": round(float(np.percentile(lat, 50)), 4),
                          "p99_ms": round(float(np.percentile(lat, 99)), 4), "launches": st["launches"],
-                         "peak_footprint_gb": round(st["peak_footprint"] / 2**30, 3)}
+                         "peak_footprint_gb": round(st["peak_footprint"] / 2**30, 3),
+                         "stable": bool(rate >= 0.95 * lam and tail <= 3.0 * head + 1.0)}
         points.append(row)
     del arena
     torch.cuda.empty_cache()
     # Equal-p99 comparison: the per-launch server's p99 at the highest rate it
-    # keeps up with (>= 95% of offered) is the latency bound; compare the
-    # highest rate each mode sustains with p99 within that bound.
+    # sustains (stable: it keeps up with >= 95% of the offered rate and its
+    # latency does not grow over the trace) is the latency bound; compare
+    # the highest rate each mode sustains with p99 within that bound.
     def sustained(mode, bound):
-        ok = [p for p in points if p[mode]["req_per_s"] >= 0.95 * p["offered_req_per_s"] and p[mode]["p99_ms"] <= bound]
+        ok = [p for p in points if p[mode]["stable"] and p[mode]["p99_ms"] <= bound]
         return max(ok, key=lambda p: p["offered_req_per_s"]) if ok else None
-    keep = [p for p in points if p["per_launch"]["req_per_s"] >= 0.95 * p["offered_req_per_s"]]
+    keep = [p for p in points if p["per_launch"]["stable"]]
     base = max(keep, key=lambda p: p["offered_req_per_s"]) if keep else points[0]
     bound = base["per_launch"]["p99_ms"]
     c = sustained("continuous", bound)
@@ -692,6 +700,16 @@ def bench_serving(hx, ctx, dev, rates=SERVE_RATES, max_requests=4000, window_s=0
           "continuous_req_per_s": c["continuous"]["req_per_s"] if c else None}
     if eq["per_launch_req_per_s"] and eq["continuous_req_per_s"]:
         eq["ratio"] = round(eq["continuous_req_per_s"] / eq["per_launch_req_per_s"], 3)
+    # the same comparison at fixed p99 targets
+    slo = []
+    for target in (2.0, 5.0, 10.0, 20.0):
+        c, pl = sustained("continuous", target), sustained("per_launch", target)
+        row = {"p99_ms": target, "continuous_req_per_s": c["continuous"]["req_per_s"] if c else None,
+               "per_launch_req_per_s": pl["per_launch"]["req_per_s"] if pl else None}
+        if row["continuous_req_per_s"] and row["per_launch_req_per_s"]:
+            row["ratio"] = round(row["continuous_req_per_s"] / row["per_launch_req_per_s"], 3)
+        slo.append(row)
+    eq["at_p99_targets"] = slo
     return {"mix": "1/3 map->reduce, 1/3 jacobi (20 sweeps, square side ~sqrt(n)), 1/3 histogram+scan; "
                    "sizes log-uniform 1K-16M elements; Poisson arrivals (seed 4)",
             "budget_gb": SERVE_BUDGET / 2**30, "points": points, "equal_p99": eq}
