@@ -457,12 +457,10 @@ def bench_hx(args, rank, world, local):
                 issue(c, s)
             gs[c] = gc
         comp_graphs.append(gs)
-    # launches per step: map->reduce 1, or 2 when its tile partials are
-    # folded by a separate launch (at most 1024 tiles); 20 sweeps + their
-    # residual fold; the histogram; the batch's rounds
-    vecs = hx.hx_tune_get(ctx).map_vecs[MR_N.bit_length() - 1]
-    mr_tiles = -(-MR_N // (128 * vecs))
-    launches_per_step = (2 if mr_tiles <= 1024 else 1) + ST_ITERS + 1 + 1 + batch.rounds
+    # launches per step: map->reduce and its partials' fold; 20 sweeps and
+    # their residual fold; the histogram; per batch round, the batched
+    # kernel and its final-combine kernel
+    launches_per_step = 2 + ST_ITERS + 1 + 1 + 2 * batch.rounds
 
     with torch.cuda.stream(stream):
         for i in range(args.warmup):

@@ -122,32 +122,36 @@ batch_kernel(const BInst *__restrict__ insts, unsigned int n_inst, const uint32_
 }
 
 // The final combine of every instance this launch completed (it had work
-// items in the launch and its slice reached its last tile), one warp per
+// items in the launch and its slice reached its last tile), one CTA per
 // instance, after the batched kernel has finished (programmatic dependent
 // launch waits for the whole grid): the sum of a map->reduce instance from
-// its tile partials in the standalone call's fixed order, the residual of a
-// stencil sweep, the bins and scan of a histogram.  Accumulators are left at
+// its tile partials in the standalone call's fixed order (all 256 threads
+// fold, one virtual lane each), the residual of a stencil sweep, the bins and
+// scan of a histogram (one warp).  Accumulators are left at
 // zero for the next use; the run counter is reset for the next launch.
 __global__ void __launch_bounds__(kBatchThreads)
 batch_final_kernel(const BInst *__restrict__ insts, unsigned int n_inst, const uint32_t *__restrict__ cta_prefix,
                    const uint32_t *__restrict__ run_prefix, int round, unsigned int *ctrl) {
+    __shared__ ff red[kMrFoldLanes];
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;");
     if (blockIdx.x == 0 && threadIdx.x == 0) ctrl[0] = 0u;
     const int lane = threadIdx.x & 31;
-    const unsigned int i = blockIdx.x * (kBatchThreads / kWarp) + (threadIdx.x >> 5);
+    const unsigned int i = blockIdx.x;   // one CTA per instance
     if (i >= n_inst) return;
     const unsigned int work = (__ldg(cta_prefix + i + 1) - __ldg(cta_prefix + i)) +
                               (__ldg(run_prefix + i + 1) - __ldg(run_prefix + i));
     const BInst &I = insts[i];
     if (work == 0 || I.t_first + I.t_count != I.tiles) return;
     if (I.kind == kKindMap) {
-        const ff sf = mr_final(I.partials, I.plan.tiles, lane);
-        if (lane == 0) {
+        const ff sf = mr_final_cta(I.partials, I.plan.tiles, red);
+        if (threadIdx.x == 0) {
             const double s = ff_to_double(sf);
             *static_cast<float *>(I.o1) = (float)s;
             if (I.o2) *static_cast<double *>(I.o2) = s;
         }
+    } else if (threadIdx.x >= kWarp) {
+        return;
     } else if (I.kind == kKindStencil) {
         if (lane == 0) static_cast<float *>(I.o0)[I.sweep0 + round] = __uint_as_float(atomicExch(I.acc, 0u));
     } else {
@@ -237,7 +241,7 @@ hx_status launch_batch_round(const hx_ctx *ctx, const BInst *d_insts, uint32_t n
     cfg.numAttrs = 1;
     cudaError_t e = cudaLaunchKernelEx(&cfg, batch_kernel, d_insts, n_inst, d_cta_prefix, d_run_prefix, round, d_ctrl);
     if (e != cudaSuccess) return cuda_fail(e, "batched kernel launch");
-    cfg.gridDim = dim3((n_inst + kBatchThreads / kWarp - 1) / (kBatchThreads / kWarp));
+    cfg.gridDim = dim3(n_inst);
     cfg.dynamicSmemBytes = 0;
     e = cudaLaunchKernelEx(&cfg, batch_final_kernel, d_insts, n_inst, d_cta_prefix, d_run_prefix, round, d_ctrl);
     if (e != cudaSuccess) return cuda_fail(e, "batched final launch");

@@ -14,6 +14,7 @@ constexpr int kBatchThreads = 256;                               // 8 warps
 constexpr int64_t kBHiTile = (int64_t)256 * 1024;                // bytes per histogram item
 constexpr int kMaxSweeps = 4096;
 static_assert(kBatchThreads == kHiBins, "the histogram finish maps one thread to one bin");
+static_assert(kBatchThreads == kMrFoldLanes, "the final combine maps one thread to one virtual lane");
 
 
 struct BInst {

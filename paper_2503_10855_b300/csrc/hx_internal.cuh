@@ -45,12 +45,11 @@ constexpr int kHiBins = 256;
 // is clean again when a call's stream work completes.
 struct WsSlot {
     float2 mr_partial[kMrMaxTiles];   // (hi, lo) tile partials
-    unsigned int mr_ticket;
     unsigned int st_ticket;
     unsigned int st_max_bits;   // running max |u'-u| as float bits (>= 0)
     unsigned int hi_ticket;
     unsigned int hi_bins[kHiBins];
-    unsigned int pad[60];
+    unsigned int pad[61];
 };
 static_assert(sizeof(WsSlot) % 256 == 0, "slot alignment");
 
@@ -179,17 +178,24 @@ __device__ __forceinline__ double ff_to_double(ff v) { return (double)v.hi + (do
 // accumulated as a compensated pair, storing out[e] = fmaf(a, x[e], y[e])
 // when out != nullptr.  The vector path (aligned, full tile) and the element
 // path produce the same sequence of operations.
+// GROUPS (2 or 3): groups of kMrUnroll vectors per operand in flight on the
+// aligned full-tile path.  The fold order does not depend on it, so the
+// standalone kernel (3 groups, 120 registers) and the batched kernel (2
+// groups, inside its 128-register budget) give the same bits.
+template <int GROUPS = 2>
 __device__ __forceinline__ ff mr_thread_partial(const float *__restrict__ x,
                                                    const float *__restrict__ y,
                                                    float *__restrict__ out, float a,
                                                    const MrPlan &p, int64_t tile,
                                                    bool aligned, int t, int nthreads) {
+    static_assert(GROUPS == 2 || GROUPS == 3, "two or three load groups");
     const int64_t base = tile * p.tile_elems;
     ff acc = {0.0f, 0.0f};
     const bool full = base + p.tile_elems <= p.n;
     if (full && aligned) {
-        // Two groups of kMrUnroll vectors per operand in flight: the loads of
-        // group g + 1 are issued before group g is computed.
+        // GROUPS groups of kMrUnroll vectors per operand in flight: the loads
+        // of groups g + 1 .. g + GROUPS - 1 are issued before group g is
+        // computed.
         const float4 *x4 = reinterpret_cast<const float4 *>(x + base);
         const float4 *y4 = reinterpret_cast<const float4 *>(y + base);
         float4 *o4 = reinterpret_cast<float4 *>(out + base);
@@ -218,13 +224,30 @@ __device__ __forceinline__ ff mr_thread_partial(const float *__restrict__ x,
             }
         };
         const int V = p.vecs_per_thread;
-        load(xa, ya, 0);
-        for (int u0 = 0; u0 < V; u0 += 2 * kMrUnroll) {
-            if (u0 + kMrUnroll < V) load(xb, yb, u0 + kMrUnroll);
-            consume(xa, ya, u0);
-            if (u0 + kMrUnroll >= V) break;
-            if (u0 + 2 * kMrUnroll < V) load(xa, ya, u0 + 2 * kMrUnroll);
-            consume(xb, yb, u0 + kMrUnroll);
+        constexpr int U = kMrUnroll;
+        if constexpr (GROUPS == 2) {
+            load(xa, ya, 0);
+            for (int u0 = 0; u0 < V; u0 += 2 * U) {
+                if (u0 + U < V) load(xb, yb, u0 + U);
+                consume(xa, ya, u0);
+                if (u0 + U >= V) break;
+                if (u0 + 2 * U < V) load(xa, ya, u0 + 2 * U);
+                consume(xb, yb, u0 + U);
+            }
+        } else {
+            float4 xc[kMrUnroll], yc[kMrUnroll];
+            load(xa, ya, 0);
+            if (U < V) load(xb, yb, U);
+            for (int u0 = 0; u0 < V; u0 += 3 * U) {
+                if (u0 + 2 * U < V) load(xc, yc, u0 + 2 * U);
+                consume(xa, ya, u0);
+                if (u0 + U >= V) break;
+                if (u0 + 3 * U < V) load(xa, ya, u0 + 3 * U);
+                consume(xb, yb, u0 + U);
+                if (u0 + 2 * U >= V) break;
+                if (u0 + 4 * U < V) load(xb, yb, u0 + 4 * U);
+                consume(xc, yc, u0 + 2 * U);
+            }
         }
     } else {
         for (int u = 0; u < p.vecs_per_thread; ++u) {
@@ -246,30 +269,78 @@ __device__ __forceinline__ ff mr_thread_partial(const float *__restrict__ x,
 
 // Partial of one map->reduce tile, computed by one whole warp (lane = its
 // lane index); the same value in every lane.
+template <int GROUPS = 2>
 __device__ __forceinline__ ff mr_tile(const float *__restrict__ x, const float *__restrict__ y,
                                       float *__restrict__ out, float a, const MrPlan &p, int64_t tile,
                                       bool aligned, int lane) {
-    return warp_sum(mr_thread_partial(x, y, out, a, p, tile, aligned, lane, kWarp));
+    return warp_sum(mr_thread_partial<GROUPS>(x, y, out, a, p, tile, aligned, lane, kWarp));
 }
 
-// Final combine of `tiles` tile partials in a fixed order, by one warp: lane
-// l folds partials l, l+32, l+64, ... then the butterfly.  Same value in
-// every lane.  The loads of kMrFinalDepth partials are issued before they
-// are folded (a lane folds up to 128 partials: one L2 round trip per group
-// of 32 instead of one per partial); the fold order is unchanged.
-constexpr int kMrFinalDepth = 32;
+// Final combine of `tiles` tile partials in one fixed order, the same
+// whether one warp or one CTA of 256 threads evaluates it.  There are 256
+// virtual lanes; virtual lane v folds partials v, v + 256, v + 512, ... in
+// order.  The 256 values are then combined by a butterfly whose levels pair
+// lanes at distance 128, 64 and 32, then 16, 8, 4, 2 and 1 (a warp
+// butterfly).  ff_add is commutative bit for bit, so both lanes of a pair get
+// the same value, and the result is in every lane.
+constexpr int kMrFoldLanes = 256;
+
+// One warp: lane l plays virtual lanes l + 32 w, w = 0..7, as eight
+// independent chains; the loads of two blocks of 256 partials (16 per lane)
+// are issued before they are folded.
 __device__ __forceinline__ ff mr_final(const float2 *partials, int64_t tiles, int lane) {
-    ff acc = {0.0f, 0.0f};
-    for (int64_t i0 = lane; i0 < tiles; i0 += (int64_t)kWarp * kMrFinalDepth) {
-        float2 q[kMrFinalDepth];
+    ff acc[8];
 #pragma unroll
-        for (int k = 0; k < kMrFinalDepth; ++k) {
-            const int64_t i = i0 + (int64_t)k * kWarp;
+    for (int w = 0; w < 8; ++w) acc[w] = ff{0.0f, 0.0f};
+    for (int64_t b0 = 0; b0 < tiles; b0 += 2 * kMrFoldLanes) {
+        float2 q[2][8];
+#pragma unroll
+        for (int bb = 0; bb < 2; ++bb)
+#pragma unroll
+            for (int w = 0; w < 8; ++w) {
+                const int64_t i = b0 + bb * kMrFoldLanes + 32 * w + lane;
+                q[bb][w] = i < tiles ? __ldcg(partials + i) : make_float2(0.0f, 0.0f);
+            }
+#pragma unroll
+        for (int bb = 0; bb < 2; ++bb)
+#pragma unroll
+            for (int w = 0; w < 8; ++w)
+                if (b0 + bb * kMrFoldLanes + 32 * w + lane < tiles) acc[w] = ff_add(acc[w], ff{q[bb][w].x, q[bb][w].y});
+    }
+#pragma unroll
+    for (int d = 4; d >= 1; d >>= 1) {   // virtual distances 128, 64, 32
+        ff t[8];
+#pragma unroll
+        for (int w = 0; w < 8; ++w) t[w] = ff_add(acc[w], acc[w ^ d]);
+#pragma unroll
+        for (int w = 0; w < 8; ++w) acc[w] = t[w];
+    }
+    return warp_sum(acc[0]);
+}
+
+// One CTA of kMrFoldLanes threads: thread v is virtual lane v (all its
+// partials' loads in flight at once for up to 4096 tiles); red: shared
+// scratch of kMrFoldLanes pairs.  Call from every thread of the CTA.
+__device__ __forceinline__ ff mr_final_cta(const float2 *partials, int64_t tiles, ff *red) {
+    const int v = threadIdx.x;
+    ff acc = {0.0f, 0.0f};
+    for (int64_t i0 = v; i0 < tiles; i0 += (int64_t)kMrFoldLanes * 16) {
+        float2 q[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            const int64_t i = i0 + (int64_t)k * kMrFoldLanes;
             q[k] = i < tiles ? __ldcg(partials + i) : make_float2(0.0f, 0.0f);
         }
 #pragma unroll
-        for (int k = 0; k < kMrFinalDepth; ++k)
-            if (i0 + (int64_t)k * kWarp < tiles) acc = ff_add(acc, ff{q[k].x, q[k].y});
+        for (int k = 0; k < 16; ++k)
+            if (i0 + (int64_t)k * kMrFoldLanes < tiles) acc = ff_add(acc, ff{q[k].x, q[k].y});
+    }
+#pragma unroll
+    for (int d = 128; d >= 32; d >>= 1) {
+        red[v] = acc;
+        __syncthreads();
+        acc = ff_add(acc, red[v ^ d]);
+        __syncthreads();
     }
     return warp_sum(acc);
 }

@@ -4,45 +4,40 @@
 // fork-chunk of Sec. 2.2), each tile's partial starts from the identity
 // (monoid-reassociate, Sec. 5.2), and the tile partials are combined by a
 // second level (fork-fission into a producer and a consumer, Sec. 5.2).  On
-// the GPU the two levels run in one launch for large n: every warp produces
-// one tile partial, and the warp that arrives last (an atomic ticket, no
-// waiting) runs the consumer in a fixed order.  For up to 1024 tiles the
-// consumer is a one-warp launch chained with programmatic dependent launch
-// instead (same order), which spares every warp a fence and a same-address
-// atomic.  Inside a tile the leaf reduction is a
-// per-lane compensated fold, then a warp-shuffle butterfly, the warp
-// reductions of Sec. 4.4.
+// the GPU the producer is one launch in which every warp stores one tile
+// partial (no fence, no same-address atomic), and the consumer is a
+// one-CTA launch chained with programmatic dependent launch that folds the
+// partials in the fixed order of mr_final_cta.  Inside a tile the leaf
+// reduction is a per-lane compensated fold, then a warp-shuffle butterfly,
+// the warp reductions of Sec. 4.4.
 #include "hx_internal.cuh"
 
 namespace hx {
 
 // One warp per tile, kMrWarpsPerCta tiles per CTA; no block-level barrier.
-// DEFER: the warp only stores its tile partial and map_reduce_final_kernel
-// (chained with programmatic dependent launch) folds them; otherwise the
-// last warp to arrive folds them in the same launch.
-template <bool DEFER>
+// A warp only stores its tile partial; map_reduce_final_kernel folds them.
+// Three load groups per operand in flight (120 registers, 4 CTAs per SM):
+// measured on B300 against two groups at 6 or 7 CTAs per SM, it is the
+// fastest from 2^22 to 2^28 elements.
 __global__ void __launch_bounds__(kMrWarpsPerCta * kWarp)
 map_reduce_kernel(const float *__restrict__ x, const float *__restrict__ y, float *__restrict__ out,
-                  float a, MrPlan p, bool aligned, WsSlot *ws, float *d_sum, double *d_sum64) {
+                  float a, MrPlan p, bool aligned, WsSlot *ws) {
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;");
     const int64_t tile = (int64_t)blockIdx.x * kMrWarpsPerCta + (threadIdx.x >> 5);
     if (tile >= p.tiles) return;
-    if (DEFER) {
-        const ff part = mr_tile(x, y, out, a, p, tile, aligned, threadIdx.x & 31);
-        if ((threadIdx.x & 31) == 0) st_keep2(ws->mr_partial + tile, make_float2(part.hi, part.lo));
-    } else {
-        mr_warp_item(x, y, out, a, p, tile, aligned, ws->mr_partial, &ws->mr_ticket, d_sum, d_sum64);
-    }
+    const ff part = mr_tile<3>(x, y, out, a, p, tile, aligned, threadIdx.x & 31);
+    if ((threadIdx.x & 31) == 0) st_keep2(ws->mr_partial + tile, make_float2(part.hi, part.lo));
 }
 
-// The consumer level of the tree as its own one-warp launch: the same fixed
-// order as the last-arrival fold.
-__global__ void __launch_bounds__(kWarp) map_reduce_final_kernel(const float2 *partials, int64_t tiles,
-                                                                 float *d_sum, double *d_sum64) {
+// The consumer level of the tree: one CTA of kMrFoldLanes threads, launched
+// after the producer has finished (programmatic dependent launch).
+__global__ void __launch_bounds__(kMrFoldLanes) map_reduce_final_kernel(const float2 *partials, int64_t tiles,
+                                                                        float *d_sum, double *d_sum64) {
+    __shared__ ff red[kMrFoldLanes];
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;");
-    const ff sf = mr_final(partials, tiles, threadIdx.x);
+    const ff sf = mr_final_cta(partials, tiles, red);
     if (threadIdx.x == 0) {
         const double s = ff_to_double(sf);
         *d_sum = (float)s;
@@ -94,15 +89,10 @@ extern "C" hx_status hx_map_reduce(hx_ctx *ctx, const float *x, const float *y, 
         cfg.stream = (cudaStream_t)stream;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        // up to 1024 tiles the separate fold wins (no same-address ticket
-        // per warp: 2^16 4.8 -> 4.1 us, 2^20 8.2 -> 7.8 us); above, the
-        // in-launch fold is as fast or faster
-        const bool defer = p.tiles <= 1024;
-        cudaError_t e = cudaLaunchKernelEx(&cfg, defer ? map_reduce_kernel<true> : map_reduce_kernel<false>, x, y,
-                                           out, a, p, aligned, ws, d_sum, d_sum64);
-        if (e == cudaSuccess && defer) {
+        cudaError_t e = cudaLaunchKernelEx(&cfg, map_reduce_kernel, x, y, out, a, p, aligned, ws);
+        if (e == cudaSuccess) {
             cfg.gridDim = dim3(1);
-            cfg.blockDim = dim3(kWarp);
+            cfg.blockDim = dim3(kMrFoldLanes);
             e = cudaLaunchKernelEx(&cfg, map_reduce_final_kernel, (const float2 *)ws->mr_partial, p.tiles, d_sum,
                                    d_sum64);
         }
