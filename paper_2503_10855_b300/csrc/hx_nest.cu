@@ -957,7 +957,9 @@ hx_status split_of(const hx_nest *n, const hx_tune_table *tune, int64_t outer, i
 // once gets longer chunks instead: one chunk per resident warp (at least one
 // per segment), a multiple of 512 elements.  Each warp then streams one long
 // chunk, and the tree above the chunks (arrival tickets, group partials)
-// shrinks by the same factor.  Explicit chunk lengths are kept.
+// shrinks by the same factor.  Explicit chunk lengths are kept.  Pure maps
+// keep the tuned chunk: without a tree to shrink, 16 KiB chunks over several
+// waves measured faster (1.03 against 0.97 of HBM for a 2^27 copy-like map).
 void one_wave(const hx_nest *n, const Shape &sh, int64_t outer, int64_t inner, int64_t warps, Split *sp) {
     if (n->tree != HX_TREE_WARP || sh.G != 32 || sh.monoid < 0 || n->chunk > 0) return;
     if (outer * sp->nchunks <= warps) return;

@@ -216,14 +216,16 @@ hx_status hx_autotune(hx_ctx *ctx, int32_t max_log2, hx_stream_t stream) {
     hx_tune_table t = ctx->tune;
     const int reps = 5;
 
-    // map->reduce tile length per class
+    // map->reduce tile length per class (vectors per lane; the standalone
+    // kernel keeps three groups of 4 in flight, so 12 and 24 are whole
+    // pipelines)
     for (int c = 10; c <= map_top && st == HX_OK; ++c) {
         const int64_t n = (int64_t)1 << c;
         const size_t stride = ((size_t)3 * n + 63) & ~(size_t)63;
         const size_t regions = std::max<size_t>(1, pool_elems / stride);
         float best = 1e30f;
         int best_v = t.map_vecs[c];
-        for (int v : {4, 8, 16, 32}) {
+        for (int v : {4, 8, 12, 16, 24, 32}) {
             if (mr_plan(n, v).vecs_per_thread != v) continue;   // forced up by the tile cap
             ctx->tune.map_vecs[c] = v;
             const float ms = time_median(s, reps, [&](int r) {
@@ -243,22 +245,27 @@ hx_status hx_autotune(hx_ctx *ctx, int32_t max_log2, hx_stream_t stream) {
         const int64_t n = (int64_t)1 << c;
         const size_t stride = ((size_t)n + 63) & ~(size_t)63;
         const size_t regions = std::max<size_t>(1, pool_elems / stride);
+        // Above 2^20 elements a large reduction takes one chunk per resident
+        // warp whatever this value, so there it is timed on the nest it still
+        // decides: a copy (a map writing out).
+        const bool as_map = c > 20;
         hx_nest nest{};
         nest.ndim = 1;
-        nest.reduce_dims = 1;
+        nest.reduce_dims = as_map ? 0 : 1;
         nest.monoid = HX_MONOID_SUM;
         nest.tree = HX_TREE_WARP;
         nest.dims[0] = n;
         nest.n_ops = 1;
         nest.ops[0].code = HX_OP_IN;
         nest.strides[0][0] = 1;
-        nest.result = res;
+        if (as_map) nest.out = pool + pool_elems - stride;   // the pool's last region
+        else nest.result = res;
         float best = 1e30f;
         int best_le = t.nest_lane_elems[c];
         for (int le : {8, 16, 32, 64, 128}) {
             ctx->tune.nest_lane_elems[c] = le;
             const float ms = time_median(s, reps, [&](int r) {
-                nest.in[0] = pool + (r % regions) * stride;
+                nest.in[0] = pool + (r % (as_map ? regions - 1 : regions)) * stride;
                 return hx_fork_reduce(ctx, &nest, stream);
             }, &st);
             if (st == HX_OK && ms < best) { best = ms; best_le = le; }
