@@ -68,8 +68,10 @@ __device__ __forceinline__ unsigned int find_instance(const uint32_t *__restrict
 __global__ void __launch_bounds__(kBatchThreads, 2)
 batch_kernel(const BInst *__restrict__ insts, unsigned int n_inst, const uint32_t *__restrict__ cta_prefix,
              const uint32_t *__restrict__ run_prefix, int round, unsigned int *ctrl) {
+    // No early launch_dependents: the final-combine kernel is launched as
+    // the CTAs exit, so its CTAs do not wait on SM slots through the tail
+    // (slots that kernels of concurrent streams can use meanwhile).
     asm volatile("griddepcontrol.wait;" ::: "memory");
-    asm volatile("griddepcontrol.launch_dependents;");
     extern __shared__ __align__(16) unsigned int sh[];   // kHiSmemBytes when the round has CTA items
     const int lane = threadIdx.x & 31;
     const unsigned int n_cta = __ldg(cta_prefix + n_inst), n_runs = __ldg(run_prefix + n_inst);
