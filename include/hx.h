@@ -92,8 +92,12 @@ hx_status hx_debug_inject_launch_failures(hx_ctx *ctx, int32_t after, int32_t co
  * MonoidReduce attribute allows (Sec. 3.4) into the reduction tree of
  * Sec. 5.2: each tile of consecutive elements belongs to one warp and is
  * summed in a fixed order (each lane folds its own elements, then a fixed
- * shuffle butterfly), and the warp that finishes last folds the tile
- * partials in a fixed order.  Partial sums are carried as compensated
+ * shuffle butterfly), and a second launch on `stream`, chained by
+ * programmatic dependent launch, folds the tile partials in a fixed order
+ * (256 virtual lanes, each folding every 256th partial, then a butterfly;
+ * the batched kernel folds an instance's partials in the same order, so an
+ * instance gives the same bits alone and in a batch).  Partial sums are
+ * carried as compensated
  * (hi, lo) pairs of fp32 numbers, about 48 significant bits.  The map and
  * the reduce are fused: out is written in the same pass (loop fusion,
  * Sec. 5.1).
@@ -118,7 +122,8 @@ hx_status hx_map_reduce(hx_ctx *ctx, const float *x, const float *y, float *out,
  * because a context allocates its workspace.
  *
  * Computes exactly what hx_map_reduce computes with the built-in default
- * tuning table (same tile plan and device code, so the same results),
+ * tuning table (same tile plan and fold order, so the same results; here
+ * the warp that finishes last folds the tile partials, in one launch),
  * without a context and without allocating:
  * the reduction's scratch (HX_NOALLOC_MAX_TILES tile partials plus an
  * arrival ticket, about 33 KiB) is a static device array of this library,

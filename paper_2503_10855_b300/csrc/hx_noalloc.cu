@@ -9,8 +9,9 @@
 // per-tile partials and the arrival ticket) lives in a file-scope __device__
 // array that the CUDA module holds on every device that loads this library,
 // until the process exits.  The computation is exactly hx_map_reduce's with
-// the built-in default tuning (same tile plan, same device code), so the
-// results are the same.
+// the built-in default tuning (same tile plan, same fold order: the last
+// warp to arrive evaluates the canonical partial fold that hx_map_reduce's
+// second launch evaluates with a whole CTA), so the results are the same.
 #include <mutex>
 
 #include "hx_internal.cuh"
