@@ -597,6 +597,8 @@ def bench_hx(args, rank, world, local):
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
+        if args.log:
+            append_log(args.log, line)
     ctx.close()
     if dist:
         dist.destroy_process_group()
@@ -1086,6 +1088,45 @@ def bench_e2e(args, hx, ctx, dev, x_h, y_h, u_h, v_h, batch, batch_bufs, batch_b
                         "previous step's compute"}
 
 
+def log_rows(line):
+    """The measurements of one bench line as flat rows: one per kernel, size
+    sweep point, generic nest and serving rate, each with the run's clocks
+    and host core count."""
+    run = {"time": time.strftime("%Y-%m-%dT%H:%M:%S"), "n_gpus": line["n_gpus"],
+           "host_cores": len(os.sched_getaffinity(0)), "sm_mhz": line["clocks"].get("sm_mhz"),
+           "peak_gbs": line["roofline"]["peak"]}
+    nominal = 8000.0
+    rows = [dict(run, kind="step", ms=line["ms_per_step"], gbs=line["value"],
+                 frac_measured=line["frac_of_hbm_roofline"], frac_nominal=round(line["value"] / nominal, 4))]
+    for name, k in line["kernels"].items():
+        rows.append(dict(run, kind="kernel", name=name, ms=k["ms"], bytes=k["algorithmic_bytes"], gbs=k["GB/s"],
+                         frac_measured=k["frac_of_measured_hbm"], frac_nominal=round(k["GB/s"] / nominal, 4)))
+    for group, pts in (line.get("sweeps") or {}).items():
+        for p in pts:
+            gbs = p.get("GB/s", p.get("algorithmic_GB/s"))
+            rows.append(dict(run, kind="sweep", name=group, size=p.get("n") or p.get("grid") or p.get("input"),
+                             ms=p["ms"], gbs=gbs, frac_measured=p["frac_of_measured_hbm"],
+                             frac_nominal=round(gbs / nominal, 4)))
+    for w in ((line.get("nests") or {}).get("workloads") or []):
+        rows.append(dict(run, kind="nest", name=w["nest"], ms=w["ms"], bytes=w["algorithmic_bytes"], gbs=w["GB/s"],
+                         frac_measured=w["frac_of_measured_hbm"], frac_nominal=round(w["GB/s"] / nominal, 4)))
+    for p in ((line.get("serving") or {}).get("points") or []):
+        for mode in ("continuous", "per_launch"):
+            m = p[mode]
+            rows.append(dict(run, kind="serving", name=mode, offered_req_per_s=p["offered_req_per_s"],
+                             req_per_s=m["req_per_s"], p50_ms=m["p50_ms"], p99_ms=m["p99_ms"], stable=m["stable"]))
+    if line.get("e2e"):
+        rows.append(dict(run, kind="e2e", ms=line["e2e"]["ms_per_step"], gbs=line["e2e"]["value"]))
+    return rows
+
+
+def append_log(path, line):
+    """Append the run's rows to a JSON-lines log."""
+    with open(path, "a") as f:
+        for r in log_rows(line):
+            f.write(json.dumps(r) + "\n")
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1097,6 +1138,7 @@ def main():
     ap.add_argument("--no-serving", action="store_true", help="skip the serving sweep")
     ap.add_argument("--no-nests", action="store_true", help="skip the generic-nest section")
     ap.add_argument("--no-sweeps", action="store_true", help="skip the size sweeps")
+    ap.add_argument("--log", default=None, help="also append one JSON row per measurement to this file")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
