@@ -85,6 +85,24 @@ void hx_destroy(hx_ctx *ctx);
  * count == 0 clears the hook; negative arguments are HX_ERR_INVALID. */
 hx_status hx_debug_inject_launch_failures(hx_ctx *ctx, int32_t after, int32_t count);
 
+/* Device-side range checks (the library's debug build, libhx_debug.so,
+ * compiled with HX_DEBUG_CHECKS).  Its kernels check the index ranges of
+ * their work items (tile starts against n, partial indices against the
+ * workspace, batch runs against their instance, stencil blocks against the
+ * grid, ...) before using them; a failed check skips the work item (the
+ * results are then wrong) and records its code and two values, the first
+ * failure per kernel file only.  Nothing traps.  This call synchronises the
+ * device, then reports and clears the records:
+ *   enabled  1 in the debug build, 0 in the release build (whose kernels
+ *            check nothing; code, a and b are then 0).
+ *   code     0 when no check failed, else the first failure's code
+ *            (1 map tile start, 2 map partial index, 3 map fold length,
+ *            4 stencil block, 5 histogram split, 6 batch instance, 7 batch
+ *            run, 8 batch stencil block, 9 SRAD region tile, 10 no-alloc
+ *            tile) and the values it compared in a and b.
+ * All pointers must be non-NULL (HX_ERR_INVALID otherwise). */
+hx_status hx_debug_checks(int32_t *enabled, int32_t *code, int64_t *a, int64_t *b);
+
 /* ------------------------------------------------------------------ map->reduce
  * One fork of factor n (Sec. 3.3): thread i computes
  *     out[i] = fmaf(a, x[i], y[i])            (one rounding, fp32)

@@ -15,10 +15,14 @@ import ctypes
 import os
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "lib", "libhx.so")
+# HX_DEBUG=1 selects the debug build (device-side range checks, see
+# hx_debug_checks); otherwise the release build.
+DEBUG = os.environ.get("HX_DEBUG", "0") == "1"
+LIB_PATH = os.path.join(_HERE, "lib", "libhx_debug.so" if DEBUG else "libhx.so")
 
 if not os.path.exists(LIB_PATH):
-    raise ImportError(f"libhx.so is not built ({LIB_PATH}); run `python paper_2503_10855_b300/_build.py`")
+    raise ImportError(f"{os.path.basename(LIB_PATH)} is not built ({LIB_PATH}); run "
+                      f"`python paper_2503_10855_b300/_build.py{' --debug' if DEBUG else ''}`")
 
 _lib = ctypes.CDLL(LIB_PATH)
 
@@ -96,12 +100,31 @@ class Context:
 
 _lib.hx_debug_inject_launch_failures.argtypes = [_P, _I32, _I32]
 _lib.hx_debug_inject_launch_failures.restype = ctypes.c_int
+_lib.hx_debug_checks.argtypes = [ctypes.POINTER(_I32), ctypes.POINTER(_I32), ctypes.POINTER(_I64),
+                                 ctypes.POINTER(_I64)]
+_lib.hx_debug_checks.restype = ctypes.c_int
 
 
 def hx_debug_inject_launch_failures(ctx: "Context", count: int, after: int = 0) -> None:
     """Test hook: after ``after`` more launching calls on ``ctx``, ``count`` calls fail with HX_ERR_CUDA."""
     _check(_lib.hx_debug_inject_launch_failures(ctx.handle, int(after), int(count)),
            "hx_debug_inject_launch_failures")
+
+
+CHECK_NAMES = {1: "map tile start", 2: "map partial index", 3: "map fold length", 4: "stencil block",
+               5: "histogram split", 6: "batch instance", 7: "batch run", 8: "batch stencil block",
+               9: "SRAD region tile", 10: "no-alloc tile"}
+
+
+def hx_debug_checks():
+    """Synchronise the device and read (and clear) the device-side range-check
+    records: (enabled, code, a, b); enabled is False in the release build,
+    code 0 when no check failed (see CHECK_NAMES)."""
+    en, code = _I32(), _I32()
+    a, b = _I64(), _I64()
+    _check(_lib.hx_debug_checks(ctypes.byref(en), ctypes.byref(code), ctypes.byref(a), ctypes.byref(b)),
+           "hx_debug_checks")
+    return bool(en.value), int(code.value), int(a.value), int(b.value)
 
 
 def hx_create(device: int = 0, hbm_budget_bytes: int = 0) -> Context:

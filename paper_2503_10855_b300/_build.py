@@ -1,10 +1,13 @@
 """Build libhx.so (the C-ABI CUDA library) in-tree for sm_103a.
 
-Usage: ``python paper_2503_10855_b300/_build.py [--force] [-v]`` (run it as a
-file: importing the package requires the library this script builds).  Each ``.cu`` /
-``.cpp`` file under ``csrc/`` is compiled separately (in parallel) with nvcc
-and linked into ``paper_2503_10855_b300/lib/libhx.so`` with the CUDA runtime
-linked statically, so the library needs only the NVIDIA driver at run time.
+Usage: ``python paper_2503_10855_b300/_build.py [--force] [-v] [--debug]``
+(run it as a file: importing the package requires the library this script
+builds).  Each ``.cu`` / ``.cpp`` file under ``csrc/`` is compiled separately
+(in parallel) with nvcc and linked into ``paper_2503_10855_b300/lib/libhx.so``
+with the CUDA runtime linked statically, so the library needs only the NVIDIA
+driver at run time.  ``--debug`` builds ``lib/libhx_debug.so`` instead: the
+same sources with the device-side range checks of HX_DEBUG_CHECKS (the
+binding loads it when HX_DEBUG=1).
 """
 
 from __future__ import annotations
@@ -19,8 +22,10 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OBJ = os.path.join(PKG, "_build")
+OBJ_DEBUG = os.path.join(PKG, "_build_debug")
 LIB_DIR = os.path.join(PKG, "lib")
 LIB = os.path.join(LIB_DIR, "libhx.so")
+LIB_DEBUG = os.path.join(LIB_DIR, "libhx_debug.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -37,16 +42,18 @@ def _deps():
         glob.glob(os.path.join(ROOT, "include", "*.h"))
 
 
-def _stale() -> bool:
-    if not os.path.exists(LIB):
+def _stale(lib: str) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return any(os.path.getmtime(p) > t for p in _deps())
 
 
-def _compile(src: str, verbose: bool) -> str:
-    obj = os.path.join(OBJ, os.path.basename(src) + ".o")
+def _compile(src: str, verbose: bool, debug: bool) -> str:
+    obj = os.path.join(OBJ_DEBUG if debug else OBJ, os.path.basename(src) + ".o")
     cmd = [NVCC, *ARCH, *CFLAGS, "-c", src, "-o", obj]
+    if debug:
+        cmd.insert(1, "-DHX_DEBUG_CHECKS")
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     r = subprocess.run(cmd, capture_output=True, text=True)
@@ -57,21 +64,22 @@ def _compile(src: str, verbose: bool) -> str:
     return obj
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and not _stale():
-        return LIB
-    os.makedirs(OBJ, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, debug: bool = False) -> str:
+    lib = LIB_DEBUG if debug else LIB
+    if not force and not _stale(lib):
+        return lib
+    os.makedirs(OBJ_DEBUG if debug else OBJ, exist_ok=True)
     os.makedirs(LIB_DIR, exist_ok=True)
     with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
-        objs = list(ex.map(lambda s: _compile(s, verbose), _sources()))
-    tmp = LIB + f".{os.getpid()}.tmp"
+        objs = list(ex.map(lambda s: _compile(s, verbose, debug), _sources()))
+    tmp = lib + f".{os.getpid()}.tmp"
     cmd = [NVCC, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs, "-lnvrtc", "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, debug="--debug" in sys.argv))

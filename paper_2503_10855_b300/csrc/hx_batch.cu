@@ -78,6 +78,7 @@ batch_kernel(const BInst *__restrict__ insts, unsigned int n_inst, const uint32_
 
     for (unsigned int it = blockIdx.x; it < n_cta; it += gridDim.x) {
         const unsigned int i = find_instance(cta_prefix, n_inst, it);
+        if (!HX_CHECK(i < n_inst, kChkBatchInst, i, n_inst)) continue;
         const BInst &I = insts[i];
         batch_hist_item(I, I.t_first + (it - __ldg(cta_prefix + i)), sh);
     }
@@ -92,9 +93,17 @@ batch_kernel(const BInst *__restrict__ insts, unsigned int n_inst, const uint32_
         unsigned int next = 0u;
         if (lane == 0) next = atomicAdd(&ctrl[0], 1u);
         const unsigned int i = find_instance(run_prefix, n_inst, it);
+        if (!HX_CHECK(i < n_inst, kChkBatchInst, i, n_inst)) {
+            it = __shfl_sync(0xffffffffu, next, 0);
+            continue;
+        }
         const BInst &I = insts[i];
         const int64_t first = I.t_first + (int64_t)(it - __ldg(run_prefix + i)) * I.run_len;
         const unsigned int cnt = (unsigned int)min((int64_t)I.run_len, I.t_first + I.t_count - first);
+        if (!HX_CHECK(first >= 0 && first + cnt <= I.tiles, kChkBatchRun, first + cnt, I.tiles)) {
+            it = __shfl_sync(0xffffffffu, next, 0);
+            continue;
+        }
         if (I.kind == kKindMap) {
             const float *x = static_cast<const float *>(I.in0);
             const float *y = static_cast<const float *>(I.in1);
@@ -113,6 +122,7 @@ batch_kernel(const BInst *__restrict__ insts, unsigned int n_inst, const uint32_
                 const unsigned int tile = (unsigned int)(first + k);
                 const int wy = (int)(tile % (unsigned int)I.tiles_y), wx = (int)(tile / (unsigned int)I.tiles_y);
                 const int c_begin = wx * 128, r_begin = wy * kBatchStRows;
+                if (!HX_CHECK(c_begin < I.nx && r_begin < I.ny, kChkBatchStencil, c_begin, r_begin)) continue;
                 m = fmaxf(m, I.vec ? stencil_block_vec<kBatchStRows>(src, dst, I.nx, I.ny, c_begin, r_begin)
                                    : stencil_block_scalar<kBatchStRows>(src, dst, I.nx, I.ny, c_begin, r_begin));
             }
@@ -271,6 +281,8 @@ hx_status batch_setup(hx_ctx *ctx) {
     if (e != cudaSuccess) return cuda_fail(e, "hx_create: batch kernel set-up");
     return HX_OK;
 }
+
+HX_CHECKS_READER(checks_batch)
 
 }  // namespace hx
 

@@ -114,6 +114,35 @@ hx_status hx_debug_inject_launch_failures(hx_ctx *ctx, int32_t after, int32_t co
     return HX_OK;
 }
 
+hx_status hx_debug_checks(int32_t *enabled, int32_t *code, int64_t *a, int64_t *b) {
+    if (!enabled || !code || !a || !b) return hx::fail(HX_ERR_INVALID, "hx_debug_checks: NULL argument");
+#ifdef HX_DEBUG_CHECKS
+    *enabled = 1;
+#else
+    *enabled = 0;
+#endif
+    *code = 0;
+    *a = 0;
+    *b = 0;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return hx::cuda_fail(e, "hx_debug_checks: synchronize");
+    hx_status (*readers[])(int32_t *, int64_t *, int64_t *) = {hx::checks_map_reduce, hx::checks_stencil,
+                                                                hx::checks_histogram, hx::checks_batch,
+                                                                hx::checks_srad, hx::checks_noalloc};
+    for (auto rd : readers) {
+        int32_t c = 0;
+        int64_t x = 0, y = 0;
+        hx_status st = rd(&c, &x, &y);   // reads and clears every file's record
+        if (st != HX_OK) return st;
+        if (c != 0 && *code == 0) {
+            *code = c;
+            *a = x;
+            *b = y;
+        }
+    }
+    return HX_OK;
+}
+
 void hx_destroy(hx_ctx *ctx) {
     if (!ctx) return;
     hx::DeviceGuard g(ctx->device);

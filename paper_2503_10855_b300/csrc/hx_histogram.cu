@@ -23,6 +23,7 @@ histogram_kernel(const uint8_t *__restrict__ v, int64_t n, int head, int64_t nve
     hist_zero(sh);
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (!HX_CHECK(head + 16 * nvec + tail == n && head < 16 && tail < 16, kChkHistSplit, n, nvec)) nvec = 0;
     const unsigned int slot = hist_slot_offset();
     hist_count_strided(sh, slot, reinterpret_cast<const uint4 *>(v + head),
                        (int64_t)blockIdx.x * THREADS + threadIdx.x, (int64_t)gridDim.x * THREADS, nvec);
@@ -71,6 +72,8 @@ hx_status histogram_setup(hx_ctx *ctx) {
     }
     return HX_OK;
 }
+
+HX_CHECKS_READER(checks_histogram)
 
 }  // namespace hx
 

@@ -18,6 +18,63 @@
 
 namespace hx {
 
+// ---------------------------------------------------------------- checks
+// In the library's debug build (HX_DEBUG_CHECKS, libhx_debug.so) kernels
+// check the index ranges of their work items before using them.  A failed
+// check records (code, a, b) -- the first failure only -- and the work item
+// is skipped; nothing traps.  The record is per translation unit (the
+// library is built without relocatable device code); each kernel file
+// defines a reader with HX_CHECKS_READER and hx_debug_checks() asks them
+// all.  In the release build HX_CHECK is the constant true.
+#ifdef HX_DEBUG_CHECKS
+static __device__ unsigned long long g_check_rec[3];
+__device__ __forceinline__ bool check_ok(bool ok, int code, long long a, long long b) {
+    if (ok) return true;
+    if (atomicCAS(&g_check_rec[0], 0ull, (unsigned long long)code) == 0ull) {
+        g_check_rec[1] = (unsigned long long)a;
+        g_check_rec[2] = (unsigned long long)b;
+    }
+    return false;
+}
+#define HX_CHECK(cond, code, a, b) ::hx::check_ok((cond), (code), (long long)(a), (long long)(b))
+#define HX_CHECKS_READER(name)                                                                          \
+    hx_status name(int32_t *code, int64_t *a, int64_t *b) {                                             \
+        unsigned long long r[3] = {0, 0, 0};                                                            \
+        cudaError_t e = cudaMemcpyFromSymbol(r, g_check_rec, sizeof r);                                 \
+        if (e == cudaSuccess && r[0] != 0) {                                                            \
+            const unsigned long long z[3] = {0, 0, 0};                                                  \
+            e = cudaMemcpyToSymbol(g_check_rec, z, sizeof z);                                           \
+        }                                                                                               \
+        if (e != cudaSuccess) return cuda_fail(e, "hx_debug_checks");                                   \
+        *code = (int32_t)r[0];                                                                          \
+        *a = (int64_t)r[1];                                                                             \
+        *b = (int64_t)r[2];                                                                             \
+        return HX_OK;                                                                                   \
+    }
+#else
+#define HX_CHECK(cond, code, a, b) true
+#define HX_CHECKS_READER(name)                                                                          \
+    hx_status name(int32_t *code, int64_t *a, int64_t *b) {                                             \
+        *code = 0;                                                                                      \
+        *a = 0;                                                                                         \
+        *b = 0;                                                                                         \
+        return HX_OK;                                                                                   \
+    }
+#endif
+// Check codes (a, b): the values compared.
+enum : int {
+    kChkMapTile = 1,        // map->reduce tile start past n (tile, n)
+    kChkMapPartial = 2,     // tile partial index past the workspace (tile, capacity)
+    kChkMapFold = 3,        // tile count of a fold past the workspace (tiles, capacity)
+    kChkStencilBlock = 4,   // stencil warp block origin outside the grid (column, row)
+    kChkHistSplit = 5,      // histogram head + vectors + tail != n (n, vectors)
+    kChkBatchInst = 6,      // batch work item mapped to no instance (instance, count)
+    kChkBatchRun = 7,       // batch run past its instance's tiles (last tile, tiles)
+    kChkBatchStencil = 8,   // batch stencil block outside its grid (column, row)
+    kChkSradTile = 9,       // SRAD region tile index out of range (tile, tiles)
+    kChkNoAllocTile = 10,   // no-allocation call's tile past its scratch (tile, capacity)
+};
+
 // ---------------------------------------------------------------- constants
 constexpr int kWarp = 32;
 
@@ -611,6 +668,13 @@ inline int size_class(int64_t n) {
     return c;
 }
 hx_status batch_setup(hx_ctx *ctx);
+// Readers of each kernel file's check record (see HX_CHECKS_READER).
+hx_status checks_map_reduce(int32_t *code, int64_t *a, int64_t *b);
+hx_status checks_stencil(int32_t *code, int64_t *a, int64_t *b);
+hx_status checks_histogram(int32_t *code, int64_t *a, int64_t *b);
+hx_status checks_batch(int32_t *code, int64_t *a, int64_t *b);
+hx_status checks_srad(int32_t *code, int64_t *a, int64_t *b);
+hx_status checks_noalloc(int32_t *code, int64_t *a, int64_t *b);
 
 // Consumes one injected launch failure (hx_debug_inject_launch_failures):
 // true when the calling entry point must fail with HX_ERR_CUDA before it

@@ -26,6 +26,8 @@ map_reduce_kernel(const float *__restrict__ x, const float *__restrict__ y, floa
     asm volatile("griddepcontrol.launch_dependents;");
     const int64_t tile = (int64_t)blockIdx.x * kMrWarpsPerCta + (threadIdx.x >> 5);
     if (tile >= p.tiles) return;
+    if (!HX_CHECK(tile * p.tile_elems < p.n, kChkMapTile, tile, p.n)) return;
+    if (!HX_CHECK(tile < kMrMaxTiles, kChkMapPartial, tile, kMrMaxTiles)) return;
     const ff part = mr_tile<3>(x, y, out, a, p, tile, aligned, threadIdx.x & 31);
     if ((threadIdx.x & 31) == 0) st_keep2(ws->mr_partial + tile, make_float2(part.hi, part.lo));
 }
@@ -37,6 +39,7 @@ __global__ void __launch_bounds__(kMrFoldLanes) map_reduce_final_kernel(const fl
     __shared__ ff red[kMrFoldLanes];
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;");
+    if (!HX_CHECK(tiles <= kMrMaxTiles, kChkMapFold, tiles, kMrMaxTiles)) return;
     const ff sf = mr_final_cta(partials, tiles, red);
     if (threadIdx.x == 0) {
         const double s = ff_to_double(sf);
@@ -54,6 +57,8 @@ static bool overlaps(const void *a, size_t abytes, const void *b, size_t bbytes)
     const uintptr_t pa = (uintptr_t)a, pb = (uintptr_t)b;
     return pa < pb + bbytes && pb < pa + abytes;
 }
+
+HX_CHECKS_READER(checks_map_reduce)
 
 }  // namespace hx
 

@@ -53,6 +53,7 @@ map_reduce_noalloc_kernel(const float *__restrict__ x, const float *__restrict__
                           hx::MrPlan p, bool aligned, NoAllocScratch *scratch, float *d_sum, double *d_sum64) {
     const int64_t tile = (int64_t)blockIdx.x * hx::kMrWarpsPerCta + (threadIdx.x >> 5);
     if (tile >= p.tiles) return;
+    if (!HX_CHECK(tile < HX_NOALLOC_MAX_TILES, hx::kChkNoAllocTile, tile, HX_NOALLOC_MAX_TILES)) return;
     hx::mr_warp_item(x, y, out, a, p, tile, aligned, scratch->partial, &scratch->ticket, d_sum, d_sum64);
 }
 
@@ -62,6 +63,10 @@ __global__ void map_reduce_noalloc_empty_kernel(float *d_sum, double *d_sum64) {
 }
 
 }  // namespace
+
+namespace hx {
+HX_CHECKS_READER(checks_noalloc)
+}  // namespace hx
 
 extern "C" hx_status hx_map_reduce_noalloc(const float *x, const float *y, float *out, float a, int64_t n,
                                            float *d_sum, double *d_sum64, hx_stream_t stream) {

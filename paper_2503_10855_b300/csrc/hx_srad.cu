@@ -258,6 +258,7 @@ __global__ void __launch_bounds__(kThreads) srad_fused_kernel(const float *__res
     }
     if (in_roi) {
         const int roi_tile = (blockIdx.y - p.ty0) * p.ntx + (blockIdx.x - p.tx0);
+        if (!HX_CHECK(roi_tile >= 0 && roi_tile < p.roi_tiles, kChkSradTile, roi_tile, p.roi_tiles)) return;
         roi_publish(a, p, roi_tile, ws, q0sq_next);
     }
 }
@@ -301,6 +302,9 @@ __global__ void __launch_bounds__(kThreads) srad_update_kernel(const float *__re
 }
 
 }  // namespace
+
+HX_CHECKS_READER(checks_srad)
+
 }  // namespace hx
 
 extern "C" hx_status hx_srad(hx_ctx *ctx, float *J0, float *J1, float *C, int32_t nx, int32_t ny, int32_t iters,

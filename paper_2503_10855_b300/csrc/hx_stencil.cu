@@ -36,7 +36,7 @@ stencil_kernel(const float *__restrict__ src, float *__restrict__ dst, int nx, i
     const int c_begin = blockIdx.x * 128;
     const int r_begin = (blockIdx.y * kStWarps + warp) * R;
     float m = 0.0f;
-    if (r_begin < ny) {
+    if (r_begin < ny && HX_CHECK(c_begin < nx, kChkStencilBlock, c_begin, r_begin)) {
         m = VEC ? stencil_block_vec<R>(src, dst, nx, ny, c_begin, r_begin)
                 : stencil_block_scalar<R>(src, dst, nx, ny, c_begin, r_begin);
     }
@@ -77,6 +77,8 @@ __global__ void __launch_bounds__(256) stencil_resid_kernel(const float *__restr
         resid[blockIdx.x] = m;
     }
 }
+
+HX_CHECKS_READER(checks_stencil)
 
 }  // namespace hx
 

@@ -29,17 +29,33 @@ def test_header_declares_the_boundary():
         assert need in names
 
 
-def test_library_exports_every_declared_symbol():
+@pytest.mark.parametrize("name", ["libhx.so", "libhx_debug.so"])
+def test_library_exports_every_declared_symbol(name):
     import paper_2503_10855_b300 as hx
 
-    out = subprocess.run(["nm", "-D", "--defined-only", hx.LIB_PATH], capture_output=True, text=True,
+    path = os.path.join(os.path.dirname(hx.LIB_PATH), name)
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True,
                          check=True).stdout
     exported = {line.split()[-1] for line in out.splitlines() if line.strip()}
     missing = sorted(_declared() - exported)
     assert not missing, f"declared but not exported: {missing}"
-    lib = ctypes.CDLL(hx.LIB_PATH)
-    for name in _declared():
-        getattr(lib, name)
+    lib = ctypes.CDLL(path)
+    for sym in _declared():
+        getattr(lib, sym)
+
+
+def test_debug_checks_report_build_and_reject_null():
+    # release build: the kernels check nothing and the call says so; NULL
+    # arguments fail on the host before any device call
+    import paper_2503_10855_b300 as hx
+
+    lib = hx.lib()
+    I32, I64 = ctypes.c_int32, ctypes.c_int64
+    assert lib.hx_debug_checks(None, None, None, None) == hx.HX_ERR_INVALID
+    en = I32(-1)
+    assert lib.hx_debug_checks(ctypes.byref(en), None, ctypes.byref(I64()), ctypes.byref(I64())) == hx.HX_ERR_INVALID
+    if not hx.DEBUG:
+        assert "libhx.so" in hx.LIB_PATH
 
 
 def test_version_and_null_context_rejected_on_host():
