@@ -506,6 +506,15 @@ hx_status hx_batch_query(hx_ctx *ctx, uint64_t ticket);
  * buffers alive and untouched until the request completes. */
 typedef enum hx_serve_mode { HX_SERVE_CONTINUOUS = 0, HX_SERVE_PER_LAUNCH = 1 } hx_serve_mode;
 
+/* Completion callback: called once per request, from the server's completion
+ * thread and without the server's lock held (it may call hx_server_poll or
+ * hx_server_submit), after the request has completed (status HX_OK) or
+ * failed (HX_ERR_CUDA); latency_s as hx_server_poll reports it (for a
+ * failed request, the time until it failed).  Callbacks run in completion
+ * order, one at a time; a callback must not call hx_server_drain,
+ * hx_server_run_trace or hx_server_destroy. */
+typedef void (*hx_server_done_fn)(void *user, uint64_t req_id, hx_status status, double latency_s);
+
 typedef struct hx_server_config {
     int32_t mode;                 /* hx_serve_mode */
     int32_t max_inflight;         /* admitted, unfinished requests at most (0: 4096; at most 16384;
@@ -520,6 +529,8 @@ typedef struct hx_server_config {
                                    * least step_quantum_bytes (0: 32 MiB).  Larger requests are spread
                                    * over several steps. */
     size_t step_target_bytes;     /* continuous mode (0: 512 MiB) */
+    hx_server_done_fn on_done;    /* completion callback, or NULL */
+    void *on_done_user;           /* passed to on_done */
 } hx_server_config;
 
 typedef struct hx_server_stats {
@@ -549,8 +560,8 @@ hx_status hx_server_submit(hx_server *s, const hx_task *task, uint64_t *req_id);
  * HX_ERR_INVALID for an unknown id. */
 hx_status hx_server_poll(hx_server *s, uint64_t req_id, double *latency_s);
 
-/* Block until every submitted request has completed, at most timeout_s
- * seconds (HX_ERR_TIMEOUT otherwise).  HX_ERR_CUDA when a request completed
+/* Block until every submitted request has completed (and, with on_done,
+ * been reported), at most timeout_s seconds (HX_ERR_TIMEOUT otherwise).  HX_ERR_CUDA when a request completed
  * with a failed launch since the previous drain returned (hx_server_poll
  * tells which); HX_OK otherwise. */
 hx_status hx_server_drain(hx_server *s, double timeout_s);

@@ -17,6 +17,7 @@
 #include <mutex>
 #include <new>
 #include <thread>
+#include <tuple>
 #include <unordered_map>
 #include <vector>
 
@@ -84,6 +85,9 @@ struct hx_server {
     uint64_t failed_at_drain = 0;             // stats.failed when the last drain returned
     unsigned int *ctrl = nullptr;
     std::vector<int> free_ws;
+    // completions not yet reported to cfg.on_done: (id, status, latency)
+    std::vector<std::tuple<uint64_t, hx_status, double>> to_report;
+    bool reporting = false;                   // the completion thread is calling on_done
     uint64_t next_id = 1;
     size_t used = 0;
     int inflight = 0;
@@ -140,6 +144,8 @@ void fail_requests_locked(hx_server *s, std::vector<Req *> &rs, hx_status st) {
         r->status = st;
         r->issued_all = true;
         r->done = true;
+        r->latency = now_s() - r->arrival;
+        if (s->cfg.on_done) s->to_report.emplace_back(r->id, st, r->latency);
         s->used -= r->footprint;
         s->inflight -= 1;
         if (r->ws >= 0) {
@@ -156,6 +162,7 @@ void fail_requests_locked(hx_server *s, std::vector<Req *> &rs, hx_status st) {
     }
     s->stats.footprint_in_flight = s->used;
     s->cv_done.notify_all();
+    s->cv_compl.notify_all();
 }
 
 // Bytes of traffic one tile (histogram: one chunk) of an instance moves.
@@ -312,12 +319,27 @@ void scheduler_main(hx_server *s) {
     s->cv_compl.notify_all();
 }
 
+// Reports the collected completions to cfg.on_done with the lock released.
+void report_unlocked(hx_server *s, std::unique_lock<std::mutex> &lk) {
+    if (s->to_report.empty()) return;
+    std::vector<std::tuple<uint64_t, hx_status, double>> batch;
+    batch.swap(s->to_report);
+    s->reporting = true;
+    lk.unlock();
+    for (const auto &d : batch) s->cfg.on_done(s->cfg.on_done_user, std::get<0>(d), std::get<1>(d), std::get<2>(d));
+    lk.lock();
+    s->reporting = false;
+    s->cv_done.notify_all();
+}
+
 void completer_main(hx_server *s) {
     cudaSetDevice(s->ctx->device);
     std::unique_lock<std::mutex> lk(s->mu);
     for (;;) {
         while (s->steps.empty()) {
-            if (s->stop && s->queue.empty() && s->active.empty()) return;
+            report_unlocked(s, lk);
+            if (s->stop && s->queue.empty() && s->active.empty() && s->to_report.empty()) return;
+            if (!s->steps.empty()) break;
             s->cv_compl.wait_for(lk, std::chrono::milliseconds(5));
         }
         cudaEvent_t ev = s->steps.front().ev;
@@ -337,12 +359,14 @@ void completer_main(hx_server *s) {
             if (r->ws >= 0) s->free_ws.push_back(r->ws);
             r->ws = -1;
             s->stats.completed += 1;
+            if (s->cfg.on_done) s->to_report.emplace_back(r->id, r->status, r->latency);
         }
         s->stats.footprint_in_flight = s->used;
         if (step.slot >= 0) s->slots[step.slot].busy = false;
         else s->free_events.push_back(step.ev);
         s->cv_sched.notify_all();
         s->cv_done.notify_all();
+        report_unlocked(s, lk);
     }
 }
 
@@ -472,9 +496,10 @@ hx_status hx_server_drain(hx_server *s, double timeout_s) {
     if (!s) return hx::fail(HX_ERR_INVALID, "hx_server_drain: server is NULL");
     std::unique_lock<std::mutex> lk(s->mu);
     const auto deadline = std::chrono::steady_clock::now() + std::chrono::duration<double>(timeout_s);
-    while (s->stats.completed < s->stats.submitted) {
-        if (s->cv_done.wait_until(lk, deadline) == std::cv_status::timeout &&
-            s->stats.completed < s->stats.submitted)
+    // every request completed, and every completion reported to on_done
+    auto settled = [s] { return s->stats.completed >= s->stats.submitted && s->to_report.empty() && !s->reporting; };
+    while (!settled()) {
+        if (s->cv_done.wait_until(lk, deadline) == std::cv_status::timeout && !settled())
             return hx::fail(HX_ERR_TIMEOUT, "hx_server_drain: requests still pending at the timeout");
     }
     const bool new_failures = s->stats.failed > s->failed_at_drain;

@@ -108,10 +108,15 @@ def test_server_failed_step_fails_its_requests_and_recycles(gpu):
             else:
                 specs.append({"kind": kind, "n": 1_000_000 + 17 * k, "seed": seed0 + k})
         return [Inst(s) for s in specs]
+    reports = {}
+
+    def on_done(rid, status, latency):
+        reports.setdefault(rid, []).append(status)
+
     with hx.hx_create(0) as ctx:
         # 64 KiB slices: every request spans several steps; the third step fails
         with hx.Server(ctx, mode=0, step_quantum_bytes=64 << 10, step_target_bytes=64 << 10,
-                       max_steps_in_flight=2) as srv:
+                       max_steps_in_flight=2, on_done=on_done) as srv:
             first = wave(100)
             hx.hx_debug_inject_launch_failures(ctx, 1, after=2)
             ids = [srv.submit(i.task(hx)) for i in first]
@@ -130,6 +135,9 @@ def test_server_failed_step_fails_its_requests_and_recycles(gpu):
                 inst.check_oracle(inst.result())
             st = srv.stats()
             assert failed >= 1 and st["failed"] == failed
+            # the completion callback saw each request once, with its outcome
+            assert sorted(reports) == sorted(ids) and all(len(v) == 1 for v in reports.values())
+            assert sum(v[0] == hx.HX_ERR_CUDA for v in reports.values()) == failed
             # a second wave reuses the recycled workspace slots
             second = wave(200)
             ids = [srv.submit(i.task(hx)) for i in second]

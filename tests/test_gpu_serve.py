@@ -105,3 +105,34 @@ def test_submit_poll_drain(gpu):
             inst.check_oracle(inst.result())
         assert insts[3].s32.item() == 0.0
         assert torch.equal(insts[4].u0, insts[4].u_init)
+
+
+@pytest.mark.parametrize("mode", ["continuous", "per_launch"])
+def test_completion_callback(gpu, mode):
+    # every request is reported exactly once, after it completed, with the
+    # latency hx_server_poll reports; drain returns only after the reports
+    import threading
+
+    hx = gpu
+    specs = [{"kind": ("map_reduce", "stencil", "histogram")[k % 3], "seed": 50 + k, "a": 1.5,
+              "n": 20_000 + 91_003 * k, "nx": 40 + 17 * k, "ny": 33 + 5 * k, "iters": 1 + k % 3} for k in range(18)]
+    insts = [Inst(s) for s in specs]
+    seen, lock = [], threading.Lock()
+
+    def on_done(rid, status, latency):
+        with lock:
+            seen.append((rid, status, latency))
+
+    m = hx.HX_SERVE_CONTINUOUS if mode == "continuous" else hx.HX_SERVE_PER_LAUNCH
+    with hx.hx_create(0) as ctx:
+        with hx.Server(ctx, mode=m, on_done=on_done) as srv:
+            ids = [srv.submit(i.task(hx)) for i in insts]
+            srv.drain(60.0)
+            with lock:
+                got = {rid: (st, lat) for rid, st, lat in seen}
+            assert len(seen) == len(ids) and set(got) == set(ids)
+            for rid in ids:
+                done, lat = srv.poll(rid)
+                assert done and got[rid][0] == hx.HX_OK and got[rid][1] == lat
+        for inst in insts:
+            inst.check_oracle(inst.result())
