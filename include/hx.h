@@ -99,7 +99,8 @@ hx_status hx_debug_inject_launch_failures(hx_ctx *ctx, int32_t after, int32_t co
  *            (1 map tile start, 2 map partial index, 3 map fold length,
  *            4 stencil block, 5 histogram split, 6 batch instance, 7 batch
  *            run, 8 batch stencil block, 9 SRAD region tile, 10 no-alloc
- *            tile) and the values it compared in a and b.
+ *            tile, 11 nest chunk partial, 12 nest group partial, 13 nest
+ *            arrival ticket) and the values it compared in a and b.
  * All pointers must be non-NULL (HX_ERR_INVALID otherwise). */
 hx_status hx_debug_checks(int32_t *enabled, int32_t *code, int64_t *a, int64_t *b);
 

@@ -113,7 +113,8 @@ def hx_debug_inject_launch_failures(ctx: "Context", count: int, after: int = 0) 
 
 CHECK_NAMES = {1: "map tile start", 2: "map partial index", 3: "map fold length", 4: "stencil block",
                5: "histogram split", 6: "batch instance", 7: "batch run", 8: "batch stencil block",
-               9: "SRAD region tile", 10: "no-alloc tile"}
+               9: "SRAD region tile", 10: "no-alloc tile", 11: "nest chunk partial", 12: "nest group partial",
+               13: "nest arrival ticket"}
 
 
 def hx_debug_checks():

@@ -128,7 +128,8 @@ hx_status hx_debug_checks(int32_t *enabled, int32_t *code, int64_t *a, int64_t *
     if (e != cudaSuccess) return hx::cuda_fail(e, "hx_debug_checks: synchronize");
     hx_status (*readers[])(int32_t *, int64_t *, int64_t *) = {hx::checks_map_reduce, hx::checks_stencil,
                                                                 hx::checks_histogram, hx::checks_batch,
-                                                                hx::checks_srad, hx::checks_noalloc};
+                                                                hx::checks_srad, hx::checks_noalloc,
+                                                                hx::checks_nest};
     for (auto rd : readers) {
         int32_t c = 0;
         int64_t x = 0, y = 0;

@@ -73,6 +73,8 @@ enum : int {
     kChkBatchStencil = 8,   // batch stencil block outside its grid (column, row)
     kChkSradTile = 9,       // SRAD region tile index out of range (tile, tiles)
     kChkNoAllocTile = 10,   // no-allocation call's tile past its scratch (tile, capacity)
+    // 11 nest chunk partial, 12 nest group partial, 13 nest arrival ticket:
+    // checked inside the generated nest kernels (same meaning: index, capacity)
 };
 
 // ---------------------------------------------------------------- constants
@@ -675,6 +677,7 @@ hx_status checks_histogram(int32_t *code, int64_t *a, int64_t *b);
 hx_status checks_batch(int32_t *code, int64_t *a, int64_t *b);
 hx_status checks_srad(int32_t *code, int64_t *a, int64_t *b);
 hx_status checks_noalloc(int32_t *code, int64_t *a, int64_t *b);
+hx_status checks_nest(int32_t *code, int64_t *a, int64_t *b);   // every loaded generated nest kernel
 
 // Consumes one injected launch failure (hx_debug_inject_launch_failures):
 // true when the calling entry point must fail with HX_ERR_CUDA before it

@@ -54,6 +54,23 @@ constexpr int kNestBlock = 256;
 const char *kPrelude = R"CUDA(
 typedef long long i64;
 typedef unsigned long long u64;
+// Range checks of the debug build (HX_DEBUG_CHECKS): the first failure's
+// code and values in hx_check_rec, the access skipped, nothing trapped.
+#ifdef HX_DEBUG_CHECKS
+extern "C" __device__ unsigned long long hx_check_rec[3];
+__device__ unsigned long long hx_check_rec[3];
+__device__ __forceinline__ bool check_ok(bool ok, int code, long long a, long long b) {
+    if (ok) return true;
+    if (atomicCAS(&hx_check_rec[0], 0ull, (unsigned long long)code) == 0ull) {
+        hx_check_rec[1] = (unsigned long long)a;
+        hx_check_rec[2] = (unsigned long long)b;
+    }
+    return false;
+}
+#define HX_CHECK(cond, code, a, b) check_ok((cond), (code), (long long)(a), (long long)(b))
+#else
+#define HX_CHECK(cond, code, a, b) true
+#endif
 struct NestParams {
     const float *in[4];
     i64 st[4][3];
@@ -339,6 +356,8 @@ __device__ __forceinline__ void item_tree(const NestParams &p, const Seg &g, i64
     const i64 grp = c >> 5;
     const int gsize = (int)min((i64)32, p.nchunks - grp * 32);
     unsigned *t1 = p.tick + g.s * p.ngroups + grp;
+    if (!HX_CHECK(item < HX_NEST_CAP, 11, item, HX_NEST_CAP)) return;
+    if (!HX_CHECK(g.s * p.ngroups + grp < HX_NEST_TICK, 13, g.s * p.ngroups + grp, HX_NEST_TICK)) return;
     unsigned last = 0;
     if (lane == 0) {
         part_store(p.part + item, acc);
@@ -357,6 +376,8 @@ __device__ __forceinline__ void item_tree(const NestParams &p, const Seg &g, i64
         return;
     }
     // Level 2: the last group of the segment folds the group partials.
+    if (!HX_CHECK(g.s * p.ngroups + grp < HX_NEST_CAP2 && g.s < HX_NEST_TICK2, 12, g.s * p.ngroups + grp,
+                  HX_NEST_CAP2)) return;
     last = 0;
     if (lane == 0) {
         *t1 = 0u;
@@ -499,6 +520,7 @@ extern "C" __global__ void __launch_bounds__(256) hx_nest_kernel(const NestParam
             write_result(p, g.s, acc);
             continue;
         }
+        if (!HX_CHECK(item < HX_NEST_CAP && g.s < HX_NEST_TICK, 11, item, HX_NEST_CAP)) continue;
         part_store(p.part + item, acc);
         __threadfence();
         if (atomicAdd(p.tick + g.s, 1u) == (unsigned)(p.nchunks - 1)) {
@@ -769,6 +791,11 @@ std::string generate(const hx_nest *n, const Shape &sh) {
     src += fmt("#define MONOID %d\n#define TREE %d\n#define G %d\n#define U %d\n#define VEC %d\n", sh.monoid, sh.tree,
                sh.G, sh.U, sh.vec ? 1 : 0);
     src += fmt("#define HAS_OUT %d\n#define HAS_RES64 %d\n", sh.has_out ? 1 : 0, sh.has_res64 ? 1 : 0);
+    src += fmt("#define HX_NEST_CAP %d\n#define HX_NEST_CAP2 %d\n#define HX_NEST_TICK %d\n#define HX_NEST_TICK2 %d\n",
+               hx::kNestCap, hx::kNestCap2, hx::kNestTick, hx::kNestTick2);
+#ifdef HX_DEBUG_CHECKS
+    src += "#define HX_DEBUG_CHECKS 1\n";
+#endif
     src += kPrelude;
     bool inner_index_used = false;
     for (int d = sh.m; d < sh.ndim; ++d) inner_index_used = inner_index_used || sh.index_used[d];
@@ -998,6 +1025,37 @@ void magic(int64_t d, uint32_t *m, uint32_t *s) {
 }
 
 }  // namespace
+
+namespace hx {
+// The check records of every loaded generated kernel (debug build): the
+// first non-empty one is reported; all are cleared.
+hx_status checks_nest(int32_t *code, int64_t *a, int64_t *b) {
+    *code = 0;
+    *a = 0;
+    *b = 0;
+#ifdef HX_DEBUG_CHECKS
+    std::lock_guard<std::mutex> lk(g_mu);
+    for (auto &kv : g_cache) {
+        Compiled *c = kv.second;
+        if (!c->lib) continue;
+        void *d = nullptr;
+        size_t bytes = 0;
+        cudaError_t e = cudaLibraryGetGlobal(&d, &bytes, c->lib, "hx_check_rec");
+        if (e != cudaSuccess || bytes < 3 * sizeof(unsigned long long)) return cuda_fail(e, "hx_debug_checks: nest record");
+        unsigned long long r[3];
+        e = cudaMemcpy(r, d, sizeof r, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess && r[0] != 0) e = cudaMemset(d, 0, sizeof r);
+        if (e != cudaSuccess) return cuda_fail(e, "hx_debug_checks: nest record");
+        if (r[0] != 0 && *code == 0) {
+            *code = (int32_t)r[0];
+            *a = (int64_t)r[1];
+            *b = (int64_t)r[2];
+        }
+    }
+#endif
+    return HX_OK;
+}
+}  // namespace hx
 
 extern "C" {
 

@@ -81,6 +81,22 @@ with hx.hx_create(0) as ctx:
         ref32, _ = oracle.srad(J, 3, 0.5, roi, "f32")
         ok &= np.array_equal(out.cpu().numpy().view(np.uint32), ref32.view(np.uint32))
         hx.hx_srad(ctx, J0, torch.empty_like(J0), 2, 0.5, roi, fused=False)
+    # generic nests: warp tree with one and several chunks per segment,
+    # narrow segments, a permuted 3-D view, the chunk and sequential trees
+    big = torch.rand(1 << 22, device=dev) * 2 - 1
+    nest_cases = [
+        ([("in", 0)], [big], (1 << 22,), 1, "sum", "warp"),
+        ([("in", 0)], [big.view(1024, 4096)], (1024, 4096), 1, "max", "warp"),
+        ([("in", 0)], [big[: (1 << 22) - 8].view(-1, 8)], (((1 << 22) - 8) // 8, 8), 1, "argmin", "warp"),
+        ([("in", 0)], [big.view(64, 256, 256).permute(1, 0, 2)], (256, 64, 256), 2, "sum", "warp"),
+        ([("in", 0), "abs"], [big[:100_003]], (100_003,), 1, "max", "chunk"),
+        ([("in", 0)], [big[:4099]], (4099,), 1, "prod", "seq"),
+    ]
+    for prog, ins, dims, rd, mono, tree in nest_cases:
+        _, res, _, r64 = hx.fork_reduce(ctx, prog, ins, dims, rd, mono, want_result64=(mono in ("sum", "prod")),
+                                        tree=tree)
+        if mono == "sum" and rd == 1 and len(dims) == 1:
+            ok &= abs(float(r64.item()) - float(big.double().sum().item())) <= 1e-9 * float(big.abs().sum())
     torch.cuda.synchronize()
     enabled, code, a, b = hx.hx_debug_checks()
 print(json.dumps({"enabled": enabled, "code": code, "a": a, "b": b, "results_ok": bool(ok)}))
