@@ -1077,6 +1077,14 @@ def bench_e2e(args, hx, ctx, dev, x_h, y_h, u_h, v_h, batch, batch_bufs, batch_b
         b.record(s)
         torch.cuda.synchronize()
     ms = a.elapsed_time(b) / steps
+    # the last step's read-back must hold this step's results: the histogram
+    # exactly, the map->reduce sum within the fp64 reference's tolerance
+    got_bins = res_h[16 + 4 * ST_ITERS:16 + 4 * ST_ITERS + 1024].view(torch.int32).numpy().view(np.uint32)
+    want_bins = np.bincount(v_h.ravel(), minlength=256).astype(np.uint32)
+    ref_out = 1.5 * x_h.astype(np.float64) + y_h.astype(np.float64)
+    got_sum = float(res_h[8:16].view(torch.float64).item())
+    if not np.array_equal(got_bins, want_bins) or abs(got_sum - ref_out.sum()) > 1e-5 * np.abs(ref_out).sum():
+        raise RuntimeError("e2e: the read-back results differ from the step's expected results")
     for p in plans:
         p.close()
     del arenas, views, stage
