@@ -233,7 +233,7 @@ hx_status hx_histogram(hx_ctx *ctx, const uint8_t *v, int64_t n, uint32_t *d_bin
  *            the same pass); 0: region reduce, coefficient and update as
  *            three kernels per iteration.  Both give bit-identical results.
  *   1 <= nx, ny <= 65536, nx*ny <= 2^31; the region must be non-empty and
- *   inside the image and span at most 65536 tiles of 16 x 128 pixels.
+ *   inside the image and span at most 65536 tiles of 32 x 128 pixels.
  * A homogeneous region (q0sq == 0) makes the coefficient 0/0: the image
  * becomes NaN, as the formula says. */
 hx_status hx_srad(hx_ctx *ctx, float *J0, float *J1, float *C, int32_t nx, int32_t ny, int32_t iters,

@@ -6,7 +6,7 @@
 // (Sec. 5.1) and turns the large sum into a GPU-only reduction tree
 // (Sec. 5.2).  Here:
 //
-//   fused (one kernel per iteration): a CTA loads its 16 x 128 output tile
+//   fused (one kernel per iteration): a CTA loads its 32 x 128 output tile
 //   of J plus a halo into shared memory, computes c for the tile and one
 //   extra row and column (the south / east neighbours' coefficients) into
 //   shared memory, writes J', and accumulates the region-of-interest sums of
@@ -29,7 +29,7 @@ namespace hx {
 namespace {
 
 constexpr int kTX = 128;          // tile columns
-constexpr int kTY = 16;           // tile rows
+constexpr int kTY = 32;           // tile rows
 constexpr int kThreads = 256;
 constexpr int kJsW = kTX + 8;     // J tile: rows i0-1 .. i0+TY+1, cols j0-1 .. j0+TX+1 at x = 3 .. 133
 constexpr int kJsH = kTY + 3;
