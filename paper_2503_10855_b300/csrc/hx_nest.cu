@@ -28,9 +28,9 @@
 //   HX_TREE_SEQ    the untransformed loop: one thread folds a whole segment.
 // Sums and products accumulate in float-float (hi, lo) pairs; extrema are
 // exact.  The combination order depends only on the nest's sizes, schedule,
-// chunk and tuning table -- not on pointer alignment (the float4 and scalar
-// load paths assign the same elements to the same lanes) -- so results are
-// bit-identical from run to run.
+// chunk, tuning table and the number of warps the device holds at once --
+// not on pointer alignment (the float4 and scalar load paths assign the same
+// elements to the same lanes) -- so results are bit-identical from run to run.
 #include <nvrtc.h>
 
 #include <cstdarg>
@@ -1000,6 +1000,53 @@ void one_wave(const hx_nest *n, const Shape &sh, int64_t outer, int64_t inner, i
     sp->ngroups = (sp->nchunks + 31) / 32;
 }
 
+// A large warp-tree SUM takes about 2.7 chunks per resident warp instead of
+// one.  The grid holds at most 2048 threads per SM, so a warp then folds one
+// to three chunks and the CTAs run as waves whose last one is nearly full.
+// Measured on a B300 (fraction of copy bandwidth, one chunk per warp against
+// this split): 2^28 sum 0.95 -> 1.01, 1024 x 512 x 512 permuted reduce
+// 0.90 -> 0.95, rows of 163840 0.93 -> 1.03, rows of 65536 0.95 -> 1.01.
+// Load counts just above a whole number of waves (x = items / resident warps
+// in 2.0-2.2 or 1.1-1.3) measured 0.77-0.94, so x is kept in 1.8-2.9.
+// Chunks of a multiple of 16384 elements (64 KiB) measured 3-4 % slower than
+// their neighbours and are avoided.  Chunks shorter than 8192 elements (a 2^26
+// sum) lose more to the larger tree than they gain, and the exact monoids
+// (max, min, argmax ...) measured fastest at one chunk per warp (max |x| over
+// 2^28: 0.97 against 0.91), so both keep one_wave.  Returns whether it split.
+bool spread_sum(const hx_nest *n, const Shape &sh, int64_t outer, int64_t inner, int64_t warps, Split *sp) {
+    if (n->tree != HX_TREE_WARP || sh.G != 32 || sh.monoid != HX_MONOID_SUM || n->chunk > 0 || warps < 1) return false;
+    const double target = 2.7 * (double)warps;
+    if ((double)(outer * sp->nchunks) <= target) return false;
+    int64_t p0 = (int64_t)(target / (double)outer + 0.5);
+    if (p0 < 1) p0 = 1;
+    int64_t best_chunk = 0;
+    int best_bad = 4;
+    double best_dist = 0;
+    for (int64_t d = 0; d <= 16; ++d) {
+        for (int side = 0; side < 2; ++side) {
+            if (d == 0 && side == 1) continue;
+            const int64_t p = side == 0 ? p0 + d : p0 - d;
+            if (p < 1 || p > sp->nchunks) continue;   // p <= the tuned count keeps the workspace bounds
+            int64_t chunk = (inner + p - 1) / p;
+            chunk = (chunk + 511) / 512 * 512;
+            const int64_t nch = (inner + chunk - 1) / chunk;
+            const double x = (double)(outer * nch) / (double)warps;
+            const int bad = (chunk % 16384 == 0 ? 2 : 0) + (x >= 1.8 && x <= 2.9 ? 0 : 1);
+            const double dist = x > 2.7 ? x - 2.7 : 2.7 - x;
+            if (bad < best_bad || (bad == best_bad && dist < best_dist)) {
+                best_bad = bad;
+                best_dist = dist;
+                best_chunk = chunk;
+            }
+        }
+    }
+    if (best_chunk < 8192) return false;
+    sp->chunk = best_chunk;
+    sp->nchunks = (inner + best_chunk - 1) / best_chunk;
+    sp->ngroups = (sp->nchunks + 31) / 32;
+    return true;
+}
+
 hx_status prepare(const hx_nest *n, const hx_tune_table *tune, Compiled **c, Shape *sh, Split *sp, int64_t *outer,
                   int64_t *inner) {
     hx_status st = validate(n);
@@ -1095,7 +1142,8 @@ hx_status hx_fork_reduce(hx_ctx *ctx, const hx_nest *nest, hx_stream_t stream) {
     if (st != HX_OK) return st;
     st = load(c);
     if (st != HX_OK) return st;
-    one_wave(nest, sh, outer, inner, (int64_t)ctx->num_sms * c->ctas_per_sm * (kNestBlock / 32), &sp);
+    const int64_t warps = (int64_t)ctx->num_sms * c->ctas_per_sm * (kNestBlock / 32);
+    if (!spread_sum(nest, sh, outer, inner, warps, &sp)) one_wave(nest, sh, outer, inner, warps, &sp);
     if (hx::take_injected_failure(ctx))
         return hx::fail(HX_ERR_CUDA, "hx_fork_reduce: injected launch failure (test hook)");
     hx::NestWs *ws = ctx->nest_ws + (slot - ctx->ws);

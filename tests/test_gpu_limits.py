@@ -157,7 +157,7 @@ def test_nest_reductions_past_2p31(gpu, ctx):
     period = 1024
     k = torch.arange(period, dtype=torch.float64, device=DEV)
     x = (1.0 + k / period).float().repeat(n // period + 1)[:n]
-    # sum over a linear input (float4 slots, one chunk per resident warp)
+    # sum over a linear input (float4 slots, about 2.7 chunks per resident warp)
     _, r, _, r64 = gpu.fork_reduce(ctx, [("in", 0)], [x], (n,), 1, "sum", want_result64=True)
     torch.cuda.synchronize()
     exact = _ramp_sum(n)

@@ -180,6 +180,16 @@ def test_large_full_reduce_caps_partials(gpu):
             _check(hx, ctx, [("in", 0), "abs"], [x], ident, (n,), 1, monoid, want_out=False)
 
 
+@pytest.mark.parametrize("dims", [(700, 150_001), (110_000_003,)])
+def test_large_sums_spread_chunks(gpu, dims):
+    # sums past 2.7 chunks per resident warp get longer chunks, about 2.7 per
+    # warp (ragged last chunks; the odd row length takes the element path)
+    hx = gpu
+    x = _np(dims, 121)
+    with hx.hx_create(0) as ctx:
+        _check(hx, ctx, [("in", 0), ("in", 0), "mul"], [x], ident, dims, 1, "sum", want_out=False)
+
+
 def test_empty_segments_give_identities(gpu):
     hx = gpu
     with hx.hx_create(0) as ctx:
