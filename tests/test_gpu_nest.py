@@ -190,6 +190,16 @@ def test_large_sums_spread_chunks(gpu, dims):
         _check(hx, ctx, [("in", 0), ("in", 0), "mul"], [x], ident, dims, 1, "sum", want_out=False)
 
 
+def test_large_dot_spreads_chunks(gpu):
+    # a two-input sum (2 CTAs per SM, so fewer resident warps) past the
+    # spreading threshold, with an odd length (element path, ragged last chunk)
+    hx = gpu
+    n = 100_000_001
+    x, y = _np((n,), 122), _np((n,), 123)
+    with hx.hx_create(0) as ctx:
+        _check(hx, ctx, [("in", 0), ("in", 1), "mul"], [x, y], ident, (n,), 1, "sum", want_out=False)
+
+
 def test_empty_segments_give_identities(gpu):
     hx = gpu
     with hx.hx_create(0) as ctx:
