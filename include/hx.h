@@ -274,7 +274,10 @@ hx_status hx_srad(hx_ctx *ctx, float *J0, float *J1, float *C, int32_t nx, int32
  *               result_index = its position r inside the segment (0..I-1);
  *               (-inf / +inf, -1) when the segment is empty or all NaN.
  * Every result is deterministic: the combination order depends only on the
- * sizes, the tree, the chunk and the tuning table.
+ * sizes, the tree, the chunk, the tuning table and, for HX_TREE_WARP with
+ * chunk 0, how many warps the device holds at once.  (A large reduction gets
+ * longer chunks than the tuning table's: about 2.7 per resident warp for SUM,
+ * one per resident warp for the other monoids.)
  *
  * Reduction schedule (`tree`), after the paper's reduction-tree schedule
  * (Sec. 5.2: chunk, reassociate the monoid, fission) and its lowering of
@@ -377,7 +380,7 @@ hx_status hx_nest_source(const hx_nest *nest, char *buf, size_t cap, size_t *len
  *   nest_lane_elems[c]  elements per lane of one warp-tree chunk of a
  *                    generic nest whose segments hold n elements, n in class
  *                    c (a multiple of 8 in [8, 512]; raised automatically so
- *                    that a nest never needs more than 16384 chunk partials).
+ *                    that a nest never needs more than 65536 chunk partials).
  *                    Like map_vecs it fixes the summation tree.
  *   batch_map_run, batch_stencil_run: tiles per warp run in batches.
  * Size class c holds sizes in [2^c, 2^(c+1)); sizes 0 and 1 are class 0.
