@@ -91,6 +91,7 @@ struct hx_server {
     uint64_t next_id = 1;
     size_t used = 0;
     int inflight = 0;
+    bool issuing = false;                     // per-launch mode: launches in progress without the lock
     bool stop = false;
     hx_server_stats stats{};
     std::thread sched, compl_thr;
@@ -264,11 +265,27 @@ bool issue_step_locked(hx_server *s) {
     return true;
 }
 
-// Per-launch mode: each admitted request as its own standalone call(s).
-bool issue_per_launch_locked(hx_server *s) {
-    bool any = false;
-    for (Req *r : s->active) {
-        const hx_task &t = r->task;
+// Per-launch mode: each admitted request as its own standalone call(s).  A
+// stencil request is 20 or more launches, so the launches run with the lock
+// released: the completion thread (which takes the lock between events) and
+// submitters are not held up by a backlog being issued.  The requests taken
+// from `active` are reachable from this thread only until their step is
+// queued.
+bool issue_per_launch(hx_server *s, std::unique_lock<std::mutex> &lk) {
+    if (s->active.empty()) return false;
+    std::vector<Req *> batch;
+    batch.swap(s->active);
+    s->issuing = true;
+    for (Req *r : batch) {
+        const hx_task t = r->task;
+        cudaEvent_t ev = nullptr;
+        if (!s->free_events.empty()) {
+            ev = s->free_events.back();
+            s->free_events.pop_back();
+        }
+        s->stats.launches += 1;
+        r->issued_all = true;
+        lk.unlock();
         hx_status st = HX_OK;
         if (t.kind == HX_TASK_MAP_REDUCE)
             st = hx_map_reduce(s->ctx, t.u.mr.x, t.u.mr.y, t.u.mr.out, t.u.mr.a, t.u.mr.n, t.u.mr.sum, t.u.mr.sum64,
@@ -278,16 +295,12 @@ bool issue_per_launch_locked(hx_server *s) {
                               (hx_stream_t)s->stream);
         else
             st = hx_histogram(s->ctx, t.u.hi.v, t.u.hi.n, t.u.hi.bins, t.u.hi.scan, (hx_stream_t)s->stream);
-        s->stats.launches += 1;
-        r->issued_all = true;
-        cudaEvent_t ev = nullptr;
-        if (!s->free_events.empty()) {
-            ev = s->free_events.back();
-            s->free_events.pop_back();
-        } else if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+        if (!ev && cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+            ev = nullptr;
             st = HX_ERR_CUDA;
         }
         if (st == HX_OK && cudaEventRecord(ev, s->stream) != cudaSuccess) st = HX_ERR_CUDA;
+        lk.lock();
         std::vector<Req *> one{r};
         if (st != HX_OK) {
             if (ev) s->free_events.push_back(ev);
@@ -297,12 +310,12 @@ bool issue_per_launch_locked(hx_server *s) {
             step.ev = ev;
             step.finishing = one;
             s->steps.push_back(std::move(step));
+            s->cv_compl.notify_one();
         }
-        any = true;
     }
-    s->active.clear();
-    if (any) s->cv_compl.notify_one();
-    return any;
+    s->issuing = false;
+    s->cv_compl.notify_all();
+    return true;
 }
 
 void scheduler_main(hx_server *s) {
@@ -313,7 +326,7 @@ void scheduler_main(hx_server *s) {
         if (s->stop && s->queue.empty() && s->active.empty()) break;
         bool issued = false;
         if (!s->active.empty())
-            issued = s->cfg.mode == HX_SERVE_CONTINUOUS ? issue_step_locked(s) : issue_per_launch_locked(s);
+            issued = s->cfg.mode == HX_SERVE_CONTINUOUS ? issue_step_locked(s) : issue_per_launch(s, lk);
         if (!issued) s->cv_sched.wait_for(lk, std::chrono::microseconds(200));
     }
     s->cv_compl.notify_all();
@@ -338,7 +351,7 @@ void completer_main(hx_server *s) {
     for (;;) {
         while (s->steps.empty()) {
             report_unlocked(s, lk);
-            if (s->stop && s->queue.empty() && s->active.empty() && s->to_report.empty()) return;
+            if (s->stop && s->queue.empty() && s->active.empty() && !s->issuing && s->to_report.empty()) return;
             if (!s->steps.empty()) break;
             s->cv_compl.wait_for(lk, std::chrono::milliseconds(5));
         }
