@@ -647,6 +647,40 @@ def _serve_tasks(hx, arena, trace):
     return tasks
 
 
+def serving_comparison(points, targets=(2.0, 5.0, 10.0, 20.0)):
+    """Equal-p99 comparison of the serving sweep's two modes.
+
+    The latency bound is the per-launch server's p99 at the highest rate it
+    sustains (stable: it keeps up with >= 95% of the offered rate and its
+    latency does not grow over the trace); the highest rate each mode
+    sustains with p99 within that bound is compared, and the same at fixed
+    p99 targets.  ``points``: one dict per offered rate with a "continuous"
+    and a "per_launch" entry (req_per_s, p99_ms, stable)."""
+    def sustained(mode, bound):
+        ok = [p for p in points if p[mode]["stable"] and p[mode]["p99_ms"] <= bound]
+        return max(ok, key=lambda p: p["offered_req_per_s"]) if ok else None
+    keep = [p for p in points if p["per_launch"]["stable"]]
+    base = max(keep, key=lambda p: p["offered_req_per_s"]) if keep else points[0]
+    bound = base["per_launch"]["p99_ms"]
+    c = sustained("continuous", bound)
+    pl = sustained("per_launch", bound)
+    eq = {"p99_bound_ms": bound,
+          "per_launch_req_per_s": pl["per_launch"]["req_per_s"] if pl else None,
+          "continuous_req_per_s": c["continuous"]["req_per_s"] if c else None}
+    if eq["per_launch_req_per_s"] and eq["continuous_req_per_s"]:
+        eq["ratio"] = round(eq["continuous_req_per_s"] / eq["per_launch_req_per_s"], 3)
+    slo = []
+    for target in targets:
+        c, pl = sustained("continuous", target), sustained("per_launch", target)
+        row = {"p99_ms": target, "continuous_req_per_s": c["continuous"]["req_per_s"] if c else None,
+               "per_launch_req_per_s": pl["per_launch"]["req_per_s"] if pl else None}
+        if row["continuous_req_per_s"] and row["per_launch_req_per_s"]:
+            row["ratio"] = round(row["continuous_req_per_s"] / row["per_launch_req_per_s"], 3)
+        slo.append(row)
+    eq["at_p99_targets"] = slo
+    return eq
+
+
 def bench_serving(hx, ctx, dev, rates=SERVE_RATES, max_requests=4000, window_s=0.25):
     """Open-loop Poisson serving at several offered rates, continuous batching
     vs one launch per request, same requests, same device buffers."""
@@ -683,33 +717,7 @@ def bench_serving(hx, ctx, dev, rates=SERVE_RATES, max_requests=4000, window_s=0
         points.append(row)
     del arena
     torch.cuda.empty_cache()
-    # Equal-p99 comparison: the per-launch server's p99 at the highest rate it
-    # sustains (stable: it keeps up with >= 95% of the offered rate and its
-    # latency does not grow over the trace) is the latency bound; compare
-    # the highest rate each mode sustains with p99 within that bound.
-    def sustained(mode, bound):
-        ok = [p for p in points if p[mode]["stable"] and p[mode]["p99_ms"] <= bound]
-        return max(ok, key=lambda p: p["offered_req_per_s"]) if ok else None
-    keep = [p for p in points if p["per_launch"]["stable"]]
-    base = max(keep, key=lambda p: p["offered_req_per_s"]) if keep else points[0]
-    bound = base["per_launch"]["p99_ms"]
-    c = sustained("continuous", bound)
-    pl = sustained("per_launch", bound)
-    eq = {"p99_bound_ms": bound,
-          "per_launch_req_per_s": pl["per_launch"]["req_per_s"] if pl else None,
-          "continuous_req_per_s": c["continuous"]["req_per_s"] if c else None}
-    if eq["per_launch_req_per_s"] and eq["continuous_req_per_s"]:
-        eq["ratio"] = round(eq["continuous_req_per_s"] / eq["per_launch_req_per_s"], 3)
-    # the same comparison at fixed p99 targets
-    slo = []
-    for target in (2.0, 5.0, 10.0, 20.0):
-        c, pl = sustained("continuous", target), sustained("per_launch", target)
-        row = {"p99_ms": target, "continuous_req_per_s": c["continuous"]["req_per_s"] if c else None,
-               "per_launch_req_per_s": pl["per_launch"]["req_per_s"] if pl else None}
-        if row["continuous_req_per_s"] and row["per_launch_req_per_s"]:
-            row["ratio"] = round(row["continuous_req_per_s"] / row["per_launch_req_per_s"], 3)
-        slo.append(row)
-    eq["at_p99_targets"] = slo
+    eq = serving_comparison(points)
     return {"mix": "1/3 map->reduce, 1/3 jacobi (20 sweeps, square side ~sqrt(n)), 1/3 histogram+scan; "
                    "sizes log-uniform 1K-16M elements; Poisson arrivals (seed 4)",
             "budget_gb": SERVE_BUDGET / 2**30, "points": points, "equal_p99": eq}
