@@ -25,6 +25,8 @@ MAP_PINS = [pins.test_map_reduce_golden_tiny, pins.test_map_reduce_arithmetic_se
 STENCIL_PINS = [pins.test_jacobi_golden_corner_spike, pins.test_jacobi_interior_spike,
                 pins.test_jacobi_linear_field_closed_form, pins.test_jacobi_matches_scipy_nearest_correlation,
                 pins.test_jacobi_residual_is_max_step_change]
+F32_STENCIL_PINS = [pins.test_jacobi_f32_equals_f64_on_coarse_dyadics, pins.test_jacobi_f32_within_rounding_bound_of_f64]
+MONOID_PINS = [pins.test_monoid_reduce_against_library]
 HIST_PINS = [pins.test_histogram_golden_tiny, pins.test_histogram_matches_bincount_and_cumsum,
              pins.test_histogram_closed_forms]
 
@@ -104,6 +106,20 @@ MUTANTS = {
     "srad_roi_rows_from_zero": ("for (int64_t i = r0; i < r1; i++)", "for (int64_t i = 0; i < r1; i++)", SRAD_PINS),
     "srad_dS_from_north": ("T dS = cur[is * nx + j] - Jc;", "T dS = cur[clampi(i - 1, 0, ny - 1) * nx + j] - Jc;",
                            SRAD_PINS),
+    "stencil_f32_north_is_south": ("float north = cur[clampi(i - 1, 0, ny - 1) * nx + j];",
+                                   "float north = cur[clampi(i + 1, 0, ny - 1) * nx + j];", F32_STENCIL_PINS),
+    "stencil_f32_weight": ("float v = 0.25f * (ns + we);", "float v = 0.2f * (ns + we);", F32_STENCIL_PINS),
+    "stencil_f32_resid_signed": ("float d = fabsf(v - cur[i * nx + j]);", "float d = v - cur[i * nx + j];",
+                                 F32_STENCIL_PINS),
+    "stencil_f32_periodic": ("float west  = cur[i * nx + clampi(j - 1, 0, nx - 1)];",
+                             "float west  = cur[i * nx + (j - 1 + nx) % nx];", F32_STENCIL_PINS),
+    "monoid_max_init_zero": ("case 1: acc = -INFINITY; break;", "case 1: acc = 0.0; break;", MONOID_PINS),
+    "monoid_min_is_max": ("case 2: acc = (v < acc) ? v : acc; break;", "case 2: acc = (v > acc) ? v : acc; break;",
+                          MONOID_PINS),
+    "monoid_dropped_y": ("double v = a * (double)x[i] + (y ? (double)y[i] : 0.0);", "double v = a * (double)x[i];",
+                         MONOID_PINS),
+    "monoid_prod_init_zero": ("case 3: acc = 1.0; break;\n    default: return 1;",
+                              "case 3: acc = 0.0; break;\n    default: return 1;", MONOID_PINS),
     "nest_min_keeps_pos_zero": ("if (v < best || (v == 0.0f && best == 0.0f && !signbit(best) && signbit(v))) best = v;",
                                 "if (v < best) best = v;", NEST_PINS),
 }
