@@ -40,7 +40,8 @@ NEST_PINS = [*(lambda op=op: npins.test_nest_binary_ops_match_numpy_single(op) f
              lambda: npins.test_nest_row_arg_extrema_match_numpy("argmin", npins.np.argmin),
              npins.test_nest_3d_partial_reductions_match_numpy, npins.test_nest_strided_and_broadcast_inputs,
              npins.test_nest_index_op_matches_index_grid, npins.test_nest_fold_order_is_thread_id_order,
-             npins.test_nest_nan_and_empty_rules, npins.test_nest_signed_zero_rules]
+             npins.test_nest_nan_and_empty_rules, npins.test_nest_signed_zero_rules,
+             npins.test_nest_min_max_ops_skip_nan, npins.test_nest_unary_ops_special_values]
 
 SRAD_PINS = [lambda: spins.test_srad_conserves_mass(0.5, (17, 23)), spins.test_srad_transpose_symmetry,
              lambda: spins.test_srad_maximum_principle(1.0),
@@ -120,6 +121,17 @@ MUTANTS = {
                          MONOID_PINS),
     "monoid_prod_init_zero": ("case 3: acc = 1.0; break;\n    default: return 1;",
                               "case 3: acc = 0.0; break;\n    default: return 1;", MONOID_PINS),
+    "nest_argmin_last_tie": ("if (!isnan(v) && (best_i < 0 || v < best)) { best = v; best_i = r; }",
+                             "if (!isnan(v) && (best_i < 0 || v <= best)) { best = v; best_i = r; }", NEST_PINS),
+    "nest_argmax_takes_nan": ("if (!isnan(v) && (best_i < 0 || v > best)) { best = v; best_i = r; }",
+                              "if ((best_i < 0 || v > best)) { best = v; best_i = r; }", NEST_PINS),
+    "nest_div_swapped": ("else if (code == 7) st[sp++] = a / b;", "else if (code == 7) st[sp++] = b / a;", NEST_PINS),
+    "nest_min_op_propagates_nan": ("else if (code == 11) st[sp++] = isnan(a) ? b : (isnan(b) ? a : (b < a ? b : a));",
+                                   "else if (code == 11) st[sp++] = (b < a ? b : a);", NEST_PINS),
+    "nest_abs_keeps_neg_zero": ("st[sp++] = code == 9 ? -a : (code == 10 ? fabsf(a) : sqrtf(a));",
+                                "st[sp++] = code == 9 ? -a : (code == 10 ? (a < 0 ? -a : a) : sqrtf(a));", NEST_PINS),
+    "nest_sqrt_of_abs": ("st[sp++] = code == 9 ? -a : (code == 10 ? fabsf(a) : sqrtf(a));",
+                         "st[sp++] = code == 9 ? -a : (code == 10 ? fabsf(a) : sqrtf(fabsf(a)));", NEST_PINS),
     "nest_min_keeps_pos_zero": ("if (v < best || (v == 0.0f && best == 0.0f && !signbit(best) && signbit(v))) best = v;",
                                 "if (v < best) best = v;", NEST_PINS),
 }

@@ -49,6 +49,33 @@ def test_nest_unary_ops_match_numpy_single(op):
     np.testing.assert_array_equal(out.view(np.uint32), UNARY[op](x).view(np.uint32))
 
 
+def test_nest_min_max_ops_skip_nan():
+    # MIN / MAX return the other operand when one is NaN (IEEE minNum /
+    # maxNum, numpy's fmin / fmax); NaNs sit in x and y at disjoint places
+    x = _grid((31, 29), 21)
+    y = _grid((31, 29), 22)
+    x.reshape(-1)[::7] = np.nan
+    y.reshape(-1)[3::11] = np.nan
+    for op, ref in (("min", np.fmin), ("max", np.fmax)):
+        out, _, _ = oracle.fork_reduce([("in", 0), ("in", 1), op], [x, y], x.shape, 0)
+        np.testing.assert_array_equal(out.view(np.uint32), ref(x, y).view(np.uint32))
+
+
+def test_nest_unary_ops_special_values():
+    # signed zeros, infinities, NaN and a subnormal through NEG / ABS bit for
+    # bit against numpy; SQRT keeps -0, and is NaN for every negative input
+    sp = np.array([-0.0, 0.0, -1.5, 2.25, np.inf, -np.inf, np.nan, 1e-45, -1e-45], np.float32)
+    for op in ("neg", "abs"):
+        out, _, _ = oracle.fork_reduce([("in", 0), op], [sp], sp.shape, 0)
+        np.testing.assert_array_equal(out.view(np.uint32), UNARY[op](sp).view(np.uint32))
+    out, _, _ = oracle.fork_reduce([("in", 0), "sqrt"], [sp], sp.shape, 0)
+    ok = ~(np.signbit(sp) & (sp != 0)) & ~np.isnan(sp)
+    with np.errstate(invalid="ignore"):
+        ref = np.sqrt(sp)
+    np.testing.assert_array_equal(out[ok].view(np.uint32), ref[ok].view(np.uint32))
+    assert np.all(np.isnan(out[~ok]))
+
+
 def test_nest_const_and_operand_order():
     x = _grid((5, 7), 14)
     out, _, _ = oracle.fork_reduce([("const", 2), ("in", 0), "sub", ("const", 1), "div"], [x], x.shape, 0,
