@@ -27,6 +27,7 @@ STENCIL_PINS = [pins.test_jacobi_golden_corner_spike, pins.test_jacobi_interior_
                 pins.test_jacobi_residual_is_max_step_change]
 F32_STENCIL_PINS = [pins.test_jacobi_f32_equals_f64_on_coarse_dyadics, pins.test_jacobi_f32_within_rounding_bound_of_f64]
 MONOID_PINS = [pins.test_monoid_reduce_against_library]
+SRAD32_PINS = [lambda: spins.test_srad_f32_follows_f64()]
 HIST_PINS = [pins.test_histogram_golden_tiny, pins.test_histogram_matches_bincount_and_cumsum,
              pins.test_histogram_closed_forms]
 
@@ -132,6 +133,26 @@ MUTANTS = {
                                 "st[sp++] = code == 9 ? -a : (code == 10 ? (a < 0 ? -a : a) : sqrtf(a));", NEST_PINS),
     "nest_sqrt_of_abs": ("st[sp++] = code == 9 ? -a : (code == 10 ? fabsf(a) : sqrtf(a));",
                          "st[sp++] = code == 9 ? -a : (code == 10 ? fabsf(a) : sqrtf(fabsf(a)));", NEST_PINS),
+    "srad32_cS_self": ("float cN = cc[i * nx + j], cS = cc[is * nx + j];",
+                       "float cN = cc[i * nx + j], cS = cc[i * nx + j];", SRAD32_PINS),
+    "srad32_den_sign": ("float den = 1.0f + 0.25f * L;", "float den = 1.0f - 0.25f * L;", SRAD32_PINS),
+    "srad32_c_drops_den2": ("float c = den2 / (den2 + (num - q0sq * den2) * iq);",
+                            "float c = den2 / (den2 + (num - q0sq) * iq);", SRAD32_PINS),
+    "srad32_G2_one_r": ("float G2 = (((dN * dN + dS * dS) + (dW * dW + dE * dE)) * r) * r;",
+                        "float G2 = (((dN * dN + dS * dS) + (dW * dW + dE * dE)) * r);", SRAD32_PINS),
+    "srad32_step_half": ("const float k = 0.25f * lambda;", "const float k = 0.5f * lambda;", SRAD32_PINS),
+    "srad32_iq_drops_q0sq": ("const float iq = 1.0f / (q0sq * (1.0f + q0sq));", "const float iq = 1.0f / (1.0f + q0sq);",
+                             SRAD32_PINS),
+    "srad32_var_n_minus_1": ("double var = s2 / npix - (mean * mean);", "double var = s2 / (npix - 1.0) - (mean * mean);",
+                             SRAD32_PINS),
+    "hist_bin_shifted": ("for (int64_t i = 0; i < n; ++i) bins[v[i]] = bins[v[i]] + 1u;",
+                         "for (int64_t i = 0; i < n; ++i) bins[(uint8_t)(v[i] + 1)] = bins[(uint8_t)(v[i] + 1)] + 1u;",
+                         HIST_PINS),
+    "stencil_east_is_self": ("double east  = cur[i * nx + clampi(j + 1, 0, nx - 1)];",
+                             "double east  = cur[i * nx + clampi(j, 0, nx - 1)];", STENCIL_PINS),
+    "nest_prod_in_float": ("case 3: acc = acc * (double)v; break;", "case 3: acc = (float)(acc * (double)v); break;",
+                           NEST_PINS),
+    "nest_const_shifted": ("st[sp++] = consts[arg];", "st[sp++] = consts[(arg + 1) & 7];", NEST_PINS),
     "nest_min_keeps_pos_zero": ("if (v < best || (v == 0.0f && best == 0.0f && !signbit(best) && signbit(v))) best = v;",
                                 "if (v < best) best = v;", NEST_PINS),
 }
