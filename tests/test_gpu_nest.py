@@ -160,6 +160,29 @@ def test_ties_nans_signed_zeros(gpu):
                 _check(hx, ctx, [("in", 0)], [x], ident, x.shape, 1, monoid, tree=tree)
 
 
+def test_map_ops_on_special_values(gpu):
+    # MIN / MAX with NaN operands, and NEG / ABS / SQRT of signed zeros,
+    # infinities, NaN, subnormals and negatives, against the oracle.  A NaN
+    # result's payload and sign are unspecified on the GPU, so NaN results
+    # are compared by NaN-ness and every other result bit for bit.
+    hx = gpu
+    sp = np.array([-0.0, 0.0, -1.5, 2.25, np.inf, -np.inf, np.nan, 1e-45, -1e-45, 3.0], np.float32)
+    x = np.tile(sp, 40)
+    y = np.roll(x, 3)
+    progs = [([("in", 0), ("in", 1), "min"], 2), ([("in", 0), ("in", 1), "max"], 2), ([("in", 0), "neg"], 1),
+             ([("in", 0), "abs"], 1), ([("in", 0), "sqrt"], 1), ([("in", 0), ("in", 1), "min", "abs"], 2)]
+    with hx.hx_create(0) as ctx:
+        for prog, n_in in progs:
+            ins = [x, y][:n_in]
+            out, _, _, _ = hx.fork_reduce(ctx, prog, [torch.from_numpy(a).cuda() for a in ins], x.shape, 0, "sum")
+            torch.cuda.synchronize()
+            ref, _, _ = oracle.fork_reduce(prog, ins, x.shape, 0)
+            got = out.cpu().numpy()
+            nan = np.isnan(ref)
+            np.testing.assert_array_equal(np.isnan(got), nan)
+            np.testing.assert_array_equal(got[~nan].view(np.uint32), ref[~nan].view(np.uint32))
+
+
 @pytest.mark.parametrize("chunk", [256, 1000, 4096])
 def test_explicit_chunks_and_determinism(gpu, chunk):
     hx = gpu
