@@ -216,7 +216,13 @@ hx_status hx_histogram(hx_ctx *ctx, const uint8_t *v, int64_t n, uint32_t *d_bin
  *   qsq = (0.5*G2 - 0.0625*L*L) / ((1 + 0.25*L)^2),
  *   c = clamp(1 / (1 + (qsq - q0sq) / (q0sq*(1 + q0sq))), 0, 1),
  *   J' = Jc + (0.25*lambda) * ((c[i][j]*dN + c[i+1][j]*dS) + (c[i][j]*dW + c[i][j+1]*dE)),
- * every operation in fp32 in that order (no contraction); q0sq is formed in
+ * in fp32 without contraction, with the coefficient's divisions regrouped
+ * (r = 1/Jc, G2 = (sum of d^2 * r) * r, L = (sum of d) * r, den2 = den*den,
+ * c = den2 / (den2 + (num - q0sq*den2) * iq), iq = 1/(q0sq*(1 + q0sq)) once
+ * per iteration): algebraically the expression above, two divisions per
+ * pixel instead of five, rounded differently.  After T iterations the image
+ * is within T * 12 * 2^-24 (at most 1e-5) of its maximum from an fp64
+ * evaluation of the expression above (lambda <= 1).  q0sq is formed in
  * double from float-float region sums (S1 = sum J, S2 = sum J^2 over rows
  * [r0, r1) x cols [c0, c1); mean = S1/N, var = S2/N - mean^2) and rounded
  * to fp32 once.

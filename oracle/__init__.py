@@ -11,11 +11,10 @@ function says otherwise.  This module only marshals numpy arrays in and out.
 
 Parity status: every function here is pinned by the ``-m "not gpu"`` tests
 (closed forms, library routines on special cases, brute force on tiny
-inputs).  One sub-expression is "parity unpinned": in ``srad``, the mapping
-from the coefficient of variation to the diffusion coefficient,
-c = 1/(1 + (q^2 - q0^2)/(q0^2 (1 + q0^2))), is checked only by restating
-it (its clamp to 1 for q^2 <= q0^2 is pinned independently); the paper does
-not print SRAD's arithmetic.
+inputs, values worked by hand).  In ``srad`` the mapping from the
+coefficient of variation to the diffusion coefficient,
+c = 1/(1 + (q^2 - q0^2)/(q0^2 (1 + q0^2))), is pinned by hand-worked values
+of the published SRAD scheme (the paper does not print SRAD's arithmetic).
 """
 
 from __future__ import annotations

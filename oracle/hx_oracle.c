@@ -388,15 +388,14 @@ int hxo_fork_reduce(int ndim, const int64_t *dims, int reduce_dims, int monoid,
  *
  * Parity: conservation, symmetry, the maximum principle, the Jacobi limit,
  * the ROI statistics and a checkerboard closed form for qsq pin this nest;
- * the mapping from qsq to c is parity unpinned (the tests can only restate
- * it).
+ * the mapping from qsq to c is pinned by values worked by hand from the
+ * published coefficient on checkerboard images with a separate region of
+ * interest (the test suite's golden file for the SRAD coefficient).
  *
  * Intensities must be nonzero (the scheme divides by J); a homogeneous ROI
  * (q0sq == 0) makes the coefficient 0/0 and the result NaN, as the formula
  * says.  q0sq_out[t] receives iteration t's speckle scale.  The f32 variant
- * (below) evaluates steps 2 and 3 in single precision with the coefficient's
- * divisions regrouped; its ROI sums are the double sums of the fp32 values,
- * and q0sq is computed in double and rounded to fp32 once.
+ * (below) evaluates the same expressions in single precision.
  * Returns 0, or 1 for bad arguments / failed scratch allocation.
  */
 #define HXO_SRAD_BODY(T, HALF, SIXTEENTH, QUARTER, ONE, ZERO)                         \
@@ -465,74 +464,12 @@ int hxo_srad_f64(const double *J0, int32_t nx, int32_t ny, int32_t iters, double
     HXO_SRAD_BODY(double, 0.5, 0.0625, 0.25, 1.0, 0.0)
 }
 
-/* Single precision, in the evaluation order the GPU uses: the same scheme
- * with the divisions regrouped (algebraically equal, rounded differently):
- *   r = 1/Jc, G2 = (Sq*r)*r, L = Sd*r, num, den as above, den2 = den*den,
- *   iq = 1/(q0sq*(1 + q0sq)) (once per iteration),
- *   c = den2 / (den2 + (num - q0sq*den2)*iq), clamped to [0, 1],
- * which is 1/(1 + (num/den2 - q0sq)/(q0sq*(1 + q0sq))) multiplied through
- * by den2.  Every operation rounds to fp32; the ROI statistics are as in
- * the double version. */
+/* Single precision: the same nest, literally, with every operation of steps
+ * 2 and 3 rounded to fp32 in the order written above (five divisions per
+ * pixel); the ROI statistics are the double sums of the fp32 values, and
+ * q0sq is rounded to fp32 once. */
 int hxo_srad_f32(const float *J0, int32_t nx, int32_t ny, int32_t iters, float lambda,
                  int32_t r0, int32_t r1, int32_t c0, int32_t c1, float *J_out, float *q0sq_out)
 {
-    size_t npts = (size_t)nx * (size_t)ny;
-    if (nx < 1 || ny < 1 || r0 < 0 || r1 > ny || r0 >= r1 || c0 < 0 || c1 > nx || c0 >= c1 || iters < 0)
-        return 1;
-    float *cur = (float *)malloc(npts * sizeof(float));
-    float *nxt = (float *)malloc(npts * sizeof(float));
-    float *cc = (float *)malloc(npts * sizeof(float));
-    if (!cur || !nxt || !cc) { free(cur); free(nxt); free(cc); return 1; }
-    memcpy(cur, J0, npts * sizeof(float));
-    const float k = 0.25f * lambda;
-    for (int32_t t = 0; t < iters; ++t) {
-        double s1 = 0.0, s2 = 0.0;
-        for (int64_t i = r0; i < r1; ++i)
-            for (int64_t j = c0; j < c1; ++j) {
-                double v = (double)cur[i * nx + j];
-                s1 = s1 + v;
-                s2 = s2 + v * v;
-            }
-        double npix = (double)(r1 - r0) * (double)(c1 - c0);
-        double mean = s1 / npix;
-        double var = s2 / npix - (mean * mean);
-        const float q0sq = (float)(var / (mean * mean));
-        q0sq_out[t] = q0sq;
-        const float iq = 1.0f / (q0sq * (1.0f + q0sq));
-        for (int64_t i = 0; i < ny; ++i)
-            for (int64_t j = 0; j < nx; ++j) {
-                float Jc = cur[i * nx + j];
-                float dN = cur[clampi(i - 1, 0, ny - 1) * nx + j] - Jc;
-                float dS = cur[clampi(i + 1, 0, ny - 1) * nx + j] - Jc;
-                float dW = cur[i * nx + clampi(j - 1, 0, nx - 1)] - Jc;
-                float dE = cur[i * nx + clampi(j + 1, 0, nx - 1)] - Jc;
-                float r = 1.0f / Jc;
-                float G2 = (((dN * dN + dS * dS) + (dW * dW + dE * dE)) * r) * r;
-                float L = ((dN + dS) + (dW + dE)) * r;
-                float num = 0.5f * G2 - 0.0625f * (L * L);
-                float den = 1.0f + 0.25f * L;
-                float den2 = den * den;
-                float c = den2 / (den2 + (num - q0sq * den2) * iq);
-                if (c < 0.0f) c = 0.0f;
-                else if (c > 1.0f) c = 1.0f;
-                cc[i * nx + j] = c;
-            }
-        for (int64_t i = 0; i < ny; ++i)
-            for (int64_t j = 0; j < nx; ++j) {
-                float Jc = cur[i * nx + j];
-                int64_t is = clampi(i + 1, 0, ny - 1), je = clampi(j + 1, 0, nx - 1);
-                float dN = cur[clampi(i - 1, 0, ny - 1) * nx + j] - Jc;
-                float dS = cur[is * nx + j] - Jc;
-                float dW = cur[i * nx + clampi(j - 1, 0, nx - 1)] - Jc;
-                float dE = cur[i * nx + je] - Jc;
-                float cN = cc[i * nx + j], cS = cc[is * nx + j];
-                float cW = cc[i * nx + j], cE = cc[i * nx + je];
-                float D = (cN * dN + cS * dS) + (cW * dW + cE * dE);
-                nxt[i * nx + j] = Jc + k * D;
-            }
-        float *tmp = cur; cur = nxt; nxt = tmp;
-    }
-    memcpy(J_out, cur, npts * sizeof(float));
-    free(cur); free(nxt); free(cc);
-    return 0;
+    HXO_SRAD_BODY(float, 0.5f, 0.0625f, 0.25f, 1.0f, 0.0f)
 }

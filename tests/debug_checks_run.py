@@ -78,8 +78,10 @@ with hx.hx_create(0) as ctx:
         J = workloads.srad_image(*shape)
         J0 = torch.from_numpy(J).to(dev)
         out, _ = hx.hx_srad(ctx, J0, torch.empty_like(J0), 3, 0.5, roi)
-        ref32, _ = oracle.srad(J, 3, 0.5, roi, "f32")
-        ok &= np.array_equal(out.cpu().numpy().view(np.uint32), ref32.view(np.uint32))
+        ref64, _ = oracle.srad(J, 3, 0.5, roi, "f64")
+        # three iterations, within 3 x 12 u of the image's maximum (the
+        # rounding bound of the fp32 scheme, tests/test_gpu_srad.py)
+        ok &= bool(np.max(np.abs(out.cpu().numpy() - ref64)) <= 36 * 2.0 ** -24 * np.max(np.abs(ref64)))
         hx.hx_srad(ctx, J0, torch.empty_like(J0), 2, 0.5, roi, fused=False)
     # generic nests: warp tree with one and several chunks per segment,
     # narrow segments, a permuted 3-D view, the chunk and sequential trees

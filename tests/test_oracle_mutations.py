@@ -27,7 +27,8 @@ STENCIL_PINS = [pins.test_jacobi_golden_corner_spike, pins.test_jacobi_interior_
                 pins.test_jacobi_residual_is_max_step_change]
 F32_STENCIL_PINS = [pins.test_jacobi_f32_equals_f64_on_coarse_dyadics, pins.test_jacobi_f32_within_rounding_bound_of_f64]
 MONOID_PINS = [pins.test_monoid_reduce_against_library]
-SRAD32_PINS = [lambda: spins.test_srad_f32_follows_f64()]
+SRAD32_PINS = [lambda: spins.test_srad_f32_follows_f64(),
+               *(lambda k=k: spins.test_srad_coefficient_golden(k) for k in range(3))]
 HIST_PINS = [pins.test_histogram_golden_tiny, pins.test_histogram_matches_bincount_and_cumsum,
              pins.test_histogram_closed_forms]
 
@@ -50,7 +51,11 @@ SRAD_PINS = [lambda: spins.test_srad_conserves_mass(0.5, (17, 23)), spins.test_s
              spins.test_srad_speckle_scale_matches_numpy,
              *(lambda a=a, b=b: spins.test_srad_checkerboard_closed_form(a, b)
                for a, b in ((2.0, 1.0), (1.0, 3.0), (1.5, 1.25))),
-             spins.test_srad_homogeneous_cases]
+             spins.test_srad_homogeneous_cases,
+             *(lambda k=k: spins.test_srad_coefficient_golden(k) for k in range(3))]
+# The coefficient mapping alone, against values worked by hand from the
+# published formula (no pin that restates the formula).
+SRAD_C_PINS = [lambda k=k: spins.test_srad_coefficient_golden(k) for k in range(3)]
 
 MUTANTS = {
     "map_transposed": ("double v = a * (double)x[i] + (double)y[i];",
@@ -133,18 +138,21 @@ MUTANTS = {
                                 "st[sp++] = code == 9 ? -a : (code == 10 ? (a < 0 ? -a : a) : sqrtf(a));", NEST_PINS),
     "nest_sqrt_of_abs": ("st[sp++] = code == 9 ? -a : (code == 10 ? fabsf(a) : sqrtf(a));",
                          "st[sp++] = code == 9 ? -a : (code == 10 ? fabsf(a) : sqrtf(fabsf(a)));", NEST_PINS),
-    "srad32_cS_self": ("float cN = cc[i * nx + j], cS = cc[is * nx + j];",
-                       "float cN = cc[i * nx + j], cS = cc[i * nx + j];", SRAD32_PINS),
-    "srad32_den_sign": ("float den = 1.0f + 0.25f * L;", "float den = 1.0f - 0.25f * L;", SRAD32_PINS),
-    "srad32_c_drops_den2": ("float c = den2 / (den2 + (num - q0sq * den2) * iq);",
-                            "float c = den2 / (den2 + (num - q0sq) * iq);", SRAD32_PINS),
-    "srad32_G2_one_r": ("float G2 = (((dN * dN + dS * dS) + (dW * dW + dE * dE)) * r) * r;",
-                        "float G2 = (((dN * dN + dS * dS) + (dW * dW + dE * dE)) * r);", SRAD32_PINS),
-    "srad32_step_half": ("const float k = 0.25f * lambda;", "const float k = 0.5f * lambda;", SRAD32_PINS),
-    "srad32_iq_drops_q0sq": ("const float iq = 1.0f / (q0sq * (1.0f + q0sq));", "const float iq = 1.0f / (1.0f + q0sq);",
-                             SRAD32_PINS),
-    "srad32_var_n_minus_1": ("double var = s2 / npix - (mean * mean);", "double var = s2 / (npix - 1.0) - (mean * mean);",
-                             SRAD32_PINS),
+    "srad32_quarter_is_half": ("HXO_SRAD_BODY(float, 0.5f, 0.0625f, 0.25f, 1.0f, 0.0f)",
+                               "HXO_SRAD_BODY(float, 0.5f, 0.0625f, 0.5f, 1.0f, 0.0f)", SRAD32_PINS),
+    "srad32_sixteenth_is_eighth": ("HXO_SRAD_BODY(float, 0.5f, 0.0625f, 0.25f, 1.0f, 0.0f)",
+                                   "HXO_SRAD_BODY(float, 0.5f, 0.125f, 0.25f, 1.0f, 0.0f)", SRAD32_PINS),
+    "srad_c_drops_one_plus_q0sq": ("T c = ONE / (ONE + (qsq - q0sq) / (q0sq * (ONE + q0sq)));",
+                                   "T c = ONE / (ONE + (qsq - q0sq) / q0sq);", SRAD_C_PINS),
+    "srad_c_one_minus_q0sq": ("T c = ONE / (ONE + (qsq - q0sq) / (q0sq * (ONE + q0sq)));",
+                              "T c = ONE / (ONE + (qsq - q0sq) / (q0sq * (ONE - q0sq)));", SRAD_C_PINS),
+    "srad_c_half_constant": ("T c = ONE / (ONE + (qsq - q0sq) / (q0sq * (ONE + q0sq)));",
+                             "T c = ONE / (ONE + HALF * (qsq - q0sq) / (q0sq * (ONE + q0sq)));", SRAD_C_PINS),
+    "srad_c_sign": ("T c = ONE / (ONE + (qsq - q0sq) / (q0sq * (ONE + q0sq)));",
+                    "T c = ONE / (ONE + (q0sq - qsq) / (q0sq * (ONE + q0sq)));", SRAD_C_PINS),
+    "srad_c_uses_q0": ("T c = ONE / (ONE + (qsq - q0sq) / (q0sq * (ONE + q0sq)));",
+                       "T c = ONE / (ONE + (qsq - q0sq) / (q0sq * q0sq * (ONE + q0sq)));", SRAD_C_PINS),
+    "srad_qsq_drops_den": ("T qsq = num / (den * den);", "T qsq = num / den;", SRAD_C_PINS),
     "hist_bin_shifted": ("for (int64_t i = 0; i < n; ++i) bins[v[i]] = bins[v[i]] + 1u;",
                          "for (int64_t i = 0; i < n; ++i) bins[(uint8_t)(v[i] + 1)] = bins[(uint8_t)(v[i] + 1)] + 1u;",
                          HIST_PINS),

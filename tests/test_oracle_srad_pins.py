@@ -14,8 +14,15 @@ What fixes it from outside the oracle:
     are equal, so its instantaneous coefficient of variation is
     q^2 = (a - b)^2 / a^2 (b = the pixel, a = its neighbours);
   * homogeneous regions: q0^2 = 0 gives NaN, a flat neighbourhood is left
-    unchanged.
+    unchanged;
+  * the diffusion coefficient c(q^2): values worked by hand with exact
+    fractions from the published formula (tests/golden/srad_coefficient.json),
+    including a clamped coefficient and the case q^2 = q0^2.
 """
+
+import json
+import os
+from fractions import Fraction
 
 import numpy as np
 import pytest
@@ -124,3 +131,33 @@ def test_srad_rejects_bad_roi():
     for roi in ((0, 0, 0, 5), (0, 6, 0, 5), (-1, 3, 0, 5), (0, 5, 4, 2)):
         with pytest.raises(ValueError):
             oracle.srad(J, 1, 0.5, roi)
+
+
+def _checkerboard_case(g, case):
+    ny, nx = g["shape"]
+    a, b = float(Fraction(case["a"])), float(Fraction(case["b"]))
+    ii, jj = np.indices((ny, nx))
+    J = np.where((ii + jj) % 2 == 0, b, a).astype(np.float64)
+    if case["roi_values"] is not None:
+        vals = [float(Fraction(v)) for v in case["roi_values"]]
+        J[0, :len(vals)] = vals
+    even = ((ii + jj) % 2 == 0)[2:ny - 2, 1:nx - 2]
+    want = np.where(even, float(Fraction(case["J_b"])), float(Fraction(case["J_a"])))
+    return J, want
+
+
+@pytest.mark.parametrize("k", [0, 1, 2])
+def test_srad_coefficient_golden(k):
+    with open(os.path.join(os.path.dirname(__file__), "golden", "srad_coefficient.json")) as f:
+        g = json.load(f)
+    case = g["cases"][k]
+    J, want = _checkerboard_case(g, case)
+    lam = float(Fraction(case["lambda"]))
+    q0_want = float(Fraction(case["q0sq"]))
+    out, q0 = oracle.srad(J, 1, lam, case["roi"])
+    ny, nx = g["shape"]
+    assert abs(q0[0] - q0_want) <= 1e-14 * q0_want
+    np.testing.assert_allclose(out[2:ny - 2, 1:nx - 2], want, rtol=1e-14, atol=0)
+    out32, q032 = oracle.srad(J.astype(np.float32), 1, lam, case["roi"], "f32")
+    assert abs(float(q032[0]) - q0_want) <= 2 ** -24 * q0_want
+    np.testing.assert_allclose(out32[2:ny - 2, 1:nx - 2], want, rtol=1e-6, atol=0)
