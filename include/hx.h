@@ -120,6 +120,11 @@ hx_status hx_debug_checks(int32_t *enabled, int32_t *code, int64_t *a, int64_t *
  * (hi, lo) pairs of fp32 numbers, about 48 significant bits.  The map and
  * the reduce are fused: out is written in the same pass (loop fusion,
  * Sec. 5.1).
+ * Non-finite values: the pairs have fp32's exponent range.  A sum over
+ * values that include +-inf is +-inf (NaN when both infinities or a NaN
+ * occur), and a sum beyond fp32's range is +-inf in d_sum and in d_sum64
+ * alike.  A running sum that overflows although the exact sum would come
+ * back into range (cancellation after an overflow) is not defined.
  *
  *   x, y     device, n fp32 each, read-only.  Any alignment (16-byte
  *            aligned buffers take the vector path; results are identical).
@@ -152,8 +157,12 @@ hx_status hx_map_reduce(hx_ctx *ctx, const float *x, const float *y, float *out,
  *   - n must be in [0, HX_MAP_REDUCE_NOALLOC_MAX_N]; larger n returns
  *     HX_ERR_INVALID with a message.
  *   - Runs on the calling thread's current device.  The first call on a
- *     device looks up the scratch's device address (cudaGetSymbolAddress);
- *     make that first call before any stream capture begins.
+ *     device looks up the scratch's device address (cudaGetSymbolAddress)
+ *     and keeps it for the life of the process; make that first call
+ *     before any stream capture begins.  cudaDeviceReset (or destroying
+ *     and re-creating the device's primary context) unloads the library's
+ *     device module and invalidates that address: after it, do not call
+ *     this entry point on that device again in the same process.
  *   - Every call shares the one scratch array, which keeps the last call's
  *     contents; each call clears the arrival ticket on `stream` before its
  *     kernel.  Calls whose work overlaps on the GPU (different streams, or
@@ -272,7 +281,13 @@ hx_status hx_srad(hx_ctx *ctx, float *J0, float *J1, float *C, int32_t nx, int32
  * Monoids (results per segment):
  *   SUM, PROD   float-float accumulation; result = the pair rounded to
  *               fp32, result64 = hi + lo in double.  Against an exact
- *               left fold the error is far below fp32 rounding.
+ *               left fold the error is far below fp32 rounding.  The pair
+ *               has fp32's exponent range: a segment holding +-inf gives
+ *               +-inf (NaN when it holds both, or a NaN, or inf * 0), and a
+ *               sum or product beyond fp32's range gives +-inf in result
+ *               and in result64.  Partial results that leave fp32's range
+ *               although the exact value would not (cancellation after an
+ *               overflow) are not defined.
  *   MAX, MIN    exact; NaN values are skipped; +0 beats -0 for MAX and -0
  *               beats +0 for MIN; an empty segment gives -inf / +inf.
  *   ARGMAX, ARGMIN  the first thread (in thread-ID order) holding the

@@ -201,17 +201,32 @@ __device__ __forceinline__ ff two_sum(float a, float b) {
     return {s, e};
 }
 // Renormalise (s, e) with |e| small against s: hi = fl(s + e), lo = the rest.
-__device__ __forceinline__ ff fast_two_sum(float s, float e) {
+// A running value s that is not finite (an infinite operand, an fp32
+// overflow, a NaN) is kept as it is with lo = 0: its error term is inf - inf
+// = NaN and must not reach hi, so that a sum meeting +inf stays +inf, as a
+// left fold gives (Sec. 3.3).  Applied to a pair it already normalised, it
+// returns the pair unchanged.
+__device__ __forceinline__ ff ff_settle(float s, float e) {
     const float h = s + e;
-    return {h, e - (h - s)};
+    const bool fin = fabsf(s) <= 3.402823466e38f;   // false for +-inf and NaN
+    return {fin ? h : s, fin ? e - (h - s) : 0.0f};
 }
 __device__ __forceinline__ ff ff_add(ff a, ff b) {
     const ff s = two_sum(a.hi, b.hi);
-    return fast_two_sum(s.hi, s.lo + (a.lo + b.lo));
+    return ff_settle(s.hi, s.lo + (a.lo + b.lo));
 }
 __device__ __forceinline__ ff ff_add_f(ff a, float b) {
     const ff s = two_sum(a.hi, b);
-    return fast_two_sum(s.hi, s.lo + a.lo);
+    return ff_settle(s.hi, s.lo + a.lo);
+}
+// Cascaded summation (Ogita, Rump and Oishi, "Accurate sum and dot
+// product", SIAM J. Sci. Comput. 2005, Algorithm Sum2): p takes the plain
+// fp32 sum and c collects the exact TwoSum errors, without renormalising
+// each step; ff_settle renormalises the pair once per group of values.
+__device__ __forceinline__ void sum2_step(float &p, float &c, float v) {
+    const ff s = two_sum(p, v);
+    p = s.hi;
+    c += s.lo;
 }
 __device__ __forceinline__ ff ff_shfl_xor(ff v, int off) {
     return {__shfl_xor_sync(0xffffffffu, v.hi, off), __shfl_xor_sync(0xffffffffu, v.lo, off)};
@@ -234,9 +249,11 @@ __device__ __forceinline__ double ff_to_double(ff v) { return (double)v.hi + (do
 // ---------------------------------------------------------------- map->reduce
 // Sum of out[e] over the elements of tile `tile` owned by this thread, in the
 // fixed order (vector u ascending, then lane j = 0..3 within the vector),
-// accumulated as a compensated pair, storing out[e] = fmaf(a, x[e], y[e])
-// when out != nullptr.  The vector path (aligned, full tile) and the element
-// path produce the same sequence of operations.
+// storing out[e] = fmaf(a, x[e], y[e]) when out != nullptr.  The values of
+// each group of kMrUnroll vectors (16 elements) fold by Sum2 steps into the
+// running pair, which ff_settle renormalises after the group (and after a
+// ragged tile's last element).  The vector path (aligned, full tile) and the
+// element path produce the same sequence of operations.
 // GROUPS (2 or 3): groups of kMrUnroll vectors per operand in flight on the
 // aligned full-tile path.  The fold order does not depend on it, so the
 // standalone kernel (3 groups, 120 registers) and the batched kernel (2
@@ -268,6 +285,7 @@ __device__ __forceinline__ ff mr_thread_partial(const float *__restrict__ x,
             }
         };
         auto consume = [&](const float4 *xv, const float4 *yv, int u0) {
+            float sp = acc.hi, sc = acc.lo;
 #pragma unroll
             for (int k = 0; k < kMrUnroll; ++k) {
                 float4 o;
@@ -276,11 +294,12 @@ __device__ __forceinline__ ff mr_thread_partial(const float *__restrict__ x,
                 o.z = fmaf(a, xv[k].z, yv[k].z);
                 o.w = fmaf(a, xv[k].w, yv[k].w);
                 if (out) st_stream4(o4 + (int64_t)(u0 + k) * nthreads + t, o);
-                acc = ff_add_f(acc, o.x);
-                acc = ff_add_f(acc, o.y);
-                acc = ff_add_f(acc, o.z);
-                acc = ff_add_f(acc, o.w);
+                sum2_step(sp, sc, o.x);
+                sum2_step(sp, sc, o.y);
+                sum2_step(sp, sc, o.z);
+                sum2_step(sp, sc, o.w);
             }
+            acc = ff_settle(sp, sc);
         };
         const int V = p.vecs_per_thread;
         constexpr int U = kMrUnroll;
@@ -309,6 +328,7 @@ __device__ __forceinline__ ff mr_thread_partial(const float *__restrict__ x,
             }
         }
     } else {
+        float sp = 0.0f, sc = 0.0f;
         for (int u = 0; u < p.vecs_per_thread; ++u) {
             const int64_t e0 = base + ((int64_t)u * nthreads + t) * 4;
             if (e0 >= p.n) break;   // later vectors of this thread are past n too
@@ -318,10 +338,16 @@ __device__ __forceinline__ ff mr_thread_partial(const float *__restrict__ x,
                 if (e < p.n) {
                     const float o = fmaf(a, __ldg(x + e), __ldg(y + e));
                     if (out) out[e] = o;
-                    acc = ff_add_f(acc, o);
+                    sum2_step(sp, sc, o);
                 }
             }
+            if (u % kMrUnroll == kMrUnroll - 1) {
+                acc = ff_settle(sp, sc);
+                sp = acc.hi;
+                sc = acc.lo;
+            }
         }
+        acc = ff_settle(sp, sc);
     }
     return acc;
 }

@@ -137,22 +137,27 @@ __device__ __forceinline__ Acc acc_init() {
 #endif
 }
 
+// A sum or product whose running value is not finite (an infinite operand,
+// an fp32 overflow, a NaN) keeps that value with lo = 0: its error term would
+// be inf - inf = NaN, and a left fold that meets +inf gives +inf.
+__device__ __forceinline__ bool hx_finite(float v) { return fabsf(v) <= 3.402823466e38f; }
+#if MONOID == 0 || MONOID == 3
+__device__ __forceinline__ Acc acc_pair(float s, float e) {
+    const float h = s + e;
+    return hx_finite(s) ? Acc{h, e - (h - s)} : Acc{s, 0.0f};
+}
+#endif
+
 // Fold one value of thread r into a running accumulator (thread-ID order).
 __device__ __forceinline__ void acc_fold(Acc &a, float v, i64 r) {
 #if MONOID == 0
     float s = a.hi + v, bb = s - a.hi;
     float e = (a.hi - (s - bb)) + (v - bb);     // exact error of a.hi + v
-    e = e + a.lo;
-    float h = s + e;
-    a.lo = e - (h - s);
-    a.hi = h;
+    a = acc_pair(s, e + a.lo);
 #elif MONOID == 3
     float pr = a.hi * v;
     float e = fmaf(a.hi, v, -pr);               // exact error of a.hi * v
-    e = fmaf(a.lo, v, e);
-    float h = pr + e;
-    a.lo = e - (h - pr);
-    a.hi = h;
+    a = acc_pair(pr, fmaf(a.lo, v, e));
 #elif MONOID == 1
     if (v > a.v || (v == 0.0f && a.v == 0.0f && signbit(a.v) && !signbit(v))) a.v = v;
 #elif MONOID == 2
@@ -182,8 +187,9 @@ __device__ __forceinline__ void acc_fold_run(Acc &a, float v, i64 r) {
 __device__ __forceinline__ void acc_settle(Acc &a) {
 #if MONOID == 0
     float s = a.hi + a.lo, bb = s - a.hi;
-    a.lo = (a.hi - (s - bb)) + (a.lo - bb);     // exact: hi + lo unchanged
-    a.hi = s;
+    const bool fin = hx_finite(a.hi);
+    a.lo = fin ? (a.hi - (s - bb)) + (a.lo - bb) : 0.0f;     // exact: hi + lo unchanged
+    a.hi = fin ? s : a.hi;
 #endif
 }
 
@@ -195,15 +201,11 @@ __device__ __forceinline__ Acc acc_combine(Acc a, Acc b) {
 #if MONOID == 0
     float s = a.hi + b.hi, bb = s - a.hi;
     float e = (a.hi - (s - bb)) + (b.hi - bb);
-    e = e + (a.lo + b.lo);
-    float h = s + e;
-    return Acc{h, e - (h - s)};
+    return acc_pair(s, e + (a.lo + b.lo));
 #elif MONOID == 3
     float pr = a.hi * b.hi;
     float e = fmaf(a.hi, b.hi, -pr);
-    e = e + (a.hi * b.lo + a.lo * b.hi);
-    float h = pr + e;
-    return Acc{h, e - (h - pr)};
+    return acc_pair(pr, e + (a.hi * b.lo + a.lo * b.hi));
 #elif MONOID == 1
     return (b.v > a.v || (b.v == 0.0f && a.v == 0.0f && signbit(a.v) && !signbit(b.v))) ? b : a;
 #elif MONOID == 2

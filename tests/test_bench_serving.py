@@ -54,9 +54,9 @@ def test_fixed_targets():
 def test_no_stable_per_launch_point_and_unmet_targets():
     sweep = {lam: (c, (pl[0], pl[1], False)) for lam, (c, pl) in SWEEP.items()}
     eq = bench.serving_comparison(_points(sweep))
-    # no stable per-launch rate: the lowest offered rate's p99 is the bound
-    assert eq["p99_bound_ms"] == 0.5992
+    # no stable per-launch rate: no bound and no ratio, flagged
+    assert eq["p99_bound_ms"] is None and eq["ratio"] is None
     assert eq["per_launch_req_per_s"] is None and eq["continuous_req_per_s"] is None
-    assert "ratio" not in eq
+    assert eq["per_launch_never_stable"] is True
     for row in eq["at_p99_targets"]:
         assert row["per_launch_req_per_s"] is None and "ratio" not in row

@@ -4,9 +4,11 @@ Tolerances (stated once, used everywhere):
   * map output: bit-exact against the fp64 oracle rounded to fp32.  On the
     input lattice (multiples of 2^-23, a = 1.5) a*x+y is exact in fp64, so
     the correctly rounded fmaf result equals that rounding.
-  * sum: |s_gpu - s_fp64| <= 1e-5 * sum|out_i| for every size (the sum's
-    condition number bounds what any fp32-output method can reach), and
-    <= 1e-5 * |s_fp64| for the standard 2^20-element workload.
+  * sum: |s_gpu - s_fp64| <= 1e-5 * |s_fp64| wherever |s_fp64| >= 1e-3 *
+    sum|out_i| (the float-float accumulator carries about 48 bits, so the
+    relative bound holds unless the sum nearly cancels); for a nearly
+    cancelling sum, <= 1e-5 * sum|out_i| (the sum's condition number bounds
+    what any fp32-output method can reach).
   * stencil: bit-exact against the fp32 evaluation of the same expression
     ((N+S)+(W+E))*0.25 and the same residual, and within 1e-5 normwise
     (max|diff| / max|u_fp64|) of the fp64 oracle.
@@ -54,7 +56,8 @@ def _check_mr(out_g, s32, s64, x, y, a):
     if out_g is not None:
         assert np.array_equal(out_g.view(np.uint32), out_o.astype(np.float32).view(np.uint32))
     cond = np.abs(out_o).sum()
-    assert abs(s64 - s_o) <= SUM_TOL * cond + 1e-300
+    scale = abs(s_o) if abs(s_o) >= 1e-3 * cond else cond
+    assert abs(s64 - s_o) <= SUM_TOL * scale + 1e-300
     assert np.float32(s64) == np.float32(s32)
 
 
