@@ -449,9 +449,17 @@ hx_status hx_autotune(hx_ctx *ctx, int32_t max_log2, hx_stream_t stream);
  * combine of every instance the launch completed (no CTA ever waits for
  * another).
  *
- * A stencil task with iters > 1 is executed as rounds: round r runs sweep r
- * of every stencil instance that has one (plus, in round 0, all map->reduce
- * and histogram instances); rounds are consecutive launches.
+ * A stencil task with iters > 1 runs all its sweeps inside the same
+ * persistent launch (the sequential outer loop of Sec. 4.4 rule 1 kept on
+ * the device): the work items of sweep s of an instance wait until every
+ * block of its sweep s - 1 is done.  Items are taken in an order in which
+ * every wait is for items already taken, and the launch never has more CTAs
+ * than the device holds at once, so every wait ends; each wait is also
+ * bounded in time (1 s): if one runs out, the launch records HX_ERR_TIMEOUT
+ * (hx_batch_status, hx_batch_query) and its results are not valid.  With
+ * HX_BATCH_ROUNDS (or above 255 sweeps) the plan runs as rounds instead:
+ * round r runs sweep r of every stencil instance that has one (plus, in
+ * round 0, all map->reduce and histogram instances), one launch per round.
  *
  * Pointer, size and alignment rules of each task kind are those of the
  * matching standalone call.  Instances of one batch must not write
@@ -484,6 +492,13 @@ typedef struct hx_batch hx_batch;
 hx_status hx_batch_plan(hx_ctx *ctx, const hx_task *tasks, int32_t n_tasks, hx_batch **out,
                         int32_t *out_rounds);
 
+/* hx_batch_plan with flags: 0 (the default schedule, every sweep in one
+ * launch) or HX_BATCH_ROUNDS (one launch per sweep).  Both give the same
+ * results; HX_ERR_INVALID for unknown flags. */
+#define HX_BATCH_ROUNDS 1
+hx_status hx_batch_plan_ex(hx_ctx *ctx, const hx_task *tasks, int32_t n_tasks, int32_t flags, hx_batch **out,
+                           int32_t *out_rounds);
+
 /* Run a planned batch on `stream`: one persistent launch per round, no host
  * synchronisation, no allocation (may be captured in a CUDA graph).  A plan
  * must not run on two streams at once. */
@@ -491,6 +506,21 @@ hx_status hx_batch_launch(hx_batch *batch, hx_stream_t stream);
 
 /* Free a plan.  Its launches must have completed. */
 void hx_batch_free(hx_batch *batch);
+
+/* After the plan's launches have completed (the caller synchronised their
+ * stream): HX_ERR_TIMEOUT if a wait between two sweeps of an instance ran
+ * out of time in any of them since the last call (their results are then not
+ * valid), else HX_OK.  Reads and clears a word of host memory; no CUDA call. */
+hx_status hx_batch_status(hx_batch *batch);
+
+/* Test hook for the bounded waits, without a GPU fault: the waits of task
+ * `task`'s later sweeps can never be satisfied (they expect one block more
+ * than the sweep has), and every wait of the plan gives up after
+ * wait_limit_ns nanoseconds instead of 1 s.  A launch of the plan then ends
+ * by itself with HX_ERR_TIMEOUT recorded.  Meant for a plan whose task
+ * `task` is a stencil with iters > 1; other plans are unaffected.  Returns
+ * HX_ERR_INVALID for a bad task index or a negative limit. */
+hx_status hx_debug_batch_stall(hx_batch *batch, int32_t task, int64_t wait_limit_ns);
 
 /* Plan, launch on `stream` and record completion in one call; *ticket_out
  * identifies the submission for hx_batch_query.  The plan is released when
@@ -500,7 +530,8 @@ hx_status hx_batch_submit(hx_ctx *ctx, const hx_task *tasks, int32_t n_tasks, hx
 
 /* HX_OK when the submission's device work has completed, HX_ERR_BUSY while
  * it is pending, HX_ERR_INVALID for an unknown ticket (including one already
- * reported complete). */
+ * reported complete), HX_ERR_TIMEOUT when it completed but a wait between
+ * sweeps ran out of time (see hx_batch_status). */
 hx_status hx_batch_query(hx_ctx *ctx, uint64_t ticket);
 
 /* ------------------------------------------------------------------ serving

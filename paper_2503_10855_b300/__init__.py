@@ -403,6 +403,13 @@ assert ctypes.sizeof(HxTask) == 64
 
 _lib.hx_batch_plan.argtypes = [_P, ctypes.POINTER(HxTask), _I32, ctypes.POINTER(_P), ctypes.POINTER(_I32)]
 _lib.hx_batch_plan.restype = ctypes.c_int
+_lib.hx_batch_plan_ex.argtypes = [_P, ctypes.POINTER(HxTask), _I32, _I32, ctypes.POINTER(_P), ctypes.POINTER(_I32)]
+_lib.hx_batch_plan_ex.restype = ctypes.c_int
+_lib.hx_batch_status.argtypes = [_P]
+_lib.hx_batch_status.restype = ctypes.c_int
+_lib.hx_debug_batch_stall.argtypes = [_P, _I32, _I64]
+_lib.hx_debug_batch_stall.restype = ctypes.c_int
+HX_BATCH_ROUNDS = 1
 _lib.hx_batch_launch.argtypes = [_P, _P]
 _lib.hx_batch_launch.restype = ctypes.c_int
 _lib.hx_batch_free.argtypes = [_P]
@@ -471,19 +478,31 @@ def _task_array(tasks):
 class Batch:
     """A planned batch (``hx_batch``): device work-list bound to the tasks' buffers."""
 
-    def __init__(self, ctx: Context, tasks):
+    def __init__(self, ctx: Context, tasks, rounds: bool = False):
+        """``rounds``: one launch per sweep (HX_BATCH_ROUNDS) instead of every
+        sweep in one launch."""
         self.ctx = ctx
         self.keep = [getattr(t, "keep", None) for t in tasks]
         arr = _task_array(tasks)
         h = _P()
-        rounds = _I32(0)
-        _check(_lib.hx_batch_plan(ctx.handle, arr, len(tasks), ctypes.byref(h), ctypes.byref(rounds)),
-               "hx_batch_plan")
+        n_rounds = _I32(0)
+        _check(_lib.hx_batch_plan_ex(ctx.handle, arr, len(tasks), HX_BATCH_ROUNDS if rounds else 0, ctypes.byref(h),
+                                     ctypes.byref(n_rounds)), "hx_batch_plan")
         self.handle = h
-        self.rounds = rounds.value
+        self.rounds = n_rounds.value
 
     def launch(self, stream=None) -> None:
         _check(_lib.hx_batch_launch(self.handle, _stream_handle(stream)), "hx_batch_launch")
+
+    def status(self) -> None:
+        """Raise HxError (HX_ERR_TIMEOUT) if a wait between sweeps ran out of
+        time in a completed launch (call after synchronising its stream)."""
+        _check(_lib.hx_batch_status(self.handle), "hx_batch_status")
+
+    def debug_stall(self, task: int, wait_limit_ns: int) -> None:
+        """Test hook (hx_debug_batch_stall): task's later sweeps wait for a block
+        that never comes, every wait gives up after wait_limit_ns."""
+        _check(_lib.hx_debug_batch_stall(self.handle, task, wait_limit_ns), "hx_debug_batch_stall")
 
     def close(self) -> None:
         if getattr(self, "handle", None) is not None and self.handle.value:
@@ -497,8 +516,8 @@ class Batch:
             pass
 
 
-def hx_batch_plan(ctx: Context, tasks) -> Batch:
-    return Batch(ctx, tasks)
+def hx_batch_plan(ctx: Context, tasks, rounds: bool = False) -> Batch:
+    return Batch(ctx, tasks, rounds)
 
 
 def hx_batch_launch(batch: Batch, stream=None) -> None:

@@ -12,10 +12,13 @@
 // partial results (map tile partials; atomic max / add into the instance's
 // accumulator for stencils and histograms): no fences, no arrival tickets.
 // A second launch, chained with programmatic dependent launch, runs the
-// final combine of every instance the launch completed, one warp each, so no
-// worker ever waits for another.  A stencil instance with several sweeps
-// contributes one sweep per round; rounds are consecutive launches.
+// final combine of every instance the launch completed, one CTA each.  A
+// stencil instance with several sweeps runs all of them in the same launch:
+// the runs of its sweep s wait (bounded) for its sweep s - 1; no other work
+// item ever waits.  The older schedule -- one launch per sweep ("rounds") --
+// remains available for comparison.
 #include <algorithm>
+#include <cstddef>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -58,23 +61,70 @@ __device__ __forceinline__ unsigned int find_instance(const uint32_t *__restrict
     return lo;
 }
 
+__device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int *p) {
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait (lane 0 of the warp) until *cnt >= target, at most sync.limit_ns; on
+// running out, record HX_ERR_TIMEOUT and go on.  Every lane then makes its
+// own acquire of *cnt, so the grid reads that follow see the writes counted.
+__device__ __forceinline__ void wait_count(const unsigned int *cnt, unsigned int target, const BatchSync &sync,
+                                           int lane) {
+    if (lane == 0 && ld_acquire_u32(cnt) < target) {
+        const unsigned long long t0 = globaltimer_ns();
+        while (ld_acquire_u32(cnt) < target) {
+            if (globaltimer_ns() - t0 > (unsigned long long)sync.limit_ns) {
+                // host-mapped word: a plain store (no atomic over the host link)
+                *reinterpret_cast<volatile unsigned int *>(sync.err) = (unsigned int)HX_ERR_TIMEOUT;
+                break;
+            }
+            __nanosleep(64);
+        }
+    }
+    __syncwarp();
+    (void)ld_acquire_u32(cnt);
+}
+
 // Phase 1 runs the CTA items (histogram chunks, CTA c takes items c, c + G,
 // ...); phase 2 the warp runs, fetched one at a time from a counter (each
 // warp prefetches its next index while it works, and runs are large, so the
 // counter sees a few thousand atomics per launch).  The work list is not
-// stored: item j belongs to the instance whose prefix range holds j (binary
+// stored: item j belongs to the pair whose prefix range holds j (binary
 // search), and its tiles follow from the instance's slice and run length, so
-// the host only uploads one descriptor per instance.
+// the host only uploads one descriptor per instance (and, with MULTI, one
+// word per (instance, sweep) pair).
+//
+// MULTI: stencil instances may run several sweeps in this launch (the
+// sequential outer loop of Sec. 4.4 rule 1, kept inside one persistent
+// launch).  Runs are taken in pair order -- every instance's first sweep
+// before any second sweep, and so on -- so a run of sweep s waits only for
+// runs taken before it; all CTAs of the launch are resident at once, hence
+// the oldest unfinished run never waits and every wait ends.  A sweep's runs
+// count their blocks in the instance's `done` word for that sweep (after a
+// fence, so the next sweep's readers see the grid they wrote); the next
+// sweep's runs wait for the full count (bounded, see BatchSync) and read the
+// grid through L2.  Grids, residuals and results are the same as the
+// standalone calls': every block computes the same values from the same
+// inputs, and a maximum does not depend on order.
+template <bool MULTI>
 __global__ void __launch_bounds__(kBatchThreads, 2)
 batch_kernel(const BInst *__restrict__ insts, unsigned int n_inst, const uint32_t *__restrict__ cta_prefix,
-             const uint32_t *__restrict__ run_prefix, int round, unsigned int *ctrl) {
+             const uint32_t *__restrict__ run_prefix, const uint32_t *__restrict__ pairs, unsigned int n_pairs,
+             int round, unsigned int *ctrl, BatchSync sync) {
     // No early launch_dependents: the final-combine kernel is launched as
     // the CTAs exit, so its CTAs do not wait on SM slots through the tail
     // (slots that kernels of concurrent streams can use meanwhile).
     asm volatile("griddepcontrol.wait;" ::: "memory");
     extern __shared__ __align__(16) unsigned int sh[];   // kHiSmemBytes when the round has CTA items
     const int lane = threadIdx.x & 31;
-    const unsigned int n_cta = __ldg(cta_prefix + n_inst), n_runs = __ldg(run_prefix + n_inst);
+    const unsigned int n_cta = __ldg(cta_prefix + n_inst), n_runs = __ldg(run_prefix + n_pairs);
 
     for (unsigned int it = blockIdx.x; it < n_cta; it += gridDim.x) {
         const unsigned int i = find_instance(cta_prefix, n_inst, it);
@@ -92,13 +142,16 @@ batch_kernel(const BInst *__restrict__ insts, unsigned int n_inst, const uint32_
     while (it < n_runs) {
         unsigned int next = 0u;
         if (lane == 0) next = atomicAdd(&ctrl[0], 1u);
-        const unsigned int i = find_instance(run_prefix, n_inst, it);
-        if (!HX_CHECK(i < n_inst, kChkBatchInst, i, n_inst)) {
+        const unsigned int kp = find_instance(run_prefix, n_pairs, it);
+        const uint32_t pr = MULTI ? __ldg(pairs + kp) : kp;
+        const unsigned int i = pr & (kMaxPairInstances - 1u);
+        const int phase = MULTI ? (int)(pr >> 24) : 0;
+        if (!HX_CHECK(kp < n_pairs && i < n_inst, kChkBatchInst, i, n_inst)) {
             it = __shfl_sync(0xffffffffu, next, 0);
             continue;
         }
         const BInst &I = insts[i];
-        const int64_t first = I.t_first + (int64_t)(it - __ldg(run_prefix + i)) * I.run_len;
+        const int64_t first = I.t_first + (int64_t)(it - __ldg(run_prefix + kp)) * I.run_len;
         const unsigned int cnt = (unsigned int)min((int64_t)I.run_len, I.t_first + I.t_count - first);
         if (!HX_CHECK(first >= 0 && first + cnt <= I.tiles, kChkBatchRun, first + cnt, I.tiles)) {
             it = __shfl_sync(0xffffffffu, next, 0);
@@ -114,7 +167,10 @@ batch_kernel(const BInst *__restrict__ insts, unsigned int n_inst, const uint32_
                 if (lane == 0) st_keep2(I.partials + tile, make_float2(part.hi, part.lo));
             }
         } else {
-            const int sweep = I.sweep0 + round;
+            const int sweep = I.sweep0 + round + phase;
+            const bool multi = MULTI && I.n_sweeps > 1;
+            if (multi && phase > 0)
+                wait_count(I.done + (phase - 1), (unsigned int)I.t_count + (I.stall ? 1u : 0u), sync, lane);
             const float *src = static_cast<const float *>((sweep & 1) ? I.in1 : I.in0);
             float *dst = const_cast<float *>(static_cast<const float *>((sweep & 1) ? I.in0 : I.in1));
             float m = 0.0f;
@@ -123,11 +179,17 @@ batch_kernel(const BInst *__restrict__ insts, unsigned int n_inst, const uint32_
                 const int wy = (int)(tile % (unsigned int)I.tiles_y), wx = (int)(tile / (unsigned int)I.tiles_y);
                 const int c_begin = wx * 128, r_begin = wy * kBatchStRows;
                 if (!HX_CHECK(c_begin < I.nx && r_begin < I.ny, kChkBatchStencil, c_begin, r_begin)) continue;
-                m = fmaxf(m, I.vec ? stencil_block_vec<kBatchStRows>(src, dst, I.nx, I.ny, c_begin, r_begin)
-                                   : stencil_block_scalar<kBatchStRows>(src, dst, I.nx, I.ny, c_begin, r_begin));
+                m = fmaxf(m, I.vec ? stencil_block_vec<kBatchStRows, MULTI>(src, dst, I.nx, I.ny, c_begin, r_begin)
+                                   : stencil_block_scalar<kBatchStRows, MULTI>(src, dst, I.nx, I.ny, c_begin, r_begin));
             }
             m = warp_max(m);
-            if (lane == 0) atomicMax(I.acc, __float_as_uint(m));
+            if (lane == 0) atomicMax(I.acc + phase, __float_as_uint(m));
+            if (multi && phase + 1 < I.n_sweeps) {
+                // publish this run's blocks to the next sweep's readers
+                __threadfence();
+                __syncwarp();
+                if (lane == 0) atomicAdd(I.done + phase, cnt);
+            }
         }
         it = __shfl_sync(0xffffffffu, next, 0);
     }
@@ -138,9 +200,12 @@ batch_kernel(const BInst *__restrict__ insts, unsigned int n_inst, const uint32_
 // instance, after the batched kernel has finished (programmatic dependent
 // launch waits for the whole grid): the sum of a map->reduce instance from
 // its tile partials in the standalone call's fixed order (all 256 threads
-// fold, one virtual lane each), the residual of a stencil sweep, the bins and
-// scan of a histogram (one warp).  Accumulators are left at
-// zero for the next use; the run counter is reset for the next launch.
+// fold, one virtual lane each), the residual of each stencil sweep the launch
+// ran, the bins and scan of a histogram (one warp).  Accumulators and sweep
+// arrival counts are left at zero for the next use; the run counter is reset
+// for the next launch.  An instance's first pairs are its sweep-0 pairs,
+// listed for every instance in instance order, so entries i and i + 1 of the
+// run prefix bound instance i's first-pass runs in either layout.
 __global__ void __launch_bounds__(kBatchThreads)
 batch_final_kernel(const BInst *__restrict__ insts, unsigned int n_inst, const uint32_t *__restrict__ cta_prefix,
                    const uint32_t *__restrict__ run_prefix, int round, unsigned int *ctrl) {
@@ -165,7 +230,11 @@ batch_final_kernel(const BInst *__restrict__ insts, unsigned int n_inst, const u
     } else if (threadIdx.x >= kWarp) {
         return;
     } else if (I.kind == kKindStencil) {
-        if (lane == 0) static_cast<float *>(I.o0)[I.sweep0 + round] = __uint_as_float(atomicExch(I.acc, 0u));
+        // the residual of every sweep the launch ran; arrival counts back to 0
+        for (int ph = lane; ph < I.n_sweeps; ph += kWarp) {
+            static_cast<float *>(I.o0)[I.sweep0 + round + ph] = __uint_as_float(atomicExch(I.acc + ph, 0u));
+            if (ph + 1 < I.n_sweeps) I.done[ph] = 0u;
+        }
     } else {
         // lane l owns bins 8l .. 8l+7: local prefix, then a shuffle scan of
         // the lane totals
@@ -230,19 +299,23 @@ void describe_instance(const hx_ctx *ctx, const hx_task &t, BInst *out, int64_t 
         I.run_len = 1;
         *acc_words = kHiBins;
     }
+    I.n_sweeps = 1;
     I.t_first = 0;
     I.t_count = I.tiles;
 }
 
 hx_status launch_batch_round(const hx_ctx *ctx, const BInst *d_insts, uint32_t n_inst, const uint32_t *d_cta_prefix,
-                             const uint32_t *d_run_prefix, uint32_t n_cta, uint32_t n_runs, int round,
-                             unsigned int *d_ctrl, cudaStream_t stream) {
+                             const uint32_t *d_run_prefix, const uint32_t *d_pairs, uint32_t n_pairs, uint32_t n_cta,
+                             uint32_t n_runs, int round, unsigned int *d_ctrl, BatchSync sync, cudaStream_t stream) {
     if (n_cta == 0 && n_runs == 0) return HX_OK;
     if (take_injected_failure(ctx)) return fail(HX_ERR_CUDA, "batched launch: injected launch failure (test hook)");
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
-    const int64_t cap = (int64_t)ctx->num_sms * ctx->batch_ctas_per_sm[n_cta > 0 ? 1 : 0];
+    // never more CTAs than the device holds at once: the multi-sweep waits
+    // rely on every CTA of the launch being resident
+    const int multi = d_pairs ? 1 : 0;
+    const int64_t cap = (int64_t)ctx->num_sms * ctx->batch_ctas_per_sm[multi][n_cta > 0 ? 1 : 0];
     const int64_t want = std::max<int64_t>(n_cta, ((int64_t)n_runs + kBatchThreads / kWarp - 1) / (kBatchThreads / kWarp));
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)std::min<int64_t>(cap, want));
@@ -251,7 +324,10 @@ hx_status launch_batch_round(const hx_ctx *ctx, const BInst *d_insts, uint32_t n
     cfg.stream = stream;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    cudaError_t e = cudaLaunchKernelEx(&cfg, batch_kernel, d_insts, n_inst, d_cta_prefix, d_run_prefix, round, d_ctrl);
+    cudaError_t e = multi ? cudaLaunchKernelEx(&cfg, batch_kernel<true>, d_insts, n_inst, d_cta_prefix, d_run_prefix,
+                                               d_pairs, n_pairs, round, d_ctrl, sync)
+                          : cudaLaunchKernelEx(&cfg, batch_kernel<false>, d_insts, n_inst, d_cta_prefix, d_run_prefix,
+                                               d_pairs, n_inst, round, d_ctrl, sync);
     if (e != cudaSuccess) return cuda_fail(e, "batched kernel launch");
     cfg.gridDim = dim3(n_inst);
     cfg.dynamicSmemBytes = 0;
@@ -271,12 +347,15 @@ size_t task_footprint(const hx_task &t) {
 }
 
 hx_status batch_setup(hx_ctx *ctx) {
-    cudaError_t e = cudaFuncSetAttribute((void *)batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         kHiSmemBytes);
-    for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
-        int occ = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_kernel, kBatchThreads, i ? kHiSmemBytes : 0);
-        ctx->batch_ctas_per_sm[i] = occ > 0 ? occ : 1;
+    const void *fns[2] = {(const void *)batch_kernel<false>, (const void *)batch_kernel<true>};
+    cudaError_t e = cudaSuccess;
+    for (int m = 0; m < 2 && e == cudaSuccess; ++m) {
+        e = cudaFuncSetAttribute(fns[m], cudaFuncAttributeMaxDynamicSharedMemorySize, kHiSmemBytes);
+        for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+            int occ = 0;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fns[m], kBatchThreads, i ? kHiSmemBytes : 0);
+            ctx->batch_ctas_per_sm[m][i] = occ > 0 ? occ : 1;
+        }
     }
     if (e != cudaSuccess) return cuda_fail(e, "hx_create: batch kernel set-up");
     return HX_OK;
@@ -289,12 +368,19 @@ HX_CHECKS_READER(checks_batch)
 struct hx_batch {
     hx_ctx *ctx = nullptr;
     int rounds = 0;
+    bool multi = false;                    // one launch runs every sweep of every stencil instance
     uint32_t n_inst = 0;
+    uint32_t n_pairs = 0;                  // multi: (instance, sweep) pairs of the launch
     std::vector<uint32_t> n_cta, n_runs;   // per round: CTA chunks, warp runs
     void *d_mem = nullptr;
     hx::BInst *d_insts = nullptr;
-    uint32_t *d_prefix = nullptr;          // per round: CTA prefix (n_inst + 1), run prefix (n_inst + 1)
-    unsigned int *d_ctrl = nullptr;        // run counter + finished-CTA counter (reset by each launch)
+    uint32_t *d_prefix = nullptr;          // per round: CTA prefix (n_inst + 1), run prefix (n_inst + 1);
+                                           // multi: CTA prefix (n_inst + 1), run prefix (n_pairs + 1)
+    uint32_t *d_pairs = nullptr;           // multi: the pair list
+    unsigned int *d_ctrl = nullptr;        // run counter (reset by each launch)
+    unsigned int *err_h = nullptr;         // host-mapped error word of the bounded waits
+    unsigned int *err_d = nullptr;
+    long long wait_ns = hx::kDefaultWaitNs;
 };
 
 namespace hx {
@@ -342,56 +428,121 @@ hx_status validate_task(const hx_task &t, int idx, const char *who) {
 
 }  // namespace hx
 
-extern "C" hx_status hx_batch_plan(hx_ctx *ctx, const hx_task *tasks, int32_t n_tasks, hx_batch **out,
-                                   int32_t *out_rounds) {
+namespace {
+
+// Releases a partly built plan.
+void free_plan(hx_batch *b) {
+    if (!b) return;
+    if (b->d_mem) cudaFree(b->d_mem);
+    if (b->err_h) cudaFreeHost(b->err_h);
+    delete b;
+}
+
+}  // namespace
+
+extern "C" hx_status hx_batch_plan_ex(hx_ctx *ctx, const hx_task *tasks, int32_t n_tasks, int32_t flags,
+                                      hx_batch **out, int32_t *out_rounds) {
     using namespace hx;
     if (!ctx || !out) return fail(HX_ERR_INVALID, "hx_batch_plan: ctx or out is NULL");
     *out = nullptr;
     if (n_tasks < 0 || (n_tasks > 0 && !tasks)) return fail(HX_ERR_INVALID, "hx_batch_plan: bad task list");
+    if (flags & ~HX_BATCH_ROUNDS) return fail(HX_ERR_INVALID, "hx_batch_plan: unknown flags");
+    if ((uint32_t)n_tasks >= kMaxPairInstances) return fail(HX_ERR_INVALID, "hx_batch_plan: too many tasks");
     for (int i = 0; i < n_tasks; ++i) {
         hx_status st = validate_task(tasks[i], i, "hx_batch_plan");
         if (st != HX_OK) return st;
     }
     std::vector<BInst> insts(n_tasks);
-    int rounds = n_tasks > 0 ? 1 : 0;
-    int64_t n_partials = 0, n_acc = 0;
+    int max_iters = 0;
     for (int i = 0; i < n_tasks; ++i) {
         int64_t np = 0, na = 0;
         describe_instance(ctx, tasks[i], &insts[i], &np, &na);
         if (insts[i].tiles > 0xffffffffll) return fail(HX_ERR_INVALID, "hx_batch_plan: instance too large");
-        n_partials += np;
-        n_acc += na;
-        if (insts[i].kind == kKindStencil) rounds = std::max(rounds, insts[i].iters);
+        if (insts[i].kind == kKindStencil) max_iters = std::max(max_iters, insts[i].iters);
     }
-    // Prefix sums of each round's work, round by round.  Round 0 holds the
-    // one-pass instances; stencil sweep r of each instance goes to round r.
+    // Several sweeps per stencil instance run in one launch unless the caller
+    // asks for rounds (round r = sweep r of every instance, one launch each).
+    // (An instance's sweep offset is stored in 8 bits of its pair entries:
+    // batches with more than 255 sweeps run as rounds.)
+    const bool multi = max_iters > 1 && max_iters <= 255 && !(flags & HX_BATCH_ROUNDS);
+    int rounds = n_tasks > 0 ? 1 : 0;
+    if (!multi) rounds = std::max(rounds, max_iters);
+    int64_t n_partials = 0, n_acc = 0;
+    for (BInst &I : insts) {
+        if (I.kind == kKindMap) n_partials += I.tiles;
+        else if (I.kind == kKindHist) n_acc += kHiBins;
+        else {
+            if (multi && I.iters > 1) I.n_sweeps = I.iters;
+            n_acc += 2 * I.n_sweeps - 1;   // one max per sweep, one arrival count per sweep but the last
+        }
+    }
+    // Prefix sums of each launch's work.  Rounds: per round r, the CTA
+    // prefix and the run prefix over instances (round 0 holds the one-pass
+    // instances; stencil sweep r of each instance goes to round r).  Multi:
+    // one launch; CTA prefix over instances, run prefix over the pair list:
+    // every instance's first pass, then each later sweep, largest instances
+    // first within a sweep (their blocks finish earliest, so the next
+    // sweep's first runs rarely wait).
     const size_t stride = (size_t)n_tasks + 1;
-    std::vector<uint32_t> prefix((size_t)rounds * 2 * stride, 0u);
+    std::vector<uint32_t> prefix, pairs;
     std::vector<uint32_t> round_cta(rounds), round_runs(rounds);
-    for (int r = 0; r < rounds; ++r) {
-        uint32_t *cp = prefix.data() + (size_t)r * 2 * stride, *rp = cp + stride;
+    if (!multi) {
+        prefix.assign((size_t)rounds * 2 * stride, 0u);
+        for (int r = 0; r < rounds; ++r) {
+            uint32_t *cp = prefix.data() + (size_t)r * 2 * stride, *rp = cp + stride;
+            uint64_t c = 0, w = 0;
+            for (int i = 0; i < n_tasks; ++i) {
+                cp[i] = (uint32_t)c;
+                rp[i] = (uint32_t)w;
+                const BInst &I = insts[i];
+                const bool active = (I.kind == kKindStencil) ? (r < I.iters) : (r == 0);
+                if (active) {
+                    c += inst_ctas(I);
+                    w += inst_runs(I);
+                }
+            }
+            if (c > 0xffffffffull || w > 0xffffffffull)
+                return fail(HX_ERR_INVALID, "hx_batch_plan: too many work items");
+            cp[n_tasks] = (uint32_t)c;
+            rp[n_tasks] = (uint32_t)w;
+            round_cta[r] = (uint32_t)c;
+            round_runs[r] = (uint32_t)w;
+        }
+    } else {
+        std::vector<uint32_t> cp(stride, 0u), rp;
         uint64_t c = 0, w = 0;
         for (int i = 0; i < n_tasks; ++i) {
             cp[i] = (uint32_t)c;
-            rp[i] = (uint32_t)w;
-            const BInst &I = insts[i];
-            const bool active = (I.kind == kKindStencil) ? (r < I.iters) : (r == 0);
-            if (active) {
-                c += inst_ctas(I);
-                w += inst_runs(I);
-            }
+            c += inst_ctas(insts[i]);
+            pairs.push_back(make_pair((uint32_t)i, 0u));
         }
-        if (c > 0xffffffffull || w > 0xffffffffull) return fail(HX_ERR_INVALID, "hx_batch_plan: too many work items");
         cp[n_tasks] = (uint32_t)c;
-        rp[n_tasks] = (uint32_t)w;
-        round_cta[r] = (uint32_t)c;
-        round_runs[r] = (uint32_t)w;
+        std::vector<int> by_size;
+        for (int i = 0; i < n_tasks; ++i)
+            if (insts[i].n_sweeps > 1) by_size.push_back(i);
+        std::stable_sort(by_size.begin(), by_size.end(),
+                         [&](int a, int b) { return insts[a].tiles > insts[b].tiles; });
+        for (int ph = 1; ph < max_iters; ++ph)
+            for (int i : by_size)
+                if (ph < insts[i].n_sweeps) pairs.push_back(make_pair((uint32_t)i, (uint32_t)ph));
+        for (uint32_t pr : pairs) {
+            rp.push_back((uint32_t)w);
+            w += inst_runs(insts[pr & (kMaxPairInstances - 1u)]);
+        }
+        rp.push_back((uint32_t)w);
+        if (c > 0xffffffffull || w > 0xffffffffull || pairs.size() > 0xffffffffull)
+            return fail(HX_ERR_INVALID, "hx_batch_plan: too many work items");
+        prefix = cp;
+        prefix.insert(prefix.end(), rp.begin(), rp.end());
+        round_cta[0] = (uint32_t)c;
+        round_runs[0] = (uint32_t)w;
     }
 
-    // One device allocation: insts | prefixes | partials | accumulators | run counter.
+    // One device allocation: insts | prefixes | pairs | partials | accumulators | run counter.
     auto align = [](size_t v) { return (v + 255) & ~(size_t)255; };
     const size_t off_pre = align(sizeof(BInst) * insts.size());
-    const size_t off_part = off_pre + align(sizeof(uint32_t) * prefix.size());
+    const size_t off_pairs = off_pre + align(sizeof(uint32_t) * prefix.size());
+    const size_t off_part = off_pairs + align(sizeof(uint32_t) * pairs.size());
     const size_t off_acc = off_part + align(sizeof(float2) * n_partials);
     const size_t off_ctrl = off_acc + align(sizeof(unsigned int) * n_acc);
     const size_t total = off_ctrl + 256;
@@ -400,29 +551,38 @@ extern "C" hx_status hx_batch_plan(hx_ctx *ctx, const hx_task *tasks, int32_t n_
     if (!b) return fail(HX_ERR_NOMEM, "hx_batch_plan: host allocation failed");
     b->ctx = ctx;
     b->rounds = rounds;
+    b->multi = multi;
     b->n_inst = (uint32_t)n_tasks;
+    b->n_pairs = multi ? (uint32_t)pairs.size() : (uint32_t)n_tasks;
     b->n_cta = round_cta;
     b->n_runs = round_runs;
     cudaError_t e = cudaMalloc(&b->d_mem, total);
+    if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void **>(&b->err_h), 64, cudaHostAllocMapped);
+    if (e == cudaSuccess) {
+        *b->err_h = 0u;
+        e = cudaHostGetDevicePointer(reinterpret_cast<void **>(&b->err_d), b->err_h, 0);
+    }
     if (e != cudaSuccess) {
-        delete b;
-        return cuda_fail(e, "hx_batch_plan: cudaMalloc");
+        free_plan(b);
+        return cuda_fail(e, "hx_batch_plan: allocation");
     }
     char *base = static_cast<char *>(b->d_mem);
     b->d_insts = reinterpret_cast<BInst *>(base);
     b->d_prefix = reinterpret_cast<uint32_t *>(base + off_pre);
+    b->d_pairs = multi ? reinterpret_cast<uint32_t *>(base + off_pairs) : nullptr;
     b->d_ctrl = reinterpret_cast<unsigned int *>(base + off_ctrl);
     int64_t pcur = 0, acur = 0;
-    for (int i = 0; i < n_tasks; ++i) {
-        BInst &I = insts[i];
+    unsigned int *acc_base = reinterpret_cast<unsigned int *>(base + off_acc);
+    for (BInst &I : insts) {
         if (I.kind == kKindMap) {
             I.partials = reinterpret_cast<float2 *>(base + off_part) + pcur;
             pcur += I.tiles;
         } else if (I.kind == kKindStencil) {
-            I.acc = reinterpret_cast<unsigned int *>(base + off_acc) + acur;
-            acur += 1;
+            I.acc = acc_base + acur;
+            I.done = I.n_sweeps > 1 ? I.acc + I.n_sweeps : nullptr;
+            acur += 2 * I.n_sweeps - 1;
         } else {
-            I.acc = reinterpret_cast<unsigned int *>(base + off_acc) + acur;
+            I.acc = acc_base + acur;
             acur += kHiBins;
         }
     }
@@ -431,9 +591,10 @@ extern "C" hx_status hx_batch_plan(hx_ctx *ctx, const hx_task *tasks, int32_t n_
         e = cudaMemcpy(b->d_insts, insts.data(), sizeof(BInst) * insts.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !prefix.empty())
         e = cudaMemcpy(b->d_prefix, prefix.data(), sizeof(uint32_t) * prefix.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !pairs.empty() && multi)
+        e = cudaMemcpy(b->d_pairs, pairs.data(), sizeof(uint32_t) * pairs.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
-        cudaFree(b->d_mem);
-        delete b;
+        free_plan(b);
         return cuda_fail(e, "hx_batch_plan: upload");
     }
     // Instances with no tiles still owe their outputs (n == 0 sums, empty
@@ -450,8 +611,7 @@ extern "C" hx_status hx_batch_plan(hx_ctx *ctx, const hx_task *tasks, int32_t n_
             if (e == cudaSuccess && t.u.hi.scan) e = cudaMemset(t.u.hi.scan, 0, 256 * sizeof(uint32_t));
         }
         if (e != cudaSuccess) {
-            cudaFree(b->d_mem);
-            delete b;
+            free_plan(b);
             return cuda_fail(e, "hx_batch_plan: empty instance outputs");
         }
     }
@@ -460,25 +620,55 @@ extern "C" hx_status hx_batch_plan(hx_ctx *ctx, const hx_task *tasks, int32_t n_
     return HX_OK;
 }
 
+extern "C" hx_status hx_batch_plan(hx_ctx *ctx, const hx_task *tasks, int32_t n_tasks, hx_batch **out,
+                                   int32_t *out_rounds) {
+    return hx_batch_plan_ex(ctx, tasks, n_tasks, 0, out, out_rounds);
+}
+
 extern "C" hx_status hx_batch_launch(hx_batch *b, hx_stream_t stream) {
     using namespace hx;
     if (!b) return fail(HX_ERR_INVALID, "hx_batch_launch: batch is NULL");
     DeviceGuard g(b->ctx->device);
+    const BatchSync sync{b->err_d, b->wait_ns};
+    if (b->multi)
+        return launch_batch_round(b->ctx, b->d_insts, b->n_inst, b->d_prefix, b->d_prefix + b->n_inst + 1, b->d_pairs,
+                                  b->n_pairs, b->n_cta[0], b->n_runs[0], 0, b->d_ctrl, sync, (cudaStream_t)stream);
     const size_t stride = (size_t)b->n_inst + 1;
     for (int r = 0; r < b->rounds; ++r) {
         const uint32_t *cp = b->d_prefix + (size_t)r * 2 * stride;
-        hx_status st = launch_batch_round(b->ctx, b->d_insts, b->n_inst, cp, cp + stride, b->n_cta[r], b->n_runs[r],
-                                          r, b->d_ctrl, (cudaStream_t)stream);
+        hx_status st = launch_batch_round(b->ctx, b->d_insts, b->n_inst, cp, cp + stride, nullptr, b->n_inst,
+                                          b->n_cta[r], b->n_runs[r], r, b->d_ctrl, sync, (cudaStream_t)stream);
         if (st != HX_OK) return st;
     }
+    return HX_OK;
+}
+
+extern "C" hx_status hx_batch_status(hx_batch *b) {
+    using namespace hx;
+    if (!b) return fail(HX_ERR_INVALID, "hx_batch_status: batch is NULL");
+    const unsigned int e = __atomic_exchange_n(b->err_h, 0u, __ATOMIC_ACQ_REL);
+    if (e == (unsigned int)HX_ERR_TIMEOUT)
+        return fail(HX_ERR_TIMEOUT, "hx_batch_status: a sweep's wait ran out of time; results are not valid");
+    return HX_OK;
+}
+
+extern "C" hx_status hx_debug_batch_stall(hx_batch *b, int32_t task, int64_t wait_limit_ns) {
+    using namespace hx;
+    if (!b || task < 0 || (uint32_t)task >= b->n_inst || wait_limit_ns < 0)
+        return fail(HX_ERR_INVALID, "hx_debug_batch_stall: bad arguments");
+    DeviceGuard g(b->ctx->device);
+    const int one = 1;
+    cudaError_t e = cudaMemcpy(reinterpret_cast<char *>(b->d_insts + task) + offsetof(BInst, stall), &one, sizeof one,
+                               cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "hx_debug_batch_stall");
+    b->wait_ns = wait_limit_ns;
     return HX_OK;
 }
 
 extern "C" void hx_batch_free(hx_batch *b) {
     if (!b) return;
     hx::DeviceGuard g(b->ctx->device);
-    if (b->d_mem) cudaFree(b->d_mem);
-    delete b;
+    free_plan(b);
 }
 
 extern "C" hx_status hx_batch_submit(hx_ctx *ctx, const hx_task *tasks, int32_t n_tasks, hx_stream_t stream,
@@ -518,8 +708,9 @@ extern "C" hx_status hx_batch_query(hx_ctx *ctx, uint64_t ticket) {
     cudaError_t e = cudaEventQuery(it->second.second);
     if (e == cudaErrorNotReady) return HX_ERR_BUSY;
     cudaEventDestroy(it->second.second);
+    const hx_status waits = e == cudaSuccess ? hx_batch_status(it->second.first) : HX_OK;
     hx_batch_free(it->second.first);
     ctx->pending.erase(it);
     if (e != cudaSuccess) return cuda_fail(e, "hx_batch_query: device work failed");
-    return HX_OK;
+    return waits;
 }

@@ -29,7 +29,7 @@ struct BInst {
     int tiles_x;        // stencil warp blocks across
     int tiles_y;        // stencil warp blocks down
     int run_len;        // map / stencil: tiles per warp run
-    int pad2;
+    int n_sweeps;       // stencil: sweeps sweep0 .. sweep0 + n_sweeps - 1 run in this launch (1 otherwise)
     int64_t t_first;    // this launch's slice: tiles (histogram: chunks) [t_first, t_first + t_count)
     int64_t t_count;
     MrPlan plan;
@@ -39,8 +39,24 @@ struct BInst {
     void *o1;           // map sum | hist scan
     void *o2;           // map sum64
     float2 *partials;   // map tile partials (hi, lo)
-    unsigned int *acc;  // stencil: max bits (1); hist: 256 bins
+    unsigned int *acc;  // stencil: max bits, one word per sweep of the launch; hist: 256 bins
+    unsigned int *done; // stencil with n_sweeps > 1: blocks finished, per sweep but the last
+    int stall;          // test hook (hx_debug_batch_stall): this instance's waits are never satisfied
+    int pad3;
 };
+
+// Bounded waits of a launch that runs several sweeps of an instance: a run
+// of sweep s waits until every block of sweep s - 1 of its instance is done.
+// A wait gives up after limit_ns nanoseconds of %globaltimer; the kernel
+// then records HX_ERR_TIMEOUT in *err (host-mapped memory, read by the host
+// once the launch has completed) and carries on, so no wait is unbounded and
+// no later wait depends on the one that gave up.
+struct BatchSync {
+    unsigned int *err;
+    long long limit_ns;
+};
+constexpr long long kDefaultWaitNs = 1000000000ll;   // 1 s
+constexpr int kMaxStepSweeps = 128;                 // sweeps of one request in one serving step
 
 // Checks one task against the rules of its standalone call.
 hx_status validate_task(const hx_task &t, int idx, const char *who);
@@ -56,15 +72,25 @@ inline uint32_t inst_runs(const BInst &I) {
 }
 inline uint32_t inst_ctas(const BInst &I) { return I.kind == kKindHist ? (uint32_t)I.t_count : 0u; }
 
-// Launches the batched kernel for one round (n_inst instances, exclusive
-// prefix sums of their CTA chunks and warp runs, n_inst + 1 entries each on
-// the device, totals n_cta and n_runs) and after it the final-combine kernel
-// for the instances the round completes.  d_ctrl: a zeroed word the kernels
-// use as the run counter and leave zeroed (launches sharing d_ctrl must be
-// ordered, e.g. on one stream).
+// Work items of one launch in the order workers take them: every instance's
+// sweep-0 work (and all map and histogram work), then the second sweep of
+// each instance that runs several, and so on.  Entry k of a launch's pair list
+// names (instance, sweep offset) as instance | offset << 24; the run prefix
+// then has one entry per pair plus a total.  A launch whose stencils run one
+// sweep each has no pair list: entry k is instance k.
+inline uint32_t make_pair(uint32_t inst, uint32_t phase) { return inst | (phase << 24); }
+constexpr uint32_t kMaxPairInstances = 1u << 24;
+
+// Launches the batched kernel (n_inst instances; exclusive prefix sums of
+// their CTA chunks, n_inst + 1 entries, and of their warp runs per pair,
+// n_pairs + 1 entries, on the device; totals n_cta and n_runs; d_pairs NULL
+// when every stencil instance runs one sweep, and then n_pairs == n_inst) and
+// after it the final-combine kernel for the instances it completes.  d_ctrl:
+// a zeroed word the kernels use as the run counter and leave zeroed
+// (launches sharing d_ctrl must be ordered, e.g. on one stream).
 hx_status launch_batch_round(const hx_ctx *ctx, const BInst *d_insts, uint32_t n_inst, const uint32_t *d_cta_prefix,
-                             const uint32_t *d_run_prefix, uint32_t n_cta, uint32_t n_runs, int round,
-                             unsigned int *d_ctrl, cudaStream_t stream);
+                             const uint32_t *d_run_prefix, const uint32_t *d_pairs, uint32_t n_pairs, uint32_t n_cta,
+                             uint32_t n_runs, int round, unsigned int *d_ctrl, BatchSync sync, cudaStream_t stream);
 
 // Device bytes a task's buffers occupy (inputs and outputs), for admission.
 size_t task_footprint(const hx_task &t);

@@ -459,6 +459,16 @@ __device__ __forceinline__ void mr_warp_item(const float *__restrict__ x, const 
 // ---------------------------------------------------------------- stencil
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
+// Grid loads.  A launch that only reads its source grid loads it through the
+// read-only path (__ldg); a launch that runs several sweeps writes the grids
+// it later reads, so it loads through L2 only (CG: ld.global.cg, coherent
+// across SMs).  The values are the same either way.
+template <bool CG, typename T>
+__device__ __forceinline__ T grid_ld(const T *p) {
+    if constexpr (CG) return __ldcg(p);
+    else return __ldg(p);
+}
+
 __device__ __forceinline__ float jacobi_point(float n, float s, float w, float e) {
     const float ns = n + s;
     const float we = w + e;
@@ -472,7 +482,7 @@ __device__ __forceinline__ float jacobi_point(float n, float s, float w, float e
 // block in flight at once; vertical neighbours come from registers and
 // horizontal ones from the neighbouring lanes.  Rows past ny are clamped on
 // load and not stored.  Returns the lane's max |u' - u|.
-template <int R>
+template <int R, bool CG = false>
 __device__ __forceinline__ float stencil_block_vec(const float *__restrict__ src, float *__restrict__ dst,
                                                    int nx, int ny, int c_begin, int r_begin) {
     const int lane = threadIdx.x & 31;
@@ -483,7 +493,7 @@ __device__ __forceinline__ float stencil_block_vec(const float *__restrict__ src
 #pragma unroll
     for (int k = 0; k < R + 2; ++k) {
         const int r = clampi(r_begin - 1 + k, 0, ny - 1);
-        rows[k] = __ldg(reinterpret_cast<const float4 *>(src + (size_t)r * nx + cl));
+        rows[k] = grid_ld<CG>(reinterpret_cast<const float4 *>(src + (size_t)r * nx + cl));
     }
     // halo columns: lane 0 needs column c0 - 1, lane 31 column c0 + 4
     const bool need_left = (lane == 0) && valid && c0 > 0;
@@ -493,7 +503,7 @@ __device__ __forceinline__ float stencil_block_vec(const float *__restrict__ src
 #pragma unroll
     for (int k = 0; k < R; ++k) {
         const int r = min(r_begin + k, ny - 1);
-        halo[k] = (need_left || need_right) ? __ldg(src + (size_t)r * nx + hc) : 0.0f;
+        halo[k] = (need_left || need_right) ? grid_ld<CG>(src + (size_t)r * nx + hc) : 0.0f;
     }
     float m = 0.0f;
 #pragma unroll
@@ -526,7 +536,7 @@ __device__ __forceinline__ float stencil_block_vec(const float *__restrict__ src
 // [0, nx-1] when loading, which makes the clamp-to-edge rule automatic:
 // past the last column a lane just re-reads column nx-1.  Same arithmetic per
 // point as the vector path.
-template <int R>
+template <int R, bool CG = false>
 __device__ __forceinline__ float stencil_block_scalar(const float *__restrict__ src, float *__restrict__ dst,
                                                       int nx, int ny, int c_begin, int r_begin) {
     const int lane = threadIdx.x & 31;
@@ -539,14 +549,14 @@ __device__ __forceinline__ float stencil_block_scalar(const float *__restrict__ 
     for (int k = 0; k < R + 2; ++k) {
         const float *row = src + (size_t)clampi(r_begin - 1 + k, 0, ny - 1) * nx;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) rows[k][j] = __ldg(row + cc[j]);
+        for (int j = 0; j < 4; ++j) rows[k][j] = grid_ld<CG>(row + cc[j]);
     }
     const int hc = (lane == 0) ? max(c0 - 1, 0) : min(c0 + 4, nx - 1);
     float halo[R];
 #pragma unroll
     for (int k = 0; k < R; ++k) {
         const int r = min(r_begin + k, ny - 1);
-        halo[k] = (lane == 0 || lane == 31) ? __ldg(src + (size_t)r * nx + hc) : 0.0f;
+        halo[k] = (lane == 0 || lane == 31) ? grid_ld<CG>(src + (size_t)r * nx + hc) : 0.0f;
     }
     float m = 0.0f;
 #pragma unroll
@@ -577,20 +587,21 @@ __device__ __forceinline__ float stencil_block_scalar(const float *__restrict__ 
 }
 
 // ---------------------------------------------------------------- histogram
-// Shared counters are laid out [bin][slot], 256 bins x 64 slots of uint32
-// (64 KiB, dynamic shared memory).  A thread owns slot (lane + 32 * (warp &
-// 1)): one warp-wide increment touches 32 different banks whatever the data,
-// and neighbouring warps share no counter.  A bin row is 256 bytes, so the
-// byte offset of bin b in a thread's slot is (b << 8) | slot_offset, with
-// slot_offset < 256: one prmt builds it straight from the loaded word (byte k
-// of the word into bits 8-15, the slot offset into bits 0-7), and the shared
-// atomic adds the array base as an immediate.  Two instructions per byte.
-constexpr int kHiSlots = 64;
-constexpr int kHiSmemBytes = kHiBins * kHiSlots * 4;
+// Shared counters are laid out [bin][slot] with bin rows of 256 bytes
+// (64 KiB of dynamic shared memory); a thread counts into slot (lane): lane
+// l's counter of bin b is the word at byte offset (b << 8) | (l << 2), so a
+// warp-wide increment touches 32 different banks whatever the data.  Only
+// the first 32 words of each row are used: zeroing and merging touch 32 KiB
+// (measured on B300: 3-5 % faster from 2^24 to 2^28 bytes than 64 slots with
+// both halves used).  The row stride keeps the offset one prmt away from the
+// loaded word (byte k of the word into bits 8-15, the slot offset into bits
+// 0-7), and the shared atomic adds the array base as an immediate.  Two
+// instructions per byte.
+constexpr int kHiSlots = 32;
+constexpr int kHiRowWords = 64;
+constexpr int kHiSmemBytes = kHiBins * kHiRowWords * 4;
 
-__device__ __forceinline__ unsigned int hist_slot_offset() {
-    return ((threadIdx.x & 31u) << 2) | (((threadIdx.x >> 5) & 1u) << 7);
-}
+__device__ __forceinline__ unsigned int hist_slot_offset() { return (threadIdx.x & 31u) << 2; }
 __device__ __forceinline__ void hist_inc(unsigned int *sh, unsigned int byte_off) {
     atomicAdd(reinterpret_cast<unsigned int *>(reinterpret_cast<char *>(sh) + byte_off), 1u);
 }
@@ -609,39 +620,56 @@ __device__ __forceinline__ void hist_count_vec(unsigned int *sh, unsigned int sl
 __device__ __forceinline__ void hist_count_byte(unsigned int *sh, unsigned int slot, unsigned int b) {
     hist_inc(sh, (b << 8) | slot);
 }
-// Zero the counters (all threads of the CTA; a barrier must follow).
+// Zero the used half of every bin row (all threads of the CTA; a barrier
+// must follow).
 __device__ __forceinline__ void hist_zero(unsigned int *sh) {
     uint4 *s4 = reinterpret_cast<uint4 *>(sh);
-    for (int i = threadIdx.x; i < kHiSmemBytes / 16; i += blockDim.x) s4[i] = make_uint4(0, 0, 0, 0);
+    for (int i = threadIdx.x; i < kHiBins * kHiSlots / 4; i += blockDim.x)
+        s4[(i >> 3) * (kHiRowWords / 4) + (i & 7)] = make_uint4(0, 0, 0, 0);
 }
-// Fold the 64 slots of each bin (rotated start: conflict-free) and add the
-// non-zero totals into bins_out with integer atomics (exact, any order).
-// Called after a barrier; returns whether this thread issued an atomic.
+// Fold the slots of each bin and add the non-zero totals into bins_out with
+// integer atomics (exact, any order).  blockDim.x / 256 consecutive threads
+// share a bin, each summing an equal share of its slots from a start rotated
+// by the bin (conflict-free), then combine by shuffle.  Called after a
+// barrier by every thread (blockDim.x = 256, 512 or 1024); returns whether
+// this thread issued an atomic.
 __device__ __forceinline__ bool hist_merge(const unsigned int *sh, unsigned int *bins_out) {
-    bool wrote = false;
-    for (int b = threadIdx.x; b < kHiBins; b += blockDim.x) {
-        unsigned int c = 0u;
+    const int T = blockDim.x / kHiBins;
+    const int bin = threadIdx.x / T, sub = threadIdx.x % T, per = kHiSlots / T;
+    unsigned int c = 0u;
 #pragma unroll 8
-        for (int k = 0; k < kHiSlots; ++k) c += sh[b * kHiSlots + ((k + b) & (kHiSlots - 1))];
-        if (c) {
-            atomicAdd(bins_out + b, c);
-            wrote = true;
-        }
+    for (int k = 0; k < per; ++k) c += sh[bin * kHiRowWords + ((sub * per + k + bin) & (kHiSlots - 1))];
+    for (int off = 1; off < T; off <<= 1) c += __shfl_xor_sync(0xffffffffu, c, off);
+    if (sub == 0 && c) {
+        atomicAdd(bins_out + bin, c);
+        return true;
     }
-    return wrote;
+    return false;
 }
 
 // Count the 16-byte vectors v4[first], v4[first + stride], ... below nvec into
 // the shared counters, keeping the next two vectors' loads in flight while
-// the current two are counted.
-__device__ __forceinline__ void hist_count_strided(unsigned int *sh, unsigned int slot,
-                                                   const uint4 *__restrict__ v4, int64_t first, int64_t stride,
-                                                   int64_t nvec) {
+// the current two are counted.  hist_first_loads issues the first two loads
+// (so that a kernel can zero its counters while they are in flight) and
+// hist_count_from continues from them.
+struct HistPair {
+    uint4 a0, a1;
+    bool h0, h1;
+};
+__device__ __forceinline__ HistPair hist_first_loads(const uint4 *__restrict__ v4, int64_t first, int64_t stride,
+                                                     int64_t nvec) {
+    HistPair q;
+    q.h0 = first < nvec;
+    q.h1 = first + stride < nvec;
+    q.a0 = q.h0 ? ld_stream_u4(v4 + first) : make_uint4(0, 0, 0, 0);
+    q.a1 = q.h1 ? ld_stream_u4(v4 + first + stride) : make_uint4(0, 0, 0, 0);
+    return q;
+}
+__device__ __forceinline__ void hist_count_from(unsigned int *sh, unsigned int slot, const uint4 *__restrict__ v4,
+                                                int64_t first, int64_t stride, int64_t nvec, HistPair q) {
     int64_t i = first;
-    bool h0 = i < nvec, h1 = i + stride < nvec;
-    uint4 a0 = make_uint4(0, 0, 0, 0), a1 = a0;
-    if (h0) a0 = ld_stream_u4(v4 + i);
-    if (h1) a1 = ld_stream_u4(v4 + i + stride);
+    bool h0 = q.h0, h1 = q.h1;
+    uint4 a0 = q.a0, a1 = q.a1;
     while (h0) {
         const int64_t j = i + 2 * stride;
         const bool g0 = j < nvec, g1 = j + stride < nvec;
@@ -656,6 +684,11 @@ __device__ __forceinline__ void hist_count_strided(unsigned int *sh, unsigned in
         h1 = g1;
         i = j;
     }
+}
+__device__ __forceinline__ void hist_count_strided(unsigned int *sh, unsigned int slot,
+                                                   const uint4 *__restrict__ v4, int64_t first, int64_t stride,
+                                                   int64_t nvec) {
+    hist_count_from(sh, slot, v4, first, stride, nvec, hist_first_loads(v4, first, stride, nvec));
 }
 
 // ---------------------------------------------------------------- host side
@@ -673,7 +706,7 @@ struct hx_ctx {
     bool slot_used[HX_MAX_STREAMS] = {};
     hx_tune_table tune = {};             // per-size-class choices (see hx.h)
     int hist_ctas_per_sm[3] = {1, 1, 1}; // resident CTAs per SM for widths 256, 512, 1024
-    int batch_ctas_per_sm[2] = {1, 1};   // batched kernel without / with histogram counters
+    int batch_ctas_per_sm[2][2] = {{1, 1}, {1, 1}};   // batched kernel [one sweep / several][without / with histogram counters]
     // test hook: after `inject_after` more launching calls, `inject_count`
     // calls fail before launching
     mutable std::mutex inject_mu;

@@ -64,6 +64,7 @@ struct Step {
     cudaEvent_t ev = nullptr;
     int slot = -1;             // continuous mode: staging slot to release
     std::vector<Req *> finishing;
+    std::vector<Req *> members;   // continuous mode: every request with work in the step
 };
 
 }  // namespace
@@ -82,6 +83,8 @@ struct hx_server {
     std::vector<hx::Slot> slots;
     std::vector<cudaEvent_t> free_events;     // per-launch mode
     char *ws_pool = nullptr;                  // continuous mode: max_inflight workspace slots (+ run counter)
+    unsigned int *err_h = nullptr;            // host-mapped error word of the steps' bounded waits
+    unsigned int *err_d = nullptr;
     uint64_t failed_at_drain = 0;             // stats.failed when the last drain returned
     unsigned int *ctrl = nullptr;
     std::vector<int> free_ws;
@@ -174,28 +177,36 @@ int64_t tile_bytes(const BInst &I) {
 }
 
 // Continuous mode: build one step out of the next slice of every admitted
-// request (at most step_quantum_bytes of traffic each; a stencil slice never
-// crosses a sweep boundary), upload its descriptors and prefix sums, launch.
+// request (at most its share of step_target_bytes, and at least
+// step_quantum_bytes, of traffic), upload its descriptors and prefix sums,
+// launch.  A stencil slice stays within one sweep, except that a stencil
+// request at a sweep boundary takes all its remaining sweeps (up to
+// kMaxStepSweeps) when it is the only request with work, or when those
+// sweeps fit its share: the step's persistent launch then runs them one
+// after another (waits between sweeps on the device, see hx_batch.cuh).
 bool issue_step_locked(hx_server *s) {
     int slot = -1;
     for (size_t i = 0; i < s->slots.size(); ++i)
         if (!s->slots[i].busy) { slot = (int)i; break; }
     if (slot < 0 || (int)s->steps.size() >= s->cfg.max_steps_in_flight) return false;
     Slot &sl = s->slots[slot];
-    // Staging layout, uploaded with one copy: descriptors, then the CTA and
-    // run prefix arrays (n + 1 entries each), placed after the step is built.
+    // Staging layout, uploaded with one copy: descriptors, then the CTA
+    // prefix (n + 1 entries), the run prefix (one entry per pair + 1) and,
+    // when some request runs several sweeps, the pair list.
     BInst *insts = reinterpret_cast<BInst *>(sl.h);
-    std::vector<uint32_t> cpv, rpv;
+    std::vector<uint32_t> cpv;
     cpv.reserve(s->active.size() + 1);
-    rpv.reserve(s->active.size() + 1);
+    std::vector<std::pair<uint32_t, int>> multi;   // (instance, sweeps) of requests running several sweeps
+    const size_t max_extra = (size_t)s->cfg.max_step_requests;   // pairs beyond the first pass
+    size_t extra = 0;
     uint32_t n = 0;
-    uint64_t c = 0, w = 0;
+    uint64_t c = 0;
     Step step;
-    std::vector<Req *> in_step;   // every request with work (or an output) in this step
     // Slice size: the step aims at step_target_bytes of traffic shared by the
     // requests in it, but each gets at least step_quantum_bytes.
     size_t n_work = 0;
     for (Req *r : s->active) n_work += (!r->issued_all && r->inst.tiles > 0) ? 1 : 0;
+    const bool alone = n_work == 1;
     n_work = std::min<size_t>(std::max<size_t>(n_work, 1), (size_t)s->cfg.max_step_requests);
     const size_t quantum = std::max(s->cfg.step_quantum_bytes, s->cfg.step_target_bytes / n_work);
     for (Req *r : s->active) {
@@ -204,22 +215,46 @@ bool issue_step_locked(hx_server *s) {
             if (write_trivial(s->stream, r->task) != cudaSuccess) r->status = HX_ERR_CUDA;
             r->issued_all = true;
             step.finishing.push_back(r);
-            in_step.push_back(r);
+            step.members.push_back(r);
             continue;
         }
         if ((int)n >= s->cfg.max_step_requests) continue;
         BInst I = r->inst;
-        const int64_t q = std::max<int64_t>(1, (int64_t)quantum / tile_bytes(I));
-        I.t_first = r->issued;
-        I.t_count = std::min<int64_t>(q, I.tiles - r->issued);
         I.sweep0 = I.kind == kKindStencil ? r->sweep : 0;
-        if (c + inst_ctas(I) > 0xffffffffull || w + inst_runs(I) > 0xffffffffull) continue;
+        int sweeps = 1;
+        if (I.kind == kKindStencil && r->issued == 0) {
+            const int left = I.iters - r->sweep;
+            const int64_t sweep_bytes = I.tiles * tile_bytes(I);
+            if (left > 1 && (alone || (int64_t)left * sweep_bytes <= (int64_t)quantum))
+                sweeps = std::min(left, kMaxStepSweeps);
+            if (extra + (size_t)(sweeps - 1) > max_extra) sweeps = 1;
+        }
+        if (sweeps > 1) {
+            I.t_first = 0;
+            I.t_count = I.tiles;
+            I.n_sweeps = sweeps;
+            I.done = I.acc + sweeps;
+        } else {
+            const int64_t q = std::max<int64_t>(1, (int64_t)quantum / tile_bytes(I));
+            I.t_first = r->issued;
+            I.t_count = std::min<int64_t>(q, I.tiles - r->issued);
+        }
+        if (c + inst_ctas(I) > 0xffffffffull) continue;
         cpv.push_back((uint32_t)c);
-        rpv.push_back((uint32_t)w);
         c += inst_ctas(I);
-        w += inst_runs(I);
+        if (sweeps > 1) {
+            multi.emplace_back(n, sweeps);
+            extra += (size_t)(sweeps - 1);
+        }
         insts[n++] = I;
-        in_step.push_back(r);
+        step.members.push_back(r);
+        if (sweeps > 1) {
+            r->sweep += sweeps;
+            if (r->sweep < I.iters) continue;
+            r->issued_all = true;
+            step.finishing.push_back(r);
+            continue;
+        }
         r->issued += I.t_count;
         if (r->issued == I.tiles) {
             r->issued = 0;
@@ -230,29 +265,54 @@ bool issue_step_locked(hx_server *s) {
     }
     if (n == 0 && step.finishing.empty()) return false;
     cpv.push_back((uint32_t)c);
+    // pair list: every instance's first pass in order, then the later sweeps,
+    // largest instances first within a sweep
+    std::vector<uint32_t> pairs, rpv;
+    for (uint32_t i = 0; i < n; ++i) pairs.push_back(make_pair(i, 0u));
+    std::stable_sort(multi.begin(), multi.end(),
+                     [&](const std::pair<uint32_t, int> &a, const std::pair<uint32_t, int> &b) {
+                         return insts[a.first].tiles > insts[b.first].tiles;
+                     });
+    int max_sweeps = 1;
+    for (const auto &m : multi) max_sweeps = std::max(max_sweeps, m.second);
+    for (int ph = 1; ph < max_sweeps; ++ph)
+        for (const auto &m : multi)
+            if (ph < m.second) pairs.push_back(make_pair(m.first, (uint32_t)ph));
+    uint64_t w = 0;
+    for (uint32_t pr : pairs) {
+        rpv.push_back((uint32_t)w);
+        w += inst_runs(insts[pr & (kMaxPairInstances - 1u)]);
+    }
     rpv.push_back((uint32_t)w);
+    const bool use_pairs = !multi.empty();
     const size_t off_cta = ((size_t)n * sizeof(BInst) + 15) & ~(size_t)15;
     const size_t off_run = off_cta + (((size_t)(n + 1) * 4 + 15) & ~(size_t)15);
+    const size_t off_pairs = off_run + ((rpv.size() * 4 + 15) & ~(size_t)15);
+    const size_t bytes = use_pairs ? off_pairs + pairs.size() * 4 : off_run + rpv.size() * 4;
     memcpy(sl.h + off_cta, cpv.data(), (n + 1) * 4);
-    memcpy(sl.h + off_run, rpv.data(), (n + 1) * 4);
+    memcpy(sl.h + off_run, rpv.data(), rpv.size() * 4);
+    if (use_pairs) memcpy(sl.h + off_pairs, pairs.data(), pairs.size() * 4);
     s->active.erase(std::remove_if(s->active.begin(), s->active.end(), [](Req *r) { return r->issued_all; }),
                     s->active.end());
     hx_status st = HX_OK;
     if (n > 0) {
-        cudaError_t e = cudaMemcpyAsync(sl.d, sl.h, off_run + (n + 1) * 4, cudaMemcpyHostToDevice, s->stream);
+        cudaError_t e = w > 0xffffffffull ? cudaErrorInvalidValue
+                                          : cudaMemcpyAsync(sl.d, sl.h, bytes, cudaMemcpyHostToDevice, s->stream);
         if (e != cudaSuccess) st = cuda_fail(e, "server: step upload");
         if (st == HX_OK)
             st = launch_batch_round(s->ctx, reinterpret_cast<const BInst *>(sl.d), n,
                                     reinterpret_cast<const uint32_t *>(sl.d + off_cta),
-                                    reinterpret_cast<const uint32_t *>(sl.d + off_run), (uint32_t)c, (uint32_t)w, 0,
-                                    s->ctrl, s->stream);
+                                    reinterpret_cast<const uint32_t *>(sl.d + off_run),
+                                    use_pairs ? reinterpret_cast<const uint32_t *>(sl.d + off_pairs) : nullptr,
+                                    use_pairs ? (uint32_t)pairs.size() : n, (uint32_t)c, (uint32_t)w, 0, s->ctrl,
+                                    BatchSync{s->err_d, kDefaultWaitNs}, s->stream);
         s->stats.launches += 1;
     }
     if (st == HX_OK && cudaEventRecord(sl.ev, s->stream) != cudaSuccess) st = HX_ERR_CUDA;
     if (st != HX_OK) {
         // every request with work in the failed step fails, finished or not:
         // a sliced request missing this slice would compute a wrong result
-        fail_requests_locked(s, in_step, st);
+        fail_requests_locked(s, step.members, st);
         s->active.erase(std::remove_if(s->active.begin(), s->active.end(), [](Req *r) { return r->done; }),
                         s->active.end());
         return true;
@@ -362,6 +422,10 @@ void completer_main(hx_server *s) {
         lk.lock();
         Step step = std::move(s->steps.front());
         s->steps.pop_front();
+        // a wait between two sweeps that ran out of time invalidates every
+        // request that had work in the step (they complete with the error)
+        if (s->err_h && e == cudaSuccess && __atomic_exchange_n(s->err_h, 0u, __ATOMIC_ACQ_REL) != 0u)
+            for (Req *r : step.members) r->status = HX_ERR_TIMEOUT;
         for (Req *r : step.finishing) {
             if (e != cudaSuccess) r->status = HX_ERR_CUDA;
             if (r->status != HX_OK) s->stats.failed += 1;
@@ -436,13 +500,20 @@ hx_status hx_server_create(hx_ctx *ctx, const hx_server_config *cfg, hx_server *
         auto align = [](size_t v) { return (v + 255) & ~(size_t)255; };
         const size_t K = (size_t)s->cfg.max_step_requests;
         s->slots.resize((size_t)s->cfg.max_steps_in_flight + 1);
+        // descriptors, CTA prefix, run prefix and pair list (at most K
+        // first-pass pairs and K more for requests running several sweeps)
         for (Slot &sl : s->slots) {
-            sl.bytes = align(K * sizeof(BInst)) + 2 * align((K + 1) * 4);
+            sl.bytes = align(K * sizeof(BInst)) + align((K + 1) * 4) + 2 * align((2 * K + 1) * 4);
             if (e == cudaSuccess) e = cudaMallocHost(&sl.h, sl.bytes);
             if (e == cudaSuccess) e = cudaMalloc(&sl.d, sl.bytes);
             if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming);
         }
         const size_t pool = (size_t)s->cfg.max_inflight * kWsBytes;
+        if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void **>(&s->err_h), 64, cudaHostAllocMapped);
+        if (e == cudaSuccess) {
+            *s->err_h = 0u;
+            e = cudaHostGetDevicePointer(reinterpret_cast<void **>(&s->err_d), s->err_h, 0);
+        }
         if (e == cudaSuccess) e = cudaMalloc(&s->ws_pool, pool + 256);
         if (e == cudaSuccess) e = cudaMemset(s->ws_pool, 0, pool + 256);
         s->ctrl = reinterpret_cast<unsigned int *>(s->ws_pool + pool);
@@ -456,6 +527,7 @@ hx_status hx_server_create(hx_ctx *ctx, const hx_server_config *cfg, hx_server *
             if (sl.ev) cudaEventDestroy(sl.ev);
         }
         if (s->ws_pool) cudaFree(s->ws_pool);
+        if (s->err_h) cudaFreeHost(s->err_h);
         cudaStreamDestroy(s->stream);
         delete s;
         return cuda_fail(e, "hx_server_create: staging");
@@ -485,6 +557,7 @@ void hx_server_destroy(hx_server *s) {
     }
     for (cudaEvent_t ev : s->free_events) cudaEventDestroy(ev);
     if (s->ws_pool) cudaFree(s->ws_pool);
+    if (s->err_h) cudaFreeHost(s->err_h);
     cudaStreamDestroy(s->stream);
     delete s;
 }

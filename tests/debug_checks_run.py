@@ -52,7 +52,8 @@ with hx.hx_create(0) as ctx:
         bins, scan = hx.hx_histogram(ctx, v)
         b_o, _ = oracle.histogram(v.cpu().numpy())
         ok &= np.array_equal(bins.cpu().numpy().view(np.uint32), b_o)
-    # a mixed batch with several rounds (multi-sweep stencils) and histograms
+    # a mixed batch with multi-sweep stencils and histograms, planned both
+    # ways: every sweep in one launch, and one launch per sweep (rounds)
     tasks, keep = [], []
     for k in range(24):
         if k % 3 == 0:
@@ -69,11 +70,13 @@ with hx.hx_create(0) as ctx:
             vv = torch.randint(0, 256, (70_001 * k,), dtype=torch.uint8, device=dev)
             tasks.append(hx.histogram_task(vv, torch.empty(256, dtype=torch.int32, device=dev),
                                            torch.empty(256, dtype=torch.int32, device=dev)))
-    b = hx.hx_batch_plan(ctx, tasks)
-    b.launch()
-    b.launch()
-    torch.cuda.synchronize()
-    b.close()
+    for rounds in (False, True):
+        b = hx.hx_batch_plan(ctx, tasks, rounds=rounds)
+        b.launch()
+        b.launch()
+        torch.cuda.synchronize()
+        b.status()
+        b.close()
     for shape, roi in (((100, 404), (40, 60, 150, 250)), ((33, 257), (0, 33, 0, 257)), ((512, 512), (0, 128, 0, 128))):
         J = workloads.srad_image(*shape)
         J0 = torch.from_numpy(J).to(dev)

@@ -153,16 +153,104 @@ def _mixed_specs():
     return specs
 
 
+@pytest.mark.parametrize("rounds", [False, True])
 @pytest.mark.parametrize("offset", [0, 1])
-def test_mixed_batch_with_rounds(gpu, ctx, offset):
+def test_mixed_batch_multi_sweep(gpu, ctx, offset, rounds):
+    # stencils of 1-5 sweeps: all sweeps in one persistent launch (default),
+    # or one launch per sweep (rounds); both bit-identical to standalone calls
     insts = [Inst(s, offset) for s in _mixed_specs()]
-    b = _run(gpu, insts, ctx)
-    assert b.rounds == 5
+    b = gpu.hx_batch_plan(ctx, [i.task(gpu) for i in insts], rounds=rounds)
+    assert b.rounds == (5 if rounds else 1)
+    b.launch()
+    torch.cuda.synchronize()
+    b.status()
     for inst in insts:
         r = inst.result()
         _same(r, inst.standalone(gpu, ctx))
         inst.check_oracle(r)
     b.close()
+
+
+def _reset(insts):
+    for inst in insts:
+        if inst.spec["kind"] == "stencil":
+            inst.u0.copy_(inst.u_init)
+
+
+def test_multi_sweep_relaunch_and_graph_replay(gpu, ctx):
+    # the sweep counters and residual accumulators are clean after a launch:
+    # a second launch and CUDA-graph replays of the same plan give the same
+    # bits as the first launch (each from the same initial grids)
+    specs = [{"kind": "stencil", "nx": 300, "ny": 200, "iters": 7, "seed": 31},
+             {"kind": "stencil", "nx": 64, "ny": 64, "iters": 20, "seed": 32},
+             {"kind": "map_reduce", "n": 500_001, "a": 1.5, "seed": 33},
+             {"kind": "stencil", "nx": 1025, "ny": 130, "iters": 2, "seed": 34}]
+    insts = [Inst(s) for s in specs]
+    b = gpu.hx_batch_plan(ctx, [i.task(gpu) for i in insts])
+    assert b.rounds == 1
+    b.launch()
+    torch.cuda.synchronize()
+    first = [i.result() for i in insts]
+    for inst, f in zip(insts, first):
+        _same(f, inst.standalone(gpu, ctx))
+        inst.check_oracle(f)
+    _reset(insts)
+    b.launch()
+    torch.cuda.synchronize()
+    for i, f in zip(insts, first):
+        _same(i.result(), f)
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        b.launch(stream=s)
+    for _ in range(2):
+        _reset(insts)
+        g.replay()
+        torch.cuda.synchronize()
+        for i, f in zip(insts, first):
+            _same(i.result(), f)
+    b.status()
+    b.close()
+
+
+def test_multi_sweep_wait_times_out_and_reports(gpu, ctx):
+    # a wait that can never be satisfied (test hook: the instance's later
+    # sweeps expect one block more than a sweep has) gives up after 2 ms; the
+    # launch ends by itself, the plan reports HX_ERR_TIMEOUT once, and the
+    # context stays usable
+    specs = [{"kind": "stencil", "nx": 256, "ny": 96, "iters": 4, "seed": 35},
+             {"kind": "map_reduce", "n": 100_000, "a": 1.5, "seed": 36}]
+    insts = [Inst(s) for s in specs]
+    b = gpu.hx_batch_plan(ctx, [i.task(gpu) for i in insts])
+    b.debug_stall(0, 2_000_000)
+    b.launch()
+    torch.cuda.synchronize()
+    with pytest.raises(gpu.HxError) as e:
+        b.status()
+    assert e.value.status == gpu.HX_ERR_TIMEOUT
+    b.status()                      # read once, then clear
+    b.close()
+    # the unaffected map->reduce instance is still right, and a fresh plan works
+    insts[1].check_oracle(insts[1].result())
+    fresh = [Inst(s) for s in specs]
+    b2 = gpu.hx_batch_plan(ctx, [i.task(gpu) for i in fresh])
+    b2.launch()
+    torch.cuda.synchronize()
+    b2.status()
+    for inst in fresh:
+        r = inst.result()
+        _same(r, inst.standalone(gpu, ctx))
+        inst.check_oracle(r)
+    b2.close()
+
+
+def test_submit_reports_wait_timeout(gpu, ctx):
+    # hx_batch_query returns the plan's wait status with its completion
+    insts = [Inst({"kind": "stencil", "nx": 128, "ny": 64, "iters": 3, "seed": 37})]
+    t = gpu.hx_batch_submit(ctx, [i.task(gpu) for i in insts])
+    torch.cuda.synchronize()
+    assert gpu.hx_batch_query(ctx, t) is True
+    insts[0].check_oracle(insts[0].result())
 
 
 def test_batch_empty_instances(gpu, ctx):

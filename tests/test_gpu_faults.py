@@ -72,7 +72,9 @@ def test_each_entry_point_fails_once_then_runs(gpu):
                 hx.hx_debug_inject_launch_failures(ctx, bad[0], after=bad[1])
 
 
-def test_batch_round_failure_then_relaunch(gpu):
+@pytest.mark.parametrize("rounds", [True, False])
+def test_batch_round_failure_then_relaunch(gpu, rounds):
+    # rounds: round 0 runs, round 1 fails; one launch: the launch fails
     hx = gpu
     specs = [{"kind": "map_reduce", "n": 300_001, "a": 1.5, "seed": 11},
              {"kind": "stencil", "nx": 130, "ny": 77, "iters": 3, "seed": 12},
@@ -80,8 +82,8 @@ def test_batch_round_failure_then_relaunch(gpu):
              {"kind": "stencil", "nx": 64, "ny": 64, "iters": 2, "seed": 14}]
     insts = [Inst(s) for s in specs]
     with hx.hx_create(0) as ctx:
-        b = hx.hx_batch_plan(ctx, [i.task(hx) for i in insts])
-        hx.hx_debug_inject_launch_failures(ctx, 1, after=1)      # round 0 runs, round 1 fails
+        b = hx.hx_batch_plan(ctx, [i.task(hx) for i in insts], rounds=rounds)
+        hx.hx_debug_inject_launch_failures(ctx, 1, after=1 if rounds else 0)
         with pytest.raises(hx.HxError) as e:
             b.launch()
         assert e.value.status == hx.HX_ERR_CUDA

@@ -56,6 +56,22 @@ def test_sliced_requests_equal_alone(gpu):
             inst.check_oracle(r)
 
 
+def test_lone_stencil_request_runs_all_sweeps_in_one_step(gpu):
+    # a stencil request with nothing else to run takes all 20 sweeps in one
+    # step (one persistent launch that waits between sweeps on the device)
+    hx = gpu
+    spec = {"kind": "stencil", "nx": 700, "ny": 500, "iters": 20, "seed": 44}
+    inst = Inst(spec)
+    with hx.hx_create(0) as ctx:
+        with hx.Server(ctx, mode=0) as srv:
+            srv.run_trace([inst.task(hx)], [0.0])
+            st = srv.stats()
+        assert st["completed"] == 1 and st["failed"] == 0 and st["launches"] == 1
+        r = inst.result()
+        _same(r, inst.standalone(hx, ctx))
+        inst.check_oracle(r)
+
+
 def test_admission_respects_budget(gpu):
     hx = gpu
     trace = _trace(40, 200_000.0, seed=42, hi=1 << 19, iters=3)
