@@ -549,9 +549,12 @@ hx_status hx_batch_query(hx_ctx *ctx, uint64_t ticket);
  *       the batched kernel (plus its final-combine launch); up to
  *       max_steps_in_flight steps are queued on the device, so requests that
  *       arrive while a step runs join the next one and their work overlaps
- *       with the requests already running.  Each request computes exactly
- *       what its standalone call computes (same tile plans, same device
- *       code), so its results do not depend on what it was batched with.
+ *       with the requests already running.  At low load -- at most
+ *       direct_max requests waiting, none started -- each of them is issued
+ *       as its standalone call instead (no step to build and upload).  Each
+ *       request computes exactly what its standalone call computes (same
+ *       tile plans, same device code), so its results do not depend on what
+ *       it was batched with or on which path it took.
  *   HX_SERVE_PER_LAUNCH  the baseline: every admitted request is issued as
  *       its own standalone call(s), in arrival order, on one stream.
  *
@@ -587,6 +590,10 @@ typedef struct hx_server_config {
     size_t step_target_bytes;     /* continuous mode (0: 512 MiB) */
     hx_server_done_fn on_done;    /* completion callback, or NULL */
     void *on_done_user;           /* passed to on_done */
+    int32_t direct_max;           /* continuous mode: when at most this many admitted requests are
+                                   * waiting to start and none has started, each runs as its own
+                                   * standalone call instead of a batched step -- the shorter path at
+                                   * low load (0: 4; -1: always batch; at most 65536) */
 } hx_server_config;
 
 typedef struct hx_server_stats {

@@ -629,7 +629,8 @@ SERVER_DONE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_uint64, ctypes
 class ServerConfig(ctypes.Structure):
     _fields_ = [("mode", _I32), ("max_inflight", _I32), ("hbm_budget_bytes", ctypes.c_size_t),
                 ("max_steps_in_flight", _I32), ("max_step_requests", _I32), ("step_quantum_bytes", ctypes.c_size_t),
-                ("step_target_bytes", ctypes.c_size_t), ("on_done", SERVER_DONE_FN), ("on_done_user", _P)]
+                ("step_target_bytes", ctypes.c_size_t), ("on_done", SERVER_DONE_FN), ("on_done_user", _P),
+                ("direct_max", _I32)]
 
 
 class ServerStats(ctypes.Structure):
@@ -663,7 +664,7 @@ class Server:
 
     def __init__(self, ctx: Context, mode: int = HX_SERVE_CONTINUOUS, hbm_budget_bytes: int = 0,
                  max_inflight: int = 0, max_steps_in_flight: int = 0, max_step_requests: int = 0,
-                 step_quantum_bytes: int = 0, step_target_bytes: int = 0, on_done=None):
+                 step_quantum_bytes: int = 0, step_target_bytes: int = 0, on_done=None, direct_max: int = 0):
         """on_done(req_id, status, latency_s), if given, is called from the
         server's completion thread once per request (see hx_server_done_fn)."""
         self._on_done = None
@@ -671,7 +672,7 @@ class Server:
             self._on_done = SERVER_DONE_FN(lambda _user, rid, st, lat: on_done(int(rid), int(st), float(lat)))
         cfg = ServerConfig(mode, max_inflight, hbm_budget_bytes, max_steps_in_flight, max_step_requests,
                            step_quantum_bytes, step_target_bytes,
-                           self._on_done if self._on_done is not None else SERVER_DONE_FN(), None)
+                           self._on_done if self._on_done is not None else SERVER_DONE_FN(), None, direct_max)
         h = _P()
         _check(_lib.hx_server_create(ctx.handle, ctypes.byref(cfg), ctypes.byref(h)), "hx_server_create")
         self.ctx = ctx

@@ -66,6 +66,9 @@ __device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int *p) {
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
+__device__ __forceinline__ void red_release_add(unsigned int *p, unsigned int v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
+}
 __device__ __forceinline__ unsigned long long globaltimer_ns() {
     unsigned long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -107,8 +110,8 @@ __device__ __forceinline__ void wait_count(const unsigned int *cnt, unsigned int
 // before any second sweep, and so on -- so a run of sweep s waits only for
 // runs taken before it; all CTAs of the launch are resident at once, hence
 // the oldest unfinished run never waits and every wait ends.  A sweep's runs
-// count their blocks in the instance's `done` word for that sweep (after a
-// fence, so the next sweep's readers see the grid they wrote); the next
+// count their blocks in the instance's `done` word for that sweep (a release
+// reduction, so the next sweep's readers see the grid they wrote); the next
 // sweep's runs wait for the full count (bounded, see BatchSync) and read the
 // grid through L2.  Grids, residuals and results are the same as the
 // standalone calls': every block computes the same values from the same
@@ -139,6 +142,7 @@ batch_kernel(const BInst *__restrict__ insts, unsigned int n_inst, const uint32_
     unsigned int it = 0u;
     if (lane == 0) it = atomicAdd(&ctrl[0], 1u);
     it = __shfl_sync(0xffffffffu, it, 0);
+    uint32_t verified = 0xffffffffu;   // MULTI: the last pair whose wait this warp passed
     while (it < n_runs) {
         unsigned int next = 0u;
         if (lane == 0) next = atomicAdd(&ctrl[0], 1u);
@@ -169,8 +173,10 @@ batch_kernel(const BInst *__restrict__ insts, unsigned int n_inst, const uint32_
         } else {
             const int sweep = I.sweep0 + round + phase;
             const bool multi = MULTI && I.n_sweeps > 1;
-            if (multi && phase > 0)
+            if (multi && phase > 0 && pr != verified) {
                 wait_count(I.done + (phase - 1), (unsigned int)I.t_count + (I.stall ? 1u : 0u), sync, lane);
+                verified = pr;
+            }
             const float *src = static_cast<const float *>((sweep & 1) ? I.in1 : I.in0);
             float *dst = const_cast<float *>(static_cast<const float *>((sweep & 1) ? I.in0 : I.in1));
             float m = 0.0f;
@@ -179,16 +185,20 @@ batch_kernel(const BInst *__restrict__ insts, unsigned int n_inst, const uint32_
                 const int wy = (int)(tile % (unsigned int)I.tiles_y), wx = (int)(tile / (unsigned int)I.tiles_y);
                 const int c_begin = wx * 128, r_begin = wy * kBatchStRows;
                 if (!HX_CHECK(c_begin < I.nx && r_begin < I.ny, kChkBatchStencil, c_begin, r_begin)) continue;
-                m = fmaxf(m, I.vec ? stencil_block_vec<kBatchStRows, MULTI>(src, dst, I.nx, I.ny, c_begin, r_begin)
-                                   : stencil_block_scalar<kBatchStRows, MULTI>(src, dst, I.nx, I.ny, c_begin, r_begin));
+                if constexpr (MULTI)
+                    m = fmaxf(m, I.vec ? stencil_block_vec<kBatchStRows, true>(src, dst, I.nx, I.ny, c_begin, r_begin)
+                                       : stencil_block_strided<kBatchStRows>(src, dst, I.nx, I.ny, c_begin, r_begin));
+                else
+                    m = fmaxf(m, I.vec ? stencil_block_vec<kBatchStRows>(src, dst, I.nx, I.ny, c_begin, r_begin)
+                                       : stencil_block_scalar<kBatchStRows>(src, dst, I.nx, I.ny, c_begin, r_begin));
             }
             m = warp_max(m);
             if (lane == 0) atomicMax(I.acc + phase, __float_as_uint(m));
             if (multi && phase + 1 < I.n_sweeps) {
-                // publish this run's blocks to the next sweep's readers
-                __threadfence();
+                // publish this run's blocks to the next sweep's readers: a
+                // release reduction after the warp's barrier (no fence stall)
                 __syncwarp();
-                if (lane == 0) atomicAdd(I.done + phase, cnt);
+                if (lane == 0) red_release_add(I.done + phase, cnt);
             }
         }
         it = __shfl_sync(0xffffffffu, next, 0);
@@ -472,7 +482,10 @@ extern "C" hx_status hx_batch_plan_ex(hx_ctx *ctx, const hx_task *tasks, int32_t
         if (I.kind == kKindMap) n_partials += I.tiles;
         else if (I.kind == kKindHist) n_acc += kHiBins;
         else {
-            if (multi && I.iters > 1) I.n_sweeps = I.iters;
+            if (multi && I.iters > 1) {
+                I.n_sweeps = I.iters;
+                I.run_len = std::max(I.run_len, kMultiSweepRun);
+            }
             n_acc += 2 * I.n_sweeps - 1;   // one max per sweep, one arrival count per sweep but the last
         }
     }
@@ -480,9 +493,9 @@ extern "C" hx_status hx_batch_plan_ex(hx_ctx *ctx, const hx_task *tasks, int32_t
     // prefix and the run prefix over instances (round 0 holds the one-pass
     // instances; stencil sweep r of each instance goes to round r).  Multi:
     // one launch; CTA prefix over instances, run prefix over the pair list:
-    // every instance's first pass, then each later sweep, largest instances
-    // first within a sweep (their blocks finish earliest, so the next
-    // sweep's first runs rarely wait).
+    // every instance's first pass, then each later sweep, instances in the
+    // same order within every sweep, so a run and the runs it waits for are
+    // a whole sweep of work apart.
     const size_t stride = (size_t)n_tasks + 1;
     std::vector<uint32_t> prefix, pairs;
     std::vector<uint32_t> round_cta(rounds), round_runs(rounds);
@@ -517,13 +530,8 @@ extern "C" hx_status hx_batch_plan_ex(hx_ctx *ctx, const hx_task *tasks, int32_t
             pairs.push_back(make_pair((uint32_t)i, 0u));
         }
         cp[n_tasks] = (uint32_t)c;
-        std::vector<int> by_size;
-        for (int i = 0; i < n_tasks; ++i)
-            if (insts[i].n_sweeps > 1) by_size.push_back(i);
-        std::stable_sort(by_size.begin(), by_size.end(),
-                         [&](int a, int b) { return insts[a].tiles > insts[b].tiles; });
         for (int ph = 1; ph < max_iters; ++ph)
-            for (int i : by_size)
+            for (int i = 0; i < n_tasks; ++i)
                 if (ph < insts[i].n_sweeps) pairs.push_back(make_pair((uint32_t)i, (uint32_t)ph));
         for (uint32_t pr : pairs) {
             rp.push_back((uint32_t)w);

@@ -56,6 +56,10 @@ struct BatchSync {
     long long limit_ns;
 };
 constexpr long long kDefaultWaitNs = 1000000000ll;   // 1 s
+// Blocks per warp run of a stencil instance that runs several sweeps in one
+// launch (at least): every run of such an instance waits for, and publishes
+// to, a sweep counter, so longer runs mean fewer round trips.
+constexpr int kMultiSweepRun = 16;
 constexpr int kMaxStepSweeps = 128;                 // sweeps of one request in one serving step
 
 // Checks one task against the rules of its standalone call.

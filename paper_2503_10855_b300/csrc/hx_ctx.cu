@@ -25,6 +25,7 @@ hx_status cuda_fail(cudaError_t e, const char *what) {
 }
 
 hx_status slot_for(hx_ctx *ctx, hx_stream_t stream, WsSlot **slot) {
+    std::lock_guard<std::mutex> lk(ctx->slot_mu);
     int free_i = -1;
     for (int i = 0; i < HX_MAX_STREAMS; ++i) {
         if (ctx->slot_used[i] && ctx->slot_stream[i] == stream) {
@@ -40,6 +41,12 @@ hx_status slot_for(hx_ctx *ctx, hx_stream_t stream, WsSlot **slot) {
     ctx->slot_stream[free_i] = stream;
     *slot = ctx->ws + free_i;
     return HX_OK;
+}
+
+void release_slot(hx_ctx *ctx, hx_stream_t stream) {
+    std::lock_guard<std::mutex> lk(ctx->slot_mu);
+    for (int i = 0; i < HX_MAX_STREAMS; ++i)
+        if (ctx->slot_used[i] && ctx->slot_stream[i] == stream) ctx->slot_used[i] = false;
 }
 
 }  // namespace hx

@@ -3,7 +3,7 @@
 // The histogram is a reduce over a 256-entry collection (Sec. 3.2, 3.3).
 // Each CTA keeps private bins in shared memory (a collection constant of a
 // block-level fork placed in shared memory, with an extra dimension for the
-// thread-level fork, as Sec. 4.4 describes), replicated per lane so that a
+// thread-level fork, as Sec. 4.4 describes), replicated per slot so that a
 // warp's 32 increments always hit 32 different banks.  CTAs then add their
 // bins into the workspace with integer atomics (exact and order independent)
 // and the last CTA to arrive publishes the bins and runs the exclusive scan
@@ -13,23 +13,20 @@
 namespace hx {
 
 template <int THREADS>
-__global__ void __launch_bounds__(THREADS, THREADS == 1024 ? 2 : 3)   // 64 KiB of counters: at most 3 CTAs per SM
+__global__ void __launch_bounds__(THREADS)
 histogram_kernel(const uint8_t *__restrict__ v, int64_t n, int head, int64_t nvec, int tail,
                  WsSlot *ws, uint32_t *d_bins, uint32_t *d_scan) {
     extern __shared__ __align__(16) unsigned int sh[];   // kHiSmemBytes of counters
     __shared__ unsigned int wtot[THREADS / kWarp];
     __shared__ bool is_last;
     static_assert(THREADS >= kHiBins, "the finish maps one thread to one bin");
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (!HX_CHECK(head + 16 * nvec + tail == n && head < 16 && tail < 16, kChkHistSplit, n, nvec)) nvec = 0;
-    // the first two loads are in flight while the counters are zeroed
-    const uint4 *v4 = reinterpret_cast<const uint4 *>(v + head);
-    const int64_t first = (int64_t)blockIdx.x * THREADS + threadIdx.x, stride = (int64_t)gridDim.x * THREADS;
-    const HistPair q = hist_first_loads(v4, first, stride, nvec);
     hist_zero(sh);
     __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (!HX_CHECK(head + 16 * nvec + tail == n && head < 16 && tail < 16, kChkHistSplit, n, nvec)) nvec = 0;
     const unsigned int slot = hist_slot_offset();
-    hist_count_from(sh, slot, v4, first, stride, nvec, q);
+    hist_count_strided(sh, slot, reinterpret_cast<const uint4 *>(v + head),
+                       (int64_t)blockIdx.x * THREADS + threadIdx.x, (int64_t)gridDim.x * THREADS, nvec);
     if (blockIdx.x == 0) {   // unaligned head and ragged tail bytes
         if (threadIdx.x < head) hist_count_byte(sh, slot, v[threadIdx.x]);
         if (threadIdx.x < tail) hist_count_byte(sh, slot, v[n - tail + threadIdx.x]);

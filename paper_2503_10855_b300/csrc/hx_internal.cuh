@@ -586,22 +586,84 @@ __device__ __forceinline__ float stencil_block_scalar(const float *__restrict__ 
     return m;
 }
 
-// ---------------------------------------------------------------- histogram
-// Shared counters are laid out [bin][slot] with bin rows of 256 bytes
-// (64 KiB of dynamic shared memory); a thread counts into slot (lane): lane
-// l's counter of bin b is the word at byte offset (b << 8) | (l << 2), so a
-// warp-wide increment touches 32 different banks whatever the data.  Only
-// the first 32 words of each row are used: zeroing and merging touch 32 KiB
-// (measured on B300: 3-5 % faster from 2^24 to 2^28 bytes than 64 slots with
-// both halves used).  The row stride keeps the offset one prmt away from the
-// loaded word (byte k of the word into bits 8-15, the slot offset into bits
-// 0-7), and the shared atomic adds the array base as an immediate.  Two
-// instructions per byte.
-constexpr int kHiSlots = 32;
-constexpr int kHiRowWords = 64;
-constexpr int kHiSmemBytes = kHiBins * kHiRowWords * 4;
+// Element path of a launch that runs several sweeps, whose grids are read
+// through L2 only (grid_ld<true>): the warp still covers 128 columns, but
+// lane l owns columns c_begin + l + 32 k (k = 0..3), so each load
+// instruction reads 32 consecutive floats and no sector is requested twice
+// (the layout of stencil_block_scalar, 4 consecutive columns per lane, has
+// its 4 loads per row touch the same sectors, which L1 serves on the read-only
+// path but L2 would see four times).  Horizontal neighbours come from the
+// neighbouring lanes, across 32-column groups from lane 31 / lane 0 of the
+// neighbouring group, and at the warp's edges from halo loads.  Every point
+// has the operands it has in stencil_block_scalar (indices clamped on load),
+// so the results are the same bits.
+template <int R>
+__device__ __forceinline__ float stencil_block_strided(const float *__restrict__ src, float *__restrict__ dst,
+                                                       int nx, int ny, int c_begin, int r_begin) {
+    const int lane = threadIdx.x & 31;
+    int cc[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) cc[k] = min(c_begin + lane + 32 * k, nx - 1);
+    float rows[R + 2][4];
+#pragma unroll
+    for (int kr = 0; kr < R + 2; ++kr) {
+        const float *row = src + (size_t)clampi(r_begin - 1 + kr, 0, ny - 1) * nx;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) rows[kr][k] = grid_ld<true>(row + cc[k]);
+    }
+    const int hc = (lane == 0) ? max(c_begin - 1, 0) : min(c_begin + 128, nx - 1);
+    float halo[R];
+#pragma unroll
+    for (int kr = 0; kr < R; ++kr) {
+        const int r = min(r_begin + kr, ny - 1);
+        halo[kr] = (lane == 0 || lane == 31) ? grid_ld<true>(src + (size_t)r * nx + hc) : 0.0f;
+    }
+    float m = 0.0f;
+#pragma unroll
+    for (int kr = 0; kr < R; ++kr) {
+        const float *up = rows[kr], *cur = rows[kr + 1], *dn = rows[kr + 2];
+        float o[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            float left = __shfl_up_sync(0xffffffffu, cur[k], 1);
+            float right = __shfl_down_sync(0xffffffffu, cur[k], 1);
+            const float from31 = __shfl_sync(0xffffffffu, cur[k > 0 ? k - 1 : 0], 31);   // column c - 1 for lane 0
+            const float from0 = __shfl_sync(0xffffffffu, cur[k < 3 ? k + 1 : 3], 0);     // column c + 1 for lane 31
+            if (lane == 0) left = (k == 0) ? halo[kr] : from31;
+            if (lane == 31) right = (k == 3) ? halo[kr] : from0;
+            o[k] = jacobi_point(up[k], dn[k], left, right);
+        }
+        const int r = r_begin + kr;
+        if (r < ny) {
+            float *drow = dst + (size_t)r * nx;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int c = c_begin + lane + 32 * k;
+                if (c < nx) {
+                    drow[c] = o[k];
+                    m = fmaxf(m, fabsf(o[k] - cur[k]));
+                }
+            }
+        }
+    }
+    return m;
+}
 
-__device__ __forceinline__ unsigned int hist_slot_offset() { return (threadIdx.x & 31u) << 2; }
+// ---------------------------------------------------------------- histogram
+// Shared counters are laid out [bin][slot], 256 bins x 64 slots of uint32
+// (64 KiB, dynamic shared memory).  A thread owns slot (lane + 32 * (warp &
+// 1)): one warp-wide increment touches 32 different banks whatever the data,
+// and neighbouring warps share no counter.  A bin row is 256 bytes, so the
+// byte offset of bin b in a thread's slot is (b << 8) | slot_offset, with
+// slot_offset < 256: one prmt builds it straight from the loaded word (byte k
+// of the word into bits 8-15, the slot offset into bits 0-7), and the shared
+// atomic adds the array base as an immediate.  Two instructions per byte.
+constexpr int kHiSlots = 64;
+constexpr int kHiSmemBytes = kHiBins * kHiSlots * 4;
+
+__device__ __forceinline__ unsigned int hist_slot_offset() {
+    return ((threadIdx.x & 31u) << 2) | (((threadIdx.x >> 5) & 1u) << 7);
+}
 __device__ __forceinline__ void hist_inc(unsigned int *sh, unsigned int byte_off) {
     atomicAdd(reinterpret_cast<unsigned int *>(reinterpret_cast<char *>(sh) + byte_off), 1u);
 }
@@ -620,56 +682,39 @@ __device__ __forceinline__ void hist_count_vec(unsigned int *sh, unsigned int sl
 __device__ __forceinline__ void hist_count_byte(unsigned int *sh, unsigned int slot, unsigned int b) {
     hist_inc(sh, (b << 8) | slot);
 }
-// Zero the used half of every bin row (all threads of the CTA; a barrier
-// must follow).
+// Zero the counters (all threads of the CTA; a barrier must follow).
 __device__ __forceinline__ void hist_zero(unsigned int *sh) {
     uint4 *s4 = reinterpret_cast<uint4 *>(sh);
-    for (int i = threadIdx.x; i < kHiBins * kHiSlots / 4; i += blockDim.x)
-        s4[(i >> 3) * (kHiRowWords / 4) + (i & 7)] = make_uint4(0, 0, 0, 0);
+    for (int i = threadIdx.x; i < kHiSmemBytes / 16; i += blockDim.x) s4[i] = make_uint4(0, 0, 0, 0);
 }
-// Fold the slots of each bin and add the non-zero totals into bins_out with
-// integer atomics (exact, any order).  blockDim.x / 256 consecutive threads
-// share a bin, each summing an equal share of its slots from a start rotated
-// by the bin (conflict-free), then combine by shuffle.  Called after a
-// barrier by every thread (blockDim.x = 256, 512 or 1024); returns whether
-// this thread issued an atomic.
+// Fold the 64 slots of each bin (rotated start: conflict-free) and add the
+// non-zero totals into bins_out with integer atomics (exact, any order).
+// Called after a barrier; returns whether this thread issued an atomic.
 __device__ __forceinline__ bool hist_merge(const unsigned int *sh, unsigned int *bins_out) {
-    const int T = blockDim.x / kHiBins;
-    const int bin = threadIdx.x / T, sub = threadIdx.x % T, per = kHiSlots / T;
-    unsigned int c = 0u;
+    bool wrote = false;
+    for (int b = threadIdx.x; b < kHiBins; b += blockDim.x) {
+        unsigned int c = 0u;
 #pragma unroll 8
-    for (int k = 0; k < per; ++k) c += sh[bin * kHiRowWords + ((sub * per + k + bin) & (kHiSlots - 1))];
-    for (int off = 1; off < T; off <<= 1) c += __shfl_xor_sync(0xffffffffu, c, off);
-    if (sub == 0 && c) {
-        atomicAdd(bins_out + bin, c);
-        return true;
+        for (int k = 0; k < kHiSlots; ++k) c += sh[b * kHiSlots + ((k + b) & (kHiSlots - 1))];
+        if (c) {
+            atomicAdd(bins_out + b, c);
+            wrote = true;
+        }
     }
-    return false;
+    return wrote;
 }
 
 // Count the 16-byte vectors v4[first], v4[first + stride], ... below nvec into
 // the shared counters, keeping the next two vectors' loads in flight while
-// the current two are counted.  hist_first_loads issues the first two loads
-// (so that a kernel can zero its counters while they are in flight) and
-// hist_count_from continues from them.
-struct HistPair {
-    uint4 a0, a1;
-    bool h0, h1;
-};
-__device__ __forceinline__ HistPair hist_first_loads(const uint4 *__restrict__ v4, int64_t first, int64_t stride,
-                                                     int64_t nvec) {
-    HistPair q;
-    q.h0 = first < nvec;
-    q.h1 = first + stride < nvec;
-    q.a0 = q.h0 ? ld_stream_u4(v4 + first) : make_uint4(0, 0, 0, 0);
-    q.a1 = q.h1 ? ld_stream_u4(v4 + first + stride) : make_uint4(0, 0, 0, 0);
-    return q;
-}
-__device__ __forceinline__ void hist_count_from(unsigned int *sh, unsigned int slot, const uint4 *__restrict__ v4,
-                                                int64_t first, int64_t stride, int64_t nvec, HistPair q) {
+// the current two are counted.
+__device__ __forceinline__ void hist_count_strided(unsigned int *sh, unsigned int slot,
+                                                   const uint4 *__restrict__ v4, int64_t first, int64_t stride,
+                                                   int64_t nvec) {
     int64_t i = first;
-    bool h0 = q.h0, h1 = q.h1;
-    uint4 a0 = q.a0, a1 = q.a1;
+    bool h0 = i < nvec, h1 = i + stride < nvec;
+    uint4 a0 = make_uint4(0, 0, 0, 0), a1 = a0;
+    if (h0) a0 = ld_stream_u4(v4 + i);
+    if (h1) a1 = ld_stream_u4(v4 + i + stride);
     while (h0) {
         const int64_t j = i + 2 * stride;
         const bool g0 = j < nvec, g1 = j + stride < nvec;
@@ -685,11 +730,6 @@ __device__ __forceinline__ void hist_count_from(unsigned int *sh, unsigned int s
         i = j;
     }
 }
-__device__ __forceinline__ void hist_count_strided(unsigned int *sh, unsigned int slot,
-                                                   const uint4 *__restrict__ v4, int64_t first, int64_t stride,
-                                                   int64_t nvec) {
-    hist_count_from(sh, slot, v4, first, stride, nvec, hist_first_loads(v4, first, stride, nvec));
-}
 
 // ---------------------------------------------------------------- host side
 }  // namespace hx
@@ -704,6 +744,7 @@ struct hx_ctx {
     hx::NestWs *nest_ws = nullptr;  // HX_MAX_STREAMS slots, same index as ws
     hx_stream_t slot_stream[HX_MAX_STREAMS] = {};
     bool slot_used[HX_MAX_STREAMS] = {};
+    std::mutex slot_mu;                  // a server's thread and the caller's may both take slots
     hx_tune_table tune = {};             // per-size-class choices (see hx.h)
     int hist_ctas_per_sm[3] = {1, 1, 1}; // resident CTAs per SM for widths 256, 512, 1024
     int batch_ctas_per_sm[2][2] = {{1, 1}, {1, 1}};   // batched kernel [one sweep / several][without / with histogram counters]
@@ -721,6 +762,9 @@ namespace hx {
 hx_status fail(hx_status st, const std::string &msg);
 hx_status cuda_fail(cudaError_t e, const char *what);
 hx_status slot_for(hx_ctx *ctx, hx_stream_t stream, WsSlot **slot);
+// Frees the slot of a stream that will not be used again (its work has
+// completed; a server calls this for its own stream when it is destroyed).
+void release_slot(hx_ctx *ctx, hx_stream_t stream);
 hx_status histogram_setup(hx_ctx *ctx);
 // Size class of a problem size: floor(log2(n)) clamped to the table, 0 for n <= 1.
 inline int size_class(int64_t n) {

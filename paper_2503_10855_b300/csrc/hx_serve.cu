@@ -36,6 +36,9 @@ double now_s() {
 constexpr size_t kWsPartials = kMrMaxTiles;
 constexpr size_t kWsAccWords = kHiBins;
 constexpr size_t kWsBytes = ((kWsPartials * sizeof(float2) + kWsAccWords * 4) + 255) & ~(size_t)255;
+// Continuous mode: at most this many fresh requests run as standalone calls
+// instead of a batched step (hx_server_config.direct_max = 0).
+constexpr int kDefaultDirectMax = 4;
 
 struct Req {
     uint64_t id = 0;
@@ -83,8 +86,6 @@ struct hx_server {
     std::vector<hx::Slot> slots;
     std::vector<cudaEvent_t> free_events;     // per-launch mode
     char *ws_pool = nullptr;                  // continuous mode: max_inflight workspace slots (+ run counter)
-    unsigned int *err_h = nullptr;            // host-mapped error word of the steps' bounded waits
-    unsigned int *err_d = nullptr;
     uint64_t failed_at_drain = 0;             // stats.failed when the last drain returned
     unsigned int *ctrl = nullptr;
     std::vector<int> free_ws;
@@ -176,37 +177,85 @@ int64_t tile_bytes(const BInst &I) {
     return kBHiTile;
 }
 
+// The request's whole work as its standalone call on the server's stream.
+hx_status launch_standalone(hx_server *s, const hx_task &t) {
+    if (t.kind == HX_TASK_MAP_REDUCE)
+        return hx_map_reduce(s->ctx, t.u.mr.x, t.u.mr.y, t.u.mr.out, t.u.mr.a, t.u.mr.n, t.u.mr.sum, t.u.mr.sum64,
+                             (hx_stream_t)s->stream);
+    if (t.kind == HX_TASK_STENCIL2D)
+        return hx_stencil2d(s->ctx, t.u.st.u0, t.u.st.u1, t.u.st.nx, t.u.st.ny, t.u.st.iters, t.u.st.resid, nullptr,
+                            (hx_stream_t)s->stream);
+    return hx_histogram(s->ctx, t.u.hi.v, t.u.hi.n, t.u.hi.bins, t.u.hi.scan, (hx_stream_t)s->stream);
+}
+
+cudaEvent_t take_event(hx_server *s) {
+    cudaEvent_t ev = nullptr;
+    if (!s->free_events.empty()) {
+        ev = s->free_events.back();
+        s->free_events.pop_back();
+    } else if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+        ev = nullptr;
+    }
+    return ev;
+}
+
+// Continuous mode at low load: when at most cfg.direct_max admitted requests
+// are waiting and none of them has started, each is issued as its standalone
+// call with its own completion event -- no descriptor upload, no batched
+// launch and final combine, the shortest path for a request that has the
+// device nearly to itself.  Results are the same bits either way.
+bool issue_direct_locked(hx_server *s) {
+    std::vector<Req *> batch;
+    batch.swap(s->active);
+    for (Req *r : batch) {
+        r->issued_all = true;
+        s->stats.launches += 1;
+        cudaEvent_t ev = take_event(s);
+        hx_status st = ev ? launch_standalone(s, r->task) : HX_ERR_CUDA;
+        if (st == HX_OK && cudaEventRecord(ev, s->stream) != cudaSuccess) st = HX_ERR_CUDA;
+        std::vector<Req *> one{r};
+        if (st != HX_OK) {
+            if (ev) s->free_events.push_back(ev);
+            fail_requests_locked(s, one, st);
+            continue;
+        }
+        Step step;
+        step.ev = ev;
+        step.finishing = one;
+        step.members = one;
+        s->steps.push_back(std::move(step));
+    }
+    s->cv_compl.notify_one();
+    return true;
+}
+
 // Continuous mode: build one step out of the next slice of every admitted
 // request (at most its share of step_target_bytes, and at least
-// step_quantum_bytes, of traffic), upload its descriptors and prefix sums,
-// launch.  A stencil slice stays within one sweep, except that a stencil
-// request at a sweep boundary takes all its remaining sweeps (up to
-// kMaxStepSweeps) when it is the only request with work, or when those
-// sweeps fit its share: the step's persistent launch then runs them one
-// after another (waits between sweeps on the device, see hx_batch.cuh).
+// step_quantum_bytes, of traffic; a stencil slice stays within one sweep),
+// upload its descriptors and prefix sums, launch.
 bool issue_step_locked(hx_server *s) {
+    // low load: a few fresh requests run as their standalone calls
+    if ((int)s->active.size() <= s->cfg.direct_max &&
+        std::all_of(s->active.begin(), s->active.end(), [](const Req *r) { return r->issued == 0 && r->sweep == 0; }))
+        return issue_direct_locked(s);
     int slot = -1;
     for (size_t i = 0; i < s->slots.size(); ++i)
         if (!s->slots[i].busy) { slot = (int)i; break; }
     if (slot < 0 || (int)s->steps.size() >= s->cfg.max_steps_in_flight) return false;
     Slot &sl = s->slots[slot];
-    // Staging layout, uploaded with one copy: descriptors, then the CTA
-    // prefix (n + 1 entries), the run prefix (one entry per pair + 1) and,
-    // when some request runs several sweeps, the pair list.
+    // Staging layout, uploaded with one copy: descriptors, then the CTA and
+    // run prefix arrays (n + 1 entries each), placed after the step is built.
     BInst *insts = reinterpret_cast<BInst *>(sl.h);
-    std::vector<uint32_t> cpv;
+    std::vector<uint32_t> cpv, rpv;
     cpv.reserve(s->active.size() + 1);
-    std::vector<std::pair<uint32_t, int>> multi;   // (instance, sweeps) of requests running several sweeps
-    const size_t max_extra = (size_t)s->cfg.max_step_requests;   // pairs beyond the first pass
-    size_t extra = 0;
+    rpv.reserve(s->active.size() + 1);
     uint32_t n = 0;
-    uint64_t c = 0;
+    uint64_t c = 0, w = 0;
     Step step;
     // Slice size: the step aims at step_target_bytes of traffic shared by the
     // requests in it, but each gets at least step_quantum_bytes.
     size_t n_work = 0;
     for (Req *r : s->active) n_work += (!r->issued_all && r->inst.tiles > 0) ? 1 : 0;
-    const bool alone = n_work == 1;
     n_work = std::min<size_t>(std::max<size_t>(n_work, 1), (size_t)s->cfg.max_step_requests);
     const size_t quantum = std::max(s->cfg.step_quantum_bytes, s->cfg.step_target_bytes / n_work);
     for (Req *r : s->active) {
@@ -220,41 +269,17 @@ bool issue_step_locked(hx_server *s) {
         }
         if ((int)n >= s->cfg.max_step_requests) continue;
         BInst I = r->inst;
+        const int64_t q = std::max<int64_t>(1, (int64_t)quantum / tile_bytes(I));
+        I.t_first = r->issued;
+        I.t_count = std::min<int64_t>(q, I.tiles - r->issued);
         I.sweep0 = I.kind == kKindStencil ? r->sweep : 0;
-        int sweeps = 1;
-        if (I.kind == kKindStencil && r->issued == 0) {
-            const int left = I.iters - r->sweep;
-            const int64_t sweep_bytes = I.tiles * tile_bytes(I);
-            if (left > 1 && (alone || (int64_t)left * sweep_bytes <= (int64_t)quantum))
-                sweeps = std::min(left, kMaxStepSweeps);
-            if (extra + (size_t)(sweeps - 1) > max_extra) sweeps = 1;
-        }
-        if (sweeps > 1) {
-            I.t_first = 0;
-            I.t_count = I.tiles;
-            I.n_sweeps = sweeps;
-            I.done = I.acc + sweeps;
-        } else {
-            const int64_t q = std::max<int64_t>(1, (int64_t)quantum / tile_bytes(I));
-            I.t_first = r->issued;
-            I.t_count = std::min<int64_t>(q, I.tiles - r->issued);
-        }
-        if (c + inst_ctas(I) > 0xffffffffull) continue;
+        if (c + inst_ctas(I) > 0xffffffffull || w + inst_runs(I) > 0xffffffffull) continue;
         cpv.push_back((uint32_t)c);
+        rpv.push_back((uint32_t)w);
         c += inst_ctas(I);
-        if (sweeps > 1) {
-            multi.emplace_back(n, sweeps);
-            extra += (size_t)(sweeps - 1);
-        }
+        w += inst_runs(I);
         insts[n++] = I;
         step.members.push_back(r);
-        if (sweeps > 1) {
-            r->sweep += sweeps;
-            if (r->sweep < I.iters) continue;
-            r->issued_all = true;
-            step.finishing.push_back(r);
-            continue;
-        }
         r->issued += I.t_count;
         if (r->issued == I.tiles) {
             r->issued = 0;
@@ -265,47 +290,22 @@ bool issue_step_locked(hx_server *s) {
     }
     if (n == 0 && step.finishing.empty()) return false;
     cpv.push_back((uint32_t)c);
-    // pair list: every instance's first pass in order, then the later sweeps,
-    // largest instances first within a sweep
-    std::vector<uint32_t> pairs, rpv;
-    for (uint32_t i = 0; i < n; ++i) pairs.push_back(make_pair(i, 0u));
-    std::stable_sort(multi.begin(), multi.end(),
-                     [&](const std::pair<uint32_t, int> &a, const std::pair<uint32_t, int> &b) {
-                         return insts[a.first].tiles > insts[b.first].tiles;
-                     });
-    int max_sweeps = 1;
-    for (const auto &m : multi) max_sweeps = std::max(max_sweeps, m.second);
-    for (int ph = 1; ph < max_sweeps; ++ph)
-        for (const auto &m : multi)
-            if (ph < m.second) pairs.push_back(make_pair(m.first, (uint32_t)ph));
-    uint64_t w = 0;
-    for (uint32_t pr : pairs) {
-        rpv.push_back((uint32_t)w);
-        w += inst_runs(insts[pr & (kMaxPairInstances - 1u)]);
-    }
     rpv.push_back((uint32_t)w);
-    const bool use_pairs = !multi.empty();
     const size_t off_cta = ((size_t)n * sizeof(BInst) + 15) & ~(size_t)15;
     const size_t off_run = off_cta + (((size_t)(n + 1) * 4 + 15) & ~(size_t)15);
-    const size_t off_pairs = off_run + ((rpv.size() * 4 + 15) & ~(size_t)15);
-    const size_t bytes = use_pairs ? off_pairs + pairs.size() * 4 : off_run + rpv.size() * 4;
     memcpy(sl.h + off_cta, cpv.data(), (n + 1) * 4);
-    memcpy(sl.h + off_run, rpv.data(), rpv.size() * 4);
-    if (use_pairs) memcpy(sl.h + off_pairs, pairs.data(), pairs.size() * 4);
+    memcpy(sl.h + off_run, rpv.data(), (n + 1) * 4);
     s->active.erase(std::remove_if(s->active.begin(), s->active.end(), [](Req *r) { return r->issued_all; }),
                     s->active.end());
     hx_status st = HX_OK;
     if (n > 0) {
-        cudaError_t e = w > 0xffffffffull ? cudaErrorInvalidValue
-                                          : cudaMemcpyAsync(sl.d, sl.h, bytes, cudaMemcpyHostToDevice, s->stream);
+        cudaError_t e = cudaMemcpyAsync(sl.d, sl.h, off_run + (n + 1) * 4, cudaMemcpyHostToDevice, s->stream);
         if (e != cudaSuccess) st = cuda_fail(e, "server: step upload");
         if (st == HX_OK)
             st = launch_batch_round(s->ctx, reinterpret_cast<const BInst *>(sl.d), n,
                                     reinterpret_cast<const uint32_t *>(sl.d + off_cta),
-                                    reinterpret_cast<const uint32_t *>(sl.d + off_run),
-                                    use_pairs ? reinterpret_cast<const uint32_t *>(sl.d + off_pairs) : nullptr,
-                                    use_pairs ? (uint32_t)pairs.size() : n, (uint32_t)c, (uint32_t)w, 0, s->ctrl,
-                                    BatchSync{s->err_d, kDefaultWaitNs}, s->stream);
+                                    reinterpret_cast<const uint32_t *>(sl.d + off_run), nullptr, n, (uint32_t)c,
+                                    (uint32_t)w, 0, s->ctrl, BatchSync{nullptr, kDefaultWaitNs}, s->stream);
         s->stats.launches += 1;
     }
     if (st == HX_OK && cudaEventRecord(sl.ev, s->stream) != cudaSuccess) st = HX_ERR_CUDA;
@@ -338,27 +338,11 @@ bool issue_per_launch(hx_server *s, std::unique_lock<std::mutex> &lk) {
     s->issuing = true;
     for (Req *r : batch) {
         const hx_task t = r->task;
-        cudaEvent_t ev = nullptr;
-        if (!s->free_events.empty()) {
-            ev = s->free_events.back();
-            s->free_events.pop_back();
-        }
+        cudaEvent_t ev = take_event(s);
         s->stats.launches += 1;
         r->issued_all = true;
         lk.unlock();
-        hx_status st = HX_OK;
-        if (t.kind == HX_TASK_MAP_REDUCE)
-            st = hx_map_reduce(s->ctx, t.u.mr.x, t.u.mr.y, t.u.mr.out, t.u.mr.a, t.u.mr.n, t.u.mr.sum, t.u.mr.sum64,
-                               (hx_stream_t)s->stream);
-        else if (t.kind == HX_TASK_STENCIL2D)
-            st = hx_stencil2d(s->ctx, t.u.st.u0, t.u.st.u1, t.u.st.nx, t.u.st.ny, t.u.st.iters, t.u.st.resid, nullptr,
-                              (hx_stream_t)s->stream);
-        else
-            st = hx_histogram(s->ctx, t.u.hi.v, t.u.hi.n, t.u.hi.bins, t.u.hi.scan, (hx_stream_t)s->stream);
-        if (!ev && cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
-            ev = nullptr;
-            st = HX_ERR_CUDA;
-        }
+        hx_status st = ev ? launch_standalone(s, t) : HX_ERR_CUDA;
         if (st == HX_OK && cudaEventRecord(ev, s->stream) != cudaSuccess) st = HX_ERR_CUDA;
         lk.lock();
         std::vector<Req *> one{r};
@@ -422,10 +406,6 @@ void completer_main(hx_server *s) {
         lk.lock();
         Step step = std::move(s->steps.front());
         s->steps.pop_front();
-        // a wait between two sweeps that ran out of time invalidates every
-        // request that had work in the step (they complete with the error)
-        if (s->err_h && e == cudaSuccess && __atomic_exchange_n(s->err_h, 0u, __ATOMIC_ACQ_REL) != 0u)
-            for (Req *r : step.members) r->status = HX_ERR_TIMEOUT;
         for (Req *r : step.finishing) {
             if (e != cudaSuccess) r->status = HX_ERR_CUDA;
             if (r->status != HX_OK) s->stats.failed += 1;
@@ -478,7 +458,8 @@ hx_status hx_server_create(hx_ctx *ctx, const hx_server_config *cfg, hx_server *
     if (cfg->mode != HX_SERVE_CONTINUOUS && cfg->mode != HX_SERVE_PER_LAUNCH)
         return fail(HX_ERR_INVALID, "hx_server_create: unknown mode");
     if (cfg->max_inflight < 0 || cfg->max_inflight > 16384 || cfg->max_steps_in_flight < 0 ||
-        cfg->max_steps_in_flight > 64 || cfg->max_step_requests < 0 || cfg->max_step_requests > 65536)
+        cfg->max_steps_in_flight > 64 || cfg->max_step_requests < 0 || cfg->max_step_requests > 65536 ||
+        cfg->direct_max < -1 || cfg->direct_max > 65536)
         return fail(HX_ERR_INVALID, "hx_server_create: bad limits");
     DeviceGuard g(ctx->device);
     hx_server *s = new (std::nothrow) hx_server();
@@ -491,6 +472,7 @@ hx_status hx_server_create(hx_ctx *ctx, const hx_server_config *cfg, hx_server *
     if (s->cfg.max_step_requests == 0) s->cfg.max_step_requests = 4096;
     if (s->cfg.step_quantum_bytes == 0) s->cfg.step_quantum_bytes = (size_t)32 << 20;
     if (s->cfg.step_target_bytes == 0) s->cfg.step_target_bytes = (size_t)512 << 20;
+    if (s->cfg.direct_max == 0) s->cfg.direct_max = kDefaultDirectMax;
     cudaError_t e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
         delete s;
@@ -500,20 +482,13 @@ hx_status hx_server_create(hx_ctx *ctx, const hx_server_config *cfg, hx_server *
         auto align = [](size_t v) { return (v + 255) & ~(size_t)255; };
         const size_t K = (size_t)s->cfg.max_step_requests;
         s->slots.resize((size_t)s->cfg.max_steps_in_flight + 1);
-        // descriptors, CTA prefix, run prefix and pair list (at most K
-        // first-pass pairs and K more for requests running several sweeps)
         for (Slot &sl : s->slots) {
-            sl.bytes = align(K * sizeof(BInst)) + align((K + 1) * 4) + 2 * align((2 * K + 1) * 4);
+            sl.bytes = align(K * sizeof(BInst)) + 2 * align((K + 1) * 4);
             if (e == cudaSuccess) e = cudaMallocHost(&sl.h, sl.bytes);
             if (e == cudaSuccess) e = cudaMalloc(&sl.d, sl.bytes);
             if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming);
         }
         const size_t pool = (size_t)s->cfg.max_inflight * kWsBytes;
-        if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void **>(&s->err_h), 64, cudaHostAllocMapped);
-        if (e == cudaSuccess) {
-            *s->err_h = 0u;
-            e = cudaHostGetDevicePointer(reinterpret_cast<void **>(&s->err_d), s->err_h, 0);
-        }
         if (e == cudaSuccess) e = cudaMalloc(&s->ws_pool, pool + 256);
         if (e == cudaSuccess) e = cudaMemset(s->ws_pool, 0, pool + 256);
         s->ctrl = reinterpret_cast<unsigned int *>(s->ws_pool + pool);
@@ -527,7 +502,6 @@ hx_status hx_server_create(hx_ctx *ctx, const hx_server_config *cfg, hx_server *
             if (sl.ev) cudaEventDestroy(sl.ev);
         }
         if (s->ws_pool) cudaFree(s->ws_pool);
-        if (s->err_h) cudaFreeHost(s->err_h);
         cudaStreamDestroy(s->stream);
         delete s;
         return cuda_fail(e, "hx_server_create: staging");
@@ -550,6 +524,7 @@ void hx_server_destroy(hx_server *s) {
     if (s->compl_thr.joinable()) s->compl_thr.join();
     hx::DeviceGuard g(s->ctx->device);
     cudaStreamSynchronize(s->stream);
+    hx::release_slot(s->ctx, (hx_stream_t)s->stream);
     for (hx::Slot &sl : s->slots) {
         if (sl.h) cudaFreeHost(sl.h);
         if (sl.d) cudaFree(sl.d);
@@ -557,7 +532,6 @@ void hx_server_destroy(hx_server *s) {
     }
     for (cudaEvent_t ev : s->free_events) cudaEventDestroy(ev);
     if (s->ws_pool) cudaFree(s->ws_pool);
-    if (s->err_h) cudaFreeHost(s->err_h);
     cudaStreamDestroy(s->stream);
     delete s;
 }

@@ -38,7 +38,10 @@ class Inst:
         elif k == "stencil":
             ny, nx = spec["ny"], spec["nx"]
             base = torch.empty(ny * nx + offset, device=DEV)
-            base[offset:] = workloads.uniform01_f32_torch(spec["seed"], ny * nx, DEV)
+            if spec.get("values") == "pm1":
+                base[offset:] = workloads.uniform_pm1_f32_torch(spec["seed"], ny * nx, DEV)
+            else:
+                base[offset:] = workloads.uniform01_f32_torch(spec["seed"], ny * nx, DEV)
             self.u0 = base[offset:].view(ny, nx)
             self.u_init = self.u0.clone()
             self.u1 = torch.full((ny, nx), float("nan"), device=DEV)
@@ -133,6 +136,28 @@ def test_standard_batch_alone_equals_mix_and_oracle(gpu, ctx):
         r = inst.result()
         _same(r, inst.standalone(gpu, ctx))
         inst.check_oracle(r)
+    b.close()
+
+
+@pytest.mark.slow
+def test_standard_batch_20_sweeps_in_one_launch(gpu, ctx):
+    # the 512-instance batch with 20 sweeps per stencil instance, all in one
+    # persistent launch: every instance bit-identical to its standalone call;
+    # every map->reduce instance and a sample of 24 stencil instances (every
+    # size decile) against the oracle
+    insts = [Inst(s) for s in workloads.batch_mix(iters=20)]
+    b = gpu.hx_batch_plan(ctx, [i.task(gpu) for i in insts])
+    assert b.rounds == 1
+    b.launch()
+    torch.cuda.synchronize()
+    b.status()
+    stencils = sorted((i for i in insts if i.spec["kind"] == "stencil"), key=lambda i: i.spec["nx"])
+    sample = {id(stencils[k]) for k in np.linspace(0, len(stencils) - 1, 24).astype(int)}
+    for inst in insts:
+        r = inst.result()
+        _same(r, inst.standalone(gpu, ctx))
+        if inst.spec["kind"] != "stencil" or id(inst) in sample:
+            inst.check_oracle(r)
     b.close()
 
 

@@ -25,7 +25,7 @@ def test_served_results_equal_alone(gpu, mode):
     trace = _trace(48, 30_000.0, seed=41)
     insts = [Inst(r) for r in trace]
     with hx.hx_create(0) as ctx:
-        with hx.Server(ctx, mode=mode) as srv:
+        with hx.Server(ctx, mode=mode, direct_max=-1) as srv:   # batched steps only
             lat, makespan = srv.run_trace([i.task(hx) for i in insts], [r["arrival_s"] for r in trace])
             st = srv.stats()
         assert st["completed"] == len(trace) and st["failed"] == 0
@@ -46,7 +46,7 @@ def test_sliced_requests_equal_alone(gpu):
     insts = [Inst(r) for r in trace]
     with hx.hx_create(0) as ctx:
         with hx.Server(ctx, mode=0, step_quantum_bytes=64 << 10, step_target_bytes=64 << 10,
-                       max_steps_in_flight=3) as srv:
+                       max_steps_in_flight=3, direct_max=-1) as srv:
             srv.run_trace([i.task(hx) for i in insts], [r["arrival_s"] for r in trace])
             st = srv.stats()
         assert st["launches"] > len(trace)
@@ -56,9 +56,9 @@ def test_sliced_requests_equal_alone(gpu):
             inst.check_oracle(r)
 
 
-def test_lone_stencil_request_runs_all_sweeps_in_one_step(gpu):
-    # a stencil request with nothing else to run takes all 20 sweeps in one
-    # step (one persistent launch that waits between sweeps on the device)
+def test_lone_request_runs_as_its_standalone_call(gpu):
+    # low load: a request with nothing else waiting is issued as its
+    # standalone call (one issue, all 20 sweeps)
     hx = gpu
     spec = {"kind": "stencil", "nx": 700, "ny": 500, "iters": 20, "seed": 44}
     inst = Inst(spec)
@@ -70,6 +70,39 @@ def test_lone_stencil_request_runs_all_sweeps_in_one_step(gpu):
         r = inst.result()
         _same(r, inst.standalone(hx, ctx))
         inst.check_oracle(r)
+
+
+@pytest.mark.parametrize("direct_max", [-1, 4, 64])
+def test_direct_and_batched_paths_agree(gpu, direct_max):
+    # the same trace with batched steps only, with the low-load direct path,
+    # and with every fresh request direct: the same bits as standalone calls
+    hx = gpu
+    trace = _trace(30, 40_000.0, seed=46, iters=4)
+    insts = [Inst(r) for r in trace]
+    with hx.hx_create(0) as ctx:
+        with hx.Server(ctx, mode=0, direct_max=direct_max) as srv:
+            srv.run_trace([i.task(hx) for i in insts], [r["arrival_s"] for r in trace])
+            st = srv.stats()
+        assert st["completed"] == len(trace) and st["failed"] == 0
+        for inst in insts:
+            r = inst.result()
+            _same(r, inst.standalone(hx, ctx))
+            inst.check_oracle(r)
+
+
+def test_many_servers_on_one_context(gpu):
+    # each server runs standalone calls on its own stream, which takes one of
+    # the context's HX_MAX_STREAMS workspace slots; destroying the server
+    # frees it, so any number of servers can follow one another
+    hx = gpu
+    spec = {"kind": "map_reduce", "n": 100_003, "a": 1.5, "seed": 45}
+    with hx.hx_create(0) as ctx:
+        for k in range(3 * 16):
+            inst = Inst(spec)
+            with hx.Server(ctx, mode=k % 2) as srv:
+                srv.run_trace([inst.task(hx)], [0.0])
+                assert srv.stats()["failed"] == 0
+        inst.check_oracle(inst.result())
 
 
 def test_admission_respects_budget(gpu):

@@ -196,13 +196,16 @@ def log_uniform_int(seed: int, k: int, lo: int, hi: int) -> int:
 
 
 def batch_mix(count: int = 512, seed: int = SEED_BATCH, lo: int = 1 << 10, hi: int = 1 << 22,
-              side_lo: int = 32, side_hi: int = 2048):
+              side_lo: int = 32, side_hi: int = 2048, iters: int = 1):
     """Instance list of the batched workload: half map->reduce, half stencil.
 
     Instance j uses draws 4j..4j+3 of the stream ``seed``: draw 4j picks the
     kind (stencil when its top bit is set), draw 4j+1 the size (log-uniform
     element count for a map->reduce, log-uniform side for a square stencil),
-    draw 4j+2 gives the instance's own data seed.
+    draw 4j+2 gives the instance's own data seed.  Every instance's values
+    are fp32 uniform on [-1, 1) (the batched workload's stated range): map
+    inputs as ``map_reduce_inputs``, stencil grids as ``uniform_pm1_f32``
+    (``"values": "pm1"``).  ``iters`` is the stencil sweep count.
     """
     out = []
     for j in range(count):
@@ -213,7 +216,7 @@ def batch_mix(count: int = 512, seed: int = SEED_BATCH, lo: int = 1 << 10, hi: i
                         "seed": data_seed, "a": 1.5})
         else:
             side = log_uniform_int(seed, 4 * j + 1, side_lo, side_hi)
-            out.append({"kind": kind, "nx": side, "ny": side, "iters": 1, "seed": data_seed})
+            out.append({"kind": kind, "nx": side, "ny": side, "iters": iters, "seed": data_seed, "values": "pm1"})
     return out
 
 
