@@ -1068,6 +1068,39 @@ def bench_batch_sweeps(hx, ctx, batch_bufs, stream, peak, sweeps=20, reps=5):
         del g
         b.close()
     out["one_launch_speedup"] = round(out["rounds"]["ms"] / out["one_launch"]["ms"], 3)
+    # other batch shapes, 20 sweeps each: one launch against rounds
+    shapes = []
+    for count, lo, hi in ((512, 32, 128), (64, 32, 2048), (8, 1024, 4096), (1, 4096, 4096)):
+        keep, st_tasks, per_sweep = [], [], 0
+        for j in range(count):
+            side = int(workloads.log_uniform_int(99, j, lo, hi)) if lo < hi else lo
+            u0 = workloads.uniform_pm1_f32_torch(j, side * side, stream.device).view(side, side)
+            u1, r = torch.empty_like(u0), torch.empty(sweeps, device=u0.device)
+            keep += [u0, u1, r]
+            st_tasks.append(hx.stencil_task(u0, u1, sweeps, r))
+            per_sweep += 8 * side * side
+        row = {"instances": count, "sides": f"{lo}-{hi}" if lo < hi else str(lo), "bytes_per_sweep": per_sweep}
+        for name, rounds in (("one_launch_ms", False), ("rounds_ms", True)):
+            b = hx.hx_batch_plan(ctx, st_tasks, rounds=rounds)
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=stream):
+                b.launch(stream=stream)
+            with torch.cuda.stream(stream):
+                g.replay()
+                ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+                for a, e in ev:
+                    a.record(stream)
+                    g.replay()
+                    e.record(stream)
+                stream.synchronize()
+            b.status()
+            row[name] = round(statistics.median(a.elapsed_time(e) for a, e in ev), 4)
+            del g
+            b.close()
+        row["one_launch_speedup"] = round(row["rounds_ms"] / row["one_launch_ms"], 3)
+        shapes.append(row)
+        del keep
+    out["shapes"] = shapes
     return out
 
 
