@@ -457,7 +457,8 @@ hx_status hx_autotune(hx_ctx *ctx, int32_t max_log2, hx_stream_t stream);
  * than the device holds at once, so every wait ends; each wait is also
  * bounded in time (1 s): if one runs out, the launch records HX_ERR_TIMEOUT
  * (hx_batch_status, hx_batch_query) and its results are not valid.  With
- * HX_BATCH_ROUNDS (or above 255 sweeps) the plan runs as rounds instead:
+ * HX_BATCH_ROUNDS, above 255 sweeps, or by default when fewer than 4 stencil
+ * tasks have iters > 1, the plan runs as rounds instead:
  * round r runs sweep r of every stencil instance that has one (plus, in
  * round 0, all map->reduce and histogram instances), one launch per round.
  *
@@ -492,10 +493,13 @@ typedef struct hx_batch hx_batch;
 hx_status hx_batch_plan(hx_ctx *ctx, const hx_task *tasks, int32_t n_tasks, hx_batch **out,
                         int32_t *out_rounds);
 
-/* hx_batch_plan with flags: 0 (the default schedule, every sweep in one
- * launch) or HX_BATCH_ROUNDS (one launch per sweep).  Both give the same
- * results; HX_ERR_INVALID for unknown flags. */
+/* hx_batch_plan with flags: 0 (the default schedule: every sweep in one
+ * launch when at least 4 stencil tasks have iters > 1, else rounds),
+ * HX_BATCH_ROUNDS (one launch per sweep) or HX_BATCH_ONE_LAUNCH (every sweep
+ * in one launch, whatever the task count; at most 255 sweeps).  All give the
+ * same results; HX_ERR_INVALID for unknown or conflicting flags. */
 #define HX_BATCH_ROUNDS 1
+#define HX_BATCH_ONE_LAUNCH 2
 hx_status hx_batch_plan_ex(hx_ctx *ctx, const hx_task *tasks, int32_t n_tasks, int32_t flags, hx_batch **out,
                            int32_t *out_rounds);
 

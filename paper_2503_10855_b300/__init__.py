@@ -409,7 +409,7 @@ _lib.hx_batch_status.argtypes = [_P]
 _lib.hx_batch_status.restype = ctypes.c_int
 _lib.hx_debug_batch_stall.argtypes = [_P, _I32, _I64]
 _lib.hx_debug_batch_stall.restype = ctypes.c_int
-HX_BATCH_ROUNDS = 1
+HX_BATCH_ROUNDS, HX_BATCH_ONE_LAUNCH = 1, 2
 _lib.hx_batch_launch.argtypes = [_P, _P]
 _lib.hx_batch_launch.restype = ctypes.c_int
 _lib.hx_batch_free.argtypes = [_P]
@@ -478,16 +478,18 @@ def _task_array(tasks):
 class Batch:
     """A planned batch (``hx_batch``): device work-list bound to the tasks' buffers."""
 
-    def __init__(self, ctx: Context, tasks, rounds: bool = False):
-        """``rounds``: one launch per sweep (HX_BATCH_ROUNDS) instead of every
-        sweep in one launch."""
+    def __init__(self, ctx: Context, tasks, rounds=None):
+        """``rounds``: None for the default schedule, True for one launch per
+        sweep (HX_BATCH_ROUNDS), False for every sweep in one launch
+        (HX_BATCH_ONE_LAUNCH)."""
         self.ctx = ctx
         self.keep = [getattr(t, "keep", None) for t in tasks]
         arr = _task_array(tasks)
         h = _P()
         n_rounds = _I32(0)
-        _check(_lib.hx_batch_plan_ex(ctx.handle, arr, len(tasks), HX_BATCH_ROUNDS if rounds else 0, ctypes.byref(h),
-                                     ctypes.byref(n_rounds)), "hx_batch_plan")
+        flags = 0 if rounds is None else (HX_BATCH_ROUNDS if rounds else HX_BATCH_ONE_LAUNCH)
+        _check(_lib.hx_batch_plan_ex(ctx.handle, arr, len(tasks), flags, ctypes.byref(h), ctypes.byref(n_rounds)),
+               "hx_batch_plan")
         self.handle = h
         self.rounds = n_rounds.value
 
@@ -516,7 +518,7 @@ class Batch:
             pass
 
 
-def hx_batch_plan(ctx: Context, tasks, rounds: bool = False) -> Batch:
+def hx_batch_plan(ctx: Context, tasks, rounds=None) -> Batch:
     return Batch(ctx, tasks, rounds)
 
 

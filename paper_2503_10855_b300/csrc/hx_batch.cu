@@ -81,14 +81,19 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
 __device__ __forceinline__ void wait_count(const unsigned int *cnt, unsigned int target, const BatchSync &sync,
                                            int lane) {
     if (lane == 0 && ld_acquire_u32(cnt) < target) {
+        // exponential back-off (32 ns .. 1 us): when many warps wait on one
+        // instance's counter, their polls would otherwise crowd the L2 slice
+        // that also serves the arrivals they wait for
         const unsigned long long t0 = globaltimer_ns();
+        unsigned int nap = 32;
         while (ld_acquire_u32(cnt) < target) {
             if (globaltimer_ns() - t0 > (unsigned long long)sync.limit_ns) {
                 // host-mapped word: a plain store (no atomic over the host link)
                 *reinterpret_cast<volatile unsigned int *>(sync.err) = (unsigned int)HX_ERR_TIMEOUT;
                 break;
             }
-            __nanosleep(64);
+            __nanosleep(nap);
+            nap = min(2 * nap, 1024u);
         }
     }
     __syncwarp();
@@ -456,25 +461,31 @@ extern "C" hx_status hx_batch_plan_ex(hx_ctx *ctx, const hx_task *tasks, int32_t
     if (!ctx || !out) return fail(HX_ERR_INVALID, "hx_batch_plan: ctx or out is NULL");
     *out = nullptr;
     if (n_tasks < 0 || (n_tasks > 0 && !tasks)) return fail(HX_ERR_INVALID, "hx_batch_plan: bad task list");
-    if (flags & ~HX_BATCH_ROUNDS) return fail(HX_ERR_INVALID, "hx_batch_plan: unknown flags");
+    if ((flags & ~(HX_BATCH_ROUNDS | HX_BATCH_ONE_LAUNCH)) || flags == (HX_BATCH_ROUNDS | HX_BATCH_ONE_LAUNCH))
+        return fail(HX_ERR_INVALID, "hx_batch_plan: unknown or conflicting flags");
     if ((uint32_t)n_tasks >= kMaxPairInstances) return fail(HX_ERR_INVALID, "hx_batch_plan: too many tasks");
     for (int i = 0; i < n_tasks; ++i) {
         hx_status st = validate_task(tasks[i], i, "hx_batch_plan");
         if (st != HX_OK) return st;
     }
     std::vector<BInst> insts(n_tasks);
-    int max_iters = 0;
+    int max_iters = 0, n_multi = 0;
     for (int i = 0; i < n_tasks; ++i) {
         int64_t np = 0, na = 0;
         describe_instance(ctx, tasks[i], &insts[i], &np, &na);
         if (insts[i].tiles > 0xffffffffll) return fail(HX_ERR_INVALID, "hx_batch_plan: instance too large");
         if (insts[i].kind == kKindStencil) max_iters = std::max(max_iters, insts[i].iters);
+        if (insts[i].kind == kKindStencil && insts[i].iters > 1 && insts[i].tiles > 0) ++n_multi;
     }
     // Several sweeps per stencil instance run in one launch unless the caller
-    // asks for rounds (round r = sweep r of every instance, one launch each).
-    // (An instance's sweep offset is stored in 8 bits of its pair entries:
-    // batches with more than 255 sweeps run as rounds.)
-    const bool multi = max_iters > 1 && max_iters <= 255 && !(flags & HX_BATCH_ROUNDS);
+    // asks for rounds (round r = sweep r of every instance, one launch each),
+    // or, by default, when fewer than kMinMultiInstances instances have
+    // several sweeps: the sweeps of one instance then wait for each other
+    // across the whole device.  (An instance's sweep offset is stored in 8
+    // bits of its pair entries: batches with more than 255 sweeps run as
+    // rounds.)
+    const bool multi = max_iters > 1 && max_iters <= 255 && !(flags & HX_BATCH_ROUNDS) &&
+                       ((flags & HX_BATCH_ONE_LAUNCH) || n_multi >= kMinMultiInstances);
     int rounds = n_tasks > 0 ? 1 : 0;
     if (!multi) rounds = std::max(rounds, max_iters);
     int64_t n_partials = 0, n_acc = 0;
@@ -482,12 +493,22 @@ extern "C" hx_status hx_batch_plan_ex(hx_ctx *ctx, const hx_task *tasks, int32_t
         if (I.kind == kKindMap) n_partials += I.tiles;
         else if (I.kind == kKindHist) n_acc += kHiBins;
         else {
-            if (multi && I.iters > 1) {
-                I.n_sweeps = I.iters;
-                I.run_len = std::max(I.run_len, kMultiSweepRun);
-            }
+            if (multi && I.iters > 1) I.n_sweeps = I.iters;
             n_acc += 2 * I.n_sweeps - 1;   // one max per sweep, one arrival count per sweep but the last
         }
+    }
+    if (multi) {
+        // Run length of the multi-sweep instances: long runs mean fewer waits
+        // and publications (up to kMultiSweepRun blocks), but an instance's
+        // next sweep waits for all of this one, so a sweep of the batch needs
+        // about two runs per resident warp to keep the device busy.
+        int64_t blocks = 0;
+        for (const BInst &I : insts)
+            if (I.n_sweeps > 1) blocks += I.tiles;
+        const int64_t warps = (int64_t)ctx->num_sms * ctx->batch_ctas_per_sm[1][0] * (kBatchThreads / kWarp);
+        const int run = (int)std::max<int64_t>(1, std::min<int64_t>(kMultiSweepRun, blocks / (2 * warps)));
+        for (BInst &I : insts)
+            if (I.n_sweeps > 1) I.run_len = run;
     }
     // Prefix sums of each launch's work.  Rounds: per round r, the CTA
     // prefix and the run prefix over instances (round 0 holds the one-pass

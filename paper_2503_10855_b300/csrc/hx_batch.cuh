@@ -56,13 +56,20 @@ struct BatchSync {
     long long limit_ns;
 };
 constexpr long long kDefaultWaitNs = 1000000000ll;   // 1 s
-// Blocks per warp run of a stencil instance that runs several sweeps in one
-// launch (at least): every run of such an instance waits for, and publishes
-// to, a sweep counter, so longer runs mean fewer round trips, while a sweep
-// of an instance cannot use more warps than it has runs.  Measured on the
-// 512-instance, 20-sweep batch (B300): 4 blocks 4.51 ms, 8 blocks 4.41 ms,
-// 16 blocks 4.55 ms, 32 blocks 4.80 ms.
+// Blocks per warp run (at most) of a stencil instance that runs several
+// sweeps in one launch: every run of such an instance waits for, and
+// publishes to, a sweep counter, so longer runs mean fewer round trips, while
+// a sweep cannot use more warps than it has runs (the planner shortens runs
+// until a sweep of the launch has about two per resident warp).  Measured on
+// the 512-instance, 20-sweep batch (B300): 4 blocks 4.51 ms, 8 blocks
+// 4.41 ms, 16 blocks 4.55 ms, 32 blocks 4.80 ms.
 constexpr int kMultiSweepRun = 8;
+// A plan runs several sweeps of its instances in one launch by default only
+// if at least this many stencil instances have several sweeps.  Measured on
+// B300, 20 sweeps: one 4096^2 grid took 0.76 ms in one launch against
+// 0.55 ms as rounds, while 8 grids of sides 1024-4096 took 1.07 ms against
+// 1.23 ms.
+constexpr int kMinMultiInstances = 4;
 constexpr int kMaxStepSweeps = 128;                 // sweeps of one request in one serving step
 
 // Checks one task against the rules of its standalone call.

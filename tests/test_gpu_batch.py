@@ -1,6 +1,8 @@
 """Batched persistent launch: every instance bit-identical to its standalone
 call, and matching the oracle (tolerances as in test_gpu_parity)."""
 
+import ctypes
+
 import numpy as np
 import pytest
 import torch
@@ -211,7 +213,7 @@ def test_multi_sweep_relaunch_and_graph_replay(gpu, ctx):
              {"kind": "map_reduce", "n": 500_001, "a": 1.5, "seed": 33},
              {"kind": "stencil", "nx": 1025, "ny": 130, "iters": 2, "seed": 34}]
     insts = [Inst(s) for s in specs]
-    b = gpu.hx_batch_plan(ctx, [i.task(gpu) for i in insts])
+    b = gpu.hx_batch_plan(ctx, [i.task(gpu) for i in insts], rounds=False)   # one launch (3 multi-sweep tasks)
     assert b.rounds == 1
     b.launch()
     torch.cuda.synchronize()
@@ -246,7 +248,7 @@ def test_multi_sweep_wait_times_out_and_reports(gpu, ctx):
     specs = [{"kind": "stencil", "nx": 256, "ny": 96, "iters": 4, "seed": 35},
              {"kind": "map_reduce", "n": 100_000, "a": 1.5, "seed": 36}]
     insts = [Inst(s) for s in specs]
-    b = gpu.hx_batch_plan(ctx, [i.task(gpu) for i in insts])
+    b = gpu.hx_batch_plan(ctx, [i.task(gpu) for i in insts], rounds=False)
     b.debug_stall(0, 2_000_000)
     b.launch()
     torch.cuda.synchronize()
@@ -258,7 +260,7 @@ def test_multi_sweep_wait_times_out_and_reports(gpu, ctx):
     # the unaffected map->reduce instance is still right, and a fresh plan works
     insts[1].check_oracle(insts[1].result())
     fresh = [Inst(s) for s in specs]
-    b2 = gpu.hx_batch_plan(ctx, [i.task(gpu) for i in fresh])
+    b2 = gpu.hx_batch_plan(ctx, [i.task(gpu) for i in fresh], rounds=False)
     b2.launch()
     torch.cuda.synchronize()
     b2.status()
@@ -267,6 +269,29 @@ def test_multi_sweep_wait_times_out_and_reports(gpu, ctx):
         _same(r, inst.standalone(gpu, ctx))
         inst.check_oracle(r)
     b2.close()
+
+
+def test_default_schedule(gpu, ctx):
+    # one launch when at least 4 stencil tasks have several sweeps, else
+    # rounds; either way the same bits
+    few = [Inst({"kind": "stencil", "nx": 70, "ny": 50, "iters": 3, "seed": 40 + k}) for k in range(3)]
+    many = [Inst({"kind": "stencil", "nx": 70, "ny": 50, "iters": 3, "seed": 40 + k}) for k in range(4)]
+    for insts, rounds in ((few, 3), (many, 1)):
+        b = gpu.hx_batch_plan(ctx, [i.task(gpu) for i in insts])
+        assert b.rounds == rounds
+        b.launch()
+        torch.cuda.synchronize()
+        b.status()
+        for inst in insts:
+            r = inst.result()
+            _same(r, inst.standalone(gpu, ctx))
+            inst.check_oracle(r)
+        b.close()
+    # both schedule flags at once, or an unknown flag, are rejected
+    h = ctypes.c_void_p()
+    for flags in (gpu.HX_BATCH_ROUNDS | gpu.HX_BATCH_ONE_LAUNCH, 4):
+        st = gpu.lib().hx_batch_plan_ex(ctx.handle, (gpu.HxTask * 1)(), 0, flags, ctypes.byref(h), None)
+        assert st == gpu.HX_ERR_INVALID
 
 
 def test_submit_reports_wait_timeout(gpu, ctx):
