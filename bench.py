@@ -702,6 +702,29 @@ def serving_comparison(points, targets=(2.0, 5.0, 10.0, 20.0)):
     return eq
 
 
+def timeline_summary(tl):
+    """Steps of one serving run from the server's timeline: how many, the
+    share issued as standalone calls, mean requests per batched step, mean
+    step time (issue to completion seen), and steps in flight (time-weighted
+    mean and maximum over the run)."""
+    if not tl:
+        return {"steps": 0}
+    batched = [r for r in tl if not r["direct"]]
+    ev = sorted([(r["issue_s"], 1) for r in tl] + [(r["done_s"], -1) for r in tl if r["done_s"] >= 0])
+    cur = peak = 0
+    area = 0.0
+    for (t, d), nxt in zip(ev, ev[1:] + [(ev[-1][0], 0)]):
+        cur += d
+        peak = max(peak, cur)
+        area += cur * (nxt[0] - t)
+    span = ev[-1][0] - ev[0][0]
+    done = [r["done_s"] - r["issue_s"] for r in tl if r["done_s"] >= 0]
+    return {"steps": len(tl), "direct_share": round(1.0 - len(batched) / len(tl), 3),
+            "requests_per_batched_step": round(float(np.mean([r["requests"] for r in batched])), 2) if batched else None,
+            "step_ms_mean": round(1e3 * float(np.mean(done)), 4) if done else None,
+            "steps_in_flight_mean": round(area / span, 2) if span > 0 else None, "steps_in_flight_max": peak}
+
+
 def bench_serving(hx, ctx, dev, rates=SERVE_RATES, repeats=3, duration_s=1.0, max_requests=10000, distinct=4000,
                   direct_max=0):
     """Open-loop Poisson serving at several offered rates, continuous batching
@@ -735,6 +758,7 @@ def bench_serving(hx, ctx, dev, rates=SERVE_RATES, repeats=3, duration_s=1.0, ma
                 with hx.Server(ctx, mode=mode, hbm_budget_bytes=SERVE_BUDGET, direct_max=direct_max) as srv:
                     lat, makespan = srv.run_trace(tasks, arrivals, timeout_s=300.0)
                     st = srv.stats()
+                    tls = timeline_summary(srv.timeline()) if name == "continuous" else None
                 lat = np.array(lat) * 1e3
                 # a queue that keeps up has stationary latency: the last tenth
                 # of the requests (in arrival order) waits no longer than about
@@ -745,7 +769,8 @@ def bench_serving(hx, ctx, dev, rates=SERVE_RATES, repeats=3, duration_s=1.0, ma
                 runs[name].append({"req_per_s": rate, "p50_ms": float(np.percentile(lat, 50)),
                                    "p99_ms": float(np.percentile(lat, 99)), "launches": st["launches"],
                                    "peak_footprint_gb": st["peak_footprint"] / 2**30,
-                                   "stable": bool(rate >= 0.95 * lam and tail <= 3.0 * head + 1.0)})
+                                   "stable": bool(rate >= 0.95 * lam and tail <= 3.0 * head + 1.0),
+                                   "timeline": tls})
         for name, rs in runs.items():
             med = lambda key: float(np.median([r[key] for r in rs]))  # noqa: E731
             row[name] = {"req_per_s": round(med("req_per_s"), 1), "p50_ms": round(med("p50_ms"), 4),
@@ -754,6 +779,10 @@ def bench_serving(hx, ctx, dev, rates=SERVE_RATES, repeats=3, duration_s=1.0, ma
                          "stable": sum(r["stable"] for r in rs) * 2 > len(rs),
                          "p99_ms_runs": [round(r["p99_ms"], 4) for r in rs],
                          "req_per_s_runs": [round(r["req_per_s"], 1) for r in rs]}
+            if name == "continuous":
+                # the steps of the run with the median p99 (server timeline)
+                mid = sorted(rs, key=lambda r: r["p99_ms"])[len(rs) // 2]
+                row[name]["timeline"] = mid["timeline"]
         points.append(row)
     del arena
     torch.cuda.empty_cache()

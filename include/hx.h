@@ -511,6 +511,15 @@ hx_status hx_batch_launch(hx_batch *batch, hx_stream_t stream);
 /* Free a plan.  Its launches must have completed. */
 void hx_batch_free(hx_batch *batch);
 
+/* A text description of a plan, one line per instance: its kind and sizes,
+ * tile plan or blocks per sweep, run length, load path and schedule (a
+ * stand-in for the IR debugger of the paper's tool chain, which draws its
+ * programs as graphs).  Writes at most len bytes including the terminating
+ * NUL (buf may be NULL when len is 0); *needed (nullable) receives the size
+ * the whole text needs.  Setting the environment variable HX_DUMP_PLAN=1
+ * prints every new plan's description to stderr.  Host only. */
+hx_status hx_batch_describe(const hx_batch *batch, char *buf, size_t len, size_t *needed);
+
 /* After the plan's launches have completed (the caller synchronised their
  * stream): HX_ERR_TIMEOUT if a wait between two sweeps of an instance ran
  * out of time in any of them since the last call (their results are then not
@@ -626,6 +635,20 @@ hx_status hx_server_submit(hx_server *s, const hx_task *task, uint64_t *req_id);
  * NULL), HX_ERR_BUSY while pending, HX_ERR_CUDA if its launch failed,
  * HX_ERR_INVALID for an unknown id. */
 hx_status hx_server_poll(hx_server *s, uint64_t req_id, double *latency_s);
+
+/* The server's timeline (no profiler needed): one record per step it issued
+ * -- a batched step, or a request's standalone call (low-load path and
+ * per-launch mode) -- for the first 65536 steps, in issue order.  Times are
+ * seconds since hx_server_create: when the step was issued, and when the
+ * completion thread saw it finish (-1 while pending).  Copies at most max
+ * records into out; *n receives how many there are. */
+typedef struct hx_server_step_record {
+    double issue_s;
+    double done_s;
+    int32_t requests;   /* requests with work (or an output) in the step */
+    int32_t direct;     /* 1: one request's standalone call; 0: a batched step */
+} hx_server_step_record;
+hx_status hx_server_get_timeline(hx_server *s, hx_server_step_record *out, int32_t max, int32_t *n);
 
 /* Block until every submitted request has completed (and, with on_done,
  * been reported), at most timeout_s seconds (HX_ERR_TIMEOUT otherwise).  HX_ERR_CUDA when a request completed

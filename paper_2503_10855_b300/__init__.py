@@ -410,6 +410,8 @@ _lib.hx_batch_status.restype = ctypes.c_int
 _lib.hx_debug_batch_stall.argtypes = [_P, _I32, _I64]
 _lib.hx_debug_batch_stall.restype = ctypes.c_int
 HX_BATCH_ROUNDS, HX_BATCH_ONE_LAUNCH = 1, 2
+_lib.hx_batch_describe.argtypes = [_P, ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]
+_lib.hx_batch_describe.restype = ctypes.c_int
 _lib.hx_batch_launch.argtypes = [_P, _P]
 _lib.hx_batch_launch.restype = ctypes.c_int
 _lib.hx_batch_free.argtypes = [_P]
@@ -500,6 +502,14 @@ class Batch:
         """Raise HxError (HX_ERR_TIMEOUT) if a wait between sweeps ran out of
         time in a completed launch (call after synchronising its stream)."""
         _check(_lib.hx_batch_status(self.handle), "hx_batch_status")
+
+    def describe(self) -> str:
+        """The plan as text (hx_batch_describe): one line per instance."""
+        need = ctypes.c_size_t(0)
+        _check(_lib.hx_batch_describe(self.handle, None, 0, ctypes.byref(need)), "hx_batch_describe")
+        buf = ctypes.create_string_buffer(need.value)
+        _check(_lib.hx_batch_describe(self.handle, buf, need.value, None), "hx_batch_describe")
+        return buf.value.decode()
 
     def debug_stall(self, task: int, wait_limit_ns: int) -> None:
         """Test hook (hx_debug_batch_stall): task's later sweeps wait for a block
@@ -653,6 +663,12 @@ _lib.hx_server_poll.argtypes = [_P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_dou
 _lib.hx_server_poll.restype = ctypes.c_int
 _lib.hx_server_drain.argtypes = [_P, ctypes.c_double]
 _lib.hx_server_drain.restype = ctypes.c_int
+class ServerStepRecord(ctypes.Structure):
+    _fields_ = [("issue_s", ctypes.c_double), ("done_s", ctypes.c_double), ("requests", _I32), ("direct", _I32)]
+
+
+_lib.hx_server_get_timeline.argtypes = [_P, ctypes.POINTER(ServerStepRecord), _I32, ctypes.POINTER(_I32)]
+_lib.hx_server_get_timeline.restype = ctypes.c_int
 _lib.hx_server_get_stats.argtypes = [_P, ctypes.POINTER(ServerStats)]
 _lib.hx_server_get_stats.restype = ctypes.c_int
 _lib.hx_server_run_trace.argtypes = [_P, ctypes.POINTER(HxTask), ctypes.POINTER(ctypes.c_double), _I32,
@@ -698,6 +714,16 @@ class Server:
 
     def drain(self, timeout_s: float = 60.0) -> None:
         _check(_lib.hx_server_drain(self.handle, timeout_s), "hx_server_drain")
+
+    def timeline(self, max_records: int = 1 << 16) -> list:
+        """The server's step records (hx_server_get_timeline) as dicts."""
+        n = _I32(0)
+        _check(_lib.hx_server_get_timeline(self.handle, None, 0, ctypes.byref(n)), "hx_server_get_timeline")
+        k = min(n.value, max_records)
+        arr = (ServerStepRecord * max(k, 1))()
+        _check(_lib.hx_server_get_timeline(self.handle, arr, k, ctypes.byref(n)), "hx_server_get_timeline")
+        return [{"issue_s": r.issue_s, "done_s": r.done_s, "requests": r.requests, "direct": bool(r.direct)}
+                for r in arr[:k]]
 
     def stats(self) -> dict:
         st = ServerStats()

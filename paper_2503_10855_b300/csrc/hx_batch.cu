@@ -19,7 +19,9 @@
 // remains available for comparison.
 #include <algorithm>
 #include <cstddef>
+#include <cstdlib>
 #include <cstring>
+#include <string>
 #include <new>
 #include <vector>
 
@@ -387,6 +389,7 @@ struct hx_batch {
     uint32_t n_inst = 0;
     uint32_t n_pairs = 0;                  // multi: (instance, sweep) pairs of the launch
     std::vector<uint32_t> n_cta, n_runs;   // per round: CTA chunks, warp runs
+    std::vector<hx::BInst> insts;          // host copy of the descriptors (hx_batch_describe)
     void *d_mem = nullptr;
     hx::BInst *d_insts = nullptr;
     uint32_t *d_prefix = nullptr;          // per round: CTA prefix (n_inst + 1), run prefix (n_inst + 1);
@@ -644,8 +647,62 @@ extern "C" hx_status hx_batch_plan_ex(hx_ctx *ctx, const hx_task *tasks, int32_t
             return cuda_fail(e, "hx_batch_plan: empty instance outputs");
         }
     }
+    b->insts = insts;
     *out = b;
     if (out_rounds) *out_rounds = rounds;
+    if (const char *dump = getenv("HX_DUMP_PLAN"); dump && dump[0] == '1') {
+        size_t need = 0;
+        hx_batch_describe(b, nullptr, 0, &need);
+        std::string text(need, '\0');
+        hx_batch_describe(b, text.data(), need, nullptr);
+        fputs(text.c_str(), stderr);
+    }
+    return HX_OK;
+}
+
+extern "C" hx_status hx_batch_describe(const hx_batch *b, char *buf, size_t len, size_t *needed) {
+    using namespace hx;
+    if (!b || (len > 0 && !buf)) return fail(HX_ERR_INVALID, "hx_batch_describe: bad arguments");
+    std::string t;
+    char line[256];
+    uint64_t runs = 0, ctas = 0;
+    for (int r = 0; r < b->rounds; ++r) {
+        runs += b->n_runs[r];
+        ctas += b->n_cta[r];
+    }
+    snprintf(line, sizeof line, "hx batch plan: %u instances, %s, %d launch%s of the batched kernel (each followed by "
+             "its final combine), %llu warp runs, %llu CTA items\n", b->n_inst,
+             b->multi ? "every sweep in one launch" : (b->rounds > 1 ? "one launch per sweep (rounds)" : "one pass"),
+             b->rounds, b->rounds == 1 ? "" : "es", (unsigned long long)runs, (unsigned long long)ctas);
+    t += line;
+    if (b->multi) {
+        snprintf(line, sizeof line, "  work order: %u (instance, sweep) pairs, sweep-major; a run of sweep s waits "
+                 "for sweep s-1 of its instance (bounded, %.3f s)\n", b->n_pairs, b->wait_ns * 1e-9);
+        t += line;
+    }
+    static const char *kinds[3] = {"map->reduce", "stencil", "histogram"};
+    for (uint32_t i = 0; i < b->n_inst; ++i) {
+        const BInst &I = b->insts[i];
+        if (I.kind == kKindMap)
+            snprintf(line, sizeof line, "  [%u] %s n=%lld tiles=%lld x %lld elements, runs of %d, %s path\n", i,
+                     kinds[I.kind], (long long)I.n, (long long)I.tiles, (long long)I.plan.tile_elems, I.run_len,
+                     I.vec ? "float4" : "element");
+        else if (I.kind == kKindStencil)
+            snprintf(line, sizeof line, "  [%u] %s %d x %d, %d sweep%s%s, %lld blocks of %d x 128 per sweep, runs of "
+                     "%d, %s path\n", i, kinds[I.kind], I.ny, I.nx, I.iters, I.iters == 1 ? "" : "s",
+                     I.n_sweeps > 1 ? " in one launch" : (I.iters > 1 ? " as rounds" : ""), (long long)I.tiles,
+                     kBatchStRows, I.run_len, I.vec ? "float4" : (b->multi && I.n_sweeps > 1 ? "lane-strided" : "element"));
+        else
+            snprintf(line, sizeof line, "  [%u] %s n=%lld bytes, %lld CTA chunks of %lld bytes\n", i, kinds[I.kind],
+                     (long long)I.n, (long long)I.tiles, (long long)kBHiTile);
+        t += line;
+    }
+    if (needed) *needed = t.size() + 1;
+    if (len > 0) {
+        const size_t n = std::min(len - 1, t.size());
+        memcpy(buf, t.data(), n);
+        buf[n] = '\0';
+    }
     return HX_OK;
 }
 

@@ -64,6 +64,7 @@ struct Slot {   // staging for one step: descriptors and prefix sums, pinned hos
 };
 
 struct Step {
+    int64_t record = -1;       // index into the server's timeline, or -1
     cudaEvent_t ev = nullptr;
     int slot = -1;             // continuous mode: staging slot to release
     std::vector<Req *> finishing;
@@ -98,6 +99,8 @@ struct hx_server {
     bool issuing = false;                     // per-launch mode: launches in progress without the lock
     bool stop = false;
     hx_server_stats stats{};
+    double created = 0.0;                     // timeline origin (steady clock)
+    std::vector<hx_server_step_record> timeline;   // one record per issued step (the first kTimelineMax)
     std::thread sched, compl_thr;
 };
 
@@ -127,6 +130,19 @@ void admit_locked(hx_server *s) {
         s->stats.peak_footprint = std::max(s->stats.peak_footprint, s->used);
         s->active.push_back(r);
     }
+}
+
+constexpr size_t kTimelineMax = (size_t)1 << 16;
+
+// Queues an issued step and records it in the timeline (called with the
+// lock held).
+void push_step_locked(hx_server *s, Step &&step, int direct) {
+    if (s->timeline.size() < kTimelineMax) {
+        step.record = (int64_t)s->timeline.size();
+        const size_t n = std::max(step.members.size(), step.finishing.size());
+        s->timeline.push_back({now_s() - s->created, -1.0, (int32_t)n, direct});
+    }
+    s->steps.push_back(std::move(step));
 }
 
 // Outputs of requests with no device work (empty map->reduce or histogram):
@@ -223,7 +239,7 @@ bool issue_direct_locked(hx_server *s) {
         step.ev = ev;
         step.finishing = one;
         step.members = one;
-        s->steps.push_back(std::move(step));
+        push_step_locked(s, std::move(step), 1);
     }
     s->cv_compl.notify_one();
     return true;
@@ -320,7 +336,7 @@ bool issue_step_locked(hx_server *s) {
     sl.busy = true;
     step.ev = sl.ev;
     step.slot = slot;
-    s->steps.push_back(std::move(step));
+    push_step_locked(s, std::move(step), 0);
     s->cv_compl.notify_one();
     return true;
 }
@@ -353,7 +369,7 @@ bool issue_per_launch(hx_server *s, std::unique_lock<std::mutex> &lk) {
             Step step;
             step.ev = ev;
             step.finishing = one;
-            s->steps.push_back(std::move(step));
+            push_step_locked(s, std::move(step), 1);
             s->cv_compl.notify_one();
         }
     }
@@ -406,6 +422,7 @@ void completer_main(hx_server *s) {
         lk.lock();
         Step step = std::move(s->steps.front());
         s->steps.pop_front();
+        if (step.record >= 0) s->timeline[(size_t)step.record].done_s = t - s->created;
         for (Req *r : step.finishing) {
             if (e != cudaSuccess) r->status = HX_ERR_CUDA;
             if (r->status != HX_OK) s->stats.failed += 1;
@@ -466,6 +483,7 @@ hx_status hx_server_create(hx_ctx *ctx, const hx_server_config *cfg, hx_server *
     if (!s) return fail(HX_ERR_NOMEM, "hx_server_create: host allocation failed");
     s->ctx = ctx;
     s->cfg = *cfg;
+    s->created = now_s();
     if (s->cfg.max_inflight == 0) s->cfg.max_inflight = 4096;
     if (s->cfg.hbm_budget_bytes == 0) s->cfg.hbm_budget_bytes = ctx->hbm_budget;
     if (s->cfg.max_steps_in_flight == 0) s->cfg.max_steps_in_flight = 4;
@@ -565,6 +583,15 @@ hx_status hx_server_drain(hx_server *s, double timeout_s) {
     const bool new_failures = s->stats.failed > s->failed_at_drain;
     s->failed_at_drain = s->stats.failed;
     return new_failures ? hx::fail(HX_ERR_CUDA, "hx_server_drain: some requests' launches failed") : HX_OK;
+}
+
+hx_status hx_server_get_timeline(hx_server *s, hx_server_step_record *out, int32_t max, int32_t *n) {
+    if (!s || !n || max < 0 || (max > 0 && !out)) return hx::fail(HX_ERR_INVALID, "hx_server_get_timeline: bad arguments");
+    std::lock_guard<std::mutex> lk(s->mu);
+    const size_t k = std::min(s->timeline.size(), (size_t)max);
+    std::copy(s->timeline.begin(), s->timeline.begin() + k, out);
+    *n = (int32_t)s->timeline.size();
+    return HX_OK;
 }
 
 hx_status hx_server_get_stats(hx_server *s, hx_server_stats *out) {

@@ -60,3 +60,16 @@ def test_no_stable_per_launch_point_and_unmet_targets():
     assert eq["per_launch_never_stable"] is True
     for row in eq["at_p99_targets"]:
         assert row["per_launch_req_per_s"] is None and "ratio" not in row
+
+
+def test_timeline_summary_by_hand():
+    # steps [0, 1] (batched, 3 requests), [0.5, 1.5] (direct), [2, 3]
+    # (batched, 5 requests): in flight 1, 2, 1, 0, 1 over 0.5, 0.5, 0.5,
+    # 0.5, 1 s -> mean 3 / 3 s = 1, max 2
+    tl = [{"issue_s": 0.0, "done_s": 1.0, "requests": 3, "direct": False},
+          {"issue_s": 0.5, "done_s": 1.5, "requests": 1, "direct": True},
+          {"issue_s": 2.0, "done_s": 3.0, "requests": 5, "direct": False}]
+    s = bench.timeline_summary(tl)
+    assert s == {"steps": 3, "direct_share": 0.333, "requests_per_batched_step": 4.0, "step_ms_mean": 1000.0,
+                 "steps_in_flight_mean": 1.0, "steps_in_flight_max": 2}
+    assert bench.timeline_summary([]) == {"steps": 0}

@@ -356,3 +356,34 @@ def test_batch_rejects_bad_task(gpu, ctx):
     bad = gpu.stencil_task(x.view(2, 4), x.view(2, 4), 1, torch.zeros(1, device=DEV))
     with pytest.raises(gpu.HxError):
         gpu.hx_batch_plan(ctx, [bad])
+
+
+def test_describe_plan(gpu, ctx):
+    # the plan as text: header, the work order of a one-launch plan, one line
+    # per instance; a buffer shorter than the text is truncated and terminated
+    insts = [Inst({"kind": "stencil", "nx": 70, "ny": 50, "iters": 3, "seed": 50 + k}) for k in range(4)]
+    insts.append(Inst({"kind": "map_reduce", "n": 100_003, "a": 1.5, "seed": 55}))
+    insts.append(Inst({"kind": "histogram", "n": 70_001, "seed": 56}))
+    b = gpu.hx_batch_plan(ctx, [i.task(gpu) for i in insts])
+    text = b.describe()
+    lines = text.splitlines()
+    assert lines[0].startswith("hx batch plan: 6 instances, every sweep in one launch, 1 launch ")
+    assert "(instance, sweep) pairs" in lines[1] and lines[1].strip().startswith("work order: 14 ")
+    body = lines[2:]
+    assert len(body) == 6
+    for k in range(4):
+        assert body[k].startswith(f"  [{k}] stencil 50 x 70, 3 sweeps in one launch")
+    assert body[4].startswith("  [4] map->reduce n=100003 ")
+    assert body[5].startswith("  [5] histogram n=70001 bytes")
+    need = ctypes.c_size_t(0)
+    assert gpu.lib().hx_batch_describe(b.handle, None, 0, ctypes.byref(need)) == gpu.HX_OK
+    assert need.value == len(text) + 1
+    short = ctypes.create_string_buffer(16)
+    assert gpu.lib().hx_batch_describe(b.handle, short, 16, None) == gpu.HX_OK
+    assert short.value.decode() == text[:15]
+    b.close()
+    r = gpu.hx_batch_plan(ctx, [i.task(gpu) for i in insts], rounds=True)
+    rtext = r.describe()
+    assert rtext.startswith("hx batch plan: 6 instances, one launch per sweep (rounds), 3 launches ")
+    assert "work order" not in rtext and "3 sweeps as rounds" in rtext
+    r.close()

@@ -90,6 +90,32 @@ def test_direct_and_batched_paths_agree(gpu, direct_max):
             inst.check_oracle(r)
 
 
+def test_timeline_records_steps(gpu):
+    # one record per issued step, in issue order, each finished after it was
+    # issued; the requests over all steps cover every request at least once;
+    # with the direct path off every step is batched, with every fresh
+    # request direct each request's first step is its standalone call
+    hx = gpu
+    trace = _trace(30, 40_000.0, seed=47, iters=4)
+    for direct_max in (-1, 64):
+        insts = [Inst(r) for r in trace]
+        with hx.hx_create(0) as ctx:
+            with hx.Server(ctx, mode=0, direct_max=direct_max) as srv:
+                srv.run_trace([i.task(hx) for i in insts], [r["arrival_s"] for r in trace])
+                st = srv.stats()
+                tl = srv.timeline()
+        assert len(tl) == st["launches"] > 0
+        issue = [r["issue_s"] for r in tl]
+        assert issue == sorted(issue) and issue[0] >= 0.0
+        assert all(r["done_s"] >= r["issue_s"] and r["requests"] >= 1 for r in tl)
+        assert sum(r["requests"] for r in tl) >= len(trace)
+        direct = [r for r in tl if r["direct"]]
+        if direct_max < 0:
+            assert not direct
+        else:
+            assert direct and all(r["requests"] == 1 for r in direct)
+
+
 def test_many_servers_on_one_context(gpu):
     # each server runs standalone calls on its own stream, which takes one of
     # the context's HX_MAX_STREAMS workspace slots; destroying the server
