@@ -5,9 +5,10 @@
 // block-level fork placed in shared memory, with an extra dimension for the
 // thread-level fork, as Sec. 4.4 describes), replicated per slot so that a
 // warp's 32 increments always hit 32 different banks.  CTAs then add their
-// bins into the workspace with integer atomics (exact and order independent)
-// and the last CTA to arrive publishes the bins and runs the exclusive scan
-// (a sequential fold over 256 entries, done as a warp-shuffle scan).
+// bins into one of kHiReplicas copies of the bins in the workspace with
+// integer atomics (exact and order independent), and the last CTA to arrive
+// adds the copies, publishes the bins and runs the exclusive scan (a
+// sequential fold over 256 entries, done as a warp-shuffle scan).
 #include "hx_internal.cuh"
 
 namespace hx {
@@ -32,16 +33,26 @@ histogram_kernel(const uint8_t *__restrict__ v, int64_t n, int head, int64_t nve
         if (threadIdx.x < tail) hist_count_byte(sh, slot, v[n - tail + threadIdx.x]);
     }
     __syncthreads();
-    if (hist_merge(sh, ws->hi_bins)) __threadfence();   // only threads that wrote bins
+    if (hist_merge(sh, ws->hi_bins[blockIdx.x % kHiReplicas])) __threadfence();   // only threads that wrote bins
     __syncthreads();
     if (threadIdx.x == 0) is_last = atomicAdd(&ws->hi_ticket, 1u) == gridDim.x - 1;
     __syncthreads();
     if (!is_last) return;
     __threadfence();
-    // Final: publish the bins, exclusive scan, reset the workspace.
+    // Final: add the copies that CTAs used (reading them from L2, where the
+    // atomics were performed) and zero them, publish the bins, exclusive
+    // scan, reset the ticket.
     unsigned int c = 0u;
     if (threadIdx.x < kHiBins) {
-        c = atomicExch(&ws->hi_bins[threadIdx.x], 0u);
+        const int used = gridDim.x < kHiReplicas ? (int)gridDim.x : kHiReplicas;
+        unsigned int part[kHiReplicas];
+#pragma unroll
+        for (int r = 0; r < kHiReplicas; ++r) part[r] = r < used ? __ldcg(&ws->hi_bins[r][threadIdx.x]) : 0u;
+#pragma unroll
+        for (int r = 0; r < kHiReplicas; ++r) {
+            c += part[r];
+            if (r < used) ws->hi_bins[r][threadIdx.x] = 0u;
+        }
         d_bins[threadIdx.x] = c;
     }
     unsigned int incl = c;
