@@ -607,6 +607,17 @@ typedef struct hx_server_config {
                                    * waiting to start and none has started, each runs as its own
                                    * standalone call instead of a batched step -- the shorter path at
                                    * low load (0: 4; -1: always batch; at most 65536) */
+    int64_t direct_sweep_bytes;   /* continuous mode: a stencil request that has not started and whose
+                                   * sweep moves at least this many bytes (8 per grid point) runs as its
+                                   * standalone call even while other requests wait.  Its sweeps are
+                                   * large enough to fill the device alone, and in batched steps it
+                                   * would advance one sweep per step.  (0: 16 MiB; -1: never) */
+    int32_t max_step_sweeps;      /* continuous mode: a stencil request at a sweep boundary whose sweep
+                                   * moves less than direct_sweep_bytes (16 MiB when that is -1) runs up
+                                   * to this many of its remaining sweeps inside one batched step, one
+                                   * after another on the device (0: 128, the most; 1: one sweep per
+                                   * step) */
+    int32_t pad_;
 } hx_server_config;
 
 typedef struct hx_server_stats {
@@ -649,6 +660,15 @@ typedef struct hx_server_step_record {
     int32_t direct;     /* 1: one request's standalone call; 0: a batched step */
 } hx_server_step_record;
 hx_status hx_server_get_timeline(hx_server *s, hx_server_step_record *out, int32_t max, int32_t *n);
+
+/* Test hook (continuous mode): the next batched step that runs several
+ * sweeps of a request gets one such request whose waits between sweeps can
+ * never be satisfied, and every wait of that step gives up after
+ * wait_limit_ns nanoseconds.  The step ends by itself; every request with
+ * work in it completes with HX_ERR_TIMEOUT (hx_server_poll), and
+ * hx_server_drain reports the failure.  One-shot.  HX_ERR_INVALID for a
+ * negative limit or a per-launch server. */
+hx_status hx_debug_server_stall(hx_server *s, int64_t wait_limit_ns);
 
 /* Block until every submitted request has completed (and, with on_done,
  * been reported), at most timeout_s seconds (HX_ERR_TIMEOUT otherwise).  HX_ERR_CUDA when a request completed

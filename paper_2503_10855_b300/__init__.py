@@ -642,7 +642,8 @@ class ServerConfig(ctypes.Structure):
     _fields_ = [("mode", _I32), ("max_inflight", _I32), ("hbm_budget_bytes", ctypes.c_size_t),
                 ("max_steps_in_flight", _I32), ("max_step_requests", _I32), ("step_quantum_bytes", ctypes.c_size_t),
                 ("step_target_bytes", ctypes.c_size_t), ("on_done", SERVER_DONE_FN), ("on_done_user", _P),
-                ("direct_max", _I32)]
+                ("direct_max", _I32), ("direct_sweep_bytes", ctypes.c_int64), ("max_step_sweeps", _I32),
+                ("pad_", _I32)]
 
 
 class ServerStats(ctypes.Structure):
@@ -668,6 +669,8 @@ class ServerStepRecord(ctypes.Structure):
 
 
 _lib.hx_server_get_timeline.argtypes = [_P, ctypes.POINTER(ServerStepRecord), _I32, ctypes.POINTER(_I32)]
+_lib.hx_debug_server_stall.argtypes = [_P, _I64]
+_lib.hx_debug_server_stall.restype = ctypes.c_int
 _lib.hx_server_get_timeline.restype = ctypes.c_int
 _lib.hx_server_get_stats.argtypes = [_P, ctypes.POINTER(ServerStats)]
 _lib.hx_server_get_stats.restype = ctypes.c_int
@@ -682,7 +685,8 @@ class Server:
 
     def __init__(self, ctx: Context, mode: int = HX_SERVE_CONTINUOUS, hbm_budget_bytes: int = 0,
                  max_inflight: int = 0, max_steps_in_flight: int = 0, max_step_requests: int = 0,
-                 step_quantum_bytes: int = 0, step_target_bytes: int = 0, on_done=None, direct_max: int = 0):
+                 step_quantum_bytes: int = 0, step_target_bytes: int = 0, on_done=None, direct_max: int = 0,
+                 direct_sweep_bytes: int = 0, max_step_sweeps: int = 0):
         """on_done(req_id, status, latency_s), if given, is called from the
         server's completion thread once per request (see hx_server_done_fn)."""
         self._on_done = None
@@ -690,7 +694,8 @@ class Server:
             self._on_done = SERVER_DONE_FN(lambda _user, rid, st, lat: on_done(int(rid), int(st), float(lat)))
         cfg = ServerConfig(mode, max_inflight, hbm_budget_bytes, max_steps_in_flight, max_step_requests,
                            step_quantum_bytes, step_target_bytes,
-                           self._on_done if self._on_done is not None else SERVER_DONE_FN(), None, direct_max)
+                           self._on_done if self._on_done is not None else SERVER_DONE_FN(), None, direct_max,
+                           direct_sweep_bytes, max_step_sweeps)
         h = _P()
         _check(_lib.hx_server_create(ctx.handle, ctypes.byref(cfg), ctypes.byref(h)), "hx_server_create")
         self.ctx = ctx
@@ -714,6 +719,10 @@ class Server:
 
     def drain(self, timeout_s: float = 60.0) -> None:
         _check(_lib.hx_server_drain(self.handle, timeout_s), "hx_server_drain")
+
+    def debug_stall(self, wait_limit_ns: int) -> None:
+        """Test hook: stall the next multi-sweep step (hx_debug_server_stall)."""
+        _check(_lib.hx_debug_server_stall(self.handle, int(wait_limit_ns)), "hx_debug_server_stall")
 
     def timeline(self, max_records: int = 1 << 16) -> list:
         """The server's step records (hx_server_get_timeline) as dicts."""

@@ -39,6 +39,12 @@ constexpr size_t kWsBytes = ((kWsPartials * sizeof(float2) + kWsAccWords * 4) + 
 // Continuous mode: at most this many fresh requests run as standalone calls
 // instead of a batched step (hx_server_config.direct_max = 0).
 constexpr int kDefaultDirectMax = 4;
+// Continuous mode: a fresh stencil request whose sweep moves at least this
+// many bytes runs as its standalone call (hx_server_config.direct_sweep_bytes
+// = 0).  A 16 MiB sweep (a 1448 x 1448 grid) fills the device on its own.
+constexpr int64_t kDefaultDirectSweepBytes = (int64_t)16 << 20;
+static_assert(2 * kMaxStepSweeps - 1 <= (int)kWsAccWords,
+              "a request's workspace holds one maximum per sweep and one arrival count per sweep but the last");
 
 struct Req {
     uint64_t id = 0;
@@ -87,6 +93,10 @@ struct hx_server {
     std::vector<hx::Slot> slots;
     std::vector<cudaEvent_t> free_events;     // per-launch mode
     char *ws_pool = nullptr;                  // continuous mode: max_inflight workspace slots (+ run counter)
+    unsigned int *err_h = nullptr;            // host-mapped error word of the steps' bounded waits
+    unsigned int *err_d = nullptr;
+    bool stall_next = false;                  // test hook: stall the next multi-sweep step (hx_debug_server_stall)
+    long long stall_wait_ns = 0;
     uint64_t failed_at_drain = 0;             // stats.failed when the last drain returned
     unsigned int *ctrl = nullptr;
     std::vector<int> free_ws;
@@ -215,15 +225,12 @@ cudaEvent_t take_event(hx_server *s) {
     return ev;
 }
 
-// Continuous mode at low load: when at most cfg.direct_max admitted requests
-// are waiting and none of them has started, each is issued as its standalone
-// call with its own completion event -- no descriptor upload, no batched
-// launch and final combine, the shortest path for a request that has the
-// device nearly to itself.  Results are the same bits either way.
-bool issue_direct_locked(hx_server *s) {
-    std::vector<Req *> batch;
-    batch.swap(s->active);
-    for (Req *r : batch) {
+// Issues each of `rs` (admitted requests that have not started) as its
+// standalone call on the server's stream, with its own completion event --
+// no descriptor upload, no batched launch and final combine.  Results are the
+// same bits either way.
+void issue_direct_locked(hx_server *s, const std::vector<Req *> &rs) {
+    for (Req *r : rs) {
         r->issued_all = true;
         s->stats.launches += 1;
         cudaEvent_t ev = take_event(s);
@@ -242,31 +249,62 @@ bool issue_direct_locked(hx_server *s) {
         push_step_locked(s, std::move(step), 1);
     }
     s->cv_compl.notify_one();
-    return true;
 }
+
+bool fresh(const Req *r) { return r->issued == 0 && r->sweep == 0 && !r->issued_all; }
 
 // Continuous mode: build one step out of the next slice of every admitted
 // request (at most its share of step_target_bytes, and at least
-// step_quantum_bytes, of traffic; a stencil slice stays within one sweep),
-// upload its descriptors and prefix sums, launch.
+// step_quantum_bytes, of traffic), upload its descriptors and prefix sums,
+// launch.  A stencil slice stays within one sweep, except that a stencil
+// request at a sweep boundary whose sweep is below the direct-issue size
+// takes up to cfg.max_step_sweeps of its remaining sweeps: the step's
+// persistent launch runs them one after another (bounded waits between an
+// instance's sweeps, see hx_batch.cuh), so a small stencil request needs one
+// step instead of one per sweep.
 bool issue_step_locked(hx_server *s) {
-    // low load: a few fresh requests run as their standalone calls
-    if ((int)s->active.size() <= s->cfg.direct_max &&
-        std::all_of(s->active.begin(), s->active.end(), [](const Req *r) { return r->issued == 0 && r->sweep == 0; }))
-        return issue_direct_locked(s);
+    // low load: when at most cfg.direct_max requests wait and none has
+    // started, each runs as its standalone call (the shortest path for a
+    // request that has the device nearly to itself)
+    if ((int)s->active.size() <= s->cfg.direct_max && std::all_of(s->active.begin(), s->active.end(), fresh)) {
+        std::vector<Req *> all;
+        all.swap(s->active);
+        issue_direct_locked(s, all);
+        return true;
+    }
+    // a stencil request with large sweeps runs as its standalone call at any
+    // load: in batched steps it would advance one sweep per step
+    if (s->cfg.direct_sweep_bytes > 0) {
+        std::vector<Req *> big;
+        for (Req *r : s->active)
+            if (r->task.kind == HX_TASK_STENCIL2D && fresh(r) && r->inst.tiles > 0 && r->task.u.st.iters > 0 &&
+                8 * (int64_t)r->task.u.st.nx * r->task.u.st.ny >= s->cfg.direct_sweep_bytes)
+                big.push_back(r);
+        if (!big.empty()) {
+            issue_direct_locked(s, big);
+            s->active.erase(std::remove_if(s->active.begin(), s->active.end(), [](Req *r) { return r->issued_all; }),
+                            s->active.end());
+            if (s->active.empty()) return true;
+        }
+    }
     int slot = -1;
     for (size_t i = 0; i < s->slots.size(); ++i)
         if (!s->slots[i].busy) { slot = (int)i; break; }
     if (slot < 0 || (int)s->steps.size() >= s->cfg.max_steps_in_flight) return false;
     Slot &sl = s->slots[slot];
-    // Staging layout, uploaded with one copy: descriptors, then the CTA and
-    // run prefix arrays (n + 1 entries each), placed after the step is built.
+    // Staging layout, uploaded with one copy: descriptors, then the CTA
+    // prefix (n + 1 entries), the run prefix (one entry per pair + 1) and,
+    // when some request runs several sweeps, the pair list.
     BInst *insts = reinterpret_cast<BInst *>(sl.h);
-    std::vector<uint32_t> cpv, rpv;
+    std::vector<uint32_t> cpv;
     cpv.reserve(s->active.size() + 1);
-    rpv.reserve(s->active.size() + 1);
+    std::vector<std::pair<uint32_t, int>> multi;   // (instance, sweeps) of requests running several sweeps
+    const size_t max_extra = (size_t)s->cfg.max_step_requests;   // pairs beyond the first pass
+    const int64_t multi_below = s->cfg.direct_sweep_bytes > 0 ? s->cfg.direct_sweep_bytes : kDefaultDirectSweepBytes;
+    size_t extra = 0;
     uint32_t n = 0;
-    uint64_t c = 0, w = 0;
+    uint64_t c = 0;
+    int64_t multi_blocks = 0;
     Step step;
     // Slice size: the step aims at step_target_bytes of traffic shared by the
     // requests in it, but each gets at least step_quantum_bytes.
@@ -285,17 +323,40 @@ bool issue_step_locked(hx_server *s) {
         }
         if ((int)n >= s->cfg.max_step_requests) continue;
         BInst I = r->inst;
-        const int64_t q = std::max<int64_t>(1, (int64_t)quantum / tile_bytes(I));
-        I.t_first = r->issued;
-        I.t_count = std::min<int64_t>(q, I.tiles - r->issued);
         I.sweep0 = I.kind == kKindStencil ? r->sweep : 0;
-        if (c + inst_ctas(I) > 0xffffffffull || w + inst_runs(I) > 0xffffffffull) continue;
+        int sweeps = 1;
+        if (I.kind == kKindStencil && r->issued == 0 && s->cfg.max_step_sweeps > 1 &&
+            8 * (int64_t)I.nx * I.ny < multi_below) {
+            sweeps = std::min({I.iters - r->sweep, s->cfg.max_step_sweeps, kMaxStepSweeps});
+            if (extra + (size_t)(sweeps - 1) > max_extra) sweeps = 1;
+        }
+        if (sweeps > 1) {
+            I.t_first = 0;
+            I.t_count = I.tiles;
+            I.n_sweeps = sweeps;
+            I.done = I.acc + sweeps;
+        } else {
+            const int64_t q = std::max<int64_t>(1, (int64_t)quantum / tile_bytes(I));
+            I.t_first = r->issued;
+            I.t_count = std::min<int64_t>(q, I.tiles - r->issued);
+        }
+        if (c + inst_ctas(I) > 0xffffffffull) continue;
         cpv.push_back((uint32_t)c);
-        rpv.push_back((uint32_t)w);
         c += inst_ctas(I);
-        w += inst_runs(I);
+        if (sweeps > 1) {
+            multi.emplace_back(n, sweeps);
+            extra += (size_t)(sweeps - 1);
+            multi_blocks += I.tiles;
+        }
         insts[n++] = I;
         step.members.push_back(r);
+        if (sweeps > 1) {
+            r->sweep += sweeps;
+            if (r->sweep < I.iters) continue;
+            r->issued_all = true;
+            step.finishing.push_back(r);
+            continue;
+        }
         r->issued += I.t_count;
         if (r->issued == I.tiles) {
             r->issued = 0;
@@ -306,22 +367,56 @@ bool issue_step_locked(hx_server *s) {
     }
     if (n == 0 && step.finishing.empty()) return false;
     cpv.push_back((uint32_t)c);
+    // Several sweeps: runs as short as keep about two per resident warp in a
+    // sweep (at most kMultiSweepRun blocks), as the batch planner does; the
+    // pair list is every instance's first pass in order, then each later
+    // sweep of the multi-sweep instances in instance order.
+    if (!multi.empty()) {
+        const int64_t warps = (int64_t)s->ctx->num_sms * s->ctx->batch_ctas_per_sm[1][0] * (kBatchThreads / kWarp);
+        const int run = (int)std::max<int64_t>(1, std::min<int64_t>(kMultiSweepRun, multi_blocks / (2 * warps)));
+        for (const auto &m : multi) insts[m.first].run_len = run;
+    }
+    std::vector<uint32_t> pairs, rpv;
+    for (uint32_t i = 0; i < n; ++i) pairs.push_back(make_pair(i, 0u));
+    int max_sweeps = 1;
+    for (const auto &m : multi) max_sweeps = std::max(max_sweeps, m.second);
+    for (int ph = 1; ph < max_sweeps; ++ph)
+        for (const auto &m : multi)
+            if (ph < m.second) pairs.push_back(make_pair(m.first, (uint32_t)ph));
+    uint64_t w = 0;
+    for (uint32_t pr : pairs) {
+        rpv.push_back((uint32_t)w);
+        w += inst_runs(insts[pr & (kMaxPairInstances - 1u)]);
+    }
     rpv.push_back((uint32_t)w);
+    const bool use_pairs = !multi.empty();
+    BatchSync sync{s->err_d, kDefaultWaitNs};
+    if (use_pairs && s->stall_next) {   // test hook: one instance's waits can never be satisfied
+        insts[multi.front().first].stall = 1;
+        sync.limit_ns = s->stall_wait_ns;
+        s->stall_next = false;
+    }
     const size_t off_cta = ((size_t)n * sizeof(BInst) + 15) & ~(size_t)15;
     const size_t off_run = off_cta + (((size_t)(n + 1) * 4 + 15) & ~(size_t)15);
+    const size_t off_pairs = off_run + ((rpv.size() * 4 + 15) & ~(size_t)15);
+    const size_t bytes = use_pairs ? off_pairs + pairs.size() * 4 : off_run + rpv.size() * 4;
     memcpy(sl.h + off_cta, cpv.data(), (n + 1) * 4);
-    memcpy(sl.h + off_run, rpv.data(), (n + 1) * 4);
+    memcpy(sl.h + off_run, rpv.data(), rpv.size() * 4);
+    if (use_pairs) memcpy(sl.h + off_pairs, pairs.data(), pairs.size() * 4);
     s->active.erase(std::remove_if(s->active.begin(), s->active.end(), [](Req *r) { return r->issued_all; }),
                     s->active.end());
     hx_status st = HX_OK;
     if (n > 0) {
-        cudaError_t e = cudaMemcpyAsync(sl.d, sl.h, off_run + (n + 1) * 4, cudaMemcpyHostToDevice, s->stream);
+        cudaError_t e = w > 0xffffffffull ? cudaErrorInvalidValue
+                                          : cudaMemcpyAsync(sl.d, sl.h, bytes, cudaMemcpyHostToDevice, s->stream);
         if (e != cudaSuccess) st = cuda_fail(e, "server: step upload");
         if (st == HX_OK)
             st = launch_batch_round(s->ctx, reinterpret_cast<const BInst *>(sl.d), n,
                                     reinterpret_cast<const uint32_t *>(sl.d + off_cta),
-                                    reinterpret_cast<const uint32_t *>(sl.d + off_run), nullptr, n, (uint32_t)c,
-                                    (uint32_t)w, 0, s->ctrl, BatchSync{nullptr, kDefaultWaitNs}, s->stream);
+                                    reinterpret_cast<const uint32_t *>(sl.d + off_run),
+                                    use_pairs ? reinterpret_cast<const uint32_t *>(sl.d + off_pairs) : nullptr,
+                                    use_pairs ? (uint32_t)pairs.size() : n, (uint32_t)c, (uint32_t)w, 0, s->ctrl,
+                                    sync, s->stream);
         s->stats.launches += 1;
     }
     if (st == HX_OK && cudaEventRecord(sl.ev, s->stream) != cudaSuccess) st = HX_ERR_CUDA;
@@ -423,6 +518,10 @@ void completer_main(hx_server *s) {
         Step step = std::move(s->steps.front());
         s->steps.pop_front();
         if (step.record >= 0) s->timeline[(size_t)step.record].done_s = t - s->created;
+        // a wait between two sweeps that ran out of time invalidates every
+        // request that had work in the step (they complete with the error)
+        if (s->err_h && e == cudaSuccess && __atomic_exchange_n(s->err_h, 0u, __ATOMIC_ACQ_REL) != 0u)
+            for (Req *r : step.members) r->status = HX_ERR_TIMEOUT;
         for (Req *r : step.finishing) {
             if (e != cudaSuccess) r->status = HX_ERR_CUDA;
             if (r->status != HX_OK) s->stats.failed += 1;
@@ -476,7 +575,8 @@ hx_status hx_server_create(hx_ctx *ctx, const hx_server_config *cfg, hx_server *
         return fail(HX_ERR_INVALID, "hx_server_create: unknown mode");
     if (cfg->max_inflight < 0 || cfg->max_inflight > 16384 || cfg->max_steps_in_flight < 0 ||
         cfg->max_steps_in_flight > 64 || cfg->max_step_requests < 0 || cfg->max_step_requests > 65536 ||
-        cfg->direct_max < -1 || cfg->direct_max > 65536)
+        cfg->direct_max < -1 || cfg->direct_max > 65536 || cfg->direct_sweep_bytes < -1 ||
+        cfg->max_step_sweeps < 0 || cfg->max_step_sweeps > kMaxStepSweeps)
         return fail(HX_ERR_INVALID, "hx_server_create: bad limits");
     DeviceGuard g(ctx->device);
     hx_server *s = new (std::nothrow) hx_server();
@@ -491,6 +591,8 @@ hx_status hx_server_create(hx_ctx *ctx, const hx_server_config *cfg, hx_server *
     if (s->cfg.step_quantum_bytes == 0) s->cfg.step_quantum_bytes = (size_t)32 << 20;
     if (s->cfg.step_target_bytes == 0) s->cfg.step_target_bytes = (size_t)512 << 20;
     if (s->cfg.direct_max == 0) s->cfg.direct_max = kDefaultDirectMax;
+    if (s->cfg.direct_sweep_bytes == 0) s->cfg.direct_sweep_bytes = kDefaultDirectSweepBytes;
+    if (s->cfg.max_step_sweeps == 0) s->cfg.max_step_sweeps = kMaxStepSweeps;
     cudaError_t e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
         delete s;
@@ -501,7 +603,9 @@ hx_status hx_server_create(hx_ctx *ctx, const hx_server_config *cfg, hx_server *
         const size_t K = (size_t)s->cfg.max_step_requests;
         s->slots.resize((size_t)s->cfg.max_steps_in_flight + 1);
         for (Slot &sl : s->slots) {
-            sl.bytes = align(K * sizeof(BInst)) + 2 * align((K + 1) * 4);
+            // descriptors, CTA prefix, run prefix and pair list (at most K
+            // first passes and K later sweeps)
+            sl.bytes = align(K * sizeof(BInst)) + align((K + 1) * 4) + align((2 * K + 1) * 4) + align(2 * K * 4);
             if (e == cudaSuccess) e = cudaMallocHost(&sl.h, sl.bytes);
             if (e == cudaSuccess) e = cudaMalloc(&sl.d, sl.bytes);
             if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming);
@@ -511,6 +615,11 @@ hx_status hx_server_create(hx_ctx *ctx, const hx_server_config *cfg, hx_server *
         if (e == cudaSuccess) e = cudaMemset(s->ws_pool, 0, pool + 256);
         s->ctrl = reinterpret_cast<unsigned int *>(s->ws_pool + pool);
         for (int i = s->cfg.max_inflight - 1; i >= 0; --i) s->free_ws.push_back(i);
+        if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void **>(&s->err_h), 64, cudaHostAllocMapped);
+        if (e == cudaSuccess) {
+            *s->err_h = 0u;
+            e = cudaHostGetDevicePointer(reinterpret_cast<void **>(&s->err_d), s->err_h, 0);
+        }
         if (e == cudaSuccess) e = cudaDeviceSynchronize();
     }
     if (e != cudaSuccess) {
@@ -520,6 +629,7 @@ hx_status hx_server_create(hx_ctx *ctx, const hx_server_config *cfg, hx_server *
             if (sl.ev) cudaEventDestroy(sl.ev);
         }
         if (s->ws_pool) cudaFree(s->ws_pool);
+        if (s->err_h) cudaFreeHost(s->err_h);
         cudaStreamDestroy(s->stream);
         delete s;
         return cuda_fail(e, "hx_server_create: staging");
@@ -550,6 +660,7 @@ void hx_server_destroy(hx_server *s) {
     }
     for (cudaEvent_t ev : s->free_events) cudaEventDestroy(ev);
     if (s->ws_pool) cudaFree(s->ws_pool);
+    if (s->err_h) cudaFreeHost(s->err_h);
     cudaStreamDestroy(s->stream);
     delete s;
 }
@@ -583,6 +694,16 @@ hx_status hx_server_drain(hx_server *s, double timeout_s) {
     const bool new_failures = s->stats.failed > s->failed_at_drain;
     s->failed_at_drain = s->stats.failed;
     return new_failures ? hx::fail(HX_ERR_CUDA, "hx_server_drain: some requests' launches failed") : HX_OK;
+}
+
+hx_status hx_debug_server_stall(hx_server *s, int64_t wait_limit_ns) {
+    if (!s || wait_limit_ns < 0) return hx::fail(HX_ERR_INVALID, "hx_debug_server_stall: bad arguments");
+    if (s->cfg.mode != HX_SERVE_CONTINUOUS)
+        return hx::fail(HX_ERR_INVALID, "hx_debug_server_stall: continuous mode only");
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stall_next = true;
+    s->stall_wait_ns = wait_limit_ns;
+    return HX_OK;
 }
 
 hx_status hx_server_get_timeline(hx_server *s, hx_server_step_record *out, int32_t max, int32_t *n) {

@@ -2,6 +2,8 @@
 (bit-identical to its standalone call, and matching the oracle), in both the
 continuous-batching and the per-launch modes; admission respects the budget."""
 
+import ctypes
+
 import numpy as np
 import pytest
 import torch
@@ -46,7 +48,7 @@ def test_sliced_requests_equal_alone(gpu):
     insts = [Inst(r) for r in trace]
     with hx.hx_create(0) as ctx:
         with hx.Server(ctx, mode=0, step_quantum_bytes=64 << 10, step_target_bytes=64 << 10,
-                       max_steps_in_flight=3, direct_max=-1) as srv:
+                       max_steps_in_flight=3, direct_max=-1, max_step_sweeps=1) as srv:
             srv.run_trace([i.task(hx) for i in insts], [r["arrival_s"] for r in trace])
             st = srv.stats()
         assert st["launches"] > len(trace)
@@ -114,6 +116,85 @@ def test_timeline_records_steps(gpu):
             assert not direct
         else:
             assert direct and all(r["requests"] == 1 for r in direct)
+
+
+@pytest.mark.parametrize("max_step_sweeps", [1, 3, 128])
+def test_multi_sweep_steps(gpu, max_step_sweeps):
+    # batched steps only; a stencil request takes up to max_step_sweeps of
+    # its remaining sweeps per step (one launch runs them one after another):
+    # the same bits as the standalone calls, and fewer steps than one sweep
+    # per step
+    hx = gpu
+    trace = _trace(30, 40_000.0, seed=49, iters=7)
+    insts = [Inst(r) for r in trace]
+    with hx.hx_create(0) as ctx:
+        with hx.Server(ctx, mode=0, direct_max=-1, direct_sweep_bytes=-1, max_step_sweeps=max_step_sweeps) as srv:
+            srv.run_trace([i.task(hx) for i in insts], [r["arrival_s"] for r in trace])
+            st = srv.stats()
+        assert st["completed"] == len(trace) and st["failed"] == 0
+        if max_step_sweeps == 128:
+            assert st["launches"] < len(trace)
+        for inst in insts:
+            r = inst.result()
+            _same(r, inst.standalone(hx, ctx))
+            inst.check_oracle(r)
+
+
+def test_multi_sweep_step_wait_times_out(gpu):
+    # a step whose wait between two sweeps can never be satisfied ends by
+    # itself after the limit (no fault, no hang); the stencil request in it
+    # completes with HX_ERR_TIMEOUT, drain reports the failure, and the next
+    # wave on the same server is correct
+    hx = gpu
+    lib = hx.lib()
+    specs = [{"kind": "stencil", "nx": 300, "ny": 200, "iters": 3, "seed": 60},
+             {"kind": "map_reduce", "n": 100_003, "a": 1.5, "seed": 61}]
+    lat = ctypes.c_double()
+    with hx.hx_create(0) as ctx:
+        with hx.Server(ctx, mode=0, direct_max=-1, direct_sweep_bytes=-1) as srv:
+            srv.debug_stall(2_000_000)
+            first = [Inst(s) for s in specs]
+            ids = [srv.submit(i.task(hx)) for i in first]
+            with pytest.raises(hx.HxError):
+                srv.drain(60.0)
+            assert lib.hx_server_poll(srv.handle, ids[0], ctypes.byref(lat)) == hx.HX_ERR_TIMEOUT
+            assert lib.hx_server_poll(srv.handle, ids[1], ctypes.byref(lat)) in (hx.HX_OK, hx.HX_ERR_TIMEOUT)
+            again = [Inst(s) for s in specs]
+            ids = [srv.submit(i.task(hx)) for i in again]
+            srv.drain(60.0)
+            assert all(srv.poll(rid)[0] for rid in ids)
+        for inst in again:
+            r = inst.result()
+            _same(r, inst.standalone(hx, ctx))
+            inst.check_oracle(r)
+        with hx.Server(ctx, mode=1) as srv:
+            with pytest.raises(hx.HxError):
+                srv.debug_stall(1000)
+
+
+@pytest.mark.parametrize("direct_sweep_bytes", [8 * 64 * 64, -1])
+def test_large_stencils_run_standalone(gpu, direct_sweep_bytes):
+    # batched steps otherwise (direct_max = -1): each stencil request whose
+    # sweep moves at least direct_sweep_bytes runs once as its standalone
+    # call, everything else in batched steps; the same bits either way
+    hx = gpu
+    trace = _trace(36, 40_000.0, seed=48, iters=4)
+    insts = [Inst(r) for r in trace]
+    big = sum(1 for r in trace if r["kind"] == "stencil" and direct_sweep_bytes > 0 and
+              8 * r["nx"] * r["ny"] >= direct_sweep_bytes)
+    assert direct_sweep_bytes < 0 or 0 < big < len(trace)
+    with hx.hx_create(0) as ctx:
+        with hx.Server(ctx, mode=0, direct_max=-1, direct_sweep_bytes=direct_sweep_bytes) as srv:
+            srv.run_trace([i.task(hx) for i in insts], [r["arrival_s"] for r in trace])
+            st = srv.stats()
+            tl = srv.timeline()
+        assert st["completed"] == len(trace) and st["failed"] == 0
+        direct = [r for r in tl if r["direct"]]
+        assert len(direct) == big and all(r["requests"] == 1 for r in direct)
+        for inst in insts:
+            r = inst.result()
+            _same(r, inst.standalone(hx, ctx))
+            inst.check_oracle(r)
 
 
 def test_many_servers_on_one_context(gpu):
