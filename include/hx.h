@@ -451,14 +451,17 @@ hx_status hx_autotune(hx_ctx *ctx, int32_t max_log2, hx_stream_t stream);
  *
  * A stencil task with iters > 1 runs all its sweeps inside the same
  * persistent launch (the sequential outer loop of Sec. 4.4 rule 1 kept on
- * the device): the work items of sweep s of an instance wait until every
- * block of its sweep s - 1 is done.  Items are taken in an order in which
- * every wait is for items already taken, and the launch never has more CTAs
- * than the device holds at once, so every wait ends; each wait is also
+ * the device): a block of sweep s of an instance waits until it and its
+ * north, south, west and east neighbouring blocks have finished sweep s - 1,
+ * so an instance's sweeps overlap as a wavefront.  Items are taken in an
+ * order in which every wait is for items already taken, and the launch never
+ * has more CTAs than the device holds at once, so every wait ends; each
+ * wait is also
  * bounded in time (1 s): if one runs out, the launch records HX_ERR_TIMEOUT
  * (hx_batch_status, hx_batch_query) and its results are not valid.  With
- * HX_BATCH_ROUNDS, above 255 sweeps, or by default when fewer than 4 stencil
- * tasks have iters > 1, the plan runs as rounds instead:
+ * HX_BATCH_ROUNDS, above 255 sweeps, or by default when the stencil tasks
+ * with iters > 1 move more than 512 MiB per sweep (8 bytes per grid point),
+ * the plan runs as rounds instead:
  * round r runs sweep r of every stencil instance that has one (plus, in
  * round 0, all map->reduce and histogram instances), one launch per round.
  *
@@ -494,7 +497,8 @@ hx_status hx_batch_plan(hx_ctx *ctx, const hx_task *tasks, int32_t n_tasks, hx_b
                         int32_t *out_rounds);
 
 /* hx_batch_plan with flags: 0 (the default schedule: every sweep in one
- * launch when at least 4 stencil tasks have iters > 1, else rounds),
+ * launch when the stencil tasks with iters > 1 move at most 512 MiB per
+ * sweep, else rounds),
  * HX_BATCH_ROUNDS (one launch per sweep) or HX_BATCH_ONE_LAUNCH (every sweep
  * in one launch, whatever the task count; at most 255 sweeps).  All give the
  * same results; HX_ERR_INVALID for unknown or conflicting flags. */
@@ -590,7 +594,7 @@ typedef void (*hx_server_done_fn)(void *user, uint64_t req_id, hx_status status,
 typedef struct hx_server_config {
     int32_t mode;                 /* hx_serve_mode */
     int32_t max_inflight;         /* admitted, unfinished requests at most (0: 4096; at most 16384;
-                                   * continuous mode keeps 34 KiB of device workspace per slot) */
+                                   * continuous mode keeps 49 KiB of device workspace per slot) */
     size_t hbm_budget_bytes;      /* admission budget (0: the context's budget; 0 there too: unlimited).
                                    * A request larger than the budget is admitted only when nothing else
                                    * is in flight. */
@@ -631,7 +635,7 @@ typedef struct hx_server_stats {
 typedef struct hx_server hx_server;
 
 /* Start a server (its threads, its stream and, in continuous mode, one
- * descriptor staging buffer per queued step plus 34 KiB of workspace per
+ * descriptor staging buffer per queued step plus 49 KiB of workspace per
  * in-flight slot) on ctx's device. */
 hx_status hx_server_create(hx_ctx *ctx, const hx_server_config *cfg, hx_server **out);
 

@@ -68,27 +68,46 @@ __device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int *p) {
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
-__device__ __forceinline__ void red_release_add(unsigned int *p, unsigned int v) {
-    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
-}
 __device__ __forceinline__ unsigned long long globaltimer_ns() {
     unsigned long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
 
-// Wait (lane 0 of the warp) until *cnt >= target, at most sync.limit_ns; on
-// running out, record HX_ERR_TIMEOUT and go on.  Every lane then makes its
-// own acquire of *cnt, so the grid reads that follow see the writes counted.
-__device__ __forceinline__ void wait_count(const unsigned int *cnt, unsigned int target, const BatchSync &sync,
-                                           int lane) {
-    if (lane == 0 && ld_acquire_u32(cnt) < target) {
-        // exponential back-off (32 ns .. 1 us): when many warps wait on one
-        // instance's counter, their polls would otherwise crowd the L2 slice
-        // that also serves the arrivals they wait for
+__device__ __forceinline__ void st_release_u32(unsigned int *p, unsigned int v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Waits until the blocks a run of sweep `phase` depends on have finished
+// sweep phase - 1.  The run is blocks first .. first + cnt - 1 (block t is
+// column t / tiles_y, row t % tiles_y; consecutive blocks go down a column),
+// so its dependencies are each block itself and its west and east
+// neighbours, plus the north neighbour of the first block and the south
+// neighbour of the last (the other north / south neighbours are blocks of
+// the run).  Lane 3k + j checks block k itself (j = 0), west (1) or east (2);
+// lanes 3 cnt and 3 cnt + 1 the north and south ends: one progress word per
+// lane, so a satisfied wait costs one round trip.  A lane polls its word with
+// ld.acquire, exponential back-off (32 ns .. 1 us) and a deadline of
+// sync.limit_ns; on running out it records HX_ERR_TIMEOUT and gives up.  The
+// warp barrier then orders every lane's grid reads after the acquires.
+__device__ __forceinline__ void wait_blocks(const BInst &I, int64_t first, unsigned int cnt, int phase,
+                                            const BatchSync &sync, int lane) {
+    const int64_t ty = I.tiles_y, last = first + cnt - 1;
+    int64_t dep = -1;
+    if (lane < 3 * (int)cnt) {
+        const int64_t t = first + lane / 3;
+        const int j = lane % 3;
+        dep = j == 0 ? t : (j == 1 ? (t >= ty ? t - ty : -1) : (t + ty < I.tiles ? t + ty : -1));
+    } else if (lane == 3 * (int)cnt) {
+        dep = first % ty > 0 ? first - 1 : -1;
+    } else if (lane == 3 * (int)cnt + 1) {
+        dep = last % ty + 1 < ty ? last + 1 : -1;
+    }
+    const unsigned int need = (unsigned int)phase + (I.stall ? (1u << 20) : 0u);
+    if (dep >= 0 && ld_acquire_u32(I.done + dep) < need) {
         const unsigned long long t0 = globaltimer_ns();
         unsigned int nap = 32;
-        while (ld_acquire_u32(cnt) < target) {
+        while (ld_acquire_u32(I.done + dep) < need) {
             if (globaltimer_ns() - t0 > (unsigned long long)sync.limit_ns) {
                 // host-mapped word: a plain store (no atomic over the host link)
                 *reinterpret_cast<volatile unsigned int *>(sync.err) = (unsigned int)HX_ERR_TIMEOUT;
@@ -99,7 +118,6 @@ __device__ __forceinline__ void wait_count(const unsigned int *cnt, unsigned int
         }
     }
     __syncwarp();
-    (void)ld_acquire_u32(cnt);
 }
 
 // Phase 1 runs the CTA items (histogram chunks, CTA c takes items c, c + G,
@@ -113,16 +131,17 @@ __device__ __forceinline__ void wait_count(const unsigned int *cnt, unsigned int
 //
 // MULTI: stencil instances may run several sweeps in this launch (the
 // sequential outer loop of Sec. 4.4 rule 1, kept inside one persistent
-// launch).  Runs are taken in pair order -- every instance's first sweep
-// before any second sweep, and so on -- so a run of sweep s waits only for
-// runs taken before it; all CTAs of the launch are resident at once, hence
-// the oldest unfinished run never waits and every wait ends.  A sweep's runs
-// count their blocks in the instance's `done` word for that sweep (a release
-// reduction, so the next sweep's readers see the grid they wrote); the next
-// sweep's runs wait for the full count (bounded, see BatchSync) and read the
-// grid through L2.  Grids, residuals and results are the same as the
-// standalone calls': every block computes the same values from the same
-// inputs, and a maximum does not depend on order.
+// launch).  Runs are taken in pair order, in which an instance's sweep s - 1
+// comes before its sweep s, so a run waits only for runs taken before it:
+// the oldest unfinished run is always being processed and never waits, and
+// every wait ends.  After computing its blocks a run publishes each block's
+// progress (a release store of the sweeps done); a run of sweep s waits until
+// its blocks and their four neighbours have finished sweep s - 1 (bounded,
+// see BatchSync) and reads the grid through L2.  Sweeps of an instance
+// therefore overlap as a wavefront instead of meeting at a barrier.  Grids,
+// residuals and results are the same as the standalone calls': every block
+// computes the same values from the same inputs, and a maximum does not
+// depend on order.
 template <bool MULTI>
 __global__ void __launch_bounds__(kBatchThreads, 2)
 batch_kernel(const BInst *__restrict__ insts, unsigned int n_inst, const uint32_t *__restrict__ cta_prefix,
@@ -149,7 +168,6 @@ batch_kernel(const BInst *__restrict__ insts, unsigned int n_inst, const uint32_
     unsigned int it = 0u;
     if (lane == 0) it = atomicAdd(&ctrl[0], 1u);
     it = __shfl_sync(0xffffffffu, it, 0);
-    uint32_t verified = 0xffffffffu;   // MULTI: the last pair whose wait this warp passed
     while (it < n_runs) {
         unsigned int next = 0u;
         if (lane == 0) next = atomicAdd(&ctrl[0], 1u);
@@ -180,10 +198,7 @@ batch_kernel(const BInst *__restrict__ insts, unsigned int n_inst, const uint32_
         } else {
             const int sweep = I.sweep0 + round + phase;
             const bool multi = MULTI && I.n_sweeps > 1;
-            if (multi && phase > 0 && pr != verified) {
-                wait_count(I.done + (phase - 1), (unsigned int)I.t_count + (I.stall ? 1u : 0u), sync, lane);
-                verified = pr;
-            }
+            if (multi && phase > 0) wait_blocks(I, first, cnt, phase, sync, lane);
             const float *src = static_cast<const float *>((sweep & 1) ? I.in1 : I.in0);
             float *dst = const_cast<float *>(static_cast<const float *>((sweep & 1) ? I.in0 : I.in1));
             float m = 0.0f;
@@ -202,10 +217,10 @@ batch_kernel(const BInst *__restrict__ insts, unsigned int n_inst, const uint32_
             m = warp_max(m);
             if (lane == 0) atomicMax(I.acc + phase, __float_as_uint(m));
             if (multi && phase + 1 < I.n_sweeps) {
-                // publish this run's blocks to the next sweep's readers: a
-                // release reduction after the warp's barrier (no fence stall)
+                // publish this run's blocks to the next sweep's readers:
+                // release stores after the warp's barrier (no fence stall)
                 __syncwarp();
-                if (lane == 0) red_release_add(I.done + phase, cnt);
+                if (lane < (int)cnt) st_release_u32(I.done + first + lane, (unsigned int)(phase + 1));
             }
         }
         it = __shfl_sync(0xffffffffu, next, 0);
@@ -218,11 +233,12 @@ batch_kernel(const BInst *__restrict__ insts, unsigned int n_inst, const uint32_
 // launch waits for the whole grid): the sum of a map->reduce instance from
 // its tile partials in the standalone call's fixed order (all 256 threads
 // fold, one virtual lane each), the residual of each stencil sweep the launch
-// ran, the bins and scan of a histogram (one warp).  Accumulators and sweep
-// arrival counts are left at zero for the next use; the run counter is reset
-// for the next launch.  An instance's first pairs are its sweep-0 pairs,
-// listed for every instance in instance order, so entries i and i + 1 of the
-// run prefix bound instance i's first-pass runs in either layout.
+// ran, the bins and scan of a histogram (one warp).  Accumulators and block
+// progress words are left at zero for the next use; the run counter is reset
+// for the next launch.  Whether an instance had work: its CTA chunks, plus,
+// in a launch without a pair list, entries i and i + 1 of the run prefix; a
+// launch with a pair list (run_prefix NULL here) runs every instance's whole
+// slice.
 __global__ void __launch_bounds__(kBatchThreads)
 batch_final_kernel(const BInst *__restrict__ insts, unsigned int n_inst, const uint32_t *__restrict__ cta_prefix,
                    const uint32_t *__restrict__ run_prefix, int round, unsigned int *ctrl) {
@@ -233,10 +249,16 @@ batch_final_kernel(const BInst *__restrict__ insts, unsigned int n_inst, const u
     const int lane = threadIdx.x & 31;
     const unsigned int i = blockIdx.x;   // one CTA per instance
     if (i >= n_inst) return;
-    const unsigned int work = (__ldg(cta_prefix + i + 1) - __ldg(cta_prefix + i)) +
-                              (__ldg(run_prefix + i + 1) - __ldg(run_prefix + i));
     const BInst &I = insts[i];
+    // whether the instance had work in this launch: its CTA chunks and its
+    // first-pass runs (a pair-ordered launch, run_prefix NULL, gives every
+    // instance its whole slice)
+    const unsigned int work = (__ldg(cta_prefix + i + 1) - __ldg(cta_prefix + i)) +
+                              (run_prefix ? __ldg(run_prefix + i + 1) - __ldg(run_prefix + i)
+                                          : (I.t_count > 0 && I.kind != kKindHist ? 1u : 0u));
     if (work == 0 || I.t_first + I.t_count != I.tiles) return;
+    if (I.kind == kKindStencil && I.n_sweeps > 1)   // progress words back to zero
+        for (int64_t k = threadIdx.x; k < I.tiles; k += blockDim.x) I.done[k] = 0u;
     if (I.kind == kKindMap) {
         const ff sf = mr_final_cta(I.partials, I.plan.tiles, red);
         if (threadIdx.x == 0) {
@@ -247,11 +269,9 @@ batch_final_kernel(const BInst *__restrict__ insts, unsigned int n_inst, const u
     } else if (threadIdx.x >= kWarp) {
         return;
     } else if (I.kind == kKindStencil) {
-        // the residual of every sweep the launch ran; arrival counts back to 0
-        for (int ph = lane; ph < I.n_sweeps; ph += kWarp) {
+        // the residual of every sweep the launch ran
+        for (int ph = lane; ph < I.n_sweeps; ph += kWarp)
             static_cast<float *>(I.o0)[I.sweep0 + round + ph] = __uint_as_float(atomicExch(I.acc + ph, 0u));
-            if (ph + 1 < I.n_sweeps) I.done[ph] = 0u;
-        }
     } else {
         // lane l owns bins 8l .. 8l+7: local prefix, then a shuffle scan of
         // the lane totals
@@ -348,7 +368,8 @@ hx_status launch_batch_round(const hx_ctx *ctx, const BInst *d_insts, uint32_t n
     if (e != cudaSuccess) return cuda_fail(e, "batched kernel launch");
     cfg.gridDim = dim3(n_inst);
     cfg.dynamicSmemBytes = 0;
-    e = cudaLaunchKernelEx(&cfg, batch_final_kernel, d_insts, n_inst, d_cta_prefix, d_run_prefix, round, d_ctrl);
+    e = cudaLaunchKernelEx(&cfg, batch_final_kernel, d_insts, n_inst, d_cta_prefix, multi ? nullptr : d_run_prefix,
+                           round, d_ctrl);
     if (e != cudaSuccess) return cuda_fail(e, "batched final launch");
     return HX_OK;
 }
@@ -472,23 +493,24 @@ extern "C" hx_status hx_batch_plan_ex(hx_ctx *ctx, const hx_task *tasks, int32_t
         if (st != HX_OK) return st;
     }
     std::vector<BInst> insts(n_tasks);
-    int max_iters = 0, n_multi = 0;
+    int max_iters = 0;
+    int64_t multi_sweep_bytes = 0;
     for (int i = 0; i < n_tasks; ++i) {
         int64_t np = 0, na = 0;
         describe_instance(ctx, tasks[i], &insts[i], &np, &na);
         if (insts[i].tiles > 0xffffffffll) return fail(HX_ERR_INVALID, "hx_batch_plan: instance too large");
         if (insts[i].kind == kKindStencil) max_iters = std::max(max_iters, insts[i].iters);
-        if (insts[i].kind == kKindStencil && insts[i].iters > 1 && insts[i].tiles > 0) ++n_multi;
+        if (insts[i].kind == kKindStencil && insts[i].iters > 1 && insts[i].tiles > 0)
+            multi_sweep_bytes += 8 * (int64_t)insts[i].nx * insts[i].ny;
     }
     // Several sweeps per stencil instance run in one launch unless the caller
     // asks for rounds (round r = sweep r of every instance, one launch each),
-    // or, by default, when fewer than kMinMultiInstances instances have
-    // several sweeps: the sweeps of one instance then wait for each other
-    // across the whole device.  (An instance's sweep offset is stored in 8
-    // bits of its pair entries: batches with more than 255 sweeps run as
-    // rounds.)
+    // or, by default, when the multi-sweep instances move more than
+    // kOneLaunchMaxSweepBytes per sweep.  (An instance's sweep offset is
+    // stored in 8 bits of its pair entries: batches with more than 255 sweeps
+    // run as rounds.)
     const bool multi = max_iters > 1 && max_iters <= 255 && !(flags & HX_BATCH_ROUNDS) &&
-                       ((flags & HX_BATCH_ONE_LAUNCH) || n_multi >= kMinMultiInstances);
+                       ((flags & HX_BATCH_ONE_LAUNCH) || multi_sweep_bytes <= kOneLaunchMaxSweepBytes);
     int rounds = n_tasks > 0 ? 1 : 0;
     if (!multi) rounds = std::max(rounds, max_iters);
     int64_t n_partials = 0, n_acc = 0;
@@ -497,14 +519,14 @@ extern "C" hx_status hx_batch_plan_ex(hx_ctx *ctx, const hx_task *tasks, int32_t
         else if (I.kind == kKindHist) n_acc += kHiBins;
         else {
             if (multi && I.iters > 1) I.n_sweeps = I.iters;
-            n_acc += 2 * I.n_sweeps - 1;   // one max per sweep, one arrival count per sweep but the last
+            n_acc += I.n_sweeps + (I.n_sweeps > 1 ? I.tiles : 0);   // one max per sweep, one progress word per block
         }
     }
     if (multi) {
         // Run length of the multi-sweep instances: long runs mean fewer waits
         // and publications (up to kMultiSweepRun blocks), but an instance's
-        // next sweep waits for all of this one, so a sweep of the batch needs
-        // about two runs per resident warp to keep the device busy.
+        // next sweep waits for this one, so a sweep of the batch needs about
+        // two runs per resident warp to keep the device busy.
         int64_t blocks = 0;
         for (const BInst &I : insts)
             if (I.n_sweeps > 1) blocks += I.tiles;
@@ -518,8 +540,8 @@ extern "C" hx_status hx_batch_plan_ex(hx_ctx *ctx, const hx_task *tasks, int32_t
     // instances; stencil sweep r of each instance goes to round r).  Multi:
     // one launch; CTA prefix over instances, run prefix over the pair list:
     // every instance's first pass, then each later sweep, instances in the
-    // same order within every sweep, so a run and the runs it waits for are
-    // a whole sweep of work apart.
+    // same order within every sweep, so a block and the blocks it waits for
+    // are about a whole sweep of work apart.
     const size_t stride = (size_t)n_tasks + 1;
     std::vector<uint32_t> prefix, pairs;
     std::vector<uint32_t> round_cta(rounds), round_runs(rounds);
@@ -612,7 +634,7 @@ extern "C" hx_status hx_batch_plan_ex(hx_ctx *ctx, const hx_task *tasks, int32_t
         } else if (I.kind == kKindStencil) {
             I.acc = acc_base + acur;
             I.done = I.n_sweeps > 1 ? I.acc + I.n_sweeps : nullptr;
-            acur += 2 * I.n_sweeps - 1;
+            acur += I.n_sweeps + (I.n_sweeps > 1 ? I.tiles : 0);
         } else {
             I.acc = acc_base + acur;
             acur += kHiBins;
@@ -676,8 +698,8 @@ extern "C" hx_status hx_batch_describe(const hx_batch *b, char *buf, size_t len,
              b->rounds, b->rounds == 1 ? "" : "es", (unsigned long long)runs, (unsigned long long)ctas);
     t += line;
     if (b->multi) {
-        snprintf(line, sizeof line, "  work order: %u (instance, sweep) pairs, sweep-major; a run of sweep s waits "
-                 "for sweep s-1 of its instance (bounded, %.3f s)\n", b->n_pairs, b->wait_ns * 1e-9);
+        snprintf(line, sizeof line, "  work order: %u (instance, sweep) pairs, sweep-major; a block of sweep s waits "
+                 "for itself and its 4 neighbours in sweep s-1 (bounded, %.3f s)\n", b->n_pairs, b->wait_ns * 1e-9);
         t += line;
     }
     static const char *kinds[3] = {"map->reduce", "stencil", "histogram"};

@@ -40,17 +40,20 @@ struct BInst {
     void *o2;           // map sum64
     float2 *partials;   // map tile partials (hi, lo)
     unsigned int *acc;  // stencil: max bits, one word per sweep of the launch; hist: 256 bins
-    unsigned int *done; // stencil with n_sweeps > 1: blocks finished, per sweep but the last
+    unsigned int *done; // stencil with n_sweeps > 1: one progress word per block (tiles of them), the
+                        // sweeps of this launch the block has finished; zero between launches
     int stall;          // test hook (hx_debug_batch_stall): this instance's waits are never satisfied
     int pad3;
 };
 
-// Bounded waits of a launch that runs several sweeps of an instance: a run
-// of sweep s waits until every block of sweep s - 1 of its instance is done.
-// A wait gives up after limit_ns nanoseconds of %globaltimer; the kernel
-// then records HX_ERR_TIMEOUT in *err (host-mapped memory, read by the host
-// once the launch has completed) and carries on, so no wait is unbounded and
-// no later wait depends on the one that gave up.
+// Bounded waits of a launch that runs several sweeps of an instance: a block
+// of sweep s waits until it and its four neighbouring blocks (north, south,
+// west, east) have finished sweep s - 1 -- they wrote the cells it reads,
+// and they read the cells it overwrites (the grids alternate).  A wait gives
+// up after limit_ns nanoseconds of %globaltimer; the kernel then records
+// HX_ERR_TIMEOUT in *err (host-mapped memory, read by the host once the
+// launch has completed) and carries on, so no wait is unbounded and no later
+// wait depends on the one that gave up.
 struct BatchSync {
     unsigned int *err;
     long long limit_ns;
@@ -58,19 +61,21 @@ struct BatchSync {
 constexpr long long kDefaultWaitNs = 1000000000ll;   // 1 s
 // Blocks per warp run (at most) of a stencil instance that runs several
 // sweeps in one launch: every run of such an instance waits for, and
-// publishes to, a sweep counter, so longer runs mean fewer round trips, while
-// a sweep cannot use more warps than it has runs (the planner shortens runs
-// until a sweep of the launch has about two per resident warp).  Measured on
-// the 512-instance, 20-sweep batch (B300): 4 blocks 4.51 ms, 8 blocks
-// 4.41 ms, 16 blocks 4.55 ms, 32 blocks 4.80 ms.
+// publishes, its blocks' progress, so longer runs mean fewer round trips,
+// while a sweep cannot use more warps than it has runs (the planner shortens
+// runs until a sweep of the launch has about two per resident warp).
 constexpr int kMultiSweepRun = 8;
 // A plan runs several sweeps of its instances in one launch by default only
-// if at least this many stencil instances have several sweeps.  Measured on
-// B300, 20 sweeps: one 4096^2 grid took 0.76 ms in one launch against
-// 0.55 ms as rounds, while 8 grids of sides 1024-4096 took 1.07 ms against
-// 1.23 ms.
-constexpr int kMinMultiInstances = 4;
+// if its multi-sweep instances move at most this many bytes per sweep.  With
+// larger sweeps a launch per sweep hides its launch gaps and its one-sweep
+// blocks (read-only loads through L1) are cheaper.  Measured on B300, 20
+// sweeps, one launch against rounds: one 4096^2 grid 0.479 against 0.544 ms,
+// 8 grids of sides 1024-4096 1.09 against 1.22 ms, 64 grids of 32-2048 1.07
+// against 1.19 ms, and 252 grids of 32-2048 (1 GB per sweep) 4.27 against
+// 3.98 ms.
+constexpr int64_t kOneLaunchMaxSweepBytes = (int64_t)512 << 20;
 constexpr int kMaxStepSweeps = 128;                 // sweeps of one request in one serving step
+
 
 // Checks one task against the rules of its standalone call.
 hx_status validate_task(const hx_task &t, int idx, const char *who);
@@ -86,12 +91,12 @@ inline uint32_t inst_runs(const BInst &I) {
 }
 inline uint32_t inst_ctas(const BInst &I) { return I.kind == kKindHist ? (uint32_t)I.t_count : 0u; }
 
-// Work items of one launch in the order workers take them: every instance's
-// sweep-0 work (and all map and histogram work), then the second sweep of
-// each instance that runs several, and so on.  Entry k of a launch's pair list
-// names (instance, sweep offset) as instance | offset << 24; the run prefix
-// then has one entry per pair plus a total.  A launch whose stencils run one
-// sweep each has no pair list: entry k is instance k.
+// Work items of one launch in the order workers take them, listed as
+// (instance, sweep offset) pairs: a pair's work waits only for pairs listed
+// before it (an instance's sweep s - 1 comes before its sweep s).  Entry k of
+// a launch's pair list names (instance, sweep offset) as instance | offset
+// << 24; the run prefix then has one entry per pair plus a total.  A launch
+// whose stencils run one sweep each has no pair list: entry k is instance k.
 inline uint32_t make_pair(uint32_t inst, uint32_t phase) { return inst | (phase << 24); }
 constexpr uint32_t kMaxPairInstances = 1u << 24;
 

@@ -32,10 +32,12 @@ double now_s() {
 
 // Per-request device workspace, kept from admission to completion so that a
 // request's work can be split over several steps: tile partials, histogram
-// or residual accumulator.
+// or residual accumulator, and the block progress words of a stencil request
+// that runs several sweeps in one step (zero between uses).
 constexpr size_t kWsPartials = kMrMaxTiles;
 constexpr size_t kWsAccWords = kHiBins;
-constexpr size_t kWsBytes = ((kWsPartials * sizeof(float2) + kWsAccWords * 4) + 255) & ~(size_t)255;
+constexpr size_t kWsProgWords = 4096;
+constexpr size_t kWsBytes = ((kWsPartials * sizeof(float2) + (kWsAccWords + kWsProgWords) * 4) + 255) & ~(size_t)255;
 // Continuous mode: at most this many fresh requests run as standalone calls
 // instead of a batched step (hx_server_config.direct_max = 0).
 constexpr int kDefaultDirectMax = 4;
@@ -43,8 +45,7 @@ constexpr int kDefaultDirectMax = 4;
 // many bytes runs as its standalone call (hx_server_config.direct_sweep_bytes
 // = 0).  A 16 MiB sweep (a 1448 x 1448 grid) fills the device on its own.
 constexpr int64_t kDefaultDirectSweepBytes = (int64_t)16 << 20;
-static_assert(2 * kMaxStepSweeps - 1 <= (int)kWsAccWords,
-              "a request's workspace holds one maximum per sweep and one arrival count per sweep but the last");
+static_assert(kMaxStepSweeps <= (int)kWsAccWords, "a request's workspace holds one maximum per sweep");
 
 struct Req {
     uint64_t id = 0;
@@ -184,7 +185,7 @@ void fail_requests_locked(hx_server *s, std::vector<Req *> &rs, hx_status st) {
             // accumulators (ordered after its steps already on the stream)
             // before the slot serves another request
             char *w = s->ws_pool + (size_t)r->ws * kWsBytes;
-            cudaMemsetAsync(w + kWsPartials * sizeof(float2), 0, kWsAccWords * 4, s->stream);
+            cudaMemsetAsync(w + kWsPartials * sizeof(float2), 0, (kWsAccWords + kWsProgWords) * 4, s->stream);
             s->free_ws.push_back(r->ws);
         }
         r->ws = -1;
@@ -326,7 +327,7 @@ bool issue_step_locked(hx_server *s) {
         I.sweep0 = I.kind == kKindStencil ? r->sweep : 0;
         int sweeps = 1;
         if (I.kind == kKindStencil && r->issued == 0 && s->cfg.max_step_sweeps > 1 &&
-            8 * (int64_t)I.nx * I.ny < multi_below) {
+            8 * (int64_t)I.nx * I.ny < multi_below && I.tiles <= (int64_t)kWsProgWords) {
             sweeps = std::min({I.iters - r->sweep, s->cfg.max_step_sweeps, kMaxStepSweeps});
             if (extra + (size_t)(sweeps - 1) > max_extra) sweeps = 1;
         }
@@ -334,7 +335,7 @@ bool issue_step_locked(hx_server *s) {
             I.t_first = 0;
             I.t_count = I.tiles;
             I.n_sweeps = sweeps;
-            I.done = I.acc + sweeps;
+            I.done = I.acc + kWsAccWords;   // the workspace's progress words
         } else {
             const int64_t q = std::max<int64_t>(1, (int64_t)quantum / tile_bytes(I));
             I.t_first = r->issued;

@@ -148,7 +148,7 @@ def test_standard_batch_20_sweeps_in_one_launch(gpu, ctx):
     # every map->reduce instance and a sample of 24 stencil instances (every
     # size decile) against the oracle
     insts = [Inst(s) for s in workloads.batch_mix(iters=20)]
-    b = gpu.hx_batch_plan(ctx, [i.task(gpu) for i in insts])
+    b = gpu.hx_batch_plan(ctx, [i.task(gpu) for i in insts], rounds=False)
     assert b.rounds == 1
     b.launch()
     torch.cuda.synchronize()
@@ -213,7 +213,7 @@ def test_multi_sweep_relaunch_and_graph_replay(gpu, ctx):
              {"kind": "map_reduce", "n": 500_001, "a": 1.5, "seed": 33},
              {"kind": "stencil", "nx": 1025, "ny": 130, "iters": 2, "seed": 34}]
     insts = [Inst(s) for s in specs]
-    b = gpu.hx_batch_plan(ctx, [i.task(gpu) for i in insts], rounds=False)   # one launch (3 multi-sweep tasks)
+    b = gpu.hx_batch_plan(ctx, [i.task(gpu) for i in insts], rounds=False)   # one launch
     assert b.rounds == 1
     b.launch()
     torch.cuda.synchronize()
@@ -272,21 +272,26 @@ def test_multi_sweep_wait_times_out_and_reports(gpu, ctx):
 
 
 def test_default_schedule(gpu, ctx):
-    # one launch when at least 4 stencil tasks have several sweeps, else
-    # rounds; either way the same bits
-    few = [Inst({"kind": "stencil", "nx": 70, "ny": 50, "iters": 3, "seed": 40 + k}) for k in range(3)]
-    many = [Inst({"kind": "stencil", "nx": 70, "ny": 50, "iters": 3, "seed": 40 + k}) for k in range(4)]
-    for insts, rounds in ((few, 3), (many, 1)):
-        b = gpu.hx_batch_plan(ctx, [i.task(gpu) for i in insts])
-        assert b.rounds == rounds
-        b.launch()
-        torch.cuda.synchronize()
-        b.status()
-        for inst in insts:
-            r = inst.result()
-            _same(r, inst.standalone(gpu, ctx))
-            inst.check_oracle(r)
-        b.close()
+    # one launch when the multi-sweep stencils move at most 512 MiB per
+    # sweep (8 bytes per point), else rounds; either way the same bits
+    small = [Inst({"kind": "stencil", "nx": 70, "ny": 50, "iters": 3, "seed": 40 + k}) for k in range(3)]
+    b = gpu.hx_batch_plan(ctx, [i.task(gpu) for i in small])
+    assert b.rounds == 1
+    b.launch()
+    torch.cuda.synchronize()
+    b.status()
+    for inst in small:
+        r = inst.result()
+        _same(r, inst.standalone(gpu, ctx))
+        inst.check_oracle(r)
+    b.close()
+    # 8192 x 8193 points: 537 MB per sweep (planned only)
+    big = Inst({"kind": "stencil", "nx": 8192, "ny": 8193, "iters": 2, "seed": 47})
+    b = gpu.hx_batch_plan(ctx, [big.task(gpu)] + [i.task(gpu) for i in small])
+    assert b.rounds == 3
+    b.close()
+    del big
+    torch.cuda.empty_cache()
     # both schedule flags at once, or an unknown flag, are rejected
     h = ctypes.c_void_p()
     for flags in (gpu.HX_BATCH_ROUNDS | gpu.HX_BATCH_ONE_LAUNCH, 4):
