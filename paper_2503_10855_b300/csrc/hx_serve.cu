@@ -107,7 +107,7 @@ struct hx_server {
     uint64_t next_id = 1;
     size_t used = 0;
     int inflight = 0;
-    bool issuing = false;                     // per-launch mode: launches in progress without the lock
+    bool issuing = false;                     // standalone launches in progress without the lock
     bool stop = false;
     hx_server_stats stats{};
     double created = 0.0;                     // timeline origin (steady clock)
@@ -230,13 +230,20 @@ cudaEvent_t take_event(hx_server *s) {
 // standalone call on the server's stream, with its own completion event --
 // no descriptor upload, no batched launch and final combine.  Results are the
 // same bits either way.
-void issue_direct_locked(hx_server *s, const std::vector<Req *> &rs) {
+void issue_direct_locked(hx_server *s, const std::vector<Req *> &rs, std::unique_lock<std::mutex> &lk) {
+    // The launches run with the lock released (a stencil request is 20 or
+    // more launches): the completion thread and submitters are not held up.
+    // The requests are no longer in `active`, and only this thread issues.
+    s->issuing = true;
     for (Req *r : rs) {
         r->issued_all = true;
         s->stats.launches += 1;
         cudaEvent_t ev = take_event(s);
-        hx_status st = ev ? launch_standalone(s, r->task) : HX_ERR_CUDA;
+        const hx_task t = r->task;
+        lk.unlock();
+        hx_status st = ev ? launch_standalone(s, t) : HX_ERR_CUDA;
         if (st == HX_OK && cudaEventRecord(ev, s->stream) != cudaSuccess) st = HX_ERR_CUDA;
+        lk.lock();
         std::vector<Req *> one{r};
         if (st != HX_OK) {
             if (ev) s->free_events.push_back(ev);
@@ -248,8 +255,10 @@ void issue_direct_locked(hx_server *s, const std::vector<Req *> &rs) {
         step.finishing = one;
         step.members = one;
         push_step_locked(s, std::move(step), 1);
+        s->cv_compl.notify_one();
     }
-    s->cv_compl.notify_one();
+    s->issuing = false;
+    s->cv_compl.notify_all();
 }
 
 bool fresh(const Req *r) { return r->issued == 0 && r->sweep == 0 && !r->issued_all; }
@@ -263,35 +272,38 @@ bool fresh(const Req *r) { return r->issued == 0 && r->sweep == 0 && !r->issued_
 // persistent launch runs them one after another (bounded waits between an
 // instance's sweeps, see hx_batch.cuh), so a small stencil request needs one
 // step instead of one per sweep.
-bool issue_step_locked(hx_server *s) {
+bool issue_step_locked(hx_server *s, std::unique_lock<std::mutex> &lk) {
     // low load: when at most cfg.direct_max requests wait and none has
     // started, each runs as its standalone call (the shortest path for a
     // request that has the device nearly to itself)
     if ((int)s->active.size() <= s->cfg.direct_max && std::all_of(s->active.begin(), s->active.end(), fresh)) {
         std::vector<Req *> all;
         all.swap(s->active);
-        issue_direct_locked(s, all);
+        issue_direct_locked(s, all, lk);
         return true;
     }
     // a stencil request with large sweeps runs as its standalone call at any
     // load: in batched steps it would advance one sweep per step
+    bool issued_direct = false;
     if (s->cfg.direct_sweep_bytes > 0) {
-        std::vector<Req *> big;
+        std::vector<Req *> big, rest;
         for (Req *r : s->active)
-            if (r->task.kind == HX_TASK_STENCIL2D && fresh(r) && r->inst.tiles > 0 && r->task.u.st.iters > 0 &&
-                8 * (int64_t)r->task.u.st.nx * r->task.u.st.ny >= s->cfg.direct_sweep_bytes)
-                big.push_back(r);
+            (r->task.kind == HX_TASK_STENCIL2D && fresh(r) && r->inst.tiles > 0 && r->task.u.st.iters > 0 &&
+                     8 * (int64_t)r->task.u.st.nx * r->task.u.st.ny >= s->cfg.direct_sweep_bytes
+                 ? big
+                 : rest)
+                .push_back(r);
         if (!big.empty()) {
-            issue_direct_locked(s, big);
-            s->active.erase(std::remove_if(s->active.begin(), s->active.end(), [](Req *r) { return r->issued_all; }),
-                            s->active.end());
+            s->active.swap(rest);
+            issue_direct_locked(s, big, lk);
+            issued_direct = true;
             if (s->active.empty()) return true;
         }
     }
     int slot = -1;
     for (size_t i = 0; i < s->slots.size(); ++i)
         if (!s->slots[i].busy) { slot = (int)i; break; }
-    if (slot < 0 || (int)s->steps.size() >= s->cfg.max_steps_in_flight) return false;
+    if (slot < 0 || (int)s->steps.size() >= s->cfg.max_steps_in_flight) return issued_direct;
     Slot &sl = s->slots[slot];
     // Staging layout, uploaded with one copy: descriptors, then the CTA
     // prefix (n + 1 entries), the run prefix (one entry per pair + 1) and,
@@ -366,7 +378,7 @@ bool issue_step_locked(hx_server *s) {
             step.finishing.push_back(r);
         }
     }
-    if (n == 0 && step.finishing.empty()) return false;
+    if (n == 0 && step.finishing.empty()) return issued_direct;
     cpv.push_back((uint32_t)c);
     // Several sweeps: runs as short as keep about two per resident warp in a
     // sweep (at most kMultiSweepRun blocks), as the batch planner does; the
@@ -482,7 +494,7 @@ void scheduler_main(hx_server *s) {
         if (s->stop && s->queue.empty() && s->active.empty()) break;
         bool issued = false;
         if (!s->active.empty())
-            issued = s->cfg.mode == HX_SERVE_CONTINUOUS ? issue_step_locked(s) : issue_per_launch(s, lk);
+            issued = s->cfg.mode == HX_SERVE_CONTINUOUS ? issue_step_locked(s, lk) : issue_per_launch(s, lk);
         if (!issued) s->cv_sched.wait_for(lk, std::chrono::microseconds(200));
     }
     s->cv_compl.notify_all();
