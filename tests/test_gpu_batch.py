@@ -206,8 +206,7 @@ def _reset(insts):
 
 def test_multi_sweep_relaunch_and_graph_replay(gpu, ctx):
     # the block progress words and residual accumulators are clean after a
-    # launch:
-    # a second launch and CUDA-graph replays of the same plan give the same
+    # launch: a second launch and CUDA-graph replays of the same plan give the same
     # bits as the first launch (each from the same initial grids)
     specs = [{"kind": "stencil", "nx": 300, "ny": 200, "iters": 7, "seed": 31},
              {"kind": "stencil", "nx": 64, "ny": 64, "iters": 20, "seed": 32},
