@@ -198,6 +198,30 @@ def test_mixed_batch_multi_sweep(gpu, ctx, offset, rounds):
     b.close()
 
 
+@pytest.mark.parametrize("shape,iters", [((1000, 1000), 12), ((601, 997), 9), ((64, 4100), 6), ((3000, 40), 5)])
+def test_one_launch_wavefront_shapes(gpu, ctx, shape, iters):
+    # one grid whose sweeps run in one launch, each block waiting only for
+    # itself and its north / south / west / east blocks in the previous
+    # sweep: several block columns (west / east dependencies), the element
+    # path (nx not a multiple of 4), a wide short grid and a tall narrow one;
+    # bit-identical to rounds and to the standalone call, and the oracle
+    ny, nx = shape
+    spec = {"kind": "stencil", "nx": nx, "ny": ny, "iters": iters, "seed": 70 + nx % 13}
+    got = []
+    for rounds in (False, True):
+        inst = Inst(spec)
+        b = gpu.hx_batch_plan(ctx, [inst.task(gpu)], rounds=rounds)
+        assert b.rounds == (iters if rounds else 1)
+        b.launch()
+        torch.cuda.synchronize()
+        b.status()
+        got.append(inst.result())
+        b.close()
+    _same(got[0], got[1])
+    _same(got[0], inst.standalone(gpu, ctx))
+    inst.check_oracle(got[0])
+
+
 def _reset(insts):
     for inst in insts:
         if inst.spec["kind"] == "stencil":
