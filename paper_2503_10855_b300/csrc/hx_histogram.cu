@@ -18,7 +18,7 @@ __global__ void __launch_bounds__(THREADS)
 histogram_kernel(const uint8_t *__restrict__ v, int64_t n, int head, int64_t nvec, int tail,
                  WsSlot *ws, uint32_t *d_bins, uint32_t *d_scan) {
     extern __shared__ __align__(16) unsigned int sh[];   // kHiSmemBytes of counters
-    __shared__ unsigned int wtot[THREADS / kWarp];
+    __shared__ unsigned int wtot[kHiBins / kWarp];
     __shared__ bool is_last;
     static_assert(THREADS >= kHiBins, "the finish maps one thread to one bin");
     hist_zero(sh);
@@ -37,24 +37,23 @@ histogram_kernel(const uint8_t *__restrict__ v, int64_t n, int head, int64_t nve
     __syncthreads();
     if (threadIdx.x == 0) is_last = atomicAdd(&ws->hi_ticket, 1u) == gridDim.x - 1;
     __syncthreads();
-    if (!is_last) return;
+    if (!is_last || threadIdx.x >= kHiBins) return;
     __threadfence();
-    // Final: add the copies that CTAs used (reading them from L2, where the
-    // atomics were performed) and zero them, publish the bins, exclusive
-    // scan, reset the ticket.
+    // Final, one thread per bin (the first kHiBins threads): add the copies
+    // that CTAs used (reading them from L2, where the atomics were performed)
+    // and zero them, publish the bins, exclusive scan over the kHiBins / 32
+    // warp totals, reset the ticket.
+    const int used = gridDim.x < kHiReplicas ? (int)gridDim.x : kHiReplicas;
+    unsigned int part[kHiReplicas];
+#pragma unroll
+    for (int r = 0; r < kHiReplicas; ++r) part[r] = r < used ? __ldcg(&ws->hi_bins[r][threadIdx.x]) : 0u;
     unsigned int c = 0u;
-    if (threadIdx.x < kHiBins) {
-        const int used = gridDim.x < kHiReplicas ? (int)gridDim.x : kHiReplicas;
-        unsigned int part[kHiReplicas];
 #pragma unroll
-        for (int r = 0; r < kHiReplicas; ++r) part[r] = r < used ? __ldcg(&ws->hi_bins[r][threadIdx.x]) : 0u;
-#pragma unroll
-        for (int r = 0; r < kHiReplicas; ++r) {
-            c += part[r];
-            if (r < used) ws->hi_bins[r][threadIdx.x] = 0u;
-        }
-        d_bins[threadIdx.x] = c;
+    for (int r = 0; r < kHiReplicas; ++r) {
+        c += part[r];
+        if (r < used) ws->hi_bins[r][threadIdx.x] = 0u;
     }
+    d_bins[threadIdx.x] = c;
     unsigned int incl = c;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
@@ -62,10 +61,13 @@ histogram_kernel(const uint8_t *__restrict__ v, int64_t n, int head, int64_t nve
         if (lane >= off) incl += t;
     }
     if (lane == 31) wtot[warp] = incl;
-    __syncthreads();
+    // a barrier of the kHiBins threads still running (named barrier 1)
+    asm volatile("bar.sync 1, %0;" ::"n"(kHiBins) : "memory");
     unsigned int before = 0u;
-    for (int w = 0; w < warp; ++w) before += wtot[w];
-    if (d_scan && threadIdx.x < kHiBins) d_scan[threadIdx.x] = before + incl - c;
+#pragma unroll
+    for (int w = 0; w < kHiBins / kWarp - 1; ++w)
+        if (w < warp) before += wtot[w];
+    if (d_scan) d_scan[threadIdx.x] = before + incl - c;
     if (threadIdx.x == 0) ws->hi_ticket = 0u;
 }
 

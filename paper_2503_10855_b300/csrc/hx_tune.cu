@@ -39,22 +39,31 @@ bool allowed_vecs(int v) { return v >= 4 && v <= 1024 && v % kMrUnroll == 0; }
 bool allowed_threads(int t) { return t == 256 || t == 512 || t == 1024; }
 bool allowed_rows(int r) { return r == 4 || r == 8 || r == 16; }
 
-// Median of `reps` timings (ms) of fn(rep) on `stream`, after one warm-up.
+// Calls per timing for a size class of 2^c elements or bytes: 16 up to 2^22,
+// fewer above, one from 2^26 (where a call streams for over 10 us).
+int burst_for(int c) { return c <= 22 ? 16 : (c <= 24 ? 4 : 1); }
+
+// Median of `reps` timings (ms per call) on `stream`, after one warm-up call.
+// A timing covers `burst` back-to-back calls fn(k), k = 1, 2, ... over the
+// whole measurement: a call of a small size class then pays the costs it
+// pays in a stream of calls (the previous call's tail, its own launch and
+// combine), not the host's launch latency of a lone call, and the median of
+// a burst is steadier than that of one microsecond-long call.
 template <class Fn>
-float time_median(cudaStream_t stream, int reps, Fn fn, hx_status *st) {
+float time_median(cudaStream_t stream, int reps, Fn fn, hx_status *st, int burst = 1) {
     std::vector<float> ms;
     cudaEvent_t a, b;
     cudaEventCreate(&a);
     cudaEventCreate(&b);
     *st = fn(0);
-    for (int r = 1; r <= reps && *st == HX_OK; ++r) {
+    for (int r = 0; r < reps && *st == HX_OK; ++r) {
         cudaEventRecord(a, stream);
-        *st = fn(r);
+        for (int j = 0; j < burst && *st == HX_OK; ++j) *st = fn(1 + r * burst + j);
         cudaEventRecord(b, stream);
         cudaEventSynchronize(b);
         float t = 0.0f;
         cudaEventElapsedTime(&t, a, b);
-        ms.push_back(t);
+        ms.push_back(t / burst);
     }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
@@ -231,7 +240,7 @@ hx_status hx_autotune(hx_ctx *ctx, int32_t max_log2, hx_stream_t stream) {
             const float ms = time_median(s, reps, [&](int r) {
                 float *base = pool + (r % regions) * stride;
                 return hx_map_reduce(ctx, base, base + n, base + 2 * n, 1.5f, n, res, nullptr, stream);
-            }, &st);
+            }, &st, burst_for(c));
             if (st == HX_OK && ms < best) { best = ms; best_v = v; }
         }
         t.map_vecs[c] = best_v;
@@ -267,7 +276,7 @@ hx_status hx_autotune(hx_ctx *ctx, int32_t max_log2, hx_stream_t stream) {
             const float ms = time_median(s, reps, [&](int r) {
                 nest.in[0] = pool + (r % (as_map ? regions - 1 : regions)) * stride;
                 return hx_fork_reduce(ctx, &nest, stream);
-            }, &st);
+            }, &st, burst_for(c));
             if (st == HX_OK && ms < best) { best = ms; best_le = le; }
         }
         t.nest_lane_elems[c] = best_le;
@@ -290,7 +299,7 @@ hx_status hx_autotune(hx_ctx *ctx, int32_t max_log2, hx_stream_t stream) {
                 const uint8_t *base = reinterpret_cast<const uint8_t *>(pool) + (r % regions) * stride;
                 return hx_histogram(ctx, base, n, reinterpret_cast<uint32_t *>(res),
                                     reinterpret_cast<uint32_t *>(res) + 256, stream);
-            }, &st);
+            }, &st, burst_for(c));
             if (st == HX_OK && ms < best) { best = ms; best_t = w; }
         }
         t.hist_threads[c] = best_t;
