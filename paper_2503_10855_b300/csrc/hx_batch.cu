@@ -239,23 +239,39 @@ batch_kernel(const BInst *__restrict__ insts, unsigned int n_inst, const uint32_
 // in a launch without a pair list, entries i and i + 1 of the run prefix; a
 // launch with a pair list (run_prefix NULL here) runs every instance's whole
 // slice.
+//
+// The descriptors and prefixes are written by the plan's synchronous copies
+// and never by a kernel, so each CTA reads its instance's descriptor (into
+// shared memory) and work count before waiting for the batched grid: only
+// the loads of what the grid wrote (partials, accumulators) remain on the
+// path after it.
 __global__ void __launch_bounds__(kBatchThreads)
 batch_final_kernel(const BInst *__restrict__ insts, unsigned int n_inst, const uint32_t *__restrict__ cta_prefix,
                    const uint32_t *__restrict__ run_prefix, int round, unsigned int *ctrl) {
     __shared__ ff red[kMrFoldLanes];
+    __shared__ BInst sI;
+    __shared__ unsigned int s_work;
+    static_assert(sizeof(BInst) % 8 == 0 && sizeof(BInst) / 8 <= kBatchThreads, "descriptor copy");
+    const int lane = threadIdx.x & 31;
+    const unsigned int i = blockIdx.x;   // one CTA per instance
+    if (i < n_inst) {
+        if (threadIdx.x < sizeof(BInst) / 8)
+            reinterpret_cast<unsigned long long *>(&sI)[threadIdx.x] =
+                __ldg(reinterpret_cast<const unsigned long long *>(insts + i) + threadIdx.x);
+        // whether the instance had work in this launch: its CTA chunks and
+        // its first-pass runs (a pair-ordered launch, run_prefix NULL, gives
+        // every instance its whole slice; that case reads sI below)
+        if (threadIdx.x == 0)
+            s_work = (__ldg(cta_prefix + i + 1) - __ldg(cta_prefix + i)) +
+                     (run_prefix ? __ldg(run_prefix + i + 1) - __ldg(run_prefix + i) : 0u);
+    }
+    __syncthreads();
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;");
     if (blockIdx.x == 0 && threadIdx.x == 0) ctrl[0] = 0u;
-    const int lane = threadIdx.x & 31;
-    const unsigned int i = blockIdx.x;   // one CTA per instance
     if (i >= n_inst) return;
-    const BInst &I = insts[i];
-    // whether the instance had work in this launch: its CTA chunks and its
-    // first-pass runs (a pair-ordered launch, run_prefix NULL, gives every
-    // instance its whole slice)
-    const unsigned int work = (__ldg(cta_prefix + i + 1) - __ldg(cta_prefix + i)) +
-                              (run_prefix ? __ldg(run_prefix + i + 1) - __ldg(run_prefix + i)
-                                          : (I.t_count > 0 && I.kind != kKindHist ? 1u : 0u));
+    const BInst &I = sI;
+    const unsigned int work = s_work + (run_prefix ? 0u : (I.t_count > 0 && I.kind != kKindHist ? 1u : 0u));
     if (work == 0 || I.t_first + I.t_count != I.tiles) return;
     if (I.kind == kKindStencil && I.n_sweeps > 1)   // progress words back to zero
         for (int64_t k = threadIdx.x; k < I.tiles; k += blockDim.x) I.done[k] = 0u;
