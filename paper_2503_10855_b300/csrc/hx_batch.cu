@@ -50,6 +50,26 @@ __device__ __forceinline__ void batch_hist_item(const BInst &I, int64_t tile, un
     __syncthreads();
 }
 
+// L2 prefetch of the rows of a stencil warp block that the previous block of
+// its run did not load, rows r_begin + 1 .. r_begin + R (clamped): each lane
+// the line of its first column.  Issued one block ahead, it keeps a second
+// block's DRAM requests in flight without holding registers, and the block's
+// own loads then find their rows in L2.  (Prefetching the halo columns too,
+// or one bulk prefetch per row, measured slower.)  A prefetch only moves
+// lines into L2, the point of coherence, so it is safe for grids that the
+// launch writes, and it changes no result.
+template <int R>
+__device__ __forceinline__ void prefetch_stencil_block(const float *src, int nx, int ny, int c_begin, int r_begin,
+                                                       int lane) {
+    const int c0 = c_begin + lane * 4;
+    if (c0 >= nx) return;
+#pragma unroll
+    for (int k = 1; k <= R; ++k) {
+        const int r = r_begin + k < ny ? r_begin + k : ny - 1;
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(src + (size_t)r * nx + c0));
+    }
+}
+
 // Index i of the instance with prefix[i] <= j < prefix[i + 1] (instances
 // with no items have equal neighbours and are never returned).
 __device__ __forceinline__ unsigned int find_instance(const uint32_t *__restrict__ prefix, unsigned int n_inst,
@@ -192,7 +212,7 @@ batch_kernel(const BInst *__restrict__ insts, unsigned int n_inst, const uint32_
             float *out = static_cast<float *>(I.o0);
             for (int64_t k = 0; k < cnt; ++k) {
                 const int64_t tile = first + k;
-                const ff part = mr_tile(x, y, out, I.a, I.plan, tile, I.vec != 0, lane);
+                const ff part = mr_tile<2, 2>(x, y, out, I.a, I.plan, tile, I.vec != 0, lane);
                 if (lane == 0) st_keep2(I.partials + tile, make_float2(part.hi, part.lo));
             }
         } else {
@@ -207,6 +227,11 @@ batch_kernel(const BInst *__restrict__ insts, unsigned int n_inst, const uint32_
                 const int wy = (int)(tile % (unsigned int)I.tiles_y), wx = (int)(tile / (unsigned int)I.tiles_y);
                 const int c_begin = wx * 128, r_begin = wy * kBatchStRows;
                 if (!HX_CHECK(c_begin < I.nx && r_begin < I.ny, kChkBatchStencil, c_begin, r_begin)) continue;
+                if (k + 1 < cnt) {   // the run's next block, one block ahead
+                    const unsigned int t1 = tile + 1u;
+                    const int wy1 = (int)(t1 % (unsigned int)I.tiles_y), wx1 = (int)(t1 / (unsigned int)I.tiles_y);
+                    prefetch_stencil_block<kBatchStRows>(src, I.nx, I.ny, wx1 * 128, wy1 * kBatchStRows, lane);
+                }
                 if constexpr (MULTI)
                     m = fmaxf(m, I.vec ? stencil_block_vec<kBatchStRows, true>(src, dst, I.nx, I.ny, c_begin, r_begin)
                                        : stencil_block_strided<kBatchStRows>(src, dst, I.nx, I.ny, c_begin, r_begin));

@@ -267,7 +267,12 @@ __device__ __forceinline__ double ff_to_double(ff v) { return (double)v.hi + (do
 // aligned full-tile path.  The fold order does not depend on it, so the
 // standalone kernel (3 groups, 120 registers) and the batched kernel (2
 // groups, inside its 128-register budget) give the same bits.
-template <int GROUPS = 2>
+//
+// PF > 0 (whole-warp calls, nthreads == 32): each load of a group also
+// prefetches into L2 the group PF groups further on, lanes 0..15 one line
+// each of its 4 vectors x 512 bytes per operand, so that later groups' loads
+// find their lines in L2.  A prefetch changes no result.
+template <int GROUPS = 2, int PF = 0>
 __device__ __forceinline__ ff mr_thread_partial(const float *__restrict__ x,
                                                    const float *__restrict__ y,
                                                    float *__restrict__ out, float a,
@@ -286,6 +291,14 @@ __device__ __forceinline__ ff mr_thread_partial(const float *__restrict__ x,
         float4 *o4 = reinterpret_cast<float4 *>(out + base);
         float4 xa[kMrUnroll], ya[kMrUnroll], xb[kMrUnroll], yb[kMrUnroll];
         auto load = [&](float4 *xv, float4 *yv, int u0) {
+            if constexpr (PF > 0) {
+                const int up = u0 + PF * kMrUnroll + (t >> 2);
+                if (t < 4 * kMrUnroll && up < p.vecs_per_thread) {
+                    const int64_t vp = (int64_t)up * kWarp + (t & 3) * 8;
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(x4 + vp));
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(y4 + vp));
+                }
+            }
 #pragma unroll
             for (int k = 0; k < kMrUnroll; ++k) {
                 const int64_t vi = (int64_t)(u0 + k) * nthreads + t;
@@ -363,11 +376,11 @@ __device__ __forceinline__ ff mr_thread_partial(const float *__restrict__ x,
 
 // Partial of one map->reduce tile, computed by one whole warp (lane = its
 // lane index); the same value in every lane.
-template <int GROUPS = 2>
+template <int GROUPS = 2, int PF = 0>
 __device__ __forceinline__ ff mr_tile(const float *__restrict__ x, const float *__restrict__ y,
                                       float *__restrict__ out, float a, const MrPlan &p, int64_t tile,
                                       bool aligned, int lane) {
-    return warp_sum(mr_thread_partial<GROUPS>(x, y, out, a, p, tile, aligned, lane, kWarp));
+    return warp_sum(mr_thread_partial<GROUPS, PF>(x, y, out, a, p, tile, aligned, lane, kWarp));
 }
 
 // Final combine of `tiles` tile partials in one fixed order, the same
