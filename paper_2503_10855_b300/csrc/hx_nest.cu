@@ -51,6 +51,13 @@ constexpr int kNestBlock = 256;
 // VEC and the HAS_* flags are #defined by the generated header in front of
 // it; the generated part also supplies struct Seg, seg_setup(), struct Buf,
 // load_group(), map_elem() and map_at().
+// L2 prefetch in the warp tree (no registers held): a group narrower than a
+// warp prefetches the segment after the one it has in flight.  Measured on
+// B300, max over 2^24 rows of 8: 0.90 -> 0.97 of HBM.  Whole-warp groups do
+// not prefetch: two load groups beyond each load took a permuted 3-D reduce
+// from 0.94 to 0.82 and a 2^28 sum from 1.01 to 0.99.
+constexpr int kNestPrefetch = 1;
+
 const char *kPrelude = R"CUDA(
 typedef long long i64;
 typedef unsigned long long u64;
@@ -103,6 +110,7 @@ __device__ __forceinline__ float hx_minnum(float a, float b) {
 __device__ __forceinline__ float hx_maxnum(float a, float b) {
     return isnan(a) ? b : (isnan(b) ? a : (b > a ? b : a));
 }
+__device__ __forceinline__ void prefetch_l2(const float *a) { asm volatile("prefetch.global.L2 [%0];" ::"l"(a)); }
 __device__ __forceinline__ float hx_comp(const float4 &v, int q) {
     return q == 0 ? v.x : (q == 1 ? v.y : (q == 2 ? v.z : v.w));
 }
@@ -450,6 +458,13 @@ extern "C" __global__ void __launch_bounds__(256) hx_nest_kernel(const NestParam
         if (i1 < p.n_items) {
             seg_whole(p, gb, i1);
             load_group(p, gb, bb, gl);
+#if HX_NEST_PF
+            if (i1 + stride < p.n_items) {   // a third segment's lines into L2
+                Seg gc;
+                seg_whole(p, gc, i1 + stride);
+                prefetch_group(p, gc, gl);
+            }
+#endif
         }
         {
             Acc acc = acc_init();
@@ -463,6 +478,13 @@ extern "C" __global__ void __launch_bounds__(256) hx_nest_kernel(const NestParam
         if (i2 < p.n_items) {
             seg_whole(p, ga, i2);
             load_group(p, ga, ba, gl);
+#if HX_NEST_PF
+            if (i2 + stride < p.n_items) {
+                Seg gc;
+                seg_whole(p, gc, i2 + stride);
+                prefetch_group(p, gc, gl);
+            }
+#endif
         }
         {
             Acc acc = acc_init();
@@ -793,6 +815,7 @@ std::string generate(const hx_nest *n, const Shape &sh) {
     src += fmt("#define MONOID %d\n#define TREE %d\n#define G %d\n#define U %d\n#define VEC %d\n", sh.monoid, sh.tree,
                sh.G, sh.U, sh.vec ? 1 : 0);
     src += fmt("#define HAS_OUT %d\n#define HAS_RES64 %d\n", sh.has_out ? 1 : 0, sh.has_res64 ? 1 : 0);
+    src += fmt("#define HX_NEST_PF %d\n", kNestPrefetch);
     src += fmt("#define HX_NEST_CAP %d\n#define HX_NEST_CAP2 %d\n#define HX_NEST_TICK %d\n#define HX_NEST_TICK2 %d\n",
                hx::kNestCap, hx::kNestCap2, hx::kNestTick, hx::kNestTick2);
 #ifdef HX_DEBUG_CHECKS
@@ -855,6 +878,24 @@ std::string generate(const hx_nest *n, const Shape &sh) {
             for (int q = 1; q < 4; ++q)
                 src += fmt("            b.x%d[j].%c = (r + %d < g.r_end) ? __ldg(g.b%d + off%d(p, r + %d)) : 0.0f;\n", k,
                            comp[q], q, k, k, q);
+        }
+    }
+    src += "        }\n    }\n}\n";
+    // the same slots' lines prefetched into L2 (no registers held): a vector
+    // slot is one 16-byte load, an element slot up to four loads
+    src += "__device__ __forceinline__ void prefetch_group(const NestParams &p, const Seg &g, i64 t0) {\n"
+           "#pragma unroll\n    for (int j = 0; j < U; ++j) {\n        const i64 t = t0 + (i64)j * G;\n"
+           "        if (t < g.nslot) {\n            const i64 r = g.r_begin + 4 * t;\n";
+    for (int k = 0; k < HX_NEST_MAX_INPUTS; ++k) {
+        if (!sh.used[k]) continue;
+        if (sh.vec) {
+            if (sh.linear[k]) src += fmt("            prefetch_l2(g.b%d + r);\n", k);
+            else src += fmt("            prefetch_l2(g.b%d + off%d(p, r));\n", k, k);
+        } else {
+            src += fmt("            prefetch_l2(g.b%d + off%d(p, r));\n", k, k);
+            if (!sh.linear[k])
+                for (int q = 1; q < 4; ++q)
+                    src += fmt("            if (r + %d < g.r_end) prefetch_l2(g.b%d + off%d(p, r + %d));\n", q, k, k, q);
         }
     }
     src += "        }\n    }\n}\n";
