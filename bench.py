@@ -916,7 +916,7 @@ def bench_srad(hx, ctx, dev, peak, ny=8192, nx=8192, iters=10, reps=3):
             "fused_mpix_per_s": round(npx / (per_it["fused"] * 1e-3) / 1e6, 1),
             "fused_algorithmic_GB/s": round(gbs, 1), "fused_frac_of_measured_hbm": round(gbs / peak, 4),
             "fused_dram_bytes_per_iteration": measured_traffic().get("srad_fused"),
-            "bound": "issue (two IEEE fp32 divisions per pixel in the coefficient)",
+            "bound": "issue (an IEEE fp32 division per pixel in the coefficient)",
             "launches_per_iteration": {"fused": 1, "unfused": 3}}
 
 

@@ -225,16 +225,20 @@ hx_status hx_histogram(hx_ctx *ctx, const uint8_t *v, int64_t n, uint32_t *d_bin
  *   qsq = (0.5*G2 - 0.0625*L*L) / ((1 + 0.25*L)^2),
  *   c = clamp(1 / (1 + (qsq - q0sq) / (q0sq*(1 + q0sq))), 0, 1),
  *   J' = Jc + (0.25*lambda) * ((c[i][j]*dN + c[i+1][j]*dS) + (c[i][j]*dW + c[i][j+1]*dE)),
- * in fp32 without contraction, with the coefficient's divisions regrouped
- * (r = 1/Jc, G2 = (sum of d^2 * r) * r, L = (sum of d) * r, den2 = den*den,
- * c = den2 / (den2 + (num - q0sq*den2) * iq), iq = 1/(q0sq*(1 + q0sq)) once
- * per iteration): algebraically the expression above, two divisions per
- * pixel instead of five, rounded differently.  After T iterations the image
- * is within T * 12 * 2^-24 (at most 1e-5) of its maximum from an fp64
- * evaluation of the expression above (lambda <= 1).  q0sq is formed in
- * double from float-float region sums (S1 = sum J, S2 = sum J^2 over rows
- * [r0, r1) x cols [c0, c1); mean = S1/N, var = S2/N - mean^2) and rounded
- * to fp32 once.
+ * in fp32 with the coefficient multiplied through by Jc^2 den^2, in which
+ * Jc^2 cancels: with S1 = (dN + dS) + (dW + dE), S2 = the sum of the d^2,
+ * E = Jc + 0.25*S1 (the mean of the four neighbours) and iq =
+ * 1/(q0sq*(1 + q0sq)) once per iteration,
+ *   c = clamp(E^2 / (E^2 + (0.5*S2 - 0.0625*S1^2 - q0sq*E^2) * iq), 0, 1),
+ * each a*b + c of it and of the update one fused multiply-add:
+ * algebraically the expression above, one division per pixel instead of
+ * five, rounded differently.  For an image with values in [m, M] (diffusion
+ * keeps every iterate there) and lambda <= 1, the result after T iterations
+ * is within T * (1 + 0.25*lambda*(132 + 24*M/m)) * 2^-24 (at most 1e-5) of
+ * M from an fp64 evaluation of the expression above, to first order.
+ * q0sq is formed in double from float-float region sums (R1 = sum J,
+ * R2 = sum J^2 over rows [r0, r1) x cols [c0, c1); mean = R1/N,
+ * var = R2/N - mean^2) and rounded to fp32 once.
  *
  *   J0, J1   device, ny x nx fp32 row-major; J0 holds the input image
  *            (nonzero intensities: the scheme divides by J).  Iterations

@@ -47,29 +47,37 @@ struct SradArgs {
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
 // Diffusion coefficient of a pixel from its value and its four neighbour
-// differences: the SRAD expression 1/(1 + (num/den^2 - q0sq)/(q0sq(1+q0sq)))
-// multiplied through by den^2, so that a pixel costs two divisions (iq =
-// 1/(q0sq(1+q0sq)) is per launch).  fp32, fixed order.
+// differences.  The SRAD expression c = 1/(1 + (q^2 - q0sq)/(q0sq(1+q0sq)))
+// with q^2 = num/den^2, num = G2/2 - L^2/16, den = 1 + L/4, G2 = S2/Jc^2 and
+// L = S1/Jc (S1, S2: the sum of the differences and of their squares) is
+// multiplied through by Jc^2 den^2, in which Jc^2 cancels:
+//     E = Jc + S1/4 (= Jc den, the mean of the four neighbours),
+//     c = E^2 / (E^2 + (S2/2 - S1^2/16 - q0sq E^2) iq)
+// with iq = 1/(q0sq(1+q0sq)) once per launch.  Algebraically the SRAD
+// expression (for Jc != 0), one division per pixel instead of five, and no
+// reciprocal of Jc.  fp32, fixed order; each a*b + c is one fused
+// multiply-add (a single rounding).
 __device__ __forceinline__ float srad_coeff(float Jc, float dN, float dS, float dW, float dE, float q0sq, float iq) {
-    const float r = 1.0f / Jc;
-    const float G2 = (((dN * dN + dS * dS) + (dW * dW + dE * dE)) * r) * r;
-    const float L = ((dN + dS) + (dW + dE)) * r;
-    const float num = 0.5f * G2 - 0.0625f * (L * L);
-    const float den = 1.0f + 0.25f * L;
-    const float den2 = den * den;
-    float c = den2 / (den2 + (num - q0sq * den2) * iq);
+    const float S1 = (dN + dS) + (dW + dE);
+    const float S2 = fmaf(dN, dN, dS * dS) + fmaf(dW, dW, dE * dE);
+    const float E = fmaf(0.25f, S1, Jc);
+    const float E2 = E * E;
+    const float nm = fmaf(-0.0625f, S1 * S1, 0.5f * S2);
+    float c = E2 / fmaf(fmaf(-q0sq, E2, nm), iq, E2);
     if (c < 0.0f) c = 0.0f;
     else if (c > 1.0f) c = 1.0f;
     return c;
 }
 
+// J' = Jc + k * D with the flux sum D = (cN dN + cS dS) + (cW dW + cE dE),
+// fused multiply-adds as above.
 __device__ __forceinline__ float srad_update(float Jc, float dN, float dS, float dW, float dE, float cN, float cS,
                                              float cW, float cE, float k) {
-    const float D = (cN * dN + cS * dS) + (cW * dW + cE * dE);
-    return Jc + k * D;
+    const float D = fmaf(cN, dN, cS * dS) + fmaf(cW, dW, cE * dE);
+    return fmaf(k, D, Jc);
 }
 
-// Region sums of one thread: S1 += v, S2 += v*v (the square kept exact as a
+// Region sums of one thread: s1 += v, s2 += v*v (the square kept exact as a
 // float-float product).
 struct RoiAcc {
     ff s1, s2;
