@@ -4,11 +4,20 @@ Each mutant is compiled on the CPU from an edited copy of the oracle source,
 swapped in for the real library, and run through the pin tests of the nest it
 touches.  At least one pin has to fail, or the pins would not protect the
 oracle against that mistake.
+
+The pins run against a mutant in a forked child process.  Some planted
+mistakes make the oracle read outside its buffers (reversed strides walk past
+the end of a strided input): such a read can crash the process, and whether it
+does depends on where the allocator placed the buffers.  In the child a crash
+counts as caught, since the mutant did not pass the pins, and it cannot end the
+test run.
 """
 
 import ctypes
 import os
+import signal
 import subprocess
+import time
 
 import pytest
 
@@ -178,20 +187,54 @@ def _load_mutant(tmp_path, name, old, new):
     return ctypes.CDLL(str(so))
 
 
-@pytest.mark.parametrize("name", sorted(MUTANTS))
-def test_pins_catch_mutant(tmp_path, monkeypatch, name):
-    old, new, tests = MUTANTS[name]
+_ORACLE_FUNCTIONS = ("hxo_map_reduce_f64", "hxo_monoid_reduce_f64", "hxo_jacobi_f64", "hxo_jacobi_f32",
+                     "hxo_histogram_u8", "hxo_fork_reduce", "hxo_srad_f64", "hxo_srad_f32")
+# child exit codes
+_CAUGHT, _NOT_CAUGHT, _ERROR = 0, 1, 2
+
+
+def _run_pins(mutant, tests):
+    """In the child: the pins against the mutant library; returns an exit code."""
     real = oracle._get()
-    mutant = _load_mutant(tmp_path, name, old, new)
-    for fn in ("hxo_map_reduce_f64", "hxo_monoid_reduce_f64", "hxo_jacobi_f64",
-               "hxo_jacobi_f32", "hxo_histogram_u8", "hxo_fork_reduce", "hxo_srad_f64", "hxo_srad_f32"):
+    for fn in _ORACLE_FUNCTIONS:
         getattr(mutant, fn).argtypes = getattr(real, fn).argtypes
         getattr(mutant, fn).restype = getattr(real, fn).restype
-    monkeypatch.setattr(oracle, "_lib", mutant)
+    oracle._lib = mutant
     failures = 0
     for t in tests:
         try:
             t()
         except (AssertionError, ValueError):
             failures += 1
-    assert failures > 0, f"no pin caught mutant {name}"
+    return _CAUGHT if failures else _NOT_CAUGHT
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_mutant(tmp_path, name):
+    old, new, tests = MUTANTS[name]
+    mutant = _load_mutant(tmp_path, name, old, new)
+    oracle._get()   # the real library is loaded before the fork
+    pid = os.fork()
+    if pid == 0:
+        code = _ERROR
+        try:
+            code = _run_pins(mutant, tests)
+        except BaseException:
+            code = _ERROR
+        finally:
+            os._exit(code)
+    deadline = time.monotonic() + 300.0
+    while True:
+        done, status = os.waitpid(pid, os.WNOHANG)
+        if done:
+            break
+        if time.monotonic() > deadline:
+            os.kill(pid, signal.SIGKILL)
+            os.waitpid(pid, 0)
+            pytest.fail(f"the pins did not finish against mutant {name}")
+        time.sleep(0.005)
+    if os.WIFSIGNALED(status):
+        return   # the mutant crashed under the pins: caught
+    code = os.WEXITSTATUS(status)
+    assert code != _ERROR, f"unexpected error running the pins against mutant {name}"
+    assert code == _CAUGHT, f"no pin caught mutant {name}"
