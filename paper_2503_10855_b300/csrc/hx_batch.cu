@@ -265,11 +265,13 @@ batch_kernel(const BInst *__restrict__ insts, unsigned int n_inst, const uint32_
 // launch with a pair list (run_prefix NULL here) runs every instance's whole
 // slice.
 //
-// The descriptors and prefixes are written by the plan's synchronous copies
-// and never by a kernel, so each CTA reads its instance's descriptor (into
-// shared memory) and work count before waiting for the batched grid: only
-// the loads of what the grid wrote (partials, accumulators) remain on the
-// path after it.
+// The descriptors and prefixes are written only by host copies, never by a
+// kernel: the plan's synchronous copies, or a server step's upload on the
+// stream ahead of the batched kernel, which cannot start before that copy
+// has completed (and this kernel starts only as the batched kernel's CTAs
+// exit).  So each CTA reads its instance's descriptor (into shared memory)
+// and work count before waiting for the batched grid: only the loads of what
+// the grid wrote (partials, accumulators) remain on the path after it.
 __global__ void __launch_bounds__(kBatchThreads)
 batch_final_kernel(const BInst *__restrict__ insts, unsigned int n_inst, const uint32_t *__restrict__ cta_prefix,
                    const uint32_t *__restrict__ run_prefix, int round, unsigned int *ctrl) {
