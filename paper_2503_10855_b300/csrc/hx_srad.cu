@@ -155,6 +155,88 @@ __global__ void __launch_bounds__(kThreads) srad_stats_kernel(const float *__res
     roi_publish(a, p, roi_tile, ws, q0sq_out);
 }
 
+// Fast path of one interior tile: no clamping, 16-byte rows, outside the
+// region of interest.  Warp w updates rows ra = i0 + 4w .. ra + 3; lane l
+// holds columns j0 + 4l .. j0 + 4l + 3 of a row as one float4, and the west
+// and east neighbours come by shuffle (lanes 0 and 31 take the halo columns
+// j0 - 1 and j0 + 128).  A warp computes the coefficients of its own four
+// rows in registers; the first of them also goes to shared memory (one row
+// per warp, in Cs), because the warp above needs it as the south neighbour of
+// its last row, and the last warp computes row i0 + 32 itself.  Lanes 0..3
+// compute the coefficients of column j0 + 128 (the east neighbour of lane
+// 31's last pixel) for the warp's four rows.  The per-pixel expressions and
+// their operands are those of the element path, so the two agree bit for
+// bit; only the data movement differs (J rows in registers, one barrier).
+__device__ __forceinline__ void srad_fast_tile(const float *__restrict__ J, float *__restrict__ Jn, int nx, int i0,
+                                               int j0, float q0sq, float iq, float k, float (*Cs)[kCsW]) {
+    constexpr unsigned kAll = 0xffffffffu;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ra = i0 + 4 * warp;
+    const bool last = warp == kThreads / 32 - 1;
+    // rows ra - 1 .. ra + 4, and ra + 5 for the last warp (its row ra + 4
+    // coefficient); halo columns of each
+    float4 Jr[7];
+    float hw[7], he[7];
+#pragma unroll
+    for (int t = 0; t < 7; ++t) {
+        if (t < 6 || last) {
+            const float *row = J + (size_t)(ra - 1 + t) * nx + j0;
+            Jr[t] = __ldg(reinterpret_cast<const float4 *>(row) + lane);
+            hw[t] = __ldg(row - 1);
+            he[t] = __ldg(row + 128);
+        } else {
+            Jr[t] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            hw[t] = he[t] = 0.0f;
+        }
+    }
+    // coefficient of row ra - 1 + t for this lane's four columns
+    auto coeff_row = [&](int t) {
+        const float4 up = Jr[t - 1], cur = Jr[t], dn = Jr[t + 1];
+        float left = __shfl_up_sync(kAll, cur.w, 1), right = __shfl_down_sync(kAll, cur.x, 1);
+        if (lane == 0) left = hw[t];
+        if (lane == 31) right = he[t];
+        float4 c;
+        c.x = srad_coeff(cur.x, up.x - cur.x, dn.x - cur.x, left - cur.x, cur.y - cur.x, q0sq, iq);
+        c.y = srad_coeff(cur.y, up.y - cur.y, dn.y - cur.y, cur.x - cur.y, cur.z - cur.y, q0sq, iq);
+        c.z = srad_coeff(cur.z, up.z - cur.z, dn.z - cur.z, cur.y - cur.z, cur.w - cur.z, q0sq, iq);
+        c.w = srad_coeff(cur.w, up.w - cur.w, dn.w - cur.w, cur.z - cur.w, right - cur.w, q0sq, iq);
+        return c;
+    };
+    float4 c[4];
+#pragma unroll
+    for (int t = 1; t <= 4; ++t) c[t - 1] = coeff_row(t);
+    float ce = 0.0f;   // lane q < 4: column j0 + 128 of row ra + q
+    if (lane < 4) {
+        const float *col = J + (size_t)(ra + lane) * nx + j0 + 128;
+        const float Jc = __ldg(col);
+        ce = srad_coeff(Jc, __ldg(col - nx) - Jc, __ldg(col + nx) - Jc, __ldg(col - 1) - Jc, __ldg(col + 1) - Jc,
+                        q0sq, iq);
+    }
+    *reinterpret_cast<float4 *>(&Cs[warp][4 * lane]) = c[0];
+    __syncthreads();
+    float4 c_south;   // coefficients of row ra + 4
+    if (last) c_south = coeff_row(5);
+    else c_south = *reinterpret_cast<const float4 *>(&Cs[warp + 1][4 * lane]);
+#pragma unroll
+    for (int t = 1; t <= 4; ++t) {
+        const float4 up = Jr[t - 1], cur = Jr[t], dn = Jr[t + 1];
+        float left = __shfl_up_sync(kAll, cur.w, 1), right = __shfl_down_sync(kAll, cur.x, 1);
+        if (lane == 0) left = hw[t];
+        if (lane == 31) right = he[t];
+        const float4 kc = c[t - 1];
+        const float4 ks = t < 4 ? c[t] : c_south;
+        float ke = __shfl_down_sync(kAll, kc.x, 1);
+        const float ke31 = __shfl_sync(kAll, ce, t - 1);
+        if (lane == 31) ke = ke31;
+        float4 o;
+        o.x = srad_update(cur.x, up.x - cur.x, dn.x - cur.x, left - cur.x, cur.y - cur.x, kc.x, ks.x, kc.x, kc.y, k);
+        o.y = srad_update(cur.y, up.y - cur.y, dn.y - cur.y, cur.x - cur.y, cur.z - cur.y, kc.y, ks.y, kc.y, kc.z, k);
+        o.z = srad_update(cur.z, up.z - cur.z, dn.z - cur.z, cur.y - cur.z, cur.w - cur.z, kc.z, ks.z, kc.z, kc.w, k);
+        o.w = srad_update(cur.w, up.w - cur.w, dn.w - cur.w, cur.z - cur.w, right - cur.w, kc.w, ks.w, kc.w, ke, k);
+        *reinterpret_cast<float4 *>(Jn + (size_t)(ra + t - 1) * nx + j0 + 4 * lane) = o;
+    }
+}
+
 // One fused iteration: coefficient in shared memory, update, and the next
 // iteration's region sums.  q0sq_next == nullptr on the last iteration.
 //
@@ -165,7 +247,12 @@ __global__ void __launch_bounds__(kThreads) srad_stats_kernel(const float *__res
 // (vec): float4 loads and stores, four pixels per thread step.  Every other
 // tile takes the element path with clamped loads.  Both evaluate the same
 // per-pixel expressions on the same operands, so they agree bit for bit.
-__global__ void __launch_bounds__(kThreads) srad_fused_kernel(const float *__restrict__ J, float *__restrict__ Jn,
+// Four CTAs per SM (a 64-register cap, a few words of spill): the fast path
+// holds a warp's J rows and coefficients in registers and is latency-bound,
+// so occupancy decides.  Measured on B300, 8192^2: 0.160 ms per iteration,
+// against 0.201 ms uncapped (98 registers, 2 CTAs per SM) and 0.215 ms at
+// five CTAs per SM (48 registers, heavy spill).
+__global__ void __launch_bounds__(kThreads, 4) srad_fused_kernel(const float *__restrict__ J, float *__restrict__ Jn,
                                                               SradArgs p, const float *q0sq_t, NestWs *ws,
                                                               float *q0sq_next, int vec) {
     __shared__ __align__(16) float Js[kJsH][kJsW];
@@ -182,53 +269,7 @@ __global__ void __launch_bounds__(kThreads) srad_fused_kernel(const float *__res
     const bool in_roi = q0sq_next && roi_tile;
     const bool fast = vec && !roi_tile && i0 >= 1 && i0 + kTY + 1 < ny && j0 >= 1 && j0 + kTX + 1 < nx;
     if (fast) {
-        // rows i0-1 .. i0+TY+1: a warp loads a row's 128 columns as float4,
-        // three lanes its halo columns
-        for (int r = warp; r < kJsH; r += kThreads / 32) {
-            const float *row = J + (size_t)(i0 - 1 + r) * nx + j0;
-            *reinterpret_cast<float4 *>(&Js[r][4 + 4 * lane]) = __ldg(reinterpret_cast<const float4 *>(row) + lane);
-            if (lane < 3) Js[r][lane == 0 ? 3 : 131 + lane] = __ldg(row + (lane == 0 ? -1 : 127 + lane));
-        }
-        __syncthreads();
-        // coefficients: 17 rows x 32 groups of 4 columns, then column 128
-        for (int w = threadIdx.x; w < kCsH * 32 + kCsH; w += kThreads) {
-            if (w < kCsH * 32) {
-                const int r = w >> 5, x = 4 + 4 * (w & 31);
-                const float4 c4 = *reinterpret_cast<const float4 *>(&Js[r + 1][x]);
-                const float4 n4 = *reinterpret_cast<const float4 *>(&Js[r][x]);
-                const float4 s4 = *reinterpret_cast<const float4 *>(&Js[r + 2][x]);
-                const float wv = Js[r + 1][x - 1], ev = Js[r + 1][x + 4];
-                float4 o;
-                o.x = srad_coeff(c4.x, n4.x - c4.x, s4.x - c4.x, wv - c4.x, c4.y - c4.x, q0sq, iq);
-                o.y = srad_coeff(c4.y, n4.y - c4.y, s4.y - c4.y, c4.x - c4.y, c4.z - c4.y, q0sq, iq);
-                o.z = srad_coeff(c4.z, n4.z - c4.z, s4.z - c4.z, c4.y - c4.z, c4.w - c4.z, q0sq, iq);
-                o.w = srad_coeff(c4.w, n4.w - c4.w, s4.w - c4.w, c4.z - c4.w, ev - c4.w, q0sq, iq);
-                *reinterpret_cast<float4 *>(&Cs[r][x]) = o;
-            } else {
-                const int r = w - kCsH * 32;
-                const float Jc = Js[r + 1][132];
-                Cs[r][132] = srad_coeff(Jc, Js[r][132] - Jc, Js[r + 2][132] - Jc, Js[r + 1][131] - Jc,
-                                        Js[r + 1][133] - Jc, q0sq, iq);
-            }
-        }
-        __syncthreads();
-        // update: 16 rows x 32 groups of 4 columns, two groups per thread
-        for (int w = threadIdx.x; w < kTY * 32; w += kThreads) {
-            const int r = w >> 5, x = 4 + 4 * (w & 31);
-            const float4 c4 = *reinterpret_cast<const float4 *>(&Js[r + 1][x]);
-            const float4 n4 = *reinterpret_cast<const float4 *>(&Js[r][x]);
-            const float4 s4 = *reinterpret_cast<const float4 *>(&Js[r + 2][x]);
-            const float wv = Js[r + 1][x - 1], ev = Js[r + 1][x + 4];
-            const float4 k4 = *reinterpret_cast<const float4 *>(&Cs[r][x]);
-            const float4 ks = *reinterpret_cast<const float4 *>(&Cs[r + 1][x]);
-            const float ke = Cs[r][x + 4];
-            float4 o;
-            o.x = srad_update(c4.x, n4.x - c4.x, s4.x - c4.x, wv - c4.x, c4.y - c4.x, k4.x, ks.x, k4.x, k4.y, p.k);
-            o.y = srad_update(c4.y, n4.y - c4.y, s4.y - c4.y, c4.x - c4.y, c4.z - c4.y, k4.y, ks.y, k4.y, k4.z, p.k);
-            o.z = srad_update(c4.z, n4.z - c4.z, s4.z - c4.z, c4.y - c4.z, c4.w - c4.z, k4.z, ks.z, k4.z, k4.w, p.k);
-            o.w = srad_update(c4.w, n4.w - c4.w, s4.w - c4.w, c4.z - c4.w, ev - c4.w, k4.w, ks.w, k4.w, ke, p.k);
-            *reinterpret_cast<float4 *>(Jn + (size_t)(i0 + r) * nx + j0 + (x - 4)) = o;
-        }
+        srad_fast_tile(J, Jn, nx, i0, j0, q0sq, iq, p.k, Cs);
         return;
     }
     // Element path.  J tile with a halo of 1 above / left and 2 below /
