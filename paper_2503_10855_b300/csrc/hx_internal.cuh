@@ -87,7 +87,11 @@ constexpr int kWarp = 32;
 constexpr int kMrMinVecs = 4;        // vectors per lane in the smallest tile (one load round)
 constexpr int kMrUnroll = 4;         // loads in flight per operand per lane
 constexpr int kMrMaxTiles = 4096;    // tile partials per instance (workspace)
-constexpr int kMrWarpsPerCta = 4;    // standalone launch: tiles per CTA
+// standalone launch: tiles (warps) per CTA.  Two: the grid's CTAs spread
+// over the SMs more evenly than with four (2^20 elements, 2048 tiles: 1024
+// CTAs, 6-7 per SM, against 512 CTAs, 3-4 per SM); measured on B300, back to
+// back, 1-2 % faster from 2^20 to 2^28 than four warps, and eight slower.
+constexpr int kMrWarpsPerCta = 2;
 
 // stencil: one warp owns a block of R rows x 128 columns (R tuned per size
 // class; kStRows is the default).

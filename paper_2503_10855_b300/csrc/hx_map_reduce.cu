@@ -16,9 +16,9 @@ namespace hx {
 
 // One warp per tile, kMrWarpsPerCta tiles per CTA; no block-level barrier.
 // A warp only stores its tile partial; map_reduce_final_kernel folds them.
-// Three load groups per operand in flight (120 registers, 4 CTAs per SM):
-// measured on B300 against two groups at 6 or 7 CTAs per SM, it is the
-// fastest from 2^22 to 2^28 elements.
+// Three load groups per operand in flight (121 registers, 8 CTAs of two
+// warps per SM): measured on B300 against two groups at 6 or 7 CTAs of four
+// warps per SM, it is the fastest from 2^22 to 2^28 elements.
 __global__ void __launch_bounds__(kMrWarpsPerCta * kWarp)
 map_reduce_kernel(const float *__restrict__ x, const float *__restrict__ y, float *__restrict__ out,
                   float a, MrPlan p, bool aligned, WsSlot *ws) {
