@@ -212,7 +212,10 @@ batch_kernel(const BInst *__restrict__ insts, unsigned int n_inst, const uint32_
             float *out = static_cast<float *>(I.o0);
             for (int64_t k = 0; k < cnt; ++k) {
                 const int64_t tile = first + k;
-                const ff part = mr_tile<2, 2>(x, y, out, I.a, I.plan, tile, I.vec != 0, lane);
+                // the run's next tile, when it is full, is prefetched as well
+                const int V = I.plan.vecs_per_thread;
+                const int pf = k + 1 < cnt && (tile + 2) * I.plan.tile_elems <= I.plan.n ? 2 * V : V;
+                const ff part = mr_tile<2, 2>(x, y, out, I.a, I.plan, tile, I.vec != 0, lane, pf);
                 if (lane == 0) st_keep2(I.partials + tile, make_float2(part.hi, part.lo));
             }
         } else {

@@ -275,13 +275,16 @@ __device__ __forceinline__ double ff_to_double(ff v) { return (double)v.hi + (do
 // PF > 0 (whole-warp calls, nthreads == 32): each load of a group also
 // prefetches into L2 the group PF groups further on, lanes 0..15 one line
 // each of its 4 vectors x 512 bytes per operand, so that later groups' loads
-// find their lines in L2.  A prefetch changes no result.
+// find their lines in L2.  Vector u of the next tile is vector V + u of this
+// one (tiles are consecutive), so pf_vecs = 2V lets the last groups prefetch
+// the next tile's first ones; pf_vecs = V (the default) stays in the tile.
+// A prefetch changes no result.
 template <int GROUPS = 2, int PF = 0>
 __device__ __forceinline__ ff mr_thread_partial(const float *__restrict__ x,
                                                    const float *__restrict__ y,
                                                    float *__restrict__ out, float a,
                                                    const MrPlan &p, int64_t tile,
-                                                   bool aligned, int t, int nthreads) {
+                                                   bool aligned, int t, int nthreads, int pf_vecs = 0) {
     static_assert(GROUPS == 2 || GROUPS == 3, "two or three load groups");
     const int64_t base = tile * p.tile_elems;
     ff acc = {0.0f, 0.0f};
@@ -297,7 +300,7 @@ __device__ __forceinline__ ff mr_thread_partial(const float *__restrict__ x,
         auto load = [&](float4 *xv, float4 *yv, int u0) {
             if constexpr (PF > 0) {
                 const int up = u0 + PF * kMrUnroll + (t >> 2);
-                if (t < 4 * kMrUnroll && up < p.vecs_per_thread) {
+                if (t < 4 * kMrUnroll && up < (pf_vecs > 0 ? pf_vecs : p.vecs_per_thread)) {
                     const int64_t vp = (int64_t)up * kWarp + (t & 3) * 8;
                     asm volatile("prefetch.global.L2 [%0];" ::"l"(x4 + vp));
                     asm volatile("prefetch.global.L2 [%0];" ::"l"(y4 + vp));
@@ -383,8 +386,8 @@ __device__ __forceinline__ ff mr_thread_partial(const float *__restrict__ x,
 template <int GROUPS = 2, int PF = 0>
 __device__ __forceinline__ ff mr_tile(const float *__restrict__ x, const float *__restrict__ y,
                                       float *__restrict__ out, float a, const MrPlan &p, int64_t tile,
-                                      bool aligned, int lane) {
-    return warp_sum(mr_thread_partial<GROUPS, PF>(x, y, out, a, p, tile, aligned, lane, kWarp));
+                                      bool aligned, int lane, int pf_vecs = 0) {
+    return warp_sum(mr_thread_partial<GROUPS, PF>(x, y, out, a, p, tile, aligned, lane, kWarp, pf_vecs));
 }
 
 // Final combine of `tiles` tile partials in one fixed order, the same
