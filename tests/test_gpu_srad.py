@@ -54,7 +54,10 @@ CASES = [((17, 23), (0, 17, 0, 23)), ((16, 128), (3, 9, 5, 100)), ((33, 257), (0
          ((130, 300), (17, 129, 130, 299)), ((1, 200), (0, 1, 10, 190)), ((200, 1), (5, 150, 0, 1)),
          ((512, 512), (0, 128, 0, 128)),
          # interior tiles on the vector path around region tiles on the element path
-         ((100, 404), (40, 60, 150, 250))]
+         ((100, 404), (40, 60, 150, 250)),
+         # a vector-path tile (rows 32..63, columns 128..255) whose last warp
+         # reads the image's last row (i0 + 33 = ny - 1)
+         ((66, 260), (0, 10, 0, 10))]
 
 
 U = 2.0 ** -24
@@ -147,12 +150,11 @@ def test_srad_full_size_one_iteration(gpu):
         assert abs(tot_out - tot_in) <= 1e-6 * tot_in
 
 
-def test_srad_vector_and_element_paths_agree(gpu):
+@pytest.mark.parametrize("ny,nx,roi", [(96, 520, (0, 16, 0, 128)), (66, 260, (0, 10, 0, 10))])
+def test_srad_vector_and_element_paths_agree(gpu, ny, nx, roi):
     # the same image with 16-byte aligned rows (vector path on interior tiles)
     # and at a 4-byte offset (element path everywhere)
     hx = gpu
-    ny, nx = 96, 520
-    roi = (0, 16, 0, 128)
     J = workloads.srad_image(ny, nx)
     with hx.hx_create(0) as ctx:
         outs = []
