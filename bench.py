@@ -833,6 +833,7 @@ def bench_nests(hx, ctx, dev, peak, reps=20):
          F * rows * cols + F * rows),
         ("max over 2^24 rows of 8", [("in", 0)], [big[: 1 << 27].view(1 << 24, 8)], (1 << 24, 8), 1, "max",
          None, res, None, F * (1 << 27) + F * (1 << 24)),
+        ("max |x| over 2^28 fp32", [("in", 0), "abs"], [big], (1 << 28,), 1, "max", None, res[:1], None, 4 << 28),
         ("argmax |x - y| over 2^27", [("in", 0), ("in", 1), "sub", "abs"], [x27, y27], (1 << 27,), 1, "argmax",
          None, res[:1], idx, 8 << 27),
         ("map out = fma(x, 1.5, y) over 2^27", [("in", 0), ("const", 0), ("in", 1), "fma"], [x27, y27],

@@ -166,6 +166,15 @@ __device__ __forceinline__ void acc_fold(Acc &a, float v, i64 r) {
     float pr = a.hi * v;
     float e = fmaf(a.hi, v, -pr);               // exact error of a.hi * v
     a = acc_pair(pr, fmaf(a.lo, v, e));
+#elif MONOID == 1 && G == 32
+    // The running value is never NaN (it starts at -inf), and fmaxf skips a
+    // NaN operand and ranks +0 above -0 (checked on B300; the parity tests
+    // pin both): the monoid's rules in one instruction.  Measured: max |x|
+    // over 2^28 0.90 -> 0.96 of HBM.  Groups narrower than a warp keep the
+    // explicit comparison (the same bits), which measured 2 % faster there.
+    a.v = fmaxf(a.v, v);
+#elif MONOID == 2 && G == 32
+    a.v = fminf(a.v, v);   // likewise: NaN skipped, -0 below +0
 #elif MONOID == 1
     if (v > a.v || (v == 0.0f && a.v == 0.0f && signbit(a.v) && !signbit(v))) a.v = v;
 #elif MONOID == 2
@@ -214,6 +223,12 @@ __device__ __forceinline__ Acc acc_combine(Acc a, Acc b) {
     float pr = a.hi * b.hi;
     float e = fmaf(a.hi, b.hi, -pr);
     return acc_pair(pr, e + (a.hi * b.lo + a.lo * b.hi));
+#elif MONOID == 1 && G == 32
+    a.v = fmaxf(a.v, b.v);
+    return a;
+#elif MONOID == 2 && G == 32
+    a.v = fminf(a.v, b.v);
+    return a;
 #elif MONOID == 1
     return (b.v > a.v || (b.v == 0.0f && a.v == 0.0f && signbit(a.v) && !signbit(b.v))) ? b : a;
 #elif MONOID == 2
