@@ -160,6 +160,34 @@ def test_ties_nans_signed_zeros(gpu):
                 _check(hx, ctx, [("in", 0)], [x], ident, x.shape, 1, monoid, tree=tree)
 
 
+def test_ties_nans_signed_zeros_short_and_long_segments(gpu):
+    # The same special values in segments of 8 (groups narrower than a warp)
+    # and in one segment of 2^20 + 5 that spans many chunks and the tree
+    # above them (whole-warp groups, whose max / min fold is fmaxf / fminf).
+    hx = gpu
+    nan = np.float32("nan")
+    s = _np((64, 8), 109)
+    s[0, :] = nan
+    s[1, ::2] = nan
+    s[2, :] = np.float32(-0.0)
+    s[2, 5] = np.float32(0.0)
+    s[3, :] = np.float32(0.0)
+    s[3, 2] = np.float32(-0.0)
+    s[4, 1] = s[4, 6] = np.float32(1e30)
+    n = (1 << 20) + 5
+    g = np.abs(_np((n,), 110)) * np.float32(-1.0) - np.float32(1.0)   # all below -1
+    g[::7] = nan
+    g[123456] = np.float32(-0.0)
+    g[987654] = np.float32(0.0)
+    g[555] = np.float32(0.0)
+    g[n - 1] = np.float32(-0.0)
+    with hx.hx_create(0) as ctx:
+        for tree in TREES:
+            for monoid in ("max", "min", "argmax", "argmin"):
+                _check(hx, ctx, [("in", 0)], [s], ident, s.shape, 1, monoid, tree=tree)
+                _check(hx, ctx, [("in", 0)], [g], ident, g.shape, 1, monoid, tree=tree)
+
+
 def test_map_ops_on_special_values(gpu):
     # MIN / MAX with NaN operands, and NEG / ABS / SQRT of signed zeros,
     # infinities, NaN, subnormals and negatives, against the oracle.  A NaN
