@@ -31,6 +31,8 @@ namespace hx {
 
 // One histogram chunk counted by the whole CTA into its shared counters
 // (dynamic shared memory, kHiSmemBytes) and added into the instance's bins.
+// Each thread keeps kBHiDepth 16-byte loads in flight.
+constexpr int kBHiDepth = 8;
 __device__ __forceinline__ void batch_hist_item(const BInst &I, int64_t tile, unsigned int *sh) {
     hist_zero(sh);
     __syncthreads();
@@ -42,7 +44,8 @@ __device__ __forceinline__ void batch_hist_item(const BInst &I, int64_t tile, un
     if (head > e - s) head = (int)(e - s);
     const int64_t nvec = (e - s - head) / 16;
     const int tail = (int)((e - s - head) % 16);
-    hist_count_strided(sh, slot, reinterpret_cast<const uint4 *>(v + s + head), threadIdx.x, kBatchThreads, nvec);
+    hist_count_strided<kBHiDepth>(sh, slot, reinterpret_cast<const uint4 *>(v + s + head), threadIdx.x,
+                                  kBatchThreads, nvec);
     if (threadIdx.x < head) hist_count_byte(sh, slot, v[s + threadIdx.x]);
     if (threadIdx.x < tail) hist_count_byte(sh, slot, v[e - tail + threadIdx.x]);
     __syncthreads();

@@ -734,28 +734,34 @@ __device__ __forceinline__ bool hist_merge(const unsigned int *sh, unsigned int 
 }
 
 // Count the 16-byte vectors v4[first], v4[first + stride], ... below nvec into
-// the shared counters, keeping the next two vectors' loads in flight while
-// the current two are counted.
+// the shared counters, keeping the next D vectors' loads in flight while the
+// current D are counted.  The standalone histogram runs wide CTAs at several
+// per SM and keeps D = 2; the batch counts a chunk with one 256-thread CTA
+// and needs a deeper pipeline for the same bytes in flight per SM.
+template <int D = 2>
 __device__ __forceinline__ void hist_count_strided(unsigned int *sh, unsigned int slot,
                                                    const uint4 *__restrict__ v4, int64_t first, int64_t stride,
                                                    int64_t nvec) {
     int64_t i = first;
-    bool h0 = i < nvec, h1 = i + stride < nvec;
-    uint4 a0 = make_uint4(0, 0, 0, 0), a1 = a0;
-    if (h0) a0 = ld_stream_u4(v4 + i);
-    if (h1) a1 = ld_stream_u4(v4 + i + stride);
-    while (h0) {
-        const int64_t j = i + 2 * stride;
-        const bool g0 = j < nvec, g1 = j + stride < nvec;
-        uint4 b0 = make_uint4(0, 0, 0, 0), b1 = b0;
-        if (g0) b0 = ld_stream_u4(v4 + j);
-        if (g1) b1 = ld_stream_u4(v4 + j + stride);
-        hist_count_vec(sh, slot, a0);
-        if (h1) hist_count_vec(sh, slot, a1);
-        a0 = b0;
-        a1 = b1;
-        h0 = g0;
-        h1 = g1;
+    uint4 a[D];
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+        a[d] = make_uint4(0, 0, 0, 0);
+        if (i + d * stride < nvec) a[d] = ld_stream_u4(v4 + i + d * stride);
+    }
+    while (i < nvec) {
+        const int64_t j = i + D * stride;
+        uint4 b[D];
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+            b[d] = make_uint4(0, 0, 0, 0);
+            if (j + d * stride < nvec) b[d] = ld_stream_u4(v4 + j + d * stride);
+        }
+#pragma unroll
+        for (int d = 0; d < D; ++d)
+            if (d == 0 || i + d * stride < nvec) hist_count_vec(sh, slot, a[d]);
+#pragma unroll
+        for (int d = 0; d < D; ++d) a[d] = b[d];
         i = j;
     }
 }

@@ -16,7 +16,7 @@ namespace hx {
 
 // One warp per tile, kMrWarpsPerCta tiles per CTA; no block-level barrier.
 // A warp only stores its tile partial; map_reduce_final_kernel folds them.
-// Three load groups per operand in flight (121 registers, 8 CTAs of two
+// Three load groups per operand in flight (124 registers, 8 CTAs of two
 // warps per SM): measured on B300 against two groups at 6 or 7 CTAs of four
 // warps per SM, it is the fastest from 2^22 to 2^28 elements.
 __global__ void __launch_bounds__(kMrWarpsPerCta * kWarp)
