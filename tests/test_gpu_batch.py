@@ -198,6 +198,27 @@ def test_mixed_batch_multi_sweep(gpu, ctx, offset, rounds):
     b.close()
 
 
+@pytest.mark.parametrize("offset", [0, 5])
+def test_histogram_chunk_residues(gpu, ctx, offset):
+    # a batch counts a histogram in chunks of 256 KiB, each by 256 threads
+    # with eight 16-byte loads in flight per thread (2048 vectors per pass):
+    # last chunks that end on, just before and just after a byte, a vector, a
+    # thread's share and a whole pass, after one or two full chunks, from an
+    # aligned and an unaligned start; exact against the standalone call and
+    # the oracle
+    chunk, pass_vecs = 256 * 1024, 2048
+    tails = [0, 1, 15, 16, 17, 16 * 255 + 3, 16 * 256, 16 * (pass_vecs - 1) + 9, 16 * pass_vecs,
+             16 * pass_vecs + 1, chunk - 1]
+    specs = [{"kind": "histogram", "n": chunk * (1 + k % 2) + t, "seed": 90 + k} for k, t in enumerate(tails)]
+    insts = [Inst(s, offset) for s in specs]
+    b = _run(gpu, insts, ctx)
+    for inst in insts:
+        r = inst.result()
+        _same(r, inst.standalone(gpu, ctx))
+        inst.check_oracle(r)
+    b.close()
+
+
 @pytest.mark.parametrize("shape,iters", [((1000, 1000), 12), ((601, 997), 9), ((64, 4100), 6), ((3000, 40), 5)])
 def test_one_launch_wavefront_shapes(gpu, ctx, shape, iters):
     # one grid whose sweeps run in one launch, each block waiting only for
